@@ -1,0 +1,409 @@
+"""Throughput of the MTP planner hot path on one node.
+
+A step is one full planner iteration (Alg. 2: tensor sampling, interpolation,
+local samples, batched rollout + cost, top-E, FP64 update) over one batch of
+candidates, launched through the C ABI (mtp_plan_step).  The default workload
+is the 7-link torque-controlled arm: 4096 candidates x 128 steps, Akima,
+graph 8 x 32, beta 0.5, 64 elites.  Each rank plans its own independent
+instance (weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  The reference arm times the FP64 CPU oracle
+on the host on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rollout-steps/s"
+BASELINE_METRIC = "rollout-steps/s & plan-steps/s at p99 re-plan latency, served/batched vs plain"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload(name: str) -> dict:
+    from paper_2505_01059_gb300 import workloads as W
+    if name == "arm7":
+        return W.chain()
+    if name == "pointmass2":
+        return W.pointmass()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_label(spec: dict, name: str) -> str:
+    return (f"{name}: {spec['dyn']} n={spec['n']} d={spec['d']} B={spec['B']} H={spec['H']} "
+            f"M={spec['M']} N={spec['N']} beta={spec['beta']} {spec['interp']} E={spec['E']}")
+
+
+def flops_per_step(spec: dict) -> int:
+    """FP32 flops (an FMA counts 2) of one rollout step of one candidate as the
+    rollout kernel computes it; transcendental MUFU ops (sincos, sqrt, rsqrt)
+    are not counted."""
+    if spec["dyn"] == "chain":
+        L = spec["n_links"]
+        pairs = L * (L - 1) // 2
+        cost = 6 * L + 12
+        rhs = 3 * L
+        mass_matrix = 15 * pairs
+        chol = L * (L - 1) + sum((L - 1 - j) * (2 * j + 1) for j in range(L))
+        solves = 2 * L * L
+        integrate = 4 * L
+        return cost + rhs + mass_matrix + chol + solves + integrate
+    if spec["dyn"] == "pointmass":
+        k = spec["n"]
+        return 9 * k + 8 + len(spec.get("obs_c", [])) * (3 * k + 3)
+    raise ValueError(spec["dyn"])
+
+
+def peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def profiled_traffic(kernel_file: str, summary: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    src = os.path.join(ROOT, "paper_2505_01059_gb300", "csrc", kernel_file)
+    prof = os.path.join(ROOT, "profiles", summary)
+    if not (os.path.exists(src) and os.path.exists(prof)):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    text = open(prof).read()
+    m_hash = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_bytes = re.search(r"dram_bytes_per_launch_full_workload:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != digest:
+        return None
+    return float(m_bytes.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"mtp_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for _, _, flags in rows:
+            for nm, v in zip(names, flags):
+                if v.lower() == "active":
+                    seen.add(nm)
+        busy = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(seen)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(spec: dict, seconds: float, sample_rows: int):
+    """Single-thread FP64 oracle: full planner iterations on `sample_rows`
+    candidates of the workload, repeated for about `seconds`."""
+    import numpy as np
+
+    import oracle
+    from paper_2505_01059_gb300 import workloads as W
+    s = dict(spec, B=sample_rows, E=min(spec["E"], sample_rows))
+    mu, sigma = W.initial_distribution(s)
+    x0 = np.array(s["x0"], np.float64)
+    steps = 0
+    its = 0
+    t0 = time.perf_counter()
+    while True:
+        out = oracle.plan_iteration(s, its, x0, mu, sigma)
+        mu, sigma = out["mu"], out["sigma"]
+        its += 1
+        steps += s["B"] * s["H"]
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return steps / dt, its / dt, its, dt
+
+
+def run_reference(args, spec, name):
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2505_01059_gb300 import workloads as W
+    # size each step's sample so that warm-up + timed steps take about
+    # args.reference_seconds on one core
+    probe = dict(spec, B=32, E=min(spec["E"], 32))
+    mu, sigma = W.initial_distribution(probe)
+    x0 = np.array(probe["x0"], np.float64)
+    t0 = time.perf_counter()
+    oracle.plan_iteration(probe, 0, x0, mu, sigma)
+    rate = 32 * spec["H"] / max(time.perf_counter() - t0, 1e-6)
+    rows = int(args.reference_seconds * rate / ((args.steps + args.warmup) * spec["H"]))
+    rows = max(8, min(rows, spec["B"]))
+    s = dict(spec, B=rows, E=min(spec["E"], rows))
+    mu, sigma = W.initial_distribution(s)
+    for it in range(args.warmup):
+        out = oracle.plan_iteration(s, it, x0, mu, sigma)
+        mu, sigma = out["mu"], out["sigma"]
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        out = oracle.plan_iteration(s, args.warmup + k, x0, mu, sigma)
+        times.append(time.perf_counter() - t0)
+        mu, sigma = out["mu"], out["sigma"]
+    total = sum(times)
+    value = rows * s["H"] * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_label(spec, name), "sample_rows_per_step": rows},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": f"each step one planner iteration on {rows} of the "
+                                   f"{spec['B']} candidates (FP64 C oracle, one thread)"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "baseline_metric": BASELINE_METRIC,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, spec, name):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    from paper_2505_01059_gb300 import _build, mtp
+    if rank == 0 or not os.path.exists(mtp.LIB_PATH):
+        _build.build_library()
+    if pg:
+        pg.barrier()
+    mtp.load_library()
+
+    spec = dict(spec, seed=spec["seed"] + 7919 * rank)  # independent instance per rank
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    x0 = torch.tensor(spec["x0"], dtype=torch.float32, device=dev)
+    ustar = torch.empty(s["n"], dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        mtp.mtp_plan_step(h, x0, 1, ustar)
+    torch.cuda.synchronize()
+
+    # timed region: eager launches with per-stage events (for the roofline),
+    # L2 flushed between steps outside the step events
+    mtp.mtp_set_profiling(h, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            mtp.mtp_plan_step(h, x0, 1, ustar)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if pg:
+        pg.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    stage_ms, n_it = mtp.mtp_stage_times(h)
+    mtp.mtp_set_profiling(h, False)
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    steps_per_iter = s["B"] * s["H"]
+    value = world * steps_per_iter * args.steps / (total_ms / 1e3)
+    plan_steps = world * args.steps / (total_ms / 1e3)
+
+    # same step through graph replay (reported alongside)
+    g_start = torch.cuda.Event(enable_timing=True)
+    g_end = torch.cuda.Event(enable_timing=True)
+    g_ms = []
+    for k in range(min(args.steps, 500)):
+        flush.zero_()
+        g_start.record(stream)
+        mtp.mtp_plan_step(h, x0, 1, ustar)
+        g_end.record(stream)
+        g_end.synchronize()
+        g_ms.append(g_start.elapsed_time(g_end))
+
+    # end to end through the host-pointer entry point: pinned x0 in, u* out
+    x0_h = torch.tensor(spec["x0"], dtype=torch.float32).pin_memory()
+    u_h = torch.empty(s["n"], dtype=torch.float32).pin_memory()
+    lat = []
+    n_e2e = min(args.steps, 2000)
+    for _ in range(min(args.warmup, 10)):
+        mtp.mtp_plan_step_host(h, x0_h, 1, u_h)
+    for _ in range(n_e2e):
+        t0 = time.perf_counter()
+        mtp.mtp_plan_step_host(h, x0_h, 1, u_h)
+        lat.append(time.perf_counter() - t0)
+    e2e_total = sum(lat)
+    if pg:
+        t = torch.tensor([e2e_total], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * steps_per_iter * n_e2e / e2e_total
+    lat_sorted = sorted(lat)
+    p50 = 1e3 * lat_sorted[len(lat) // 2]
+    p99 = 1e3 * lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+
+    # roofline of the dominant kernel (the fused rollout): FP32 ALU bound
+    rollout_ms = stage_ms[1] / max(n_it, 1)
+    fl = flops_per_step(spec) * steps_per_iter
+    achieved = fl / (rollout_ms / 1e3) / 1e12
+    pk = peaks()
+    clk = clocks.summary()
+    peak_mhz = pk.get("sm_max_mhz", 2070.0)
+    peak = fp32_peak_tflops(peak_mhz)
+    kernel_file = "rollout.cu"
+    summary = {"chain": "rollout_chain7_arm_B4096.txt", "pointmass": "rollout_pointmass2_B512.txt"}[spec["dyn"]]
+    traffic = profiled_traffic(kernel_file, summary)
+    share = {st: ms / max(sum(stage_ms), 1e-12) for st, ms in
+             zip(("generate", "rollout", "select", "update"), stage_ms)}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            r_steps, r_plans, its, dt = cpu_oracle_rate(spec, args.cpu_seconds, args.reference_rows)
+            cpu = {"value": r_steps, "unit": METRIC, "cores": 1, "kind": "oracle",
+                   "sample": f"{its} planner iterations on {args.reference_rows} of the "
+                             f"{spec['B']} candidates in {dt:.1f} s (FP64 C oracle, one thread)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_label(spec, name), "parallelism": f"replicas{world}",
+                       "iters_per_step": 1, "l2": "flushed between steps (256 MB write)",
+                       "timed_mode": "eager launches with per-stage CUDA events"},
+            "plan_steps_per_s": plan_steps,
+            "graph_replay_ms_per_step": statistics.median(g_ms) if g_ms else None,
+            "replan_latency_ms": {"p50": p50, "p99": p99, "path": "mtp_plan_step_host"},
+            "stage_ms_per_step": dict(zip(("generate", "rollout", "select", "update"),
+                                          [v / max(n_it, 1) for v in stage_ms])),
+            "stage_share": share,
+            "roofline": {"bound": "alu", "kernel": f"k_rollout_{spec['dyn']}",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "flops_per_launch": fl,
+                         "peak_note": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                      f"{peak_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 4 * s["d"],
+                    "d2h_bytes_per_step": 4 * s["n"]},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk,
+            "baseline_metric": BASELINE_METRIC,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    mtp.mtp_destroy(h)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="arm7", choices=["arm7", "pointmass2"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--reference-rows", type=int, default=512)
+    ap.add_argument("--reference-seconds", type=float, default=90.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    spec = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, spec, args.workload)
+    else:
+        run_ours(args, spec, args.workload)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * mtp.h -- C ABI of the GB300-native Model Tensor Planning (MTP) hot path.
+ *
+ * One planner iteration of MTP (arXiv 2505.01059, Alg. 2): sample paths
+ * through a random M x N multipartite graph of control knots (Def. 1,
+ * Alg. 1), interpolate them to H-step control trajectories (B-spline, Def. 2
+ * and Eqs. 3-4; Akima, Def. 3 and Eqs. 5-7; or straight lines, Sec. 3.1),
+ * mix them with local Gaussian samples around the current mean (beta-mixing,
+ * Sec. 3.3), roll every candidate out through the dynamics with per-sample
+ * randomised parameters and reduce its cost (Eq. 2), select the top-E elites
+ * and apply the softmax-weighted CEM update (Alg. 2; Sec. 2.1 for the plain
+ * CEM variant).
+ *
+ * Conventions for every entry point:
+ *   - Return value: MTP_OK, or an error code; mtp_last_error() gives text.
+ *   - Pointers named d_* are device pointers (any CUDA allocation on the
+ *     handle's device), h_* are host pointers.  The caller owns them; the
+ *     library reads/writes them stream-ordered on `stream` and keeps no
+ *     reference after the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously unless stated otherwise.
+ *   - Logical layouts are the paper's, row-major: graph Z (M, N, n), path
+ *     indices I (P, M), waypoints C (P, M, n), controls U (B, H, n), costs
+ *     (B), mean/spread mu, sigma (H, n), state x (d).
+ *   - Candidate rows of U (Alg. 2 stacking): [0, L) local Gaussian samples,
+ *     [L, L+P) graph paths, row B-1 the nominal mean; P = min(floor(beta B),
+ *     B-1), L = B-P-1.  Every control is clamped to [u_min, u_max].
+ *   - Random draws are Philox4x32-10 (Salmon et al., SC'11) with key = the
+ *     64-bit seed and counter = (index, sub-index/4, iteration, stream tag),
+ *     so results depend only on (seed, iteration), never on launch shape.
+ *   - No call traps the GPU; kernels report failures through return codes.
+ */
+#ifndef MTP_H
+#define MTP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MTP_OK = 0,
+  MTP_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
+  MTP_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed */
+  MTP_ERR_CUDA = 3,          /* a CUDA runtime call failed (text in mtp_last_error) */
+  MTP_ERR_ADMISSION = 4,     /* serving: the request does not fit the memory budget */
+  MTP_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
+  MTP_ERR_NOT_READY = 6,     /* serving: the result is not there yet */
+  MTP_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+} mtp_status;
+
+typedef enum { MTP_DYN_POINTMASS = 0, MTP_DYN_CHAIN = 1, MTP_DYN_LEGGED = 2 } mtp_dyn;
+typedef enum { MTP_INTERP_LINEAR = 0, MTP_INTERP_BSPLINE = 1, MTP_INTERP_AKIMA = 2 } mtp_interp;
+/* Knot/evaluation-time reading of Defs. 2-3: VALID_SPAN maps the horizon onto
+ * the span where the B-spline basis sums to one (and Akima's knots onto
+ * [0, 1] with i/(M-1)); PAPER_LITERAL uses t_j = j/H as printed. */
+typedef enum { MTP_TIME_VALID_SPAN = 0, MTP_TIME_PAPER_LITERAL = 1 } mtp_time_mapping;
+/* SOFTMAX: Alg. 2's softmax-weighted mean/std with floor sigma_min.
+ * PLAIN_CEM: Sec. 2.1's unweighted mean and 1/(E-1) variance. */
+typedef enum { MTP_UPDATE_SOFTMAX = 0, MTP_UPDATE_PLAIN_CEM = 1 } mtp_update_rule;
+/* Domain randomisation (Sec. 4): PER_SAMPLE gives every candidate its own
+ * model scales; SHARED rolls every candidate out on R models and averages. */
+typedef enum { MTP_DR_NONE = 0, MTP_DR_PER_SAMPLE = 1, MTP_DR_SHARED = 2 } mtp_dr_mode;
+
+#define MTP_MAX_CTRL 32
+#define MTP_MAX_LINKS 16
+#define MTP_MAX_OBSTACLES 8
+
+/* flags */
+#define MTP_FLAG_NO_KAHAN 0x1u    /* plain FP32 cost sums instead of compensated ones */
+#define MTP_FLAG_NO_GRAPH 0x2u    /* mtp_plan_step launches eagerly, no CUDA graph */
+#define MTP_FLAG_BF16_BASIS 0x4u  /* B-spline contraction with a BF16 basis and BF16
+                                     knots on the tensor cores, FP32 accumulation */
+
+/* One planning problem (Sec. 2.1 problem statement, Alg. 2 inputs, Table 3
+ * hyper-parameters).  Plain data; mtp_create copies it. */
+typedef struct mtp_problem {
+  /* system and horizon (Sec. 2.1, Eq. 2) */
+  int32_t dyn;        /* mtp_dyn */
+  int32_t ctrl_dim;   /* n: point mass k, chain L, legged L-1 */
+  int32_t state_dim;  /* d: point mass 2k, chain 2L, legged 2(L+2) */
+  int32_t horizon;    /* H (the paper's T) */
+  float dt;
+  float u_min[MTP_MAX_CTRL], u_max[MTP_MAX_CTRL]; /* control box U (Def. 1) */
+  /* planner (Alg. 2) */
+  int32_t M, N;       /* graph layers and nodes per layer */
+  int32_t B, E;       /* candidates and elites */
+  double beta;        /* mixing rate in [0, 1] */
+  double lambda;      /* softmax temperature > 0 */
+  double alpha;       /* smoothing in [0, 1) */
+  double sigma_min;   /* spread floor > 0 */
+  double mu_init, sigma_init; /* initial mean and spread (constant over H, n) */
+  int32_t interp;     /* mtp_interp */
+  int32_t bspline_degree; /* p >= 0, M >= p + 1 */
+  int32_t time_mapping;   /* mtp_time_mapping */
+  int32_t update_rule;    /* mtp_update_rule */
+  int32_t dr_mode;        /* mtp_dr_mode */
+  int32_t R;              /* models for MTP_DR_SHARED (1..64) */
+  float dr_lo, dr_hi;     /* randomisation scale range, e.g. 0.8 .. 1.2 */
+  uint64_t seed;
+  /* task model and cost */
+  float target[MTP_MAX_CTRL]; /* point mass: goal (k); chain: reach target (x, y);
+                                 legged: (height, forward velocity, pitch) */
+  float w_target, w_obs, w_ctrl, w_term;
+  int32_t n_obstacles;
+  float obs_center[MTP_MAX_OBSTACLES][MTP_MAX_CTRL];
+  float obs_radius[MTP_MAX_OBSTACLES];
+  int32_t n_links;
+  float link_mass[MTP_MAX_LINKS], link_length[MTP_MAX_LINKS];
+  float gravity;
+  float k_contact, c_contact, mu_friction, v_slip; /* legged ground contact */
+  float w_height, w_pitch, w_vel;                  /* legged cost weights */
+  uint32_t flags;     /* MTP_FLAG_* */
+} mtp_problem;
+
+typedef struct mtp_sizes {
+  int32_t B, P, L, E, H, n, d, M, N;
+} mtp_sizes;
+
+/* Device buffers owned by a handle (valid until mtp_destroy).  After
+ * mtp_plan_step they hold the last iteration's candidates and results. */
+typedef struct mtp_buffers {
+  float* U;        /* (B, H, n) */
+  float* cost;     /* (B) */
+  int32_t* elite;  /* (E), ascending cost, ties by index */
+  double* weight;  /* (E) softmax weights */
+  double* mu;      /* (H, n) FP64 mean */
+  double* sigma;   /* (H, n) FP64 spread */
+  float* ustar;    /* (n) */
+  uint32_t* iter;  /* device iteration counter */
+} mtp_buffers;
+
+typedef struct mtp_handle mtp_handle;
+
+/* sizeof(mtp_problem) as compiled into the library, so a binding can check
+ * that its mirror of the struct has the same layout. */
+size_t mtp_problem_bytes(void);
+
+/* Validates and copies `problem`, allocates the handle's device state on the
+ * current CUDA device (mean and spread initialised to mu_init / sigma_init,
+ * iteration counter 0) and precomputes the interpolation tables.
+ * Errors: MTP_ERR_INVALID_ARG (bad field; see mtp_last_error(NULL)),
+ * MTP_ERR_OUT_OF_MEMORY, MTP_ERR_CUDA.  Synchronous. */
+mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out);
+
+/* Frees everything the handle owns.  Synchronises the handle's device. */
+mtp_status mtp_destroy(mtp_handle* h);
+
+/* Text of the last error on this handle (or of the last failed mtp_create in
+ * this thread when h is NULL).  Valid until the next call on the handle. */
+const char* mtp_last_error(const mtp_handle* h);
+
+mtp_status mtp_get_sizes(const mtp_handle* h, mtp_sizes* out);
+mtp_status mtp_get_buffers(const mtp_handle* h, mtp_buffers* out);
+
+/* Def. 1 and Alg. 1 (tensor sampling for iteration `iter`): writes the graph
+ * d_Z (M, N, n), the path indices d_idx (P, M) and the gathered waypoints
+ * d_C (P, M, n).  Any output may be NULL.  Indices are bit-exact functions of
+ * (seed, iter). */
+mtp_status mtp_sample_tensor(mtp_handle* h, uint32_t iter, float* d_Z, int32_t* d_idx,
+                             float* d_C, void* stream);
+
+/* Def. 2 / Def. 3 / straight lines: interpolates `P` waypoint sets d_C
+ * (P, M, n) into d_U (P, H, n), clamped to the control box. */
+mtp_status mtp_interpolate(mtp_handle* h, const float* d_C, int32_t P, float* d_U, void* stream);
+
+/* Alg. 2 local sampling for iteration `iter`: writes rows [0, L) of d_U
+ * (B, H, n) with mu + sigma * eps (eps standard normal, Box-Muller) and row
+ * B-1 with mu, from the handle's current mean and spread; clamped. */
+mtp_status mtp_sample_local(mtp_handle* h, uint32_t iter, float* d_U, void* stream);
+
+/* Alg. 2 sampling in one launch: all B rows of d_U (B, H, n) for iteration
+ * `iter` (local samples, interpolated graph paths, the mean), clamped. */
+mtp_status mtp_generate_candidates(mtp_handle* h, uint32_t iter, float* d_U, void* stream);
+
+/* Alg. 2 batch rollout and cost (Eq. 2) of candidates row0 .. row0+rows-1:
+ * d_U points at row row0 of a (B, H, n) array, d_x0 is the start state (d),
+ * d_cost receives `rows` costs.  Model randomisation uses (iter, candidate
+ * index) so a candidate's cost does not depend on which rows are requested.
+ * With MTP_DR_SHARED the cost is the mean over the R models.  Non-finite
+ * costs are written as +inf. */
+mtp_status mtp_rollout_cost(mtp_handle* h, uint32_t iter, const float* d_x0, const float* d_U,
+                            int32_t row0, int32_t rows, float* d_cost, void* stream);
+
+/* Like mtp_rollout_cost for one candidate `row`, also writing its state
+ * trajectory d_X (H+1, d) in the paper's state coordinates. */
+mtp_status mtp_rollout_states(mtp_handle* h, uint32_t iter, const float* d_x0,
+                              const float* d_Urow, int32_t row, float* d_X, float* d_cost,
+                              void* stream);
+
+/* Alg. 2 elite selection and update: top-E of d_cost (B) in (cost, index)
+ * order into d_elite (E, may be NULL), softmax weights, FP64 weighted mean
+ * and spread of those rows of d_U (B, H, n), floor, smoothing; updates the
+ * handle's mean and spread and writes u* = U[elite[0], 0, :] to d_ustar (n,
+ * may be NULL). */
+mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U,
+                            int32_t* d_elite, float* d_ustar, void* stream);
+
+/* `iters` full planner iterations (Alg. 2 loop body) from start state d_x0
+ * (d) using and advancing the handle's iteration counter; writes the last
+ * iteration's u* to d_ustar (n).  Replays a captured CUDA graph unless
+ * MTP_FLAG_NO_GRAPH is set or profiling is on. */
+mtp_status mtp_plan_step(mtp_handle* h, const float* d_x0, int32_t iters, float* d_ustar,
+                         void* stream);
+
+/* mtp_plan_step from host memory: copies h_x0 (d floats) to the device,
+ * plans, copies u* back to h_ustar (n floats) and synchronises `stream`. */
+mtp_status mtp_plan_step_host(mtp_handle* h, const float* h_x0, int32_t iters, float* h_ustar,
+                              void* stream);
+
+/* Warm start between control steps: shifts mean and spread k steps earlier
+ * and repeats the last row (the paper leaves this open). */
+mtp_status mtp_shift(mtp_handle* h, int32_t k, void* stream);
+
+/* Checkpoint / resume of the planner state: FP64 mean and spread (H, n) and
+ * the iteration counter.  Synchronous. */
+mtp_status mtp_get_state(mtp_handle* h, double* h_mu, double* h_sigma, uint32_t* h_iter);
+mtp_status mtp_set_state(mtp_handle* h, const double* h_mu, const double* h_sigma,
+                         uint32_t iter);
+
+/* Per-stage device time: with profiling on, mtp_plan_step records CUDA
+ * events around each stage.  mtp_stage_times synchronises on them and
+ * returns the summed milliseconds of [generate, rollout, select, update]
+ * and the number of iterations recorded since the last read, then resets. */
+mtp_status mtp_set_profiling(mtp_handle* h, int32_t enable);
+mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTP_H */

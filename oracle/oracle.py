@@ -147,6 +147,8 @@ def num_graph_samples(beta: float, B: int) -> int:
 
 def make_problem(spec: dict) -> OrProblem:
     """Fill the oracle's C struct from a workload dict."""
+    if not 1 <= spec["E"] <= spec["B"]:
+        raise ValueError("the oracle needs 1 <= E <= B")
     pr = OrProblem()
     pr.dyn = DYN[spec["dyn"]]
     pr.n = spec["n"]
@@ -372,6 +374,8 @@ def rollout_states(spec, it: int, x0, Ub, b: int):
 
 def top_e(cost, E: int) -> np.ndarray:
     cost = _f64(cost)
+    if not 1 <= E <= cost.shape[0]:
+        raise ValueError("top_e needs 1 <= E <= B")
     elite = np.empty(E, np.int32)
     _load().or_top_e(_dp(cost), cost.shape[0], E, _ip(elite))
     return elite

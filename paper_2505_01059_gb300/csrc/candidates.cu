@@ -1,0 +1,256 @@
+// candidates.cu -- Alg. 2 sampling: the random multipartite graph (Def. 1),
+// path sampling (Alg. 1), interpolation (Def. 2 / Def. 3 / straight lines),
+// local Gaussian samples and the nominal-mean row, all written into the
+// (B, H, n) candidate tensor in one launch.
+//
+// Blocks [0, graph_blocks) each produce `paths_per_block` graph paths: the
+// block regenerates the whole graph Z in shared memory from Philox (it is a
+// pure function of (seed, iteration), a few KB, cheaper to recompute than to
+// synchronise across blocks), draws its paths' layer indices, gathers the
+// waypoints and interpolates them with coalesced row-major stores.  The other
+// blocks stream the local Gaussian rows and the mean row, four elements per
+// generator call.
+#include "mtp_device.cuh"
+
+namespace mtp {
+namespace {
+
+constexpr int kThreads = 256;
+
+// Eq. 6 with the end rules stated under it, 0-based knot a of M knots.
+// slope(j) is the slope of piece j (between knots j and j+1).
+template <class SlopeFn>
+__device__ __forceinline__ float akima_knot_slope(int a, int M, SlopeFn slope) {
+  if (M == 2) return slope(0);
+  if (a == 0) return slope(0);
+  if (a == M - 1) return slope(M - 2);
+  if (a == 1) return 0.5f * (slope(0) + slope(1));
+  if (a == M - 2) return 0.5f * (slope(M - 2) + slope(M - 3));
+  const float mm2 = slope(a - 2), mm1 = slope(a - 1), m0 = slope(a), mp1 = slope(a + 1);
+  const float w1 = fabsf(mp1 - m0), w2 = fabsf(mm1 - mm2);
+  if (w1 + w2 == 0.f) return 0.5f * (mm1 + m0);
+  return (w1 * mm1 + w2 * m0) / (w1 + w2);
+}
+
+// Standard normal pair by Box-Muller from two 32-bit words.
+__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& e0, float& e1) {
+  const float u1 = (float)((w0 >> 8) + 1u) * 5.9604644775390625e-8f;  // (0, 1]
+  const float u2 = (float)(w1 >> 8) * 5.9604644775390625e-8f;         // [0, 1)
+  const float radius = sqrtf(-2.f * logf(u1));
+  float sn, cs;
+  sincospif(2.f * u2, &sn, &cs);
+  e0 = radius * cs;
+  e1 = radius * sn;
+}
+
+__global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
+  extern __shared__ float smem[];
+  const Dims dm = a.dm;
+  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
+  const int H = dm.H, n = dm.n, M = dm.M, N = dm.N;
+  const int Hn = H * n;
+
+  if ((int)blockIdx.x < a.graph_blocks) {
+    const int SPB = a.paths_per_block;
+    const int b0 = blockIdx.x * SPB;
+    const int nb = min(SPB, a.graph_rows - b0);
+    float* Z = smem;
+    float* C = Z + (a.C_in ? 0 : M * N * n);
+    float* coef = C + SPB * M * n;
+    if (a.C_in == nullptr) {
+      // Def. 1: Z[m][j][:] uniform over the box, four dimensions per call.
+      const int ng = (n + 3) >> 2;
+      for (int e = threadIdx.x; e < M * N * ng; e += blockDim.x) {
+        const int node = e / ng, g = e - node * ng;
+        const uint4 r = philox(make_uint4((uint32_t)node, (uint32_t)g, iter, kTagGraph), a.key);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int i = 4 * g + w;
+          if (i < n) Z[node * n + i] = fmaf(a.umax[i] - a.umin[i], unit24(pick(r, w)), a.umin[i]);
+        }
+      }
+      __syncthreads();
+      // Alg. 1: layer indices with replacement, then C = Z[m][I[b][m]][:].
+      const int mg = (M + 3) >> 2;
+      for (int e = threadIdx.x; e < nb * mg; e += blockDim.x) {
+        const int s = e / mg, g = e - s * mg;
+        const uint4 r = philox(make_uint4((uint32_t)(b0 + s), (uint32_t)g, iter, kTagPath), a.key);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int m = 4 * g + w;
+          if (m < M) {
+            const int j = index_of(pick(r, w), (uint32_t)N);
+            const float* src = Z + (m * N + j) * n;
+            float* dst = C + (s * M + m) * n;
+            for (int i = 0; i < n; ++i) dst[i] = src[i];
+          }
+        }
+      }
+    } else {
+      const float* src = a.C_in + (size_t)b0 * M * n;
+      for (int e = threadIdx.x; e < nb * M * n; e += blockDim.x) C[e] = src[e];
+    }
+    __syncthreads();
+
+    if (a.interp == MTP_INTERP_AKIMA) {
+      // Eqs. 6-7: per (path, dimension) piece coefficients (a, b, c, d).
+      const float inv_h = a.inv_h;
+      for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
+        const int s = e / n, i = e - s * n;
+        const float* z = C + s * M * n + i;
+        auto slope = [&](int j) { return (z[(j + 1) * n] - z[j * n]) * inv_h; };
+        float* cf = coef + (size_t)(s * n + i) * (M - 1) * 4;
+        float s_left = akima_knot_slope(0, M, slope);
+        for (int k = 0; k < M - 1; ++k) {
+          const float s_right = akima_knot_slope(k + 1, M, slope);
+          const float mk = slope(k);
+          cf[4 * k + 0] = z[k * n];
+          cf[4 * k + 1] = s_left;
+          cf[4 * k + 2] = (3.f * mk - 2.f * s_left - s_right) * inv_h;
+          cf[4 * k + 3] = (s_left + s_right - 2.f * mk) * (inv_h * inv_h);
+          s_left = s_right;
+        }
+      }
+      __syncthreads();
+    }
+
+    // Interpolate and store rows b0 .. b0+nb-1 (coalesced over (t, i)).
+    float* out = a.U_graph + (size_t)b0 * Hn;
+    for (int e = threadIdx.x; e < nb * Hn; e += blockDim.x) {
+      const int s = e / Hn, rem = e - s * Hn;
+      const int t = rem / n, i = rem - t * n;
+      float u;
+      if (a.interp == MTP_INTERP_BSPLINE) {
+        // Def. 2: sum over the (p+1)-wide non-zero window of basis row t.
+        const int f = a.bfirst[t];
+        const float* brow = a.basis + (size_t)t * M;
+        const float* zc = C + s * M * n + i;
+        u = 0.f;
+        for (int q = 0; q <= a.degree; ++q) {
+          const int m = f + q;
+          if (m < M) u = fmaf(brow[m], zc[m * n], u);
+        }
+      } else if (a.interp == MTP_INTERP_AKIMA) {
+        const int k = a.seg[t];
+        const float dl = a.delta[t];
+        const float* cf = coef + ((size_t)(s * n + i) * (M - 1) + k) * 4;
+        u = fmaf(fmaf(fmaf(cf[3], dl, cf[2]), dl, cf[1]), dl, cf[0]);
+      } else {
+        const int k = a.seg[t];
+        const float w = fminf(a.delta[t] * a.inv_h, 1.f);
+        const float z0 = C[(s * M + k) * n + i], z1 = C[(s * M + k + 1) * n + i];
+        u = fmaf(w, z1 - z0, z0);
+      }
+      out[e] = clamp_box(u, a.umin[i], a.umax[i]);
+    }
+    return;
+  }
+
+  // Local rows: mu + sigma * eps, four elements of a row per generator call.
+  const int G = (Hn + 3) >> 2;
+  const long long items = (long long)a.local_rows * G + (a.U_mean ? G : 0);
+  const long long stride = (long long)(gridDim.x - a.graph_blocks) * blockDim.x;
+  for (long long e = (long long)(blockIdx.x - a.graph_blocks) * blockDim.x + threadIdx.x;
+       e < items; e += stride) {
+    const int row = (int)(e / G);
+    const int q = (int)(e - (long long)row * G);
+    if (row < a.local_rows) {
+      const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
+      float eps[4];
+      box_muller(r.x, r.y, eps[0], eps[1]);
+      box_muller(r.z, r.w, eps[2], eps[3]);
+      float* dst = a.U_local + (size_t)row * Hn;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int el = 4 * q + w;
+        if (el < Hn) {
+          const int i = el % n;
+          const float u = fmaf((float)a.sigma[el], eps[w], (float)a.mu[el]);
+          dst[el] = clamp_box(u, a.umin[i], a.umax[i]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int el = 4 * q + w;
+        if (el < Hn) {
+          const int i = el % n;
+          a.U_mean[el] = clamp_box((float)a.mu[el], a.umin[i], a.umax[i]);
+        }
+      }
+    }
+  }
+}
+
+// Def. 1 / Alg. 1 outputs for inspection: Z, I and C written to global memory.
+__global__ void k_sample_tensor(Dims dm, Key key, uint32_t iter, CandArgs box, float* Z,
+                                int32_t* I, float* C) {
+  const int n = dm.n, M = dm.M, N = dm.N, P = dm.P;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (Z)
+    for (long long e = tid; e < (long long)M * N * n; e += stride) {
+      const int node = (int)(e / n), i = (int)(e - (long long)node * n);
+      Z[e] = fmaf(box.umax[i] - box.umin[i], unit24(draw(key, node, i, iter, kTagGraph)),
+                  box.umin[i]);
+    }
+  if (I)
+    for (long long e = tid; e < (long long)P * M; e += stride) {
+      const int b = (int)(e / M), m = (int)(e - (long long)b * M);
+      I[e] = index_of(draw(key, b, m, iter, kTagPath), (uint32_t)N);
+    }
+  if (C)
+    for (long long e = tid; e < (long long)P * M * n; e += stride) {
+      const int bm = (int)(e / n), i = (int)(e - (long long)bm * n);
+      const int b = bm / M, m = bm - b * M;
+      const int j = index_of(draw(key, b, m, iter, kTagPath), (uint32_t)N);
+      C[e] = fmaf(box.umax[i] - box.umin[i], unit24(draw(key, m * N + j, i, iter, kTagGraph)),
+                  box.umin[i]);
+    }
+}
+
+}  // namespace
+
+size_t candidates_smem_bytes(const CandArgs& a) {
+  const Dims& d = a.dm;
+  size_t f = 0;
+  if (a.graph_blocks > 0) {
+    if (!a.C_in) f += (size_t)d.M * d.N * d.n;
+    f += (size_t)a.paths_per_block * d.M * d.n;
+    if (a.interp == MTP_INTERP_AKIMA) f += (size_t)a.paths_per_block * d.n * (d.M - 1) * 4;
+  }
+  return f * sizeof(float);
+}
+
+// Opt in to large dynamic shared memory on the current device (called by
+// mtp_create, outside any stream capture).
+cudaError_t init_candidate_attributes() {
+  return cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              200 * 1024);
+}
+
+cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t s) {
+  const int grid = a.graph_blocks + local_blocks;
+  if (grid <= 0) return cudaSuccess;
+  k_candidates<<<grid, kThreads, candidates_smem_bytes(a), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_tensor(const Dims& dm, Key key, uint32_t iter, const float* umin,
+                                 const float* umax, float* Z, int32_t* I, float* C,
+                                 cudaStream_t s) {
+  CandArgs box{};
+  for (int i = 0; i < dm.n; ++i) {
+    box.umin[i] = umin[i];
+    box.umax[i] = umax[i];
+  }
+  long long work = (long long)dm.M * dm.N * dm.n;
+  work = work > (long long)dm.P * dm.M * dm.n ? work : (long long)dm.P * dm.M * dm.n;
+  int grid = (int)((work + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  k_sample_tensor<<<grid, 256, 0, s>>>(dm, key, iter, box, Z, I, C);
+  return cudaGetLastError();
+}
+
+}  // namespace mtp

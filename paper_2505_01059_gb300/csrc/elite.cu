@@ -1,0 +1,269 @@
+// elite.cu -- Alg. 2 elite selection and the modified CEM update.
+//
+// k_select (one CTA): turns the B costs into order-preserving 32-bit keys
+// (NaN -> +inf, -0 -> +0), finds the E-th smallest key by a 4-pass 8-bit
+// radix select over shared memory, collects the keys below it plus the
+// lowest-index ties (a block scan in index order), sorts those E (key, index)
+// pairs with a bitonic network and computes the softmax weights in FP64.
+// k_update (many CTAs): one warp per (t, i) element reduces the weighted
+// FP64 mean and spread over the elites, applies the floor and the smoothing.
+#include "mtp_device.cuh"
+
+namespace mtp {
+namespace {
+
+constexpr int kSelThreads = 1024;
+
+__device__ __forceinline__ uint32_t order_key(float f) {
+  if (isnan(f)) f = __int_as_float(0x7f800000);
+  f = f + 0.f;  // -0 -> +0
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int B = a.B, E = a.E;
+  const int Bp = (B + 1) & ~1;
+  uint32_t* keys = reinterpret_cast<uint32_t*>(sm_raw);
+  unsigned long long* sel = reinterpret_cast<unsigned long long*>(keys + Bp);
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t s_digit, s_below, s_lt;
+  __shared__ double s_red[32];
+
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int b = tid; b < B; b += blockDim.x) keys[b] = order_key(a.cost[b]);
+  __syncthreads();
+
+  // radix select of the E-th smallest key (rank 1-based)
+  uint32_t prefix = 0, mask = 0;
+  uint32_t rank = (uint32_t)E;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int b = tid; b < B; b += blockDim.x) {
+      const uint32_t k = keys[b];
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (wid == 0) {
+      // lane l owns digits 8l .. 8l+7
+      uint32_t c[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        c[q] = hist[lane * 8 + q];
+        sum += c[q];
+      }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      uint32_t run = incl - sum;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (run < rank && rank <= run + c[q]) {
+          s_digit = (uint32_t)(lane * 8 + q);
+          s_below = run;
+        }
+        run += c[q];
+      }
+    }
+    __syncthreads();
+    prefix |= s_digit << shift;
+    mask |= 255u << shift;
+    rank -= s_below;
+    __syncthreads();
+  }
+  const uint32_t T = prefix;       // the E-th smallest key
+  const uint32_t need_eq = rank;   // how many keys equal to T are taken
+
+  // ties at T are taken in index order: block scan of per-thread tie counts
+  const int chunk = (B + blockDim.x - 1) / blockDim.x;
+  const int lo = tid * chunk, hi = min(B, lo + chunk);
+  uint32_t eq = 0;
+  for (int b = lo; b < hi; ++b) eq += (keys[b] == T);
+  uint32_t incl = eq;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  if (tid == 0) s_lt = 0;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t v = lane < nw ? warp_tot[lane] : 0u, x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < nw) warp_tot[lane] = x - v;  // exclusive warp offsets
+  }
+  __syncthreads();
+  uint32_t eq_rank = warp_tot[wid] + incl - eq;
+  const uint32_t n_lt = (uint32_t)E - need_eq;
+  for (int b = lo; b < hi; ++b) {
+    const uint32_t k = keys[b];
+    if (k < T) {
+      const uint32_t slot = atomicAdd(&s_lt, 1u);
+      sel[slot] = ((unsigned long long)k << 32) | (uint32_t)b;
+    } else if (k == T) {
+      if (eq_rank < need_eq) sel[n_lt + eq_rank] = ((unsigned long long)k << 32) | (uint32_t)b;
+      ++eq_rank;
+    }
+  }
+  const int Ep = next_pow2(E);
+  for (int i = E + tid; i < Ep; i += blockDim.x) sel[i] = ~0ull;
+  __syncthreads();
+
+  // bitonic sort of the E selected (key, index) pairs, ascending
+  for (int k = 2; k <= Ep; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < Ep; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long x = sel[i], y = sel[ixj];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            sel[i] = y;
+            sel[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // softmax weights over the elites (FP64), shifted by the best cost
+  const double best = (double)a.cost[(int)(sel[0] & 0xffffffffu)];
+  const bool uniform = (a.update_rule == MTP_UPDATE_PLAIN_CEM) || !(best < INFINITY);
+  double part = 0.0;
+  for (int k = tid; k < E; k += blockDim.x) {
+    const int idx = (int)(sel[k] & 0xffffffffu);
+    a.elite[k] = idx;
+    if (a.elite_out) a.elite_out[k] = idx;
+    double c = (double)a.cost[idx];
+    if (isnan(c)) c = INFINITY;
+    const double w = uniform ? 1.0 : exp(-(c - best) / a.lambda);
+    a.weight[k] = w;
+    part += w;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) s_red[wid] = part;
+  __syncthreads();
+  if (wid == 0) {
+    double v = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_red[0] = v;
+  }
+  __syncthreads();
+  const double total = s_red[0];
+  for (int k = tid; k < E; k += blockDim.x) a.weight[k] = a.weight[k] / total;
+  // u* = U[elite[0], 0, :]
+  const int best_row = (int)(sel[0] & 0xffffffffu);
+  for (int i = tid; i < a.n; i += blockDim.x) {
+    const float u = a.U[(size_t)best_row * a.H * a.n + i];
+    a.ustar[i] = u;
+    if (a.ustar_out) a.ustar_out[i] = u;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_update(const UpdateArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int Hn = a.H * a.n;
+  const bool cem = a.update_rule == MTP_UPDATE_PLAIN_CEM;
+  for (int e = gw; e < Hn; e += warps) {
+    double m1 = 0.0;
+    for (int k = lane; k < a.E; k += 32) {
+      const double u = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e);
+      m1 += cem ? u : a.weight[k] * u;
+    }
+    m1 = warp_sum(m1);
+    if (cem) m1 /= (double)a.E;
+    double v = 0.0;
+    for (int k = lane; k < a.E; k += 32) {
+      const double dlt = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - m1;
+      v += cem ? dlt * dlt : a.weight[k] * dlt * dlt;
+    }
+    v = warp_sum(v);
+    if (lane == 0) {
+      if (cem) {
+        const double s1 = a.E > 1 ? sqrt(v / (double)(a.E - 1)) : 0.0;
+        a.mu[e] = a.alpha * a.mu[e] + (1.0 - a.alpha) * m1;
+        a.sigma[e] = a.alpha * a.sigma[e] + (1.0 - a.alpha) * s1;
+      } else {
+        double s1 = sqrt(v);
+        if (s1 < a.sigma_min) s1 = a.sigma_min;
+        a.mu[e] = m1 + a.alpha * (a.mu[e] - m1);
+        a.sigma[e] = s1 + a.alpha * (a.sigma[e] - s1);
+      }
+    }
+  }
+  if (a.d_iter && blockIdx.x == 0 && threadIdx.x == 0) *a.d_iter += 1u;
+}
+
+__global__ void k_shift(double* mu, double* sigma, int H, int n, int k) {
+  // one thread per dimension walks the horizon forward (in place is safe:
+  // row t reads row t+k >= t)
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int t = 0; t < H; ++t) {
+    const int src = t + k < H ? t + k : H - 1;
+    mu[t * n + i] = mu[src * n + i];
+    sigma[t * n + i] = sigma[src * n + i];
+  }
+}
+
+}  // namespace
+
+size_t select_smem_bytes(int B, int E) {
+  int Ep = 1;
+  while (Ep < E) Ep <<= 1;
+  return (size_t)((B + 1) & ~1) * 4 + (size_t)Ep * 8;
+}
+
+cudaError_t init_select_attributes() {
+  return cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
+  k_select<<<1, kSelThreads, select_smem_bytes(a.B, a.E), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
+  const int Hn = a.H * a.n;
+  int blocks = (Hn + 7) / 8;  // 8 warps per block, one warp per element
+  if (blocks > 1216) blocks = 1216;
+  if (blocks < 1) blocks = 1;
+  k_update<<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift(double* mu, double* sigma, int H, int n, int k, cudaStream_t s) {
+  k_shift<<<(n + 63) / 64, 64, 0, s>>>(mu, sigma, H, n, k);
+  return cudaGetLastError();
+}
+
+}  // namespace mtp

@@ -1,0 +1,660 @@
+// mtp_abi.cu -- the C ABI of include/mtp.h: problem validation, the handle's
+// device state, host precompute of the interpolation tables (Sec. 8 step
+// "host precompute": B-spline basis of Def. 2 by the closed-form cardinal
+// B-spline, Akima / straight-line piece table of Def. 3), and the launch
+// sequence of one planner iteration (Alg. 2), replayed as a CUDA graph.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "mtp_device.cuh"
+
+using namespace mtp;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr size_t kMaxSmem = 200 * 1024;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct mtp_handle {
+  mtp_problem pr{};
+  Dims dm{};
+  int device = 0;
+  Key key{};
+  // interpolation tables
+  float* basis = nullptr;
+  int32_t* bfirst = nullptr;
+  int32_t* seg = nullptr;
+  float* delta = nullptr;
+  float inv_h = 1.f;
+  int paths_per_block = 1;
+  // planner state
+  double* mu = nullptr;
+  double* sigma = nullptr;
+  uint32_t* iter_dev = nullptr;
+  uint32_t iter_host = 0;
+  // scratch of one iteration
+  float* U = nullptr;
+  float* cost = nullptr;
+  int32_t* elite = nullptr;
+  double* weight = nullptr;
+  float* ustar = nullptr;
+  float* x0 = nullptr;
+  // replay
+  cudaStream_t cap_stream = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+  // profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t ev_used = 0;
+  std::string err;
+};
+
+namespace {
+
+mtp_status fail(mtp_handle* h, mtp_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+mtp_status cuda_fail(mtp_handle* h, cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? MTP_ERR_OUT_OF_MEMORY : MTP_ERR_CUDA, msg);
+}
+
+#define MTP_CUDA(h, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+int32_t num_graph_samples(double beta, int32_t B) {
+  int32_t P = (int32_t)std::floor(beta * (double)B);
+  if (P > B - 1) P = B - 1;
+  if (P < 0) P = 0;
+  return P;
+}
+
+// Cardinal B-spline of degree p on the integer knots 0..p+1 by the truncated
+// power form N_p(y) = 1/p! sum_k (-1)^k C(p+1, k) (y - k)_+^p.  `left` takes
+// the left limit at a knot (the closed right end of the valid span).
+double cardinal_bspline(int p, double y, bool left) {
+  double acc = 0.0, binom = 1.0, fact = 1.0;
+  for (int k = 2; k <= p; ++k) fact *= k;
+  for (int k = 0; k <= p + 1; ++k) {
+    const double z = y - k;
+    const bool on = left ? (z > 0.0) : (z >= 0.0);
+    if (on) acc += ((k & 1) ? -binom : binom) * (p == 0 ? 1.0 : std::pow(z, p));
+    binom = binom * (p + 1 - k) / (k + 1);
+  }
+  return acc / fact;
+}
+
+mtp_status validate(const mtp_problem& p) {
+  auto bad = [](const std::string& m) { return fail(nullptr, MTP_ERR_INVALID_ARG, m); };
+  if (p.dyn == MTP_DYN_POINTMASS) {
+    if (p.ctrl_dim < 1 || p.ctrl_dim > 16) return bad("point mass: ctrl_dim must be in 1..16");
+    if (p.state_dim != 2 * p.ctrl_dim) return bad("point mass: state_dim must be 2*ctrl_dim");
+    if (p.n_obstacles < 0 || p.n_obstacles > MTP_MAX_OBSTACLES) return bad("n_obstacles out of range");
+  } else if (p.dyn == MTP_DYN_CHAIN) {
+    if (p.n_links < 1 || p.n_links > 12) return bad("chain: n_links must be in 1..12");
+    if (p.ctrl_dim != p.n_links || p.state_dim != 2 * p.n_links)
+      return bad("chain: ctrl_dim must be n_links and state_dim 2*n_links");
+    for (int j = 0; j < p.n_links; ++j)
+      if (!(p.link_mass[j] > 0.f) || !(p.link_length[j] > 0.f)) return bad("chain: link mass/length must be > 0");
+  } else if (p.dyn == MTP_DYN_LEGGED) {
+    return fail(nullptr, MTP_ERR_UNSUPPORTED, "legged dynamics are not built into this library yet");
+  } else {
+    return bad("unknown dyn");
+  }
+  if (p.horizon < 1) return bad("horizon must be >= 1");
+  if (!(p.dt > 0.f)) return bad("dt must be > 0");
+  for (int i = 0; i < p.ctrl_dim; ++i)
+    if (!(p.u_min[i] < p.u_max[i]) || !std::isfinite(p.u_min[i]) || !std::isfinite(p.u_max[i]))
+      return bad("control box: need finite u_min < u_max");
+  if (p.M < 2 || p.M > 64) return bad("M must be in 2..64");
+  if (p.N < 1) return bad("N must be >= 1");
+  if (p.B < 1 || p.B > (1 << 24)) return bad("B must be in 1..2^24");
+  if (p.E < 1 || p.E > p.B) return bad("E must be in 1..B");
+  if (!(p.beta >= 0.0 && p.beta <= 1.0)) return bad("beta must be in [0, 1]");
+  if (!(p.lambda > 0.0)) return bad("lambda must be > 0");
+  if (!(p.alpha >= 0.0 && p.alpha < 1.0)) return bad("alpha must be in [0, 1)");
+  if (!(p.sigma_min > 0.0)) return bad("sigma_min must be > 0");
+  if (!(p.sigma_init >= 0.0) || !std::isfinite(p.mu_init)) return bad("bad mu_init / sigma_init");
+  if (p.interp < 0 || p.interp > 2) return bad("unknown interp");
+  if (p.interp == MTP_INTERP_BSPLINE && (p.bspline_degree < 0 || p.bspline_degree > 7 || p.M < p.bspline_degree + 1))
+    return bad("B-spline: need 0 <= degree <= 7 and M >= degree + 1");
+  if (p.time_mapping < 0 || p.time_mapping > 1) return bad("unknown time_mapping");
+  if (p.update_rule < 0 || p.update_rule > 1) return bad("unknown update_rule");
+  if (p.dr_mode < 0 || p.dr_mode > 2) return bad("unknown dr_mode");
+  if (p.dr_mode == MTP_DR_SHARED && (p.R < 1 || p.R > 64)) return bad("R must be in 1..64");
+  if (p.dr_mode != MTP_DR_NONE && !(p.dr_lo > 0.f && p.dr_lo <= p.dr_hi)) return bad("need 0 < dr_lo <= dr_hi");
+  if ((size_t)p.M * p.N * p.ctrl_dim * 4 > 160 * 1024) return bad("graph M*N*n too large for one block's shared memory");
+  if (select_smem_bytes(p.B, p.E) > kMaxSmem) return bad("B and E too large for the single-block elite selection");
+  if (p.flags & MTP_FLAG_BF16_BASIS) return fail(nullptr, MTP_ERR_UNSUPPORTED, "BF16 basis path not built yet");
+  return MTP_OK;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+}
+
+mtp_status build_tables(mtp_handle* h) {
+  const mtp_problem& p = h->pr;
+  const int H = p.horizon, M = p.M;
+  std::vector<float> basis((size_t)H * M, 0.f);
+  std::vector<int32_t> bfirst(H, 0), seg(H, 0);
+  std::vector<float> delta(H, 0.f);
+  if (p.interp == MTP_INTERP_BSPLINE) {
+    const int deg = p.bspline_degree;
+    for (int j = 0; j < H; ++j) {
+      // evaluation point in knot units (knot i at i): Def. 2 with the chosen reading
+      double x;
+      bool left = false;
+      if (p.time_mapping == MTP_TIME_PAPER_LITERAL) {
+        x = (double)((M + deg + 1) * j) / (double)H;
+      } else {
+        x = H > 1 ? (double)deg + (double)((M - deg) * j) / (double)(H - 1) : (double)deg;
+        left = (H > 1 && j == H - 1);
+      }
+      int first = -1;
+      for (int m = 0; m < M; ++m) {
+        const double v = cardinal_bspline(deg, x - m, left);
+        basis[(size_t)j * M + m] = (float)v;
+        if (v != 0.0 && first < 0) first = m;
+      }
+      if (first < 0) first = 0;
+      if (first > M - 1 - deg) first = M - 1 - deg;
+      bfirst[j] = first;
+    }
+  } else {
+    // Def. 3 knots: i/(M-1) (valid span) or i/M (paper literal); piece of step t
+    const bool lit = p.time_mapping == MTP_TIME_PAPER_LITERAL;
+    h->inv_h = lit ? (float)M : (float)(M - 1);
+    for (int j = 0; j < H; ++j) {
+      long long k = lit ? ((long long)j * M) / H : (H > 1 ? ((long long)j * (M - 1)) / (H - 1) : 0);
+      if (k > M - 2) k = M - 2;
+      const double t = lit ? (double)j / (double)H : (H > 1 ? (double)j / (double)(H - 1) : 0.0);
+      const double tk = lit ? (double)k / (double)M : (double)k / (double)(M - 1);
+      seg[j] = (int32_t)k;
+      delta[j] = (float)(t - tk);
+    }
+  }
+  MTP_CUDA(h, dalloc(&h->basis, basis.size()));
+  MTP_CUDA(h, dalloc(&h->bfirst, H));
+  MTP_CUDA(h, dalloc(&h->seg, H));
+  MTP_CUDA(h, dalloc(&h->delta, H));
+  MTP_CUDA(h, cudaMemcpy(h->basis, basis.data(), basis.size() * 4, cudaMemcpyHostToDevice));
+  MTP_CUDA(h, cudaMemcpy(h->bfirst, bfirst.data(), H * 4, cudaMemcpyHostToDevice));
+  MTP_CUDA(h, cudaMemcpy(h->seg, seg.data(), H * 4, cudaMemcpyHostToDevice));
+  MTP_CUDA(h, cudaMemcpy(h->delta, delta.data(), H * 4, cudaMemcpyHostToDevice));
+  return MTP_OK;
+}
+
+CandArgs cand_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter) {
+  CandArgs a{};
+  a.dm = h->dm;
+  a.key = h->key;
+  a.iter = iter;
+  a.d_iter = d_iter;
+  a.interp = h->pr.interp;
+  a.degree = h->pr.bspline_degree;
+  a.inv_h = h->inv_h;
+  a.basis = h->basis;
+  a.bfirst = h->bfirst;
+  a.seg = h->seg;
+  a.delta = h->delta;
+  a.paths_per_block = h->paths_per_block;
+  a.mu = h->mu;
+  a.sigma = h->sigma;
+  for (int i = 0; i < h->dm.n; ++i) {
+    a.umin[i] = h->pr.u_min[i];
+    a.umax[i] = h->pr.u_max[i];
+  }
+  return a;
+}
+
+int local_blocks_for(const mtp_handle* h, long long rows_plus_mean) {
+  const long long G = ((long long)h->dm.H * h->dm.n + 3) / 4;
+  long long items = rows_plus_mean * G;
+  long long blocks = (items + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  return (int)blocks;
+}
+
+RolloutArgs rollout_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter,
+                         const float* x0, const float* U, int row0, int rows, float* cost) {
+  RolloutArgs a{};
+  a.H = h->dm.H;
+  a.n = h->dm.n;
+  a.d = h->dm.d;
+  a.dt = h->pr.dt;
+  a.key = h->key;
+  a.iter = iter;
+  a.d_iter = d_iter;
+  a.dr_mode = h->pr.dr_mode;
+  a.R = h->pr.R;
+  a.dr_lo = h->pr.dr_lo;
+  a.dr_hi = h->pr.dr_hi;
+  a.x0 = x0;
+  a.U = U;
+  a.row0 = row0;
+  a.rows = rows;
+  a.cost = cost;
+  a.kahan = (h->pr.flags & MTP_FLAG_NO_KAHAN) ? 0 : 1;
+  return a;
+}
+
+cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
+  const mtp_problem& p = h->pr;
+  if (p.dyn == MTP_DYN_POINTMASS) {
+    PointMassModel m{};
+    for (int k = 0; k < p.ctrl_dim; ++k) m.target[k] = p.target[k];
+    m.w_target = p.w_target;
+    m.w_obs = p.w_obs;
+    m.w_ctrl = p.w_ctrl;
+    m.w_term = p.w_term;
+    m.n_obs = p.n_obstacles;
+    for (int o = 0; o < p.n_obstacles; ++o) {
+      for (int k = 0; k < p.ctrl_dim; ++k) m.obs_c[o][k] = p.obs_center[o][k];
+      m.obs_r[o] = p.obs_radius[o];
+    }
+    return launch_rollout_pointmass(a, m, s);
+  }
+  ChainModel m{};
+  for (int j = 0; j < p.n_links; ++j) {
+    m.mass[j] = p.link_mass[j];
+    m.length[j] = p.link_length[j];
+  }
+  m.gravity = p.gravity;
+  m.target[0] = p.target[0];
+  m.target[1] = p.target[1];
+  m.w_target = p.w_target;
+  m.w_ctrl = p.w_ctrl;
+  m.w_term = p.w_term;
+  return launch_rollout_chain(a, m, p.n_links, s);
+}
+
+// One Alg. 2 iteration on the handle's own buffers, iteration from iter_dev.
+cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev) {
+  cudaError_t e;
+  const Dims& dm = h->dm;
+  const size_t Hn = (size_t)dm.H * dm.n;
+  if (ev) cudaEventRecord(ev[0], s);
+  CandArgs c = cand_args(h, 0, h->iter_dev);
+  c.U_graph = h->U + Hn * dm.L;
+  c.graph_rows = dm.P;
+  c.graph_blocks = (dm.P + h->paths_per_block - 1) / h->paths_per_block;
+  c.U_local = h->U;
+  c.local_rows = dm.L;
+  c.U_mean = h->U + Hn * (dm.B - 1);
+  if ((e = launch_candidates(c, local_blocks_for(h, (long long)dm.L + 1), s)) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[1], s);
+  RolloutArgs r = rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, dm.B, h->cost);
+  if ((e = launch_rollout(h, r, s)) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[2], s);
+  SelectArgs sa{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, h->pr.lambda, h->pr.update_rule,
+                h->elite, h->weight, h->ustar, nullptr, nullptr};
+  if ((e = launch_select(sa, s)) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[3], s);
+  UpdateArgs ua{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
+                h->pr.update_rule, h->mu, h->sigma, h->iter_dev};
+  if ((e = launch_update(ua, s)) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[4], s);
+  return cudaSuccess;
+}
+
+void free_handle(mtp_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  void* ptrs[] = {h->basis, h->bfirst, h->seg, h->delta, h->mu, h->sigma, h->iter_dev,
+                  h->U, h->cost, h->elite, h->weight, h->ustar, h->x0};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mtp_problem_bytes(void) { return sizeof(mtp_problem); }
+
+mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
+  if (!problem || !out) return fail(nullptr, MTP_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  mtp_status st = validate(*problem);
+  if (st != MTP_OK) return st;
+  mtp_handle* h = new mtp_handle();
+  h->pr = *problem;
+  const mtp_problem& p = h->pr;
+  cudaGetDevice(&h->device);
+  Dims& dm = h->dm;
+  dm.B = p.B;
+  dm.P = num_graph_samples(p.beta, p.B);
+  dm.L = p.B - dm.P - 1;
+  dm.E = p.E;
+  dm.H = p.horizon;
+  dm.n = p.ctrl_dim;
+  dm.d = p.state_dim;
+  dm.M = p.M;
+  dm.N = p.N;
+  h->key.k0 = (uint32_t)(p.seed & 0xffffffffu);
+  h->key.k1 = (uint32_t)(p.seed >> 32);
+  // graph paths per block: ~2K output elements per block within shared memory
+  const long long Hn = (long long)dm.H * dm.n;
+  int spb = (int)((2048 + Hn - 1) / Hn);
+  if (spb < 1) spb = 1;
+  if (spb > 32) spb = 32;
+  for (;;) {
+    CandArgs probe{};
+    probe.dm = dm;
+    probe.interp = p.interp;
+    probe.graph_blocks = 1;
+    probe.paths_per_block = spb;
+    if (candidates_smem_bytes(probe) <= kMaxSmem || spb == 1) break;
+    spb /= 2;
+  }
+  h->paths_per_block = spb;
+  auto err = [&](mtp_status s) {
+    g_create_error = h->err;
+    free_handle(h);
+    return s;
+  };
+  cudaError_t e;
+  if ((e = init_candidate_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
+  if ((e = init_select_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
+  if ((st = build_tables(h)) != MTP_OK) return err(st);
+  const size_t rowsz = (size_t)dm.H * dm.n;
+  if ((e = dalloc(&h->mu, rowsz)) || (e = dalloc(&h->sigma, rowsz)) ||
+      (e = dalloc(&h->iter_dev, 1)) || (e = dalloc(&h->U, rowsz * dm.B)) ||
+      (e = dalloc(&h->cost, dm.B)) || (e = dalloc(&h->elite, dm.E)) ||
+      (e = dalloc(&h->weight, dm.E)) || (e = dalloc(&h->ustar, dm.n)) ||
+      (e = dalloc(&h->x0, dm.d)))
+    return err(cuda_fail(h, e, "cudaMalloc"));
+  std::vector<double> mu(rowsz, p.mu_init), sg(rowsz, p.sigma_init);
+  uint32_t zero = 0;
+  if ((e = cudaMemcpy(h->mu, mu.data(), rowsz * 8, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->sigma, sg.data(), rowsz * 8, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->iter_dev, &zero, 4, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemset(h->ustar, 0, dm.n * 4)))
+    return err(cuda_fail(h, e, "cudaMemcpy"));
+  if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return err(cuda_fail(h, e, "cudaStreamCreate"));
+  *out = h;
+  return MTP_OK;
+}
+
+mtp_status mtp_destroy(mtp_handle* h) {
+  if (!h) return MTP_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  free_handle(h);
+  return MTP_OK;
+}
+
+const char* mtp_last_error(const mtp_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+mtp_status mtp_get_sizes(const mtp_handle* h, mtp_sizes* out) {
+  if (!h || !out) return MTP_ERR_INVALID_ARG;
+  const Dims& d = h->dm;
+  *out = mtp_sizes{d.B, d.P, d.L, d.E, d.H, d.n, d.d, d.M, d.N};
+  return MTP_OK;
+}
+
+mtp_status mtp_get_buffers(const mtp_handle* h, mtp_buffers* out) {
+  if (!h || !out) return MTP_ERR_INVALID_ARG;
+  *out = mtp_buffers{h->U, h->cost, h->elite, h->weight, h->mu, h->sigma, h->ustar, h->iter_dev};
+  return MTP_OK;
+}
+
+mtp_status mtp_sample_tensor(mtp_handle* h, uint32_t iter, float* d_Z, int32_t* d_idx,
+                             float* d_C, void* stream) {
+  if (!h) return MTP_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaError_t e = launch_sample_tensor(h->dm, h->key, iter, h->pr.u_min, h->pr.u_max, d_Z, d_idx,
+                                       d_C, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sample_tensor");
+  return MTP_OK;
+}
+
+mtp_status mtp_interpolate(mtp_handle* h, const float* d_C, int32_t P, float* d_U, void* stream) {
+  if (!h || !d_C || !d_U || P < 0) return fail(h, MTP_ERR_INVALID_ARG, "interpolate: bad argument");
+  if (P == 0) return MTP_OK;
+  DeviceGuard g(h->device);
+  CandArgs c = cand_args(h, 0, nullptr);
+  c.C_in = d_C;
+  c.U_graph = d_U;
+  c.graph_rows = P;
+  c.graph_blocks = (P + h->paths_per_block - 1) / h->paths_per_block;
+  cudaError_t e = launch_candidates(c, 0, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "interpolate");
+  return MTP_OK;
+}
+
+mtp_status mtp_sample_local(mtp_handle* h, uint32_t iter, float* d_U, void* stream) {
+  if (!h || !d_U) return fail(h, MTP_ERR_INVALID_ARG, "sample_local: bad argument");
+  DeviceGuard g(h->device);
+  const size_t Hn = (size_t)h->dm.H * h->dm.n;
+  CandArgs c = cand_args(h, iter, nullptr);
+  c.U_local = d_U;
+  c.local_rows = h->dm.L;
+  c.U_mean = d_U + Hn * (h->dm.B - 1);
+  cudaError_t e = launch_candidates(c, local_blocks_for(h, (long long)h->dm.L + 1), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sample_local");
+  return MTP_OK;
+}
+
+mtp_status mtp_generate_candidates(mtp_handle* h, uint32_t iter, float* d_U, void* stream) {
+  if (!h || !d_U) return fail(h, MTP_ERR_INVALID_ARG, "generate_candidates: bad argument");
+  DeviceGuard g(h->device);
+  const Dims& dm = h->dm;
+  const size_t Hn = (size_t)dm.H * dm.n;
+  CandArgs c = cand_args(h, iter, nullptr);
+  c.U_graph = d_U + Hn * dm.L;
+  c.graph_rows = dm.P;
+  c.graph_blocks = (dm.P + h->paths_per_block - 1) / h->paths_per_block;
+  c.U_local = d_U;
+  c.local_rows = dm.L;
+  c.U_mean = d_U + Hn * (dm.B - 1);
+  cudaError_t e = launch_candidates(c, local_blocks_for(h, (long long)dm.L + 1), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "generate_candidates");
+  return MTP_OK;
+}
+
+mtp_status mtp_rollout_cost(mtp_handle* h, uint32_t iter, const float* d_x0, const float* d_U,
+                            int32_t row0, int32_t rows, float* d_cost, void* stream) {
+  if (!h || !d_x0 || !d_U || !d_cost || row0 < 0 || rows < 0 || row0 + rows > h->dm.B)
+    return fail(h, MTP_ERR_INVALID_ARG, "rollout_cost: bad argument");
+  DeviceGuard g(h->device);
+  RolloutArgs a = rollout_args(h, iter, nullptr, d_x0, d_U, row0, rows, d_cost);
+  cudaError_t e = launch_rollout(h, a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rollout_cost");
+  return MTP_OK;
+}
+
+mtp_status mtp_rollout_states(mtp_handle* h, uint32_t iter, const float* d_x0, const float* d_Urow,
+                              int32_t row, float* d_X, float* d_cost, void* stream) {
+  if (!h || !d_x0 || !d_Urow || !d_X || !d_cost || row < 0 || row >= h->dm.B)
+    return fail(h, MTP_ERR_INVALID_ARG, "rollout_states: bad argument");
+  if (h->pr.dr_mode == MTP_DR_SHARED)
+    return fail(h, MTP_ERR_INVALID_ARG, "rollout_states: one trajectory per model is ambiguous with shared models");
+  DeviceGuard g(h->device);
+  RolloutArgs a = rollout_args(h, iter, nullptr, d_x0, d_Urow, row, 1, d_cost);
+  a.X = d_X;
+  cudaError_t e = launch_rollout(h, a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rollout_states");
+  return MTP_OK;
+}
+
+mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U, int32_t* d_elite,
+                            float* d_ustar, void* stream) {
+  if (!h || !d_cost || !d_U) return fail(h, MTP_ERR_INVALID_ARG, "elite_update: bad argument");
+  DeviceGuard g(h->device);
+  const Dims& dm = h->dm;
+  cudaStream_t s = (cudaStream_t)stream;
+  SelectArgs sa{d_cost, d_U, dm.B, dm.E, dm.H, dm.n, h->pr.lambda, h->pr.update_rule,
+                h->elite, h->weight, h->ustar, d_elite, d_ustar};
+  cudaError_t e = launch_select(sa, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "select");
+  UpdateArgs ua{d_U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
+                h->pr.update_rule, h->mu, h->sigma, nullptr};
+  e = launch_update(ua, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "update");
+  return MTP_OK;
+}
+
+static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
+  cudaError_t e;
+  const bool use_graph = !(h->pr.flags & MTP_FLAG_NO_GRAPH) && !h->profiling;
+  if (!use_graph) {
+    for (int k = 0; k < iters; ++k) {
+      cudaEvent_t* ev = nullptr;
+      if (h->profiling) {
+        while (h->events.size() < h->ev_used + 5) {
+          cudaEvent_t x;
+          if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+          h->events.push_back(x);
+        }
+        ev = h->events.data() + h->ev_used;
+        h->ev_used += 5;
+      }
+      if ((e = enqueue_iteration(h, s, ev)) != cudaSuccess) return cuda_fail(h, e, "plan_step");
+    }
+    return MTP_OK;
+  }
+  // one captured graph per distinct iteration count (at most 64 iterations each)
+  int left = iters;
+  while (left > 0) {
+    const int chunk = left > 64 ? 64 : left;
+    auto it = h->graphs.find(chunk);
+    if (it == h->graphs.end()) {
+      cudaGraph_t graph;
+      if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaStreamBeginCapture");
+      for (int k = 0; k < chunk; ++k) {
+        if ((e = enqueue_iteration(h, h->cap_stream, nullptr)) != cudaSuccess) {
+          cudaStreamEndCapture(h->cap_stream, &graph);
+          return cuda_fail(h, e, "capture");
+        }
+      }
+      if ((e = cudaStreamEndCapture(h->cap_stream, &graph)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaStreamEndCapture");
+      cudaGraphExec_t exec;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+      it = h->graphs.emplace(chunk, exec).first;
+    }
+    if ((e = cudaGraphLaunch(it->second, s)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    left -= chunk;
+  }
+  return MTP_OK;
+}
+
+mtp_status mtp_plan_step(mtp_handle* h, const float* d_x0, int32_t iters, float* d_ustar, void* stream) {
+  if (!h || !d_x0 || !d_ustar || iters < 1) return fail(h, MTP_ERR_INVALID_ARG, "plan_step: bad argument");
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  MTP_CUDA(h, cudaMemcpyAsync(h->x0, d_x0, h->dm.d * 4, cudaMemcpyDeviceToDevice, s));
+  mtp_status st = plan_device(h, iters, s);
+  if (st != MTP_OK) return st;
+  MTP_CUDA(h, cudaMemcpyAsync(d_ustar, h->ustar, h->dm.n * 4, cudaMemcpyDeviceToDevice, s));
+  h->iter_host += (uint32_t)iters;
+  return MTP_OK;
+}
+
+mtp_status mtp_plan_step_host(mtp_handle* h, const float* h_x0, int32_t iters, float* h_ustar,
+                              void* stream) {
+  if (!h || !h_x0 || !h_ustar || iters < 1) return fail(h, MTP_ERR_INVALID_ARG, "plan_step_host: bad argument");
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  MTP_CUDA(h, cudaMemcpyAsync(h->x0, h_x0, h->dm.d * 4, cudaMemcpyHostToDevice, s));
+  mtp_status st = plan_device(h, iters, s);
+  if (st != MTP_OK) return st;
+  MTP_CUDA(h, cudaMemcpyAsync(h_ustar, h->ustar, h->dm.n * 4, cudaMemcpyDeviceToHost, s));
+  MTP_CUDA(h, cudaStreamSynchronize(s));
+  h->iter_host += (uint32_t)iters;
+  return MTP_OK;
+}
+
+mtp_status mtp_shift(mtp_handle* h, int32_t k, void* stream) {
+  if (!h || k < 0) return fail(h, MTP_ERR_INVALID_ARG, "shift: bad argument");
+  if (k == 0) return MTP_OK;
+  DeviceGuard g(h->device);
+  cudaError_t e = launch_shift(h->mu, h->sigma, h->dm.H, h->dm.n, k, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shift");
+  return MTP_OK;
+}
+
+mtp_status mtp_get_state(mtp_handle* h, double* h_mu, double* h_sigma, uint32_t* h_iter) {
+  if (!h) return MTP_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  const size_t bytes = (size_t)h->dm.H * h->dm.n * 8;
+  MTP_CUDA(h, cudaDeviceSynchronize());
+  if (h_mu) MTP_CUDA(h, cudaMemcpy(h_mu, h->mu, bytes, cudaMemcpyDeviceToHost));
+  if (h_sigma) MTP_CUDA(h, cudaMemcpy(h_sigma, h->sigma, bytes, cudaMemcpyDeviceToHost));
+  if (h_iter) MTP_CUDA(h, cudaMemcpy(h_iter, h->iter_dev, 4, cudaMemcpyDeviceToHost));
+  return MTP_OK;
+}
+
+mtp_status mtp_set_state(mtp_handle* h, const double* h_mu, const double* h_sigma, uint32_t iter) {
+  if (!h || !h_mu || !h_sigma) return MTP_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  const size_t bytes = (size_t)h->dm.H * h->dm.n * 8;
+  MTP_CUDA(h, cudaDeviceSynchronize());
+  MTP_CUDA(h, cudaMemcpy(h->mu, h_mu, bytes, cudaMemcpyHostToDevice));
+  MTP_CUDA(h, cudaMemcpy(h->sigma, h_sigma, bytes, cudaMemcpyHostToDevice));
+  MTP_CUDA(h, cudaMemcpy(h->iter_dev, &iter, 4, cudaMemcpyHostToDevice));
+  h->iter_host = iter;
+  return MTP_OK;
+}
+
+mtp_status mtp_set_profiling(mtp_handle* h, int32_t enable) {
+  if (!h) return MTP_ERR_INVALID_ARG;
+  h->profiling = enable != 0;
+  h->ev_used = 0;
+  return MTP_OK;
+}
+
+mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations) {
+  if (!h || !ms4) return MTP_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  for (int i = 0; i < 4; ++i) ms4[i] = 0.0;
+  const size_t n_it = h->ev_used / 5;
+  if (n_it > 0) MTP_CUDA(h, cudaEventSynchronize(h->events[h->ev_used - 1]));
+  for (size_t k = 0; k < n_it; ++k) {
+    for (int st = 0; st < 4; ++st) {
+      float ms = 0.f;
+      MTP_CUDA(h, cudaEventElapsedTime(&ms, h->events[5 * k + st], h->events[5 * k + st + 1]));
+      ms4[st] += ms;
+    }
+  }
+  if (iterations) *iterations = (int32_t)n_it;
+  h->ev_used = 0;
+  return MTP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// mtp_device.cuh -- device-side building blocks shared by the MTP kernels:
+// the counter-based generator, launch argument blocks and small helpers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mtp.h"
+
+namespace mtp {
+
+// Stream tags of the Philox counter (word 3): one independent stream per kind
+// of random draw of Alg. 2.
+enum : uint32_t {
+  kTagGraph = 1,        // Def. 1 graph waypoints
+  kTagPath = 2,         // Alg. 1 path indices
+  kTagLocal = 3,        // Alg. 2 local Gaussian samples
+  kTagParamSample = 4,  // per-candidate model scales
+  kTagParamModel = 5,   // shared randomised models
+};
+
+struct Key {
+  uint32_t k0, k1;
+};
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies with the published multipliers, key bumped by the Weyl constants.
+__device__ __forceinline__ uint4 philox(uint4 c, Key key) {
+  uint32_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t pick(uint4 v, uint32_t w) {
+  return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+
+// Word (b & 3) of the generator call at counter (a, b / 4, iter, tag).
+__device__ __forceinline__ uint32_t draw(Key key, uint32_t a, uint32_t b, uint32_t iter,
+                                         uint32_t tag) {
+  return pick(philox(make_uint4(a, b >> 2, iter, tag), key), b & 3u);
+}
+
+// Uniform in [0, 1) from the top 24 bits (exact in FP32).
+__device__ __forceinline__ float unit24(uint32_t r) {
+  return (float)(r >> 8) * 5.9604644775390625e-8f;
+}
+
+// Uniform index in [0, N): high word of r * N (multiply-high mapping).
+__device__ __forceinline__ int32_t index_of(uint32_t r, uint32_t N) {
+  return (int32_t)__umulhi(r, N);
+}
+
+__device__ __forceinline__ float clamp_box(float v, float lo, float hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Compensated (Kahan) accumulation in FP32.
+struct KahanSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x, bool kahan) {
+    if (kahan) {
+      const float y = x - c;
+      const float t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += x;
+    }
+  }
+};
+
+struct Dims {
+  int32_t B, P, L, E, H, n, d, M, N;
+};
+
+// Candidate generation (Def. 1, Alg. 1, interpolation, local sampling).
+struct CandArgs {
+  Dims dm;
+  Key key;
+  uint32_t iter;
+  const uint32_t* d_iter;  // when set, the iteration is read from here
+  int32_t interp;          // mtp_interp
+  int32_t degree;          // B-spline degree p
+  float inv_h;             // reciprocal knot spacing of the Akima / linear knots
+  const float* basis;      // (H, M) B-spline basis, row t
+  const int32_t* bfirst;   // (H) first non-zero basis column of row t
+  const int32_t* seg;      // (H) Akima / linear piece of step t
+  const float* delta;      // (H) offset of step t from the piece's left knot
+  // graph rows
+  const float* C_in;       // (P, M, n) given waypoints, or null to sample them
+  float* U_graph;          // output rows of the graph paths (graph_rows, H, n)
+  int32_t graph_rows;
+  int32_t graph_blocks;    // blocks [0, graph_blocks) make graph rows
+  int32_t paths_per_block;
+  // local rows and the mean row
+  float* U_local;          // rows [0, local_rows) or null
+  int32_t local_rows;
+  float* U_mean;           // the mean row or null
+  const double* mu;        // (H, n)
+  const double* sigma;     // (H, n)
+  float umin[MTP_MAX_CTRL], umax[MTP_MAX_CTRL];
+};
+
+struct RolloutArgs {
+  int32_t H, n, d;
+  float dt;
+  Key key;
+  uint32_t iter;
+  const uint32_t* d_iter;
+  int32_t dr_mode, R;
+  float dr_lo, dr_hi;
+  const float* x0;   // (d)
+  const float* U;    // (rows, H, n), row r is candidate row0 + r
+  int32_t row0, rows;
+  float* cost;       // (rows)
+  float* X;          // (H+1, d) states of the single requested row, or null
+  int32_t kahan;
+};
+
+struct PointMassModel {
+  float target[16];
+  float w_target, w_obs, w_ctrl, w_term;
+  int32_t n_obs;
+  float obs_c[MTP_MAX_OBSTACLES][16];
+  float obs_r[MTP_MAX_OBSTACLES];
+};
+
+struct ChainModel {
+  float mass[12], length[12];
+  float gravity;
+  float target[2];
+  float w_target, w_ctrl, w_term;
+};
+
+struct SelectArgs {
+  const float* cost;  // (B)
+  const float* U;     // (B, H, n)
+  int32_t B, E, H, n;
+  double lambda;
+  int32_t update_rule;
+  int32_t* elite;     // (E) internal
+  double* weight;     // (E) internal
+  float* ustar;       // (n) internal
+  int32_t* elite_out; // optional copy
+  float* ustar_out;   // optional copy
+};
+
+struct UpdateArgs {
+  const float* U;       // (B, H, n)
+  const int32_t* elite; // (E)
+  const double* weight; // (E)
+  int32_t E, H, n;
+  double alpha, sigma_min;
+  int32_t update_rule;
+  double* mu;           // (H, n) in/out
+  double* sigma;        // (H, n) in/out
+  uint32_t* d_iter;     // incremented once when set
+};
+
+// host-side launchers (defined in the .cu files)
+size_t candidates_smem_bytes(const CandArgs& a);
+cudaError_t init_candidate_attributes();
+cudaError_t init_select_attributes();
+cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t s);
+cudaError_t launch_sample_tensor(const Dims& dm, Key key, uint32_t iter, const float* umin,
+                                 const float* umax, float* Z, int32_t* I, float* C,
+                                 cudaStream_t s);
+cudaError_t launch_rollout_pointmass(const RolloutArgs& a, const PointMassModel& m,
+                                     cudaStream_t s);
+cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int links,
+                                 cudaStream_t s);
+cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
+size_t select_smem_bytes(int B, int E);
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_shift(double* mu, double* sigma, int H, int n, int k, cudaStream_t s);
+
+}  // namespace mtp

@@ -1,0 +1,326 @@
+// rollout.cu -- Alg. 2 batch rollout fused with the cost reduction (Eq. 2).
+//
+// One thread per candidate keeps the whole state in registers for all H
+// steps and accumulates c(x_t, u_t) with compensated FP32 sums; only the
+// final cost leaves the SM.  The loop bodies are fully unrolled over the
+// compile-time dimension (point-mass axes, chain links), so the per-step
+// linear algebra lives in registers.
+//
+// Planar chain: the dynamics are evaluated in absolute link angles phi_j
+// (phi_j = q_1 + ... + q_j).  For uniform thin rods the Lagrangian gives the
+// mass matrix A_jk = D_jk cos(phi_j - phi_k) with constant D (from the link
+// masses and lengths), velocity terms D_jk sin(phi_j - phi_k) w_k^2, gravity
+// g l_j beta_j cos(phi_j) and generalised forces tau_j - tau_{j+1}; the
+// SPD system is solved by an unrolled Cholesky.  Semi-implicit Euler in
+// (phi, w) equals semi-implicit Euler in the relative joint coordinates.
+#include "mtp_device.cuh"
+
+namespace mtp {
+namespace {
+
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ float dr_scale(const RolloutArgs& a, uint32_t iter, uint32_t unit,
+                                          uint32_t slot) {
+  if (a.dr_mode == MTP_DR_NONE) return 1.f;
+  const uint32_t tag = (a.dr_mode == MTP_DR_SHARED) ? kTagParamModel : kTagParamSample;
+  return fmaf(a.dr_hi - a.dr_lo, unit24(draw(a.key, unit, slot, iter, tag)), a.dr_lo);
+}
+
+// ---------------------------------------------------------------------------
+// k-D point mass (double integrator), control = acceleration x gain.
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ float pm_state_cost(const PointMassModel& pm, const float (&p)[K]) {
+  float dist2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float e = p[k] - pm.target[k];
+    dist2 = fmaf(e, e, dist2);
+  }
+  float pen = 0.f;
+  for (int o = 0; o < pm.n_obs; ++o) {
+    float d2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float e = p[k] - pm.obs_c[o][k];
+      d2 = fmaf(e, e, d2);
+    }
+    const float depth = pm.obs_r[o] - sqrtf(d2);
+    pen += depth > 0.f ? depth : 0.f;
+  }
+  return fmaf(pm.w_target, dist2, pm.w_obs * pen);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
+                                                         const PointMassModel pm) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.rows) return;
+  const int b = a.row0 + r;
+  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
+  const float* Ub = a.U + (size_t)r * a.H * K;
+  const int models = (a.dr_mode == MTP_DR_SHARED) ? a.R : 1;
+  const float dt = a.dt;
+  float total = 0.f;
+  for (int mdl = 0; mdl < models; ++mdl) {
+    const uint32_t unit = (a.dr_mode == MTP_DR_SHARED) ? (uint32_t)mdl : (uint32_t)b;
+    float gain[K], p[K], v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      gain[k] = dr_scale(a, iter, unit, k) * dt;
+      p[k] = a.x0[k];
+      v[k] = a.x0[K + k];
+    }
+    if (a.X) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        a.X[k] = p[k];
+        a.X[K + k] = v[k];
+      }
+    }
+    KahanSum J;
+    for (int t = 0; t < a.H; ++t) {
+      float u[K];
+      float uu = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        u[k] = __ldg(Ub + t * K + k);
+        uu = fmaf(u[k], u[k], uu);
+      }
+      J.add(fmaf(pm.w_ctrl, uu, pm_state_cost<K>(pm, p)), a.kahan);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        v[k] = fmaf(gain[k], u[k], v[k]);
+        p[k] = fmaf(dt, v[k], p[k]);
+      }
+      if (a.X) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          a.X[(size_t)(t + 1) * 2 * K + k] = p[k];
+          a.X[(size_t)(t + 1) * 2 * K + K + k] = v[k];
+        }
+      }
+    }
+    J.add(pm.w_term * pm_state_cost<K>(pm, p), a.kahan);
+    total += J.s;
+  }
+  float c = total / (float)models;
+  if (!isfinite(c)) c = __int_as_float(0x7f800000);
+  a.cost[r] = c;
+}
+
+// ---------------------------------------------------------------------------
+// Planar serial chain under joint torques.
+// ---------------------------------------------------------------------------
+template <int NL>
+struct Tri {
+  static constexpr int size = NL * (NL + 1) / 2;
+  static __device__ __forceinline__ constexpr int at(int i, int j) { return i * (i + 1) / 2 + j; }
+};
+
+template <int NL>
+__device__ __forceinline__ void chain_tip(const float (&len)[NL], const float (&c)[NL],
+                                          const float (&s)[NL], float& x, float& y) {
+  x = 0.f;
+  y = 0.f;
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    x = fmaf(len[j], c[j], x);
+    y = fmaf(len[j], s[j], y);
+  }
+}
+
+template <int NL>
+__global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
+                                                            const ChainModel cm) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.rows) return;
+  const int b = a.row0 + r;
+  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
+  const float* Ub = a.U + (size_t)r * a.H * NL;
+  const int models = (a.dr_mode == MTP_DR_SHARED) ? a.R : 1;
+  const float dt = a.dt;
+  float len[NL];
+#pragma unroll
+  for (int j = 0; j < NL; ++j) len[j] = cm.length[j];
+  float total = 0.f;
+  for (int mdl = 0; mdl < models; ++mdl) {
+    const uint32_t unit = (a.dr_mode == MTP_DR_SHARED) ? (uint32_t)mdl : (uint32_t)b;
+    // Lagrangian constants: beta_j = m_j/2 + sum_{i>j} m_i, lb_j = l_j beta_j,
+    // D_jj = l_j^2 (m_j/3 + sum_{i>j} m_i), G_j = g l_j beta_j.
+    float lb[NL], Dd[NL], G[NL];
+    {
+      float mass[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) mass[j] = cm.mass[j] * dr_scale(a, iter, unit, j);
+      float outer = 0.f;
+#pragma unroll
+      for (int j = NL - 1; j >= 0; --j) {
+        const float beta = fmaf(0.5f, mass[j], outer);
+        lb[j] = len[j] * beta;
+        Dd[j] = len[j] * len[j] * fmaf(mass[j], 1.f / 3.f, outer);
+        G[j] = cm.gravity * lb[j];
+        outer += mass[j];
+      }
+    }
+    float phi[NL], w[NL];
+    {
+      float ph = 0.f, om = 0.f;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        ph += a.x0[j];
+        om += a.x0[NL + j];
+        phi[j] = ph;
+        w[j] = om;
+      }
+    }
+    if (a.X) {
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        a.X[j] = a.x0[j];
+        a.X[NL + j] = a.x0[NL + j];
+      }
+    }
+    KahanSum J;
+    for (int t = 0; t < a.H; ++t) {
+      float c[NL], s[NL], tau[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        sincosf(phi[j], &s[j], &c[j]);
+        tau[j] = __ldg(Ub + t * NL + j);
+      }
+      // stage cost c(x_t, u_t): reach error of the tip and torque penalty
+      {
+        float x, y;
+        chain_tip<NL>(len, c, s, x, y);
+        const float ex = x - cm.target[0], ey = y - cm.target[1];
+        float tt = 0.f;
+#pragma unroll
+        for (int j = 0; j < NL; ++j) tt = fmaf(tau[j], tau[j], tt);
+        J.add(fmaf(cm.w_target, fmaf(ex, ex, ey * ey), cm.w_ctrl * tt), a.kahan);
+      }
+      // mass matrix (lower triangle) and right-hand side
+      float A[Tri<NL>::size], rhs[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        const float q_next = (j + 1 < NL) ? tau[j + 1] : 0.f;
+        rhs[j] = fmaf(-G[j], c[j], tau[j] - q_next);
+        A[Tri<NL>::at(j, j)] = Dd[j];
+      }
+#pragma unroll
+      for (int j = 1; j < NL; ++j) {
+#pragma unroll
+        for (int k = 0; k < j; ++k) {
+          const float Djk = len[k] * lb[j];
+          const float cjk = fmaf(c[j], c[k], s[j] * s[k]);   // cos(phi_j - phi_k)
+          const float sjk = fmaf(s[j], c[k], -c[j] * s[k]);  // sin(phi_j - phi_k)
+          A[Tri<NL>::at(j, k)] = Djk * cjk;
+          const float S = Djk * sjk;
+          rhs[j] = fmaf(-S, w[k] * w[k], rhs[j]);
+          rhs[k] = fmaf(S, w[j] * w[j], rhs[k]);
+        }
+      }
+      // Cholesky A = L L^T in place, then the two triangular solves
+      float inv[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        float d = A[Tri<NL>::at(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d = fmaf(-A[Tri<NL>::at(j, k)], A[Tri<NL>::at(j, k)], d);
+        inv[j] = rsqrtf(d);
+#pragma unroll
+        for (int i = j + 1; i < NL; ++i) {
+          float v = A[Tri<NL>::at(i, j)];
+#pragma unroll
+          for (int k = 0; k < j; ++k) v = fmaf(-A[Tri<NL>::at(i, k)], A[Tri<NL>::at(j, k)], v);
+          A[Tri<NL>::at(i, j)] = v * inv[j];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NL; ++i) {
+        float v = rhs[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) v = fmaf(-A[Tri<NL>::at(i, k)], rhs[k], v);
+        rhs[i] = v * inv[i];
+      }
+#pragma unroll
+      for (int i = NL - 1; i >= 0; --i) {
+        float v = rhs[i];
+#pragma unroll
+        for (int k = i + 1; k < NL; ++k) v = fmaf(-A[Tri<NL>::at(k, i)], rhs[k], v);
+        rhs[i] = v * inv[i];
+      }
+      // semi-implicit Euler in absolute coordinates
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        w[j] = fmaf(dt, rhs[j], w[j]);
+        phi[j] = fmaf(dt, w[j], phi[j]);
+      }
+      if (a.X) {
+        float* xo = a.X + (size_t)(t + 1) * 2 * NL;
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          xo[j] = phi[j] - (j ? phi[j - 1] : 0.f);
+          xo[NL + j] = w[j] - (j ? w[j - 1] : 0.f);
+        }
+      }
+    }
+    {
+      float c[NL], s[NL], x, y;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) sincosf(phi[j], &s[j], &c[j]);
+      chain_tip<NL>(len, c, s, x, y);
+      const float ex = x - cm.target[0], ey = y - cm.target[1];
+      J.add(cm.w_term * cm.w_target * fmaf(ex, ex, ey * ey), a.kahan);
+    }
+    total += J.s;
+  }
+  float cst = total / (float)models;
+  if (!isfinite(cst)) cst = __int_as_float(0x7f800000);
+  a.cost[r] = cst;
+}
+
+template <int K>
+cudaError_t pm_dispatch(const RolloutArgs& a, const PointMassModel& m, int k, cudaStream_t s) {
+  if constexpr (K <= 16) {
+    if (k == K) {
+      const int grid = (a.rows + kThreads - 1) / kThreads;
+      k_rollout_pm<K><<<grid, kThreads, 0, s>>>(a, m);
+      return cudaGetLastError();
+    }
+    return pm_dispatch<K + 1>(a, m, k, s);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <int NL>
+cudaError_t chain_dispatch(const RolloutArgs& a, const ChainModel& m, int links, cudaStream_t s) {
+  if constexpr (NL <= 12) {
+    if (links == NL) {
+      const int grid = (a.rows + kThreads - 1) / kThreads;
+      k_rollout_chain<NL><<<grid, kThreads, 0, s>>>(a, m);
+      return cudaGetLastError();
+    }
+    return chain_dispatch<NL + 1>(a, m, links, s);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_rollout_pointmass(const RolloutArgs& a, const PointMassModel& m,
+                                     cudaStream_t s) {
+  if (a.rows <= 0) return cudaSuccess;
+  return pm_dispatch<1>(a, m, a.n, s);
+}
+
+cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int links,
+                                 cudaStream_t s) {
+  if (a.rows <= 0) return cudaSuccess;
+  return chain_dispatch<1>(a, m, links, s);
+}
+
+}  // namespace mtp

@@ -1,0 +1,407 @@
+"""Thin ctypes binding of libmtp.so (include/mtp.h), same names as the C ABI.
+
+Only argument marshalling lives here: every step of the planner runs in the
+library's CUDA kernels.  Device arrays are torch CUDA tensors (their
+``data_ptr()`` is passed through), streams default to torch's current
+stream.  If libmtp.so has not been built this module raises on first use;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmtp.so")
+
+MAX_CTRL = 32
+MAX_LINKS = 16
+MAX_OBS = 8
+
+MTP_OK = 0
+STATUS = {0: "MTP_OK", 1: "MTP_ERR_INVALID_ARG", 2: "MTP_ERR_OUT_OF_MEMORY", 3: "MTP_ERR_CUDA",
+          4: "MTP_ERR_ADMISSION", 5: "MTP_ERR_TIMEOUT", 6: "MTP_ERR_NOT_READY",
+          7: "MTP_ERR_UNSUPPORTED"}
+DYN = {"pointmass": 0, "chain": 1, "legged": 2}
+INTERP = {"linear": 0, "bspline": 1, "akima": 2}
+TIME_MAPPING = {"valid_span": 0, "paper_literal": 1}
+UPDATE = {"softmax": 0, "plain_cem": 1}
+DR = {"none": 0, "per_sample": 1, "shared": 2}
+FLAG_NO_KAHAN = 0x1
+FLAG_NO_GRAPH = 0x2
+FLAG_BF16_BASIS = 0x4
+
+# every function include/mtp.h declares
+EXPORTS = [
+    "mtp_problem_bytes", "mtp_create", "mtp_destroy", "mtp_last_error", "mtp_get_sizes",
+    "mtp_get_buffers", "mtp_sample_tensor", "mtp_interpolate", "mtp_sample_local",
+    "mtp_generate_candidates", "mtp_rollout_cost", "mtp_rollout_states", "mtp_elite_update",
+    "mtp_plan_step", "mtp_plan_step_host", "mtp_shift", "mtp_get_state", "mtp_set_state",
+    "mtp_set_profiling", "mtp_stage_times",
+]
+
+
+class MtpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MtpProblem(C.Structure):
+    _fields_ = [
+        ("dyn", C.c_int32), ("ctrl_dim", C.c_int32), ("state_dim", C.c_int32),
+        ("horizon", C.c_int32), ("dt", C.c_float),
+        ("u_min", C.c_float * MAX_CTRL), ("u_max", C.c_float * MAX_CTRL),
+        ("M", C.c_int32), ("N", C.c_int32), ("B", C.c_int32), ("E", C.c_int32),
+        ("beta", C.c_double), ("lam", C.c_double), ("alpha", C.c_double),
+        ("sigma_min", C.c_double), ("mu_init", C.c_double), ("sigma_init", C.c_double),
+        ("interp", C.c_int32), ("bspline_degree", C.c_int32), ("time_mapping", C.c_int32),
+        ("update_rule", C.c_int32), ("dr_mode", C.c_int32), ("R", C.c_int32),
+        ("dr_lo", C.c_float), ("dr_hi", C.c_float), ("seed", C.c_uint64),
+        ("target", C.c_float * MAX_CTRL),
+        ("w_target", C.c_float), ("w_obs", C.c_float), ("w_ctrl", C.c_float),
+        ("w_term", C.c_float),
+        ("n_obstacles", C.c_int32),
+        ("obs_center", (C.c_float * MAX_CTRL) * MAX_OBS),
+        ("obs_radius", C.c_float * MAX_OBS),
+        ("n_links", C.c_int32),
+        ("link_mass", C.c_float * MAX_LINKS), ("link_length", C.c_float * MAX_LINKS),
+        ("gravity", C.c_float), ("k_contact", C.c_float), ("c_contact", C.c_float),
+        ("mu_friction", C.c_float), ("v_slip", C.c_float),
+        ("w_height", C.c_float), ("w_pitch", C.c_float), ("w_vel", C.c_float),
+        ("flags", C.c_uint32),
+    ]
+
+
+class MtpSizes(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("B", "P", "L", "E", "H", "n", "d", "M", "N")]
+
+
+class MtpBuffers(C.Structure):
+    _fields_ = [("U", C.c_void_p), ("cost", C.c_void_p), ("elite", C.c_void_p),
+                ("weight", C.c_void_p), ("mu", C.c_void_p), ("sigma", C.c_void_p),
+                ("ustar", C.c_void_p), ("iter", C.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmtp.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(nvcc, sm_103a); there is no CPU fallback")
+    lib = C.CDLL(path)
+    vp, i32, u32 = C.c_void_p, C.c_int32, C.c_uint32
+    sig = {
+        "mtp_problem_bytes": (C.c_size_t, []),
+        "mtp_create": (i32, [C.POINTER(MtpProblem), C.POINTER(vp)]),
+        "mtp_destroy": (i32, [vp]),
+        "mtp_last_error": (C.c_char_p, [vp]),
+        "mtp_get_sizes": (i32, [vp, C.POINTER(MtpSizes)]),
+        "mtp_get_buffers": (i32, [vp, C.POINTER(MtpBuffers)]),
+        "mtp_sample_tensor": (i32, [vp, u32, vp, vp, vp, vp]),
+        "mtp_interpolate": (i32, [vp, vp, i32, vp, vp]),
+        "mtp_sample_local": (i32, [vp, u32, vp, vp]),
+        "mtp_generate_candidates": (i32, [vp, u32, vp, vp]),
+        "mtp_rollout_cost": (i32, [vp, u32, vp, vp, i32, i32, vp, vp]),
+        "mtp_rollout_states": (i32, [vp, u32, vp, vp, i32, vp, vp, vp]),
+        "mtp_elite_update": (i32, [vp, vp, vp, vp, vp, vp]),
+        "mtp_plan_step": (i32, [vp, vp, i32, vp, vp]),
+        "mtp_plan_step_host": (i32, [vp, vp, i32, vp, vp]),
+        "mtp_shift": (i32, [vp, i32, vp]),
+        "mtp_get_state": (i32, [vp, vp, vp, vp]),
+        "mtp_set_state": (i32, [vp, vp, vp, u32]),
+        "mtp_set_profiling": (i32, [vp, i32]),
+        "mtp_stage_times": (i32, [vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if lib.mtp_problem_bytes() != C.sizeof(MtpProblem):
+        raise RuntimeError("mtp_problem layout mismatch between libmtp.so and the binding")
+    _lib = lib
+    return lib
+
+
+# ----------------------------------------------------------------------------
+# marshalling helpers
+# ----------------------------------------------------------------------------
+
+def problem_from_spec(spec: dict) -> MtpProblem:
+    """Fill the C struct from a workload dict (see ``workloads``)."""
+    p = MtpProblem()
+    p.dyn = DYN[spec["dyn"]]
+    p.ctrl_dim = spec["n"]
+    p.state_dim = spec["d"]
+    p.horizon = spec["H"]
+    p.dt = spec["dt"]
+    for i in range(spec["n"]):
+        p.u_min[i] = spec["u_min"][i]
+        p.u_max[i] = spec["u_max"][i]
+    p.M, p.N, p.B, p.E = spec["M"], spec["N"], spec["B"], spec["E"]
+    p.beta = spec["beta"]
+    p.lam = spec["lambda"]
+    p.alpha = spec["alpha"]
+    p.sigma_min = spec["sigma_min"]
+    p.mu_init = spec.get("mu_init", 0.0)
+    p.sigma_init = spec["sigma_init"]
+    p.interp = INTERP[spec["interp"]]
+    p.bspline_degree = spec.get("degree", 2)
+    p.time_mapping = TIME_MAPPING[spec.get("time_mapping", "valid_span")]
+    p.update_rule = UPDATE[spec.get("update_rule", "softmax")]
+    p.dr_mode = DR[spec.get("dr_mode", "none")]
+    p.R = spec.get("R", 1)
+    p.dr_lo = spec.get("dr_lo", 1.0)
+    p.dr_hi = spec.get("dr_hi", 1.0)
+    p.seed = spec["seed"]
+    for i, v in enumerate(spec.get("target", [])):
+        p.target[i] = v
+    p.w_target = spec.get("w_target", 1.0)
+    p.w_obs = spec.get("w_obs", 0.0)
+    p.w_ctrl = spec.get("w_ctrl", 0.0)
+    p.w_term = spec.get("w_term", 1.0)
+    obs_c = spec.get("obs_c", [])
+    p.n_obstacles = len(obs_c)
+    for o, (c, r) in enumerate(zip(obs_c, spec.get("obs_r", []))):
+        for a, v in enumerate(c):
+            p.obs_center[o][a] = v
+        p.obs_radius[o] = r
+    p.n_links = spec.get("n_links", 0)
+    for j, v in enumerate(spec.get("mass", [])):
+        p.link_mass[j] = v
+    for j, v in enumerate(spec.get("length", [])):
+        p.link_length[j] = v
+    p.gravity = spec.get("gravity", 9.81)
+    p.k_contact = spec.get("k_contact", 0.0)
+    p.c_contact = spec.get("c_contact", 0.0)
+    p.mu_friction = spec.get("mu_friction", 0.0)
+    p.v_slip = spec.get("v_slip", 0.01)
+    p.w_height = spec.get("w_height", 0.0)
+    p.w_pitch = spec.get("w_pitch", 0.0)
+    p.w_vel = spec.get("w_vel", 0.0)
+    p.flags = spec.get("flags", 0)
+    return p
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t, dtype=None, numel: int | None = None, name: str = "tensor"):
+    """Device pointer of a contiguous CUDA tensor (or 0 for None)."""
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+def _check(status: int, handle=None):
+    if status != MTP_OK:
+        lib = load_library()
+        msg = lib.mtp_last_error(handle)
+        raise MtpError(status, msg.decode() if msg else "")
+
+
+class DeviceArray:
+    """A handle-owned device buffer exposed through __cuda_array_interface__
+    (wrap it with torch.as_tensor(x, device='cuda') for a zero-copy view)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+class Handle:
+    """An mtp_handle* plus its sizes; destroyed with mtp_destroy (or on GC)."""
+
+    def __init__(self, ptr: int, spec: dict):
+        self.ptr = C.c_void_p(ptr)
+        self.spec = spec
+        s = MtpSizes()
+        _check(load_library().mtp_get_sizes(self.ptr, C.byref(s)), self.ptr)
+        self.sizes = {k: getattr(s, k) for k, _ in MtpSizes._fields_}
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            try:
+                load_library().mtp_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = C.c_void_p(0)
+
+
+# ----------------------------------------------------------------------------
+# the ABI, one wrapper per entry point
+# ----------------------------------------------------------------------------
+
+def mtp_create(spec_or_problem) -> Handle:
+    lib = load_library()
+    prob = spec_or_problem if isinstance(spec_or_problem, MtpProblem) else problem_from_spec(spec_or_problem)
+    out = C.c_void_p()
+    st = lib.mtp_create(C.byref(prob), C.byref(out))
+    if st != MTP_OK:
+        raise MtpError(st, lib.mtp_last_error(None).decode())
+    return Handle(out.value, spec_or_problem if isinstance(spec_or_problem, dict) else {})
+
+
+def mtp_destroy(h: Handle):
+    if h.ptr.value:
+        _check(load_library().mtp_destroy(h.ptr))
+        h.ptr = C.c_void_p(0)
+
+
+def mtp_get_buffers(h: Handle) -> dict:
+    b = MtpBuffers()
+    _check(load_library().mtp_get_buffers(h.ptr, C.byref(b)), h.ptr)
+    s = h.sizes
+    return {
+        "U": DeviceArray(b.U, (s["B"], s["H"], s["n"]), "<f4"),
+        "cost": DeviceArray(b.cost, (s["B"],), "<f4"),
+        "elite": DeviceArray(b.elite, (s["E"],), "<i4"),
+        "weight": DeviceArray(b.weight, (s["E"],), "<f8"),
+        "mu": DeviceArray(b.mu, (s["H"], s["n"]), "<f8"),
+        "sigma": DeviceArray(b.sigma, (s["H"], s["n"]), "<f8"),
+        "ustar": DeviceArray(b.ustar, (s["n"],), "<f4"),
+        "iter": DeviceArray(b.iter, (1,), "<u4"),
+    }
+
+
+def _f32():
+    import torch
+    return torch.float32
+
+
+def _i32():
+    import torch
+    return torch.int32
+
+
+def mtp_sample_tensor(h: Handle, it: int, Z=None, idx=None, Cw=None, stream=None):
+    s = h.sizes
+    _check(load_library().mtp_sample_tensor(
+        h.ptr, it, _dptr(Z, _f32(), s["M"] * s["N"] * s["n"], "Z"),
+        _dptr(idx, _i32(), s["P"] * s["M"], "idx"),
+        _dptr(Cw, _f32(), s["P"] * s["M"] * s["n"], "C"), _stream(stream)), h.ptr)
+
+
+def mtp_interpolate(h: Handle, Cw, U, stream=None):
+    s = h.sizes
+    P = Cw.shape[0]
+    _check(load_library().mtp_interpolate(
+        h.ptr, _dptr(Cw, _f32(), P * s["M"] * s["n"], "C"), P,
+        _dptr(U, _f32(), P * s["H"] * s["n"], "U"), _stream(stream)), h.ptr)
+
+
+def mtp_sample_local(h: Handle, it: int, U, stream=None):
+    s = h.sizes
+    _check(load_library().mtp_sample_local(
+        h.ptr, it, _dptr(U, _f32(), s["B"] * s["H"] * s["n"], "U"), _stream(stream)), h.ptr)
+
+
+def mtp_generate_candidates(h: Handle, it: int, U, stream=None):
+    s = h.sizes
+    _check(load_library().mtp_generate_candidates(
+        h.ptr, it, _dptr(U, _f32(), s["B"] * s["H"] * s["n"], "U"), _stream(stream)), h.ptr)
+
+
+def mtp_rollout_cost(h: Handle, it: int, x0, U, cost, row0: int = 0, rows: int | None = None,
+                     stream=None):
+    s = h.sizes
+    rows = U.shape[0] if rows is None else rows
+    _check(load_library().mtp_rollout_cost(
+        h.ptr, it, _dptr(x0, _f32(), s["d"], "x0"),
+        _dptr(U, _f32(), rows * s["H"] * s["n"], "U"), row0, rows,
+        _dptr(cost, _f32(), rows, "cost"), _stream(stream)), h.ptr)
+
+
+def mtp_rollout_states(h: Handle, it: int, x0, Urow, row: int, X, cost, stream=None):
+    s = h.sizes
+    _check(load_library().mtp_rollout_states(
+        h.ptr, it, _dptr(x0, _f32(), s["d"], "x0"), _dptr(Urow, _f32(), s["H"] * s["n"], "U"),
+        row, _dptr(X, _f32(), (s["H"] + 1) * s["d"], "X"), _dptr(cost, _f32(), 1, "cost"),
+        _stream(stream)), h.ptr)
+
+
+def mtp_elite_update(h: Handle, cost, U, elite=None, ustar=None, stream=None):
+    s = h.sizes
+    _check(load_library().mtp_elite_update(
+        h.ptr, _dptr(cost, _f32(), s["B"], "cost"), _dptr(U, _f32(), s["B"] * s["H"] * s["n"], "U"),
+        _dptr(elite, _i32(), s["E"], "elite"), _dptr(ustar, _f32(), s["n"], "ustar"),
+        _stream(stream)), h.ptr)
+
+
+def mtp_plan_step(h: Handle, x0, iters: int, ustar, stream=None):
+    s = h.sizes
+    _check(load_library().mtp_plan_step(
+        h.ptr, _dptr(x0, _f32(), s["d"], "x0"), iters, _dptr(ustar, _f32(), s["n"], "ustar"),
+        _stream(stream)), h.ptr)
+
+
+def mtp_plan_step_host(h: Handle, x0: np.ndarray, iters: int, ustar: np.ndarray, stream=None):
+    """x0 / ustar are float32 host arrays (numpy, or pinned torch CPU tensors)."""
+    s = h.sizes
+
+    def hptr(a, n, name):
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda or a.dtype != _f32() or not a.is_contiguous() or a.numel() < n:
+                raise ValueError(f"{name}: need a contiguous float32 host tensor of {n}")
+            return a.data_ptr()
+        if a.dtype != np.float32 or not a.flags.c_contiguous or a.size < n:
+            raise ValueError(f"{name}: need a contiguous float32 array of {n}")
+        return a.ctypes.data
+
+    _check(load_library().mtp_plan_step_host(h.ptr, hptr(x0, s["d"], "x0"), iters,
+                                             hptr(ustar, s["n"], "ustar"), _stream(stream)), h.ptr)
+
+
+def mtp_shift(h: Handle, k: int, stream=None):
+    _check(load_library().mtp_shift(h.ptr, k, _stream(stream)), h.ptr)
+
+
+def mtp_get_state(h: Handle):
+    s = h.sizes
+    mu = np.empty((s["H"], s["n"]), np.float64)
+    sg = np.empty((s["H"], s["n"]), np.float64)
+    it = C.c_uint32()
+    _check(load_library().mtp_get_state(h.ptr, mu.ctypes.data, sg.ctypes.data, C.addressof(it)),
+           h.ptr)
+    return mu, sg, int(it.value)
+
+
+def mtp_set_state(h: Handle, mu, sigma, it: int):
+    s = h.sizes
+    mu = np.ascontiguousarray(mu, np.float64).reshape(s["H"], s["n"])
+    sg = np.ascontiguousarray(sigma, np.float64).reshape(s["H"], s["n"])
+    _check(load_library().mtp_set_state(h.ptr, mu.ctypes.data, sg.ctypes.data, it), h.ptr)
+
+
+def mtp_set_profiling(h: Handle, enable: bool):
+    _check(load_library().mtp_set_profiling(h.ptr, 1 if enable else 0), h.ptr)
+
+
+def mtp_stage_times(h: Handle):
+    """(ms per stage [generate, rollout, select, update], iterations)."""
+    ms = (C.c_double * 4)()
+    n = C.c_int32()
+    _check(load_library().mtp_stage_times(h.ptr, C.addressof(ms), C.addressof(n)), h.ptr)
+    return [float(v) for v in ms], int(n.value)

@@ -1,0 +1,452 @@
+"""GPU parity: every step of one planner iteration through the C ABI against
+the FP64 oracle on the same seeded inputs.
+
+Tolerances: integers (path indices, elite indices) bit-exact; FP32 controls
+within a few FP32 ulps of the box range; rollout costs within 1e-4 relative
+(the stated FP32 target); elite sets exact wherever the cost gap at the E-th
+boundary exceeds 2e-4 relative; FP64 moments of the update within 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2505_01059_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+COST_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def mtp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_01059_gb300 import _build, mtp as m
+    _build.build_library()
+    m.load_library()
+    torch.cuda.set_device(0)
+    return m
+
+
+DEV = "cuda:0"
+
+
+def _t(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def _np(x, dtype=np.float64):
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(x, device=DEV)
+    return x.detach().cpu().numpy().astype(dtype)
+
+
+def _range(spec):
+    return np.array(spec["u_max"]) - np.array(spec["u_min"])
+
+
+def _cost_close(gpu, ref, rtol=COST_RTOL):
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    both_inf = np.isinf(gpu) & np.isinf(ref)
+    err = np.abs(gpu - ref) / np.maximum(np.abs(ref), 1.0)
+    err[both_inf] = 0.0
+    return float(err.max()) if err.size else 0.0
+
+
+# ----------------------------------------------------------------------------
+# Def. 1 / Alg. 1: graph, path indices, waypoints
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("spec", [
+    W.pointmass(),                                   # 2-D point mass, 4 x 8 graph
+    W.chain(),                                       # 7-link arm, 8 x 32 graph, 4096 candidates
+    W.pointmass(k=5, M=7, N=13, B=333, beta=0.37),   # ragged sizes
+    W.chain(links=3, M=16, N=64, B=8192, beta=0.9),
+])
+def test_sample_tensor(mtp, spec):
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    for it in (0, 5):
+        Z = torch.empty(s["M"], s["N"], s["n"], device=DEV)
+        I = torch.empty(s["P"], s["M"], dtype=torch.int32, device=DEV)
+        Cw = torch.empty(s["P"], s["M"], s["n"], device=DEV)
+        mtp.mtp_sample_tensor(h, it, Z, I, Cw)
+        Zr = orc.graph_Z(spec, it)
+        Ir = orc.path_indices(spec, it)
+        Cr = orc.gather_C(spec, Zr, Ir)
+        assert np.array_equal(_np(I, np.int32), Ir)  # bit-exact integers
+        tol = 2.0 ** -23 * np.abs(np.array(spec["u_max"]) - np.array(spec["u_min"])).max() * 2
+        assert np.abs(_np(Z) - Zr).max() <= tol
+        assert np.abs(_np(Cw) - Cr).max() <= tol
+    mtp.mtp_destroy(h)
+
+
+# ----------------------------------------------------------------------------
+# Interpolation (Def. 2, Def. 3, straight lines)
+# ----------------------------------------------------------------------------
+
+INTERP_CASES = [
+    ("bspline", 0, "valid_span", 4, 64, 2, 256),
+    ("bspline", 1, "valid_span", 6, 33, 3, 37),
+    ("bspline", 2, "valid_span", 16, 256, 15, 67),
+    ("bspline", 3, "valid_span", 4, 64, 2, 256),
+    ("bspline", 3, "paper_literal", 8, 50, 4, 19),
+    ("bspline", 5, "valid_span", 9, 17, 1, 5),
+    ("bspline", 2, "valid_span", 3, 1, 2, 3),
+    ("akima", 0, "valid_span", 8, 128, 7, 2048),
+    ("akima", 0, "valid_span", 2, 9, 2, 7),
+    ("akima", 0, "valid_span", 3, 10, 3, 7),
+    ("akima", 0, "valid_span", 4, 33, 5, 11),
+    ("akima", 0, "paper_literal", 6, 40, 2, 13),
+    ("akima", 0, "valid_span", 16, 256, 12, 31),
+    ("linear", 0, "valid_span", 5, 41, 3, 29),
+    ("linear", 0, "paper_literal", 4, 16, 2, 9),
+]
+
+
+@pytest.mark.parametrize("interp,p,mapping,M,H,n,P", INTERP_CASES)
+def test_interpolate(mtp, interp, p, mapping, M, H, n, P):
+    spec = W.pointmass(k=n, M=M, N=8, H=H, B=P + 1, beta=1.0, interp=interp, degree=p,
+                       time_mapping=mapping, u_min=[-2.0] * n, u_max=[3.0] * n)
+    h = mtp.mtp_create(spec)
+    rng = np.random.default_rng(M * 1000 + H)
+    C32 = rng.uniform(-2.0, 3.0, size=(P, M, n)).astype(np.float32)
+    U = torch.empty(P, H, n, device=DEV)
+    mtp.mtp_interpolate(h, _t(C32), U)
+    ref = np.clip(orc.interpolate(spec, C32.astype(np.float64)), -2.0, 3.0)
+    err = np.abs(_np(U) - ref).max()
+    tol = (1e-5 if interp == "akima" else 2e-6) * 5.0
+    assert err <= tol, err
+    mtp.mtp_destroy(h)
+
+
+# ----------------------------------------------------------------------------
+# Local Gaussian samples and the mean row
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("spec", [W.pointmass(), W.chain(), W.pointmass(k=3, H=7, B=50, beta=0.0)])
+def test_sample_local(mtp, spec):
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    rng = np.random.default_rng(1)
+    lo, hi = np.array(spec["u_min"]), np.array(spec["u_max"])
+    mu = rng.uniform(lo, hi, size=(s["H"], s["n"])) * 0.5
+    sigma = rng.uniform(0.05, 0.5, size=(s["H"], s["n"])) * (hi - lo)
+    mtp.mtp_set_state(h, mu, sigma, 0)
+    U = torch.zeros(s["B"], s["H"], s["n"], device=DEV)
+    it = 3
+    mtp.mtp_sample_local(h, it, U)
+    Ug = _np(U)
+    UL = orc.local_samples(spec, it, mu, sigma)
+    ref = np.clip(UL, lo, hi)
+    eps = (UL - mu) / sigma
+    tol = 2e-6 * (np.abs(mu) + sigma * (1 + np.abs(eps))) + 1e-7
+    assert np.all(np.abs(Ug[:s["L"]] - ref) <= tol)
+    assert np.allclose(Ug[-1], np.clip(mu, lo, hi), rtol=1e-7, atol=1e-7)
+    mtp.mtp_destroy(h)
+
+
+# ----------------------------------------------------------------------------
+# Fused candidate generation (all rows of U)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("spec", [W.pointmass(), W.chain(),
+                                  W.chain(links=4, B=1000, beta=0.3, interp="bspline", M=6)])
+def test_generate_candidates(mtp, spec):
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    mu, sigma = W.initial_distribution(spec)
+    U = torch.empty(s["B"], s["H"], s["n"], device=DEV)
+    it = 2
+    mtp.mtp_generate_candidates(h, it, U)
+    Ug = _np(U)
+    P, L = s["P"], s["L"]
+    Z = orc.graph_Z(spec, it)
+    UG = orc.interpolate(spec, orc.gather_C(spec, Z, orc.path_indices(spec, it)))
+    ref = orc.stack_clamp(spec, orc.local_samples(spec, it, mu, sigma), UG, mu)
+    rng_ = _range(spec).max()
+    assert np.abs(Ug[L:L + P] - ref[L:L + P]).max() <= 2e-5 * rng_
+    assert np.abs(Ug[:L] - ref[:L]).max() <= 1e-5 * rng_
+    assert np.array_equal(Ug[-1], ref[-1])
+    mtp.mtp_destroy(h)
+
+
+# ----------------------------------------------------------------------------
+# Rollout + cost (Eq. 2)
+# ----------------------------------------------------------------------------
+
+def _rand_U(spec, B, seed):
+    rng = np.random.default_rng(seed)
+    lo, hi = np.array(spec["u_min"]), np.array(spec["u_max"])
+    return rng.uniform(lo, hi, size=(B, spec["H"], spec["n"])).astype(np.float32)
+
+
+@pytest.mark.parametrize("spec", [
+    W.pointmass(),
+    W.pointmass(k=12, n_obstacles=8, H=50, B=300),
+    W.pointmass(dr_mode="per_sample", dr_lo=0.7, dr_hi=1.3, B=200),
+    W.pointmass(dr_mode="shared", R=4, dr_lo=0.7, dr_hi=1.3, B=100, H=20),
+    W.pointmass(H=1, B=17, n_obstacles=0),
+    W.chain(B=512),
+    W.chain(links=1, B=64, H=200),
+    W.chain(links=9, B=256, H=64),
+    W.chain(links=3, B=64, dr_mode="shared", R=3),
+    W.chain(links=5, B=100, mass_dr=0.0, flags=1),  # plain FP32 sums
+])
+def test_rollout_cost(mtp, spec):
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    U32 = _rand_U(spec, s["B"], 11)
+    x0 = np.array(spec["x0"], np.float32)
+    if spec["dyn"] == "chain":
+        x0 = np.random.default_rng(2).uniform(-0.3, 0.3, size=s["d"]).astype(np.float32)
+    cost = torch.empty(s["B"], device=DEV)
+    it = 7
+    mtp.mtp_rollout_cost(h, it, _t(x0), _t(U32), cost)
+    ref = orc.rollout_costs(spec, it, x0.astype(np.float64), U32.astype(np.float64))
+    assert _cost_close(_np(cost), ref) <= COST_RTOL
+    # a sub-range gives the same costs bit for bit (randomisation keyed by index)
+    sub = torch.empty(5, device=DEV)
+    r0 = s["B"] // 3
+    mtp.mtp_rollout_cost(h, it, _t(x0), _t(U32[r0:r0 + 5]), sub, row0=r0, rows=5)
+    assert torch.equal(sub, cost[r0:r0 + 5])
+    mtp.mtp_destroy(h)
+
+
+def test_rollout_cost_full_arm_workload(mtp):
+    """The 7-link workload at full size: 4096 candidates x 128 steps."""
+    spec = W.chain()
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    mu, sigma = W.initial_distribution(spec)
+    U = torch.empty(s["B"], s["H"], s["n"], device=DEV)
+    mtp.mtp_generate_candidates(h, 0, U)
+    cost = torch.empty(s["B"], device=DEV)
+    x0 = np.array(spec["x0"], np.float32)
+    mtp.mtp_rollout_cost(h, 0, _t(x0), U, cost)
+    ref = orc.rollout_costs(spec, 0, x0.astype(np.float64), _np(U))
+    assert _cost_close(_np(cost), ref) <= COST_RTOL
+    mtp.mtp_destroy(h)
+
+
+def test_pointmass_states_closed_form(mtp):
+    k, H, dt = 3, 40, 0.02
+    spec = W.pointmass(k=k, H=H, dt=dt, n_obstacles=0, u_min=[-5] * k, u_max=[5] * k, B=4)
+    h = mtp.mtp_create(spec)
+    rng = np.random.default_rng(0)
+    U = rng.uniform(-1, 1, size=(H, k)).astype(np.float32)
+    x0 = rng.normal(size=2 * k).astype(np.float32)
+    X = torch.empty(H + 1, 2 * k, device=DEV)
+    c = torch.empty(1, device=DEV)
+    mtp.mtp_rollout_states(h, 0, _t(x0), _t(U), 0, X, c)
+    Xr, Jr = orc.rollout_states(spec, 0, x0.astype(np.float64), U.astype(np.float64), 0)
+    assert np.abs(_np(X) - Xr).max() <= 1e-5 * max(1.0, np.abs(Xr).max())
+    assert _cost_close(_np(c), [Jr]) <= 1e-5
+    mtp.mtp_destroy(h)
+
+
+@pytest.mark.parametrize("links", [1, 2, 7, 12])
+def test_chain_states(mtp, links):
+    spec = W.chain(links=links, H=64, B=4, mass_dr=0.2)
+    h = mtp.mtp_create(spec)
+    rng = np.random.default_rng(links)
+    U = rng.uniform(-2, 2, size=(64, links)).astype(np.float32)
+    x0 = np.concatenate([rng.uniform(-0.5, 0.5, links), rng.uniform(-1, 1, links)]).astype(np.float32)
+    X = torch.empty(65, 2 * links, device=DEV)
+    c = torch.empty(1, device=DEV)
+    mtp.mtp_rollout_states(h, 3, _t(x0), _t(U), 2, X, c)
+    Xr, Jr = orc.rollout_states(spec, 3, x0.astype(np.float64), U.astype(np.float64), 2)
+    assert np.abs(_np(X) - Xr).max() <= 1e-3 * max(1.0, np.abs(Xr).max())
+    assert _cost_close(_np(c), [Jr]) <= COST_RTOL
+    mtp.mtp_destroy(h)
+
+
+# ----------------------------------------------------------------------------
+# Top-E and the update
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("B,E,kind", [
+    (1, 1, "rand"), (2, 2, "ties"), (33, 5, "ties"), (512, 32, "rand"), (1000, 1000, "ties"),
+    (4096, 64, "rand"), (4096, 64, "ties"), (4096, 4096, "rand"), (16384, 64, "special"),
+    (16384, 16384, "ties"), (777, 300, "special"),
+])
+def test_top_e(mtp, B, E, kind):
+    spec = W.pointmass(k=1, H=2, B=B, E=E, beta=0.0)
+    h = mtp.mtp_create(spec)
+    rng = np.random.default_rng(B + E)
+    if kind == "rand":
+        c = rng.normal(size=B).astype(np.float32)
+    elif kind == "ties":
+        c = rng.integers(0, 7, size=B).astype(np.float32)
+    else:
+        c = rng.normal(size=B).astype(np.float32)
+        c[rng.integers(0, B, 20)] = np.nan
+        c[rng.integers(0, B, 20)] = np.inf
+        c[rng.integers(0, B, 20)] = -0.0
+        c[rng.integers(0, B, 20)] = 0.0
+        c[rng.integers(0, B, 20)] = -np.inf
+    U = torch.zeros(B, 2, 1, device=DEV)
+    elite = torch.empty(E, dtype=torch.int32, device=DEV)
+    mtp.mtp_elite_update(h, _t(c), U, elite)
+    ref = orc.top_e(c.astype(np.float64), E)
+    assert np.array_equal(_np(elite, np.int32), ref)
+    mtp.mtp_destroy(h)
+
+
+@pytest.mark.parametrize("rule,alpha,E,lam", [("softmax", 0.0, 32, 0.1), ("softmax", 0.3, 64, 5.0),
+                                              ("plain_cem", 0.2, 16, 1.0), ("softmax", 0.0, 1, 1.0)])
+def test_elite_update(mtp, rule, alpha, E, lam):
+    spec = W.chain(links=3, B=700, E=E, H=20, alpha=alpha, update_rule=rule)
+    spec["lambda"] = lam
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    rng = np.random.default_rng(E)
+    U32 = _rand_U(spec, s["B"], 5)
+    c32 = rng.uniform(10, 20, size=s["B"]).astype(np.float32)
+    mu = rng.uniform(-1, 1, size=(s["H"], s["n"]))
+    sigma = rng.uniform(0.2, 1, size=(s["H"], s["n"]))
+    mtp.mtp_set_state(h, mu, sigma, 0)
+    elite = torch.empty(E, dtype=torch.int32, device=DEV)
+    ustar = torch.empty(s["n"], device=DEV)
+    mtp.mtp_elite_update(h, _t(c32), _t(U32), elite, ustar)
+    mu_g, sg_g, _ = mtp.mtp_get_state(h)
+    el_r = orc.top_e(c32.astype(np.float64), E)
+    mu_r, sg_r, us_r = orc.elite_update(spec, U32.astype(np.float64), c32.astype(np.float64), el_r,
+                                        mu, sigma)
+    assert np.array_equal(_np(elite, np.int32), el_r)
+    np.testing.assert_allclose(mu_g, mu_r, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(sg_g, sg_r, rtol=1e-9, atol=1e-12)
+    assert np.array_equal(_np(ustar), us_r)
+    mtp.mtp_destroy(h)
+
+
+# ----------------------------------------------------------------------------
+# Whole iterations (Alg. 2), teacher-forced against the oracle
+# ----------------------------------------------------------------------------
+
+def _boundary_ok(cost, E):
+    srt = np.sort(np.where(np.isnan(cost), np.inf, cost))
+    if E >= len(srt):
+        return True
+    a, b = srt[E - 1], srt[E]
+    return (b - a) > 2 * COST_RTOL * max(abs(a), 1.0)
+
+
+@pytest.mark.parametrize("spec,iters", [(W.pointmass(), 10), (W.chain(), 3),
+                                        (W.chain(links=4, B=1024, interp="bspline", M=6,
+                                                 beta=0.25), 3)])
+def test_plan_step_teacher_forced(mtp, spec, iters):
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    x0 = np.array(spec["x0"], np.float64)
+    x0_t = _t(x0)
+    ustar = torch.empty(s["n"], device=DEV)
+    buf = mtp.mtp_get_buffers(h)
+    checked = 0
+    for k in range(iters):
+        mu, sigma, it = mtp.mtp_get_state(h)
+        assert it == k
+        mtp.mtp_plan_step(h, x0_t, 1, ustar)
+        torch.cuda.synchronize()
+        Ug = _np(torch.as_tensor(buf["U"], device=DEV))
+        cg = _np(torch.as_tensor(buf["cost"], device=DEV))
+        eg = _np(torch.as_tensor(buf["elite"], device=DEV), np.int32)
+        mu_g, sg_g, _ = mtp.mtp_get_state(h)
+        ref = orc.plan_iteration(spec, k, x0, mu, sigma)
+        # candidates
+        assert np.abs(Ug - ref["U"]).max() <= 2e-5 * _range(spec).max()
+        # costs of the GPU's own candidates, rolled out by the oracle
+        c_ref = orc.rollout_costs(spec, k, x0, Ug)
+        assert _cost_close(cg, c_ref) <= COST_RTOL
+        # elites: the selection on the GPU's costs is exact; against the
+        # oracle's own costs where the E-th gap is clear
+        assert np.array_equal(eg, orc.top_e(cg.astype(np.float64), s["E"]))
+        if _boundary_ok(ref["cost"], s["E"]):
+            assert set(eg.tolist()) == set(ref["elite"].tolist())
+            checked += 1
+        # the update from the GPU's candidates and costs
+        mu_r, sg_r, us_r = orc.elite_update(spec, Ug, cg.astype(np.float64), eg, mu, sigma)
+        np.testing.assert_allclose(mu_g, mu_r, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(sg_g, sg_r, rtol=1e-9, atol=1e-12)
+        assert np.array_equal(_np(ustar), us_r)
+    assert checked >= 1
+    mtp.mtp_destroy(h)
+
+
+def test_graph_replay_equals_eager(mtp):
+    spec = W.chain(links=5, B=2048, H=64)
+    outs = []
+    for flags in (0, 2):
+        h = mtp.mtp_create(dict(spec, flags=flags))
+        x0 = _t(np.array(spec["x0"]))
+        u = torch.empty(h.sizes["n"], device=DEV)
+        mtp.mtp_plan_step(h, x0, 4, u)
+        mtp.mtp_plan_step(h, x0, 1, u)
+        mu, sg, it = mtp.mtp_get_state(h)
+        outs.append((mu, sg, it, _np(u)))
+        mtp.mtp_destroy(h)
+    assert outs[0][2] == outs[1][2] == 5
+    for a, b in zip(outs[0][:2] + (outs[0][3],), outs[1][:2] + (outs[1][3],)):
+        assert np.array_equal(a, b)
+
+
+def test_plan_step_host_and_resume(mtp):
+    spec = W.pointmass(B=1024)
+    h1 = mtp.mtp_create(spec)
+    x0 = np.array(spec["x0"], np.float32)
+    u_dev = torch.empty(2, device=DEV)
+    mtp.mtp_plan_step(h1, _t(x0), 3, u_dev)
+    mu, sg, it = mtp.mtp_get_state(h1)
+    u_host = np.empty(2, np.float32)
+    mtp.mtp_plan_step_host(h1, x0, 2, u_host)
+    mu_a, sg_a, it_a = mtp.mtp_get_state(h1)
+    # resume from the checkpoint on a fresh handle: bit-identical continuation
+    h2 = mtp.mtp_create(spec)
+    mtp.mtp_set_state(h2, mu, sg, it)
+    mtp.mtp_plan_step(h2, _t(x0), 2, u_dev)
+    mu_b, sg_b, it_b = mtp.mtp_get_state(h2)
+    assert it_a == it_b == 5
+    assert np.array_equal(mu_a, mu_b) and np.array_equal(sg_a, sg_b)
+    assert np.array_equal(u_host, _np(u_dev, np.float32))
+    mtp.mtp_destroy(h1)
+    mtp.mtp_destroy(h2)
+
+
+def test_shift(mtp):
+    spec = W.pointmass(H=9, B=16)
+    h = mtp.mtp_create(spec)
+    rng = np.random.default_rng(0)
+    mu = rng.normal(size=(9, 2))
+    sg = rng.uniform(0.1, 1, size=(9, 2))
+    mtp.mtp_set_state(h, mu, sg, 4)
+    mtp.mtp_shift(h, 3)
+    mu_g, sg_g, _ = mtp.mtp_get_state(h)
+    mu_r, sg_r = orc.shift(mu, sg, 3)
+    assert np.array_equal(mu_g, mu_r) and np.array_equal(sg_g, sg_r)
+    mtp.mtp_destroy(h)
+
+
+@pytest.mark.parametrize("bad", [dict(E=0), dict(E=10_000), dict(beta=1.5), dict(alpha=1.0),
+                                 dict(M=1), dict(sigma_min=0.0), dict(interp="bspline", degree=9),
+                                 dict(u_min=[1.0, 1.0], u_max=[0.0, 2.0]), dict(dt=0.0)])
+def test_invalid_problems_rejected(mtp, bad):
+    spec = dict(W.pointmass(B=512), **bad)
+    spec["lambda"] = 0.1
+    with pytest.raises(mtp.MtpError) as ei:
+        mtp.mtp_create(spec)
+    assert ei.value.status == 1
+
+
+def test_invalid_calls_rejected(mtp):
+    spec = W.pointmass(B=64)
+    h = mtp.mtp_create(spec)
+    cost = torch.empty(64, device=DEV)
+    U = torch.empty(64, 64, 2, device=DEV)
+    x0 = torch.zeros(4, device=DEV)
+    with pytest.raises(mtp.MtpError):
+        mtp.mtp_rollout_cost(h, 0, x0, U, cost, row0=10, rows=60)
+    with pytest.raises(ValueError):
+        mtp.mtp_rollout_cost(h, 0, x0.cpu(), U, cost)
+    mtp.mtp_destroy(h)
