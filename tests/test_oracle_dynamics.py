@@ -169,7 +169,7 @@ def test_legged_rests_on_ground(orc):
 
 
 def test_dr_per_sample_changes_cost(orc):
-    spec = W.chain(links=3, H=20, B=4, mass_dr=0.2)
+    spec = W.chain(links=3, H=20, B=4, E=2, mass_dr=0.2)
     U = np.full((2, 20, 3), 2.0)
     x0 = np.zeros(6)
     c = orc.rollout_costs(spec, 0, x0, U, row0=0)
@@ -180,7 +180,7 @@ def test_dr_per_sample_changes_cost(orc):
 
 
 def test_dr_shared_models_average(orc):
-    spec = W.chain(links=3, H=20, B=4, mass_dr=0.2, dr_mode="shared", R=3)
+    spec = W.chain(links=3, H=20, B=4, E=2, mass_dr=0.2, dr_mode="shared", R=3)
     U = np.full((1, 20, 3), 1.5)
     x0 = np.zeros(6)
     c = orc.rollout_costs(spec, 0, x0, U, row0=0)[0]

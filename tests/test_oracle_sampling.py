@@ -110,7 +110,7 @@ def test_gaussian_local_samples(orc):
 
 
 def test_gaussian_affine_map_exact(orc):
-    spec = W.pointmass(k=2, H=8, B=11, beta=0.0)
+    spec = W.pointmass(k=2, H=8, B=11, E=4, beta=0.0)
     rng = np.random.default_rng(0)
     mu = rng.normal(size=(8, 2))
     sigma = rng.uniform(0.1, 2.0, size=(8, 2))
@@ -124,7 +124,7 @@ def test_gaussian_affine_map_exact(orc):
 
 def test_stack_layout_and_clamp(orc):
     # Alg. 2 stacking order: local rows, graph rows, then the nominal mu.
-    spec = W.pointmass(k=2, H=5, B=10, beta=0.5)
+    spec = W.pointmass(k=2, H=5, B=10, E=4, beta=0.5)
     pr = orc.make_problem(spec)
     P, L = pr.P, 10 - pr.P - 1
     assert (P, L) == (5, 4)
