@@ -94,15 +94,21 @@ int32_t num_graph_samples(double beta, int32_t B) {
 }
 
 // Cardinal B-spline of degree p on the integer knots 0..p+1 by the truncated
-// power form N_p(y) = 1/p! sum_k (-1)^k C(p+1, k) (y - k)_+^p.  `left` takes
-// the left limit at a knot (the closed right end of the valid span).
+// power form N_p(y) = 1/p! sum_k (-1)^k C(p+1, k) (y - k)_+^p, evaluated only
+// inside its support and on the nearer half (N_p(y) = N_p(p+1-y)) to keep the
+// alternating sum short.  The indicator of degree 0 is half-open; `left`
+// takes the left limit (the closed right end of the valid span).
 double cardinal_bspline(int p, double y, bool left) {
+  const double end = (double)(p + 1);
+  if (y < 0.0 || y > end) return 0.0;
+  if (y == end) return (left && p == 0) ? 1.0 : 0.0;
+  if (y == 0.0) return (!left && p == 0) ? 1.0 : 0.0;
+  if (p == 0) return 1.0;  // interior of [0, 1)
+  if (y > 0.5 * end) y = end - y;  // continuous for p >= 1: no knot-side question
   double acc = 0.0, binom = 1.0, fact = 1.0;
   for (int k = 2; k <= p; ++k) fact *= k;
-  for (int k = 0; k <= p + 1; ++k) {
-    const double z = y - k;
-    const bool on = left ? (z > 0.0) : (z >= 0.0);
-    if (on) acc += ((k & 1) ? -binom : binom) * (p == 0 ? 1.0 : std::pow(z, p));
+  for (int k = 0; k <= p + 1 && y - k > 0.0; ++k) {
+    acc += ((k & 1) ? -binom : binom) * std::pow(y - k, p);
     binom = binom * (p + 1 - k) / (k + 1);
   }
   return acc / fact;

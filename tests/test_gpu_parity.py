@@ -108,7 +108,7 @@ INTERP_CASES = [
 
 @pytest.mark.parametrize("interp,p,mapping,M,H,n,P", INTERP_CASES)
 def test_interpolate(mtp, interp, p, mapping, M, H, n, P):
-    spec = W.pointmass(k=n, M=M, N=8, H=H, B=P + 1, beta=1.0, interp=interp, degree=p,
+    spec = W.pointmass(k=n, M=M, N=8, H=H, B=P + 1, E=1, beta=1.0, interp=interp, degree=p,
                        time_mapping=mapping, u_min=[-2.0] * n, u_max=[3.0] * n)
     h = mtp.mtp_create(spec)
     rng = np.random.default_rng(M * 1000 + H)
@@ -188,7 +188,7 @@ def _rand_U(spec, B, seed):
     W.pointmass(k=12, n_obstacles=8, H=50, B=300),
     W.pointmass(dr_mode="per_sample", dr_lo=0.7, dr_hi=1.3, B=200),
     W.pointmass(dr_mode="shared", R=4, dr_lo=0.7, dr_hi=1.3, B=100, H=20),
-    W.pointmass(H=1, B=17, n_obstacles=0),
+    W.pointmass(H=1, B=17, E=8, n_obstacles=0),
     W.chain(B=512),
     W.chain(links=1, B=64, H=200),
     W.chain(links=9, B=256, H=64),
@@ -233,7 +233,7 @@ def test_rollout_cost_full_arm_workload(mtp):
 
 def test_pointmass_states_closed_form(mtp):
     k, H, dt = 3, 40, 0.02
-    spec = W.pointmass(k=k, H=H, dt=dt, n_obstacles=0, u_min=[-5] * k, u_max=[5] * k, B=4)
+    spec = W.pointmass(k=k, H=H, dt=dt, n_obstacles=0, u_min=[-5] * k, u_max=[5] * k, B=4, E=2)
     h = mtp.mtp_create(spec)
     rng = np.random.default_rng(0)
     U = rng.uniform(-1, 1, size=(H, k)).astype(np.float32)
@@ -249,7 +249,7 @@ def test_pointmass_states_closed_form(mtp):
 
 @pytest.mark.parametrize("links", [1, 2, 7, 12])
 def test_chain_states(mtp, links):
-    spec = W.chain(links=links, H=64, B=4, mass_dr=0.2)
+    spec = W.chain(links=links, H=64, B=4, E=2, mass_dr=0.2)
     h = mtp.mtp_create(spec)
     rng = np.random.default_rng(links)
     U = rng.uniform(-2, 2, size=(64, links)).astype(np.float32)
@@ -415,7 +415,7 @@ def test_plan_step_host_and_resume(mtp):
 
 
 def test_shift(mtp):
-    spec = W.pointmass(H=9, B=16)
+    spec = W.pointmass(H=9, B=16, E=4)
     h = mtp.mtp_create(spec)
     rng = np.random.default_rng(0)
     mu = rng.normal(size=(9, 2))
