@@ -48,9 +48,15 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    for (int b = tid; b < B; b += blockDim.x) {
-      const uint32_t k = keys[b];
-      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+    // warp-aggregated histogram: costs of one batch share their high bytes,
+    // so lanes with equal digits add once per warp instead of contending
+    for (int base = 0; base < B; base += blockDim.x) {
+      const int b = base + tid;
+      const uint32_t k = b < B ? keys[b] : 0u;
+      const bool take = b < B && (k & mask) == prefix;
+      const uint32_t digit = take ? ((k >> shift) & 255u) : 256u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+      if (take && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (uint32_t)__popc(peers));
     }
     __syncthreads();
     if (wid == 0) {
@@ -127,23 +133,31 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   for (int i = E + tid; i < Ep; i += blockDim.x) sel[i] = ~0ull;
   __syncthreads();
 
-  // bitonic sort of the E selected (key, index) pairs, ascending
-  for (int k = 2; k <= Ep; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < Ep; i += blockDim.x) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long x = sel[i], y = sel[ixj];
-          const bool up = (i & k) == 0;
-          if ((x > y) == up) {
-            sel[i] = y;
-            sel[ixj] = x;
+  // bitonic sort of the E selected (key, index) pairs, ascending: one warp
+  // for small E (no block barriers), the whole block otherwise
+  const bool one_warp = Ep <= 256;
+  if (!one_warp || wid == 0) {
+    const int stride = one_warp ? 32 : (int)blockDim.x;
+    const int me = one_warp ? lane : tid;
+    for (int k = 2; k <= Ep; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = me; i < Ep; i += stride) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long x = sel[i], y = sel[ixj];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              sel[i] = y;
+              sel[ixj] = x;
+            }
           }
         }
+        if (one_warp) __syncwarp();
+        else __syncthreads();
       }
-      __syncthreads();
     }
   }
+  __syncthreads();
 
   // softmax weights over the elites (FP64), shifted by the best cost
   const double best = (double)a.cost[(int)(sel[0] & 0xffffffffu)];
@@ -187,22 +201,41 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) k_update(const UpdateArgs a) {
+__global__ void __launch_bounds__(128) k_update(const UpdateArgs a) {
+  constexpr int kHeld = 8;  // elites per lane kept in registers between the passes
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int Hn = a.H * a.n;
   const bool cem = a.update_rule == MTP_UPDATE_PLAIN_CEM;
   for (int e = gw; e < Hn; e += warps) {
+    double held[kHeld];
     double m1 = 0.0;
-    for (int k = lane; k < a.E; k += 32) {
+#pragma unroll
+    for (int q = 0; q < kHeld; ++q) {
+      const int k = lane + 32 * q;
+      held[q] = 0.0;
+      if (k < a.E) {
+        held[q] = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e);
+        m1 += cem ? held[q] : a.weight[k] * held[q];
+      }
+    }
+    for (int k = lane + 32 * kHeld; k < a.E; k += 32) {
       const double u = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e);
       m1 += cem ? u : a.weight[k] * u;
     }
     m1 = warp_sum(m1);
     if (cem) m1 /= (double)a.E;
     double v = 0.0;
-    for (int k = lane; k < a.E; k += 32) {
+#pragma unroll
+    for (int q = 0; q < kHeld; ++q) {
+      const int k = lane + 32 * q;
+      if (k < a.E) {
+        const double dlt = held[q] - m1;
+        v += cem ? dlt * dlt : a.weight[k] * dlt * dlt;
+      }
+    }
+    for (int k = lane + 32 * kHeld; k < a.E; k += 32) {
       const double dlt = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - m1;
       v += cem ? dlt * dlt : a.weight[k] * dlt * dlt;
     }
@@ -254,10 +287,10 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
 
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   const int Hn = a.H * a.n;
-  int blocks = (Hn + 7) / 8;  // 8 warps per block, one warp per element
-  if (blocks > 1216) blocks = 1216;
+  int blocks = (Hn + 3) / 4;  // 4 warps per block, one warp per element
+  if (blocks > 2432) blocks = 2432;
   if (blocks < 1) blocks = 1;
-  k_update<<<blocks, 256, 0, s>>>(a);
+  k_update<<<blocks, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -367,9 +367,12 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   dm.N = p.N;
   h->key.k0 = (uint32_t)(p.seed & 0xffffffffu);
   h->key.k1 = (uint32_t)(p.seed >> 32);
-  // graph paths per block: ~2K output elements per block within shared memory
+  // graph paths per block: ~4K output elements per block, and at least 16
+  // paths for Akima so its per-(path, dimension) coefficient pass is wide;
+  // shrunk until the block's shared memory fits
   const long long Hn = (long long)dm.H * dm.n;
-  int spb = (int)((2048 + Hn - 1) / Hn);
+  int spb = (int)((4096 + Hn - 1) / Hn);
+  if (p.interp == MTP_INTERP_AKIMA && spb < 16) spb = 16;
   if (spb < 1) spb = 1;
   if (spb > 32) spb = 32;
   for (;;) {

@@ -20,11 +20,45 @@ namespace {
 
 constexpr int kThreads = 128;
 
-__device__ __forceinline__ float dr_scale(const RolloutArgs& a, uint32_t iter, uint32_t unit,
-                                          uint32_t slot) {
-  if (a.dr_mode == MTP_DR_NONE) return 1.f;
+
+// Model scales of slots 0..S-1 for one model unit, four slots per generator
+// call (the same words draw() returns one at a time).
+template <int S>
+__device__ __forceinline__ void dr_scales(const RolloutArgs& a, uint32_t iter, uint32_t unit,
+                                          float (&out)[S]) {
+  if (a.dr_mode == MTP_DR_NONE) {
+#pragma unroll
+    for (int j = 0; j < S; ++j) out[j] = 1.f;
+    return;
+  }
   const uint32_t tag = (a.dr_mode == MTP_DR_SHARED) ? kTagParamModel : kTagParamSample;
-  return fmaf(a.dr_hi - a.dr_lo, unit24(draw(a.key, unit, slot, iter, tag)), a.dr_lo);
+  const float span = a.dr_hi - a.dr_lo;
+#pragma unroll
+  for (int g = 0; g < (S + 3) / 4; ++g) {
+    const uint4 r = philox(make_uint4(unit, (uint32_t)g, iter, tag), a.key);
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (4 * g + q < S) out[4 * g + q] = fmaf(span, unit24(w[q]), a.dr_lo);
+  }
+}
+
+// sin and cos of an absolute link angle: Cody-Waite reduction of x by 2 pi
+// (a two-term split of 2 pi) to [-pi, pi], then the SFU sine / cosine, whose
+// absolute error on that interval is about 4e-7.
+__device__ __forceinline__ void sincos_reduced(float x, float* s, float* c) {
+  const float k = rintf(x * 0.15915494309189535f);
+  float r = fmaf(-k, 6.28318548202514648f, x);
+  r = fmaf(-k, -1.7484556e-07f, r);
+  __sincosf(r, s, c);
+}
+
+// Threads per block: fill as many SMs as the batch allows (one thread per
+// candidate; small batches get one warp per block).
+inline int rollout_block(int rows) {
+  int bd = 128;
+  while (bd > 32 && (rows + bd - 1) / bd < 152) bd >>= 1;
+  return bd;
 }
 
 // ---------------------------------------------------------------------------
@@ -66,9 +100,10 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
   for (int mdl = 0; mdl < models; ++mdl) {
     const uint32_t unit = (a.dr_mode == MTP_DR_SHARED) ? (uint32_t)mdl : (uint32_t)b;
     float gain[K], p[K], v[K];
+    dr_scales<K>(a, iter, unit, gain);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      gain[k] = dr_scale(a, iter, unit, k) * dt;
+      gain[k] *= dt;
       p[k] = a.x0[k];
       v[k] = a.x0[K + k];
     }
@@ -80,12 +115,18 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
       }
     }
     KahanSum J;
+    float u_next[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) u_next[k] = __ldg(Ub + k);
     for (int t = 0; t < a.H; ++t) {
       float u[K];
       float uu = 0.f;
+      // controls of step t+1 are requested one step ahead
+      const int tn = (t + 1 < a.H) ? t + 1 : t;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        u[k] = __ldg(Ub + t * K + k);
+        u[k] = u_next[k];
+        u_next[k] = __ldg(Ub + tn * K + k);
         uu = fmaf(u[k], u[k], uu);
       }
       J.add(fmaf(pm.w_ctrl, uu, pm_state_cost<K>(pm, p)), a.kahan);
@@ -113,6 +154,23 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
 // ---------------------------------------------------------------------------
 // Planar serial chain under joint torques.
 // ---------------------------------------------------------------------------
+// Compile-time loop: calls f(IC<i>) for i in [B, E), so every array index
+// derived from i is a constant and the arrays stay in registers.
+template <int V>
+struct IC {
+  static constexpr int value = V;
+};
+template <int B, int E>
+struct Unroll {
+  template <class F>
+  static __device__ __forceinline__ void run(F&& f) {
+    if constexpr (B < E) {
+      f(IC<B>{});
+      Unroll<B + 1, E>::run(f);
+    }
+  }
+};
+
 template <int NL>
 struct Tri {
   static constexpr int size = NL * (NL + 1) / 2;
@@ -152,8 +210,9 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
     float lb[NL], Dd[NL], G[NL];
     {
       float mass[NL];
+      dr_scales<NL>(a, iter, unit, mass);
 #pragma unroll
-      for (int j = 0; j < NL; ++j) mass[j] = cm.mass[j] * dr_scale(a, iter, unit, j);
+      for (int j = 0; j < NL; ++j) mass[j] *= cm.mass[j];
       float outer = 0.f;
 #pragma unroll
       for (int j = NL - 1; j >= 0; --j) {
@@ -183,12 +242,17 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
       }
     }
     KahanSum J;
+    float tau_next[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) tau_next[j] = __ldg(Ub + j);
     for (int t = 0; t < a.H; ++t) {
       float c[NL], s[NL], tau[NL];
+      const int tn = (t + 1 < a.H) ? t + 1 : t;
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
-        sincosf(phi[j], &s[j], &c[j]);
-        tau[j] = __ldg(Ub + t * NL + j);
+        tau[j] = tau_next[j];
+        tau_next[j] = __ldg(Ub + tn * NL + j);  // one step ahead
+        sincos_reduced(phi[j], &s[j], &c[j]);
       }
       // stage cost c(x_t, u_t): reach error of the tip and torque penalty
       {
@@ -201,56 +265,65 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
         J.add(fmaf(cm.w_target, fmaf(ex, ex, ey * ey), cm.w_ctrl * tt), a.kahan);
       }
       // mass matrix (lower triangle) and right-hand side
-      float A[Tri<NL>::size], rhs[NL];
+      using T = Tri<NL>;
+      float A[T::size], rhs[NL], inv[NL];
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
         const float q_next = (j + 1 < NL) ? tau[j + 1] : 0.f;
         rhs[j] = fmaf(-G[j], c[j], tau[j] - q_next);
-        A[Tri<NL>::at(j, j)] = Dd[j];
+        A[T::at(j, j)] = Dd[j];
       }
-#pragma unroll
-      for (int j = 1; j < NL; ++j) {
-#pragma unroll
-        for (int k = 0; k < j; ++k) {
+      Unroll<1, NL>::run([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        Unroll<0, j>::run([&](auto K) {
+          constexpr int k = decltype(K)::value;
           const float Djk = len[k] * lb[j];
           const float cjk = fmaf(c[j], c[k], s[j] * s[k]);   // cos(phi_j - phi_k)
           const float sjk = fmaf(s[j], c[k], -c[j] * s[k]);  // sin(phi_j - phi_k)
-          A[Tri<NL>::at(j, k)] = Djk * cjk;
+          A[T::at(j, k)] = Djk * cjk;
           const float S = Djk * sjk;
           rhs[j] = fmaf(-S, w[k] * w[k], rhs[j]);
           rhs[k] = fmaf(S, w[j] * w[j], rhs[k]);
-        }
-      }
-      // Cholesky A = L L^T in place, then the two triangular solves
-      float inv[NL];
-#pragma unroll
-      for (int j = 0; j < NL; ++j) {
-        float d = A[Tri<NL>::at(j, j)];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d = fmaf(-A[Tri<NL>::at(j, k)], A[Tri<NL>::at(j, k)], d);
+        });
+      });
+      // Cholesky A = L L^T in place (inv holds 1 / L_jj), then the two
+      // triangular solves
+      Unroll<0, NL>::run([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        float d = A[T::at(j, j)];
+        Unroll<0, j>::run([&](auto K) {
+          constexpr int k = decltype(K)::value;
+          d = fmaf(-A[T::at(j, k)], A[T::at(j, k)], d);
+        });
         inv[j] = rsqrtf(d);
-#pragma unroll
-        for (int i = j + 1; i < NL; ++i) {
-          float v = A[Tri<NL>::at(i, j)];
-#pragma unroll
-          for (int k = 0; k < j; ++k) v = fmaf(-A[Tri<NL>::at(i, k)], A[Tri<NL>::at(j, k)], v);
-          A[Tri<NL>::at(i, j)] = v * inv[j];
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < NL; ++i) {
+        Unroll<j + 1, NL>::run([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          float v = A[T::at(i, j)];
+          Unroll<0, j>::run([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            v = fmaf(-A[T::at(i, k)], A[T::at(j, k)], v);
+          });
+          A[T::at(i, j)] = v * inv[j];
+        });
+      });
+      Unroll<0, NL>::run([&](auto I) {
+        constexpr int i = decltype(I)::value;
         float v = rhs[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) v = fmaf(-A[Tri<NL>::at(i, k)], rhs[k], v);
+        Unroll<0, i>::run([&](auto K) {
+          constexpr int k = decltype(K)::value;
+          v = fmaf(-A[T::at(i, k)], rhs[k], v);
+        });
         rhs[i] = v * inv[i];
-      }
-#pragma unroll
-      for (int i = NL - 1; i >= 0; --i) {
+      });
+      Unroll<0, NL>::run([&](auto I) {
+        constexpr int i = NL - 1 - decltype(I)::value;
         float v = rhs[i];
-#pragma unroll
-        for (int k = i + 1; k < NL; ++k) v = fmaf(-A[Tri<NL>::at(k, i)], rhs[k], v);
+        Unroll<i + 1, NL>::run([&](auto K) {
+          constexpr int k = decltype(K)::value;
+          v = fmaf(-A[T::at(k, i)], rhs[k], v);
+        });
         rhs[i] = v * inv[i];
-      }
+      });
       // semi-implicit Euler in absolute coordinates
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
@@ -269,7 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
     {
       float c[NL], s[NL], x, y;
 #pragma unroll
-      for (int j = 0; j < NL; ++j) sincosf(phi[j], &s[j], &c[j]);
+      for (int j = 0; j < NL; ++j) sincos_reduced(phi[j], &s[j], &c[j]);
       chain_tip<NL>(len, c, s, x, y);
       const float ex = x - cm.target[0], ey = y - cm.target[1];
       J.add(cm.w_term * cm.w_target * fmaf(ex, ex, ey * ey), a.kahan);
@@ -285,8 +358,8 @@ template <int K>
 cudaError_t pm_dispatch(const RolloutArgs& a, const PointMassModel& m, int k, cudaStream_t s) {
   if constexpr (K <= 16) {
     if (k == K) {
-      const int grid = (a.rows + kThreads - 1) / kThreads;
-      k_rollout_pm<K><<<grid, kThreads, 0, s>>>(a, m);
+      const int bd = rollout_block(a.rows);
+      k_rollout_pm<K><<<(a.rows + bd - 1) / bd, bd, 0, s>>>(a, m);
       return cudaGetLastError();
     }
     return pm_dispatch<K + 1>(a, m, k, s);
@@ -299,8 +372,8 @@ template <int NL>
 cudaError_t chain_dispatch(const RolloutArgs& a, const ChainModel& m, int links, cudaStream_t s) {
   if constexpr (NL <= 12) {
     if (links == NL) {
-      const int grid = (a.rows + kThreads - 1) / kThreads;
-      k_rollout_chain<NL><<<grid, kThreads, 0, s>>>(a, m);
+      const int bd = rollout_block(a.rows);
+      k_rollout_chain<NL><<<(a.rows + bd - 1) / bd, bd, 0, s>>>(a, m);
       return cudaGetLastError();
     }
     return chain_dispatch<NL + 1>(a, m, links, s);
