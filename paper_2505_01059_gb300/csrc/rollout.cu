@@ -19,7 +19,25 @@ namespace mtp {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kPrefetch = 4;  // control steps requested ahead of use
 
+
+// Compile-time loop: calls f(IC<i>) for i in [B, E), so every array index
+// derived from i is a constant and the arrays stay in registers.
+template <int V>
+struct IC {
+  static constexpr int value = V;
+};
+template <int B, int E>
+struct Unroll {
+  template <class F>
+  static __device__ __forceinline__ void run(F&& f) {
+    if constexpr (B < E) {
+      f(IC<B>{});
+      Unroll<B + 1, E>::run(f);
+    }
+  }
+};
 
 // Model scales of slots 0..S-1 for one model unit, four slots per generator
 // call (the same words draw() returns one at a time).
@@ -115,33 +133,42 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
       }
     }
     KahanSum J;
-    float u_next[K];
+    // controls are requested kPrefetch steps ahead into a rotating register
+    // buffer (the time loop is unrolled by kPrefetch so slots are constants)
+    float ubuf[kPrefetch][K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) u_next[k] = __ldg(Ub + k);
-    for (int t = 0; t < a.H; ++t) {
-      float u[K];
-      float uu = 0.f;
-      // controls of step t+1 are requested one step ahead
-      const int tn = (t + 1 < a.H) ? t + 1 : t;
+    for (int q = 0; q < kPrefetch; ++q)
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        u[k] = u_next[k];
-        u_next[k] = __ldg(Ub + tn * K + k);
-        uu = fmaf(u[k], u[k], uu);
-      }
-      J.add(fmaf(pm.w_ctrl, uu, pm_state_cost<K>(pm, p)), a.kahan);
+      for (int k = 0; k < K; ++k) ubuf[q][k] = __ldg(Ub + min(q, a.H - 1) * K + k);
+    for (int t0 = 0; t0 < a.H; t0 += kPrefetch) {
+      Unroll<0, kPrefetch>::run([&](auto Q) {
+        constexpr int q = decltype(Q)::value;
+        const int t = t0 + q;
+        if (t < a.H) {
+          float u[K];
+          float uu = 0.f;
+          const int tn = min(t + kPrefetch, a.H - 1);
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        v[k] = fmaf(gain[k], u[k], v[k]);
-        p[k] = fmaf(dt, v[k], p[k]);
-      }
-      if (a.X) {
+          for (int k = 0; k < K; ++k) {
+            u[k] = ubuf[q][k];
+            ubuf[q][k] = __ldg(Ub + tn * K + k);
+            uu = fmaf(u[k], u[k], uu);
+          }
+          J.add(fmaf(pm.w_ctrl, uu, pm_state_cost<K>(pm, p)), a.kahan);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          a.X[(size_t)(t + 1) * 2 * K + k] = p[k];
-          a.X[(size_t)(t + 1) * 2 * K + K + k] = v[k];
+          for (int k = 0; k < K; ++k) {
+            v[k] = fmaf(gain[k], u[k], v[k]);
+            p[k] = fmaf(dt, v[k], p[k]);
+          }
+          if (a.X) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              a.X[(size_t)(t + 1) * 2 * K + k] = p[k];
+              a.X[(size_t)(t + 1) * 2 * K + K + k] = v[k];
+            }
+          }
         }
-      }
+      });
     }
     J.add(pm.w_term * pm_state_cost<K>(pm, p), a.kahan);
     total += J.s;
@@ -154,23 +181,6 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
 // ---------------------------------------------------------------------------
 // Planar serial chain under joint torques.
 // ---------------------------------------------------------------------------
-// Compile-time loop: calls f(IC<i>) for i in [B, E), so every array index
-// derived from i is a constant and the arrays stay in registers.
-template <int V>
-struct IC {
-  static constexpr int value = V;
-};
-template <int B, int E>
-struct Unroll {
-  template <class F>
-  static __device__ __forceinline__ void run(F&& f) {
-    if constexpr (B < E) {
-      f(IC<B>{});
-      Unroll<B + 1, E>::run(f);
-    }
-  }
-};
-
 template <int NL>
 struct Tri {
   static constexpr int size = NL * (NL + 1) / 2;
@@ -242,16 +252,22 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
       }
     }
     KahanSum J;
-    float tau_next[NL];
+    float ubuf[kPrefetch][NL];
 #pragma unroll
-    for (int j = 0; j < NL; ++j) tau_next[j] = __ldg(Ub + j);
-    for (int t = 0; t < a.H; ++t) {
+    for (int q = 0; q < kPrefetch; ++q)
+#pragma unroll
+      for (int j = 0; j < NL; ++j) ubuf[q][j] = __ldg(Ub + min(q, a.H - 1) * NL + j);
+    for (int t0 = 0; t0 < a.H; t0 += kPrefetch) {
+     Unroll<0, kPrefetch>::run([&](auto Q) {
+      constexpr int q = decltype(Q)::value;
+      const int t = t0 + q;
+      if (t >= a.H) return;
       float c[NL], s[NL], tau[NL];
-      const int tn = (t + 1 < a.H) ? t + 1 : t;
+      const int tn = min(t + kPrefetch, a.H - 1);
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
-        tau[j] = tau_next[j];
-        tau_next[j] = __ldg(Ub + tn * NL + j);  // one step ahead
+        tau[j] = ubuf[q][j];
+        ubuf[q][j] = __ldg(Ub + tn * NL + j);  // kPrefetch steps ahead
         sincos_reduced(phi[j], &s[j], &c[j]);
       }
       // stage cost c(x_t, u_t): reach error of the tip and torque penalty
@@ -338,6 +354,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
           xo[NL + j] = w[j] - (j ? w[j - 1] : 0.f);
         }
       }
+     });
     }
     {
       float c[NL], s[NL], x, y;
