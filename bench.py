@@ -57,13 +57,14 @@ def flops_per_step(spec: dict) -> int:
     if spec["dyn"] == "chain":
         L = spec["n_links"]
         pairs = L * (L - 1) // 2
-        cost = 6 * L + 12
-        rhs = 3 * L
-        mass_matrix = 15 * pairs
+        cost = 6 * L + 12            # tip position, reach error, torque penalty, compensated add
+        rhs = 3 * L                  # tau_j - tau_{j+1} - g l_j beta_j cos(phi_j)
+        mass_matrix = 5 * pairs      # D_jk cos(phi_j - phi_k) below the diagonal
+        velocity = 21 * L - 4        # O(L) prefix / suffix form of the velocity terms
         chol = L * (L - 1) + sum((L - 1 - j) * (2 * j + 1) for j in range(L))
         solves = 2 * L * L
         integrate = 4 * L
-        return cost + rhs + mass_matrix + chol + solves + integrate
+        return cost + rhs + mass_matrix + velocity + chol + solves + integrate
     if spec["dyn"] == "pointmass":
         k = spec["n"]
         return 9 * k + 8 + len(spec.get("obs_c", [])) * (3 * k + 3)

@@ -148,12 +148,12 @@ __global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
 
   // Local rows: mu + sigma * eps, four elements of a row per generator call.
   const int G = (Hn + 3) >> 2;
-  const long long items = (long long)a.local_rows * G + (a.U_mean ? G : 0);
-  const long long stride = (long long)(gridDim.x - a.graph_blocks) * blockDim.x;
-  for (long long e = (long long)(blockIdx.x - a.graph_blocks) * blockDim.x + threadIdx.x;
-       e < items; e += stride) {
-    const int row = (int)(e / G);
-    const int q = (int)(e - (long long)row * G);
+  const int items = a.local_rows * G + (a.U_mean ? G : 0);
+  const int stride = (gridDim.x - a.graph_blocks) * blockDim.x;
+  for (int e = (blockIdx.x - a.graph_blocks) * blockDim.x + threadIdx.x; e < items; e += stride) {
+    const int row = e / G;
+    const int q = e - row * G;
+    int i = (4 * q) % n;  // control dimension of element 4q, then advanced in place
     if (row < a.local_rows) {
       const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
       float eps[4];
@@ -164,19 +164,17 @@ __global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
       for (int w = 0; w < 4; ++w) {
         const int el = 4 * q + w;
         if (el < Hn) {
-          const int i = el % n;
-          const float u = fmaf((float)a.sigma[el], eps[w], (float)a.mu[el]);
+          const float u = fmaf(a.sigma[el], eps[w], a.mu[el]);
           dst[el] = clamp_box(u, a.umin[i], a.umax[i]);
         }
+        if (++i == n) i = 0;
       }
     } else {
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
         const int el = 4 * q + w;
-        if (el < Hn) {
-          const int i = el % n;
-          a.U_mean[el] = clamp_box((float)a.mu[el], a.umin[i], a.umax[i]);
-        }
+        if (el < Hn) a.U_mean[el] = clamp_box(a.mu[el], a.umin[i], a.umax[i]);
+        if (++i == n) i = 0;
       }
     }
   }

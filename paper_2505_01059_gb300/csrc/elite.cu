@@ -48,15 +48,9 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    // warp-aggregated histogram: costs of one batch share their high bytes,
-    // so lanes with equal digits add once per warp instead of contending
-    for (int base = 0; base < B; base += blockDim.x) {
-      const int b = base + tid;
-      const uint32_t k = b < B ? keys[b] : 0u;
-      const bool take = b < B && (k & mask) == prefix;
-      const uint32_t digit = take ? ((k >> shift) & 255u) : 256u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, digit);
-      if (take && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (uint32_t)__popc(peers));
+    for (int b = tid; b < B; b += blockDim.x) {
+      const uint32_t k = keys[b];
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
     }
     __syncthreads();
     if (wid == 0) {
@@ -133,15 +127,35 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   for (int i = E + tid; i < Ep; i += blockDim.x) sel[i] = ~0ull;
   __syncthreads();
 
-  // bitonic sort of the E selected (key, index) pairs, ascending: one warp
-  // for small E (no block barriers), the whole block otherwise
-  const bool one_warp = Ep <= 256;
-  if (!one_warp || wid == 0) {
-    const int stride = one_warp ? 32 : (int)blockDim.x;
-    const int me = one_warp ? lane : tid;
+  // bitonic sort of the E selected (key, index) pairs, ascending: in the
+  // registers of one warp for E <= 64, through shared memory otherwise
+  if (Ep <= 64) {
+    if (wid == 0) {
+      unsigned long long v0 = lane < Ep ? sel[lane] : ~0ull;
+      unsigned long long v1 = lane + 32 < Ep ? sel[lane + 32] : ~0ull;
+      for (int k = 2; k <= 64; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          if (j == 32) {  // partner is the lane's other element (k == 64, ascending)
+            const unsigned long long lo = v0 < v1 ? v0 : v1, hi = v0 < v1 ? v1 : v0;
+            v0 = lo;
+            v1 = hi;
+          } else {
+            const bool lower = (lane & j) == 0;
+            const unsigned long long o0 = __shfl_xor_sync(0xffffffffu, v0, j);
+            const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, v1, j);
+            const bool up0 = (lane & k) == 0, up1 = ((lane + 32) & k) == 0;
+            v0 = (lower == up0) ? (v0 < o0 ? v0 : o0) : (v0 < o0 ? o0 : v0);
+            v1 = (lower == up1) ? (v1 < o1 ? v1 : o1) : (v1 < o1 ? o1 : v1);
+          }
+        }
+      }
+      if (lane < Ep) sel[lane] = v0;
+      if (lane + 32 < Ep) sel[lane + 32] = v1;
+    }
+  } else {
     for (int k = 2; k <= Ep; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = me; i < Ep; i += stride) {
+        for (int i = tid; i < Ep; i += blockDim.x) {
           const int ixj = i ^ j;
           if (ixj > i) {
             const unsigned long long x = sel[i], y = sel[ixj];
@@ -152,8 +166,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
             }
           }
         }
-        if (one_warp) __syncwarp();
-        else __syncthreads();
+        __syncthreads();
       }
     }
   }
@@ -169,7 +182,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
     if (a.elite_out) a.elite_out[k] = idx;
     double c = (double)a.cost[idx];
     if (isnan(c)) c = INFINITY;
-    const double w = uniform ? 1.0 : exp(-(c - best) / a.lambda);
+    const double w = uniform ? 1.0 : exp(-(c - best) * a.inv_lambda);
     a.weight[k] = w;
     part += w;
   }
@@ -181,11 +194,11 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
     double v = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_red[0] = v;
+    if (lane == 0) s_red[0] = 1.0 / v;
   }
   __syncthreads();
-  const double total = s_red[0];
-  for (int k = tid; k < E; k += blockDim.x) a.weight[k] = a.weight[k] / total;
+  const double inv_total = s_red[0];
+  for (int k = tid; k < E; k += blockDim.x) a.weight[k] = a.weight[k] * inv_total;
   // u* = U[elite[0], 0, :]
   const int best_row = (int)(sel[0] & 0xffffffffu);
   for (int i = tid; i < a.n; i += blockDim.x) {
@@ -243,20 +256,29 @@ __global__ void __launch_bounds__(128) k_update(const UpdateArgs a) {
     if (lane == 0) {
       if (cem) {
         const double s1 = a.E > 1 ? sqrt(v / (double)(a.E - 1)) : 0.0;
-        a.mu[e] = a.alpha * a.mu[e] + (1.0 - a.alpha) * m1;
-        a.sigma[e] = a.alpha * a.sigma[e] + (1.0 - a.alpha) * s1;
+        const double mn = a.alpha * a.mu[e] + (1.0 - a.alpha) * m1;
+        const double sn = a.alpha * a.sigma[e] + (1.0 - a.alpha) * s1;
+        a.mu[e] = mn;
+        a.sigma[e] = sn;
+        a.mu_f[e] = (float)mn;
+        a.sigma_f[e] = (float)sn;
       } else {
         double s1 = sqrt(v);
         if (s1 < a.sigma_min) s1 = a.sigma_min;
-        a.mu[e] = m1 + a.alpha * (a.mu[e] - m1);
-        a.sigma[e] = s1 + a.alpha * (a.sigma[e] - s1);
+        const double mn = m1 + a.alpha * (a.mu[e] - m1);
+        const double sn = s1 + a.alpha * (a.sigma[e] - s1);
+        a.mu[e] = mn;
+        a.sigma[e] = sn;
+        a.mu_f[e] = (float)mn;
+        a.sigma_f[e] = (float)sn;
       }
     }
   }
   if (a.d_iter && blockIdx.x == 0 && threadIdx.x == 0) *a.d_iter += 1u;
 }
 
-__global__ void k_shift(double* mu, double* sigma, int H, int n, int k) {
+__global__ void k_shift(double* mu, double* sigma, float* mu_f, float* sigma_f, int H, int n,
+                        int k) {
   // one thread per dimension walks the horizon forward (in place is safe:
   // row t reads row t+k >= t)
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -265,6 +287,8 @@ __global__ void k_shift(double* mu, double* sigma, int H, int n, int k) {
     const int src = t + k < H ? t + k : H - 1;
     mu[t * n + i] = mu[src * n + i];
     sigma[t * n + i] = sigma[src * n + i];
+    mu_f[t * n + i] = (float)mu[t * n + i];
+    sigma_f[t * n + i] = (float)sigma[t * n + i];
   }
 }
 
@@ -294,8 +318,9 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_shift(double* mu, double* sigma, int H, int n, int k, cudaStream_t s) {
-  k_shift<<<(n + 63) / 64, 64, 0, s>>>(mu, sigma, H, n, k);
+cudaError_t launch_shift(double* mu, double* sigma, float* mu_f, float* sigma_f, int H, int n, int k,
+                         cudaStream_t s) {
+  k_shift<<<(n + 63) / 64, 64, 0, s>>>(mu, sigma, mu_f, sigma_f, H, n, k);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,8 @@ struct mtp_handle {
   // planner state
   double* mu = nullptr;
   double* sigma = nullptr;
+  float* mu_f = nullptr;     // FP32 copies read by the samplers
+  float* sigma_f = nullptr;
   uint32_t* iter_dev = nullptr;
   uint32_t iter_host = 0;
   // scratch of one iteration
@@ -230,8 +232,8 @@ CandArgs cand_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter) {
   a.seg = h->seg;
   a.delta = h->delta;
   a.paths_per_block = h->paths_per_block;
-  a.mu = h->mu;
-  a.sigma = h->sigma;
+  a.mu = h->mu_f;
+  a.sigma = h->sigma_f;
   for (int i = 0; i < h->dm.n; ++i) {
     a.umin[i] = h->pr.u_min[i];
     a.umax[i] = h->pr.u_max[i];
@@ -318,12 +320,12 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev) {
   RolloutArgs r = rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, dm.B, h->cost);
   if ((e = launch_rollout(h, r, s)) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
-  SelectArgs sa{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, h->pr.lambda, h->pr.update_rule,
+  SelectArgs sa{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
                 h->elite, h->weight, h->ustar, nullptr, nullptr};
   if ((e = launch_select(sa, s)) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], s);
   UpdateArgs ua{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
-                h->pr.update_rule, h->mu, h->sigma, h->iter_dev};
+                h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
   if ((e = launch_update(ua, s)) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[4], s);
   return cudaSuccess;
@@ -333,7 +335,8 @@ void free_handle(mtp_handle* h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-  void* ptrs[] = {h->basis, h->bfirst, h->seg, h->delta, h->mu, h->sigma, h->iter_dev,
+  void* ptrs[] = {h->basis, h->bfirst, h->seg, h->delta, h->mu, h->sigma, h->mu_f, h->sigma_f,
+                  h->iter_dev,
                   h->U, h->cost, h->elite, h->weight, h->ustar, h->x0};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -396,15 +399,19 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   if ((st = build_tables(h)) != MTP_OK) return err(st);
   const size_t rowsz = (size_t)dm.H * dm.n;
   if ((e = dalloc(&h->mu, rowsz)) || (e = dalloc(&h->sigma, rowsz)) ||
+      (e = dalloc(&h->mu_f, rowsz)) || (e = dalloc(&h->sigma_f, rowsz)) ||
       (e = dalloc(&h->iter_dev, 1)) || (e = dalloc(&h->U, rowsz * dm.B)) ||
       (e = dalloc(&h->cost, dm.B)) || (e = dalloc(&h->elite, dm.E)) ||
       (e = dalloc(&h->weight, dm.E)) || (e = dalloc(&h->ustar, dm.n)) ||
       (e = dalloc(&h->x0, dm.d)))
     return err(cuda_fail(h, e, "cudaMalloc"));
   std::vector<double> mu(rowsz, p.mu_init), sg(rowsz, p.sigma_init);
+  std::vector<float> muf(rowsz, (float)p.mu_init), sgf(rowsz, (float)p.sigma_init);
   uint32_t zero = 0;
   if ((e = cudaMemcpy(h->mu, mu.data(), rowsz * 8, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(h->sigma, sg.data(), rowsz * 8, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->mu_f, muf.data(), rowsz * 4, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->sigma_f, sgf.data(), rowsz * 4, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(h->iter_dev, &zero, 4, cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(h->ustar, 0, dm.n * 4)))
     return err(cuda_fail(h, e, "cudaMemcpy"));
@@ -524,12 +531,12 @@ mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U
   DeviceGuard g(h->device);
   const Dims& dm = h->dm;
   cudaStream_t s = (cudaStream_t)stream;
-  SelectArgs sa{d_cost, d_U, dm.B, dm.E, dm.H, dm.n, h->pr.lambda, h->pr.update_rule,
+  SelectArgs sa{d_cost, d_U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
                 h->elite, h->weight, h->ustar, d_elite, d_ustar};
   cudaError_t e = launch_select(sa, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "select");
   UpdateArgs ua{d_U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
-                h->pr.update_rule, h->mu, h->sigma, nullptr};
+                h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, nullptr};
   e = launch_update(ua, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "update");
   return MTP_OK;
@@ -613,7 +620,8 @@ mtp_status mtp_shift(mtp_handle* h, int32_t k, void* stream) {
   if (!h || k < 0) return fail(h, MTP_ERR_INVALID_ARG, "shift: bad argument");
   if (k == 0) return MTP_OK;
   DeviceGuard g(h->device);
-  cudaError_t e = launch_shift(h->mu, h->sigma, h->dm.H, h->dm.n, k, (cudaStream_t)stream);
+  cudaError_t e = launch_shift(h->mu, h->sigma, h->mu_f, h->sigma_f, h->dm.H, h->dm.n, k,
+                               (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "shift");
   return MTP_OK;
 }
@@ -636,6 +644,14 @@ mtp_status mtp_set_state(mtp_handle* h, const double* h_mu, const double* h_sigm
   MTP_CUDA(h, cudaDeviceSynchronize());
   MTP_CUDA(h, cudaMemcpy(h->mu, h_mu, bytes, cudaMemcpyHostToDevice));
   MTP_CUDA(h, cudaMemcpy(h->sigma, h_sigma, bytes, cudaMemcpyHostToDevice));
+  const size_t cnt = (size_t)h->dm.H * h->dm.n;
+  std::vector<float> muf(cnt), sgf(cnt);
+  for (size_t i = 0; i < cnt; ++i) {
+    muf[i] = (float)h_mu[i];
+    sgf[i] = (float)h_sigma[i];
+  }
+  MTP_CUDA(h, cudaMemcpy(h->mu_f, muf.data(), cnt * 4, cudaMemcpyHostToDevice));
+  MTP_CUDA(h, cudaMemcpy(h->sigma_f, sgf.data(), cnt * 4, cudaMemcpyHostToDevice));
   MTP_CUDA(h, cudaMemcpy(h->iter_dev, &iter, 4, cudaMemcpyHostToDevice));
   h->iter_host = iter;
   return MTP_OK;

@@ -104,8 +104,8 @@ struct CandArgs {
   float* U_local;          // rows [0, local_rows) or null
   int32_t local_rows;
   float* U_mean;           // the mean row or null
-  const double* mu;        // (H, n)
-  const double* sigma;     // (H, n)
+  const float* mu;         // (H, n) FP32 copy of the FP64 mean
+  const float* sigma;      // (H, n) FP32 copy of the FP64 spread
   float umin[MTP_MAX_CTRL], umax[MTP_MAX_CTRL];
 };
 
@@ -144,7 +144,7 @@ struct SelectArgs {
   const float* cost;  // (B)
   const float* U;     // (B, H, n)
   int32_t B, E, H, n;
-  double lambda;
+  double inv_lambda;  // 1 / lambda
   int32_t update_rule;
   int32_t* elite;     // (E) internal
   double* weight;     // (E) internal
@@ -162,6 +162,8 @@ struct UpdateArgs {
   int32_t update_rule;
   double* mu;           // (H, n) in/out
   double* sigma;        // (H, n) in/out
+  float* mu_f;          // (H, n) FP32 copies written alongside
+  float* sigma_f;
   uint32_t* d_iter;     // incremented once when set
 };
 
@@ -180,6 +182,7 @@ cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int 
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 size_t select_smem_bytes(int B, int E);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
-cudaError_t launch_shift(double* mu, double* sigma, int H, int n, int k, cudaStream_t s);
+cudaError_t launch_shift(double* mu, double* sigma, float* mu_f, float* sigma_f, int H, int n, int k,
+                         cudaStream_t s);
 
 }  // namespace mtp

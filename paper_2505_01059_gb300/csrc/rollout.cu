@@ -289,19 +289,44 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
         rhs[j] = fmaf(-G[j], c[j], tau[j] - q_next);
         A[T::at(j, j)] = Dd[j];
       }
+      // mass matrix entries below the diagonal: D_jk = l_k lb_j for k < j
       Unroll<1, NL>::run([&](auto J) {
         constexpr int j = decltype(J)::value;
         Unroll<0, j>::run([&](auto K) {
           constexpr int k = decltype(K)::value;
-          const float Djk = len[k] * lb[j];
-          const float cjk = fmaf(c[j], c[k], s[j] * s[k]);   // cos(phi_j - phi_k)
-          const float sjk = fmaf(s[j], c[k], -c[j] * s[k]);  // sin(phi_j - phi_k)
-          A[T::at(j, k)] = Djk * cjk;
-          const float S = Djk * sjk;
-          rhs[j] = fmaf(-S, w[k] * w[k], rhs[j]);
-          rhs[k] = fmaf(S, w[j] * w[j], rhs[k]);
+          A[T::at(j, k)] = (len[k] * lb[j]) * fmaf(c[j], c[k], s[j] * s[k]);  // cos(phi_j - phi_k)
         });
       });
+      // velocity terms sum_k D_jk sin(phi_j - phi_k) w_k^2 in O(NL): with
+      // a_k = c_k w_k^2, b_k = s_k w_k^2 the sum is
+      // s_j (lb_j Pa_j + l_j Sa_j) - c_j (lb_j Pb_j + l_j Sb_j), where P sums
+      // l_k (.)_k over k < j and S sums lb_k (.)_k over k > j
+      {
+        float wa[NL], wb[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+          const float w2 = w[k] * w[k];
+          wa[k] = c[k] * w2;
+          wb[k] = s[k] * w2;
+        }
+        float Pa = 0.f, Pb = 0.f;
+        float Sa[NL], Sb[NL];
+        Sa[NL - 1] = 0.f;
+        Sb[NL - 1] = 0.f;
+#pragma unroll
+        for (int k = NL - 2; k >= 0; --k) {
+          Sa[k] = fmaf(lb[k + 1], wa[k + 1], Sa[k + 1]);
+          Sb[k] = fmaf(lb[k + 1], wb[k + 1], Sb[k + 1]);
+        }
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const float ca = fmaf(lb[j], Pa, len[j] * Sa[j]);
+          const float cb = fmaf(lb[j], Pb, len[j] * Sb[j]);
+          rhs[j] = rhs[j] - fmaf(s[j], ca, -c[j] * cb);
+          Pa = fmaf(len[j], wa[j], Pa);
+          Pb = fmaf(len[j], wb[j], Pb);
+        }
+      }
       // Cholesky A = L L^T in place (inv holds 1 / L_jj), then the two
       // triangular solves
       Unroll<0, NL>::run([&](auto J) {
