@@ -227,6 +227,36 @@ mtp_status mtp_set_state(mtp_handle* h, const double* h_mu, const double* h_sigm
 mtp_status mtp_set_profiling(mtp_handle* h, int32_t enable);
 mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations);
 
+/* Elite selection and update for callers that cannot allocate device memory.
+ *
+ * mtp_create allocates the handle's buffers with cudaMalloc.  Some callers
+ * cannot do that: code that runs inside a memory pool or arena it does not
+ * own, or a process whose device allocations are locked once it starts
+ * serving.  This entry point does the same work as mtp_elite_update (top-E
+ * of d_cost, softmax or plain-CEM weights, FP64 mean and spread of those rows
+ * of d_U, floor, smoothing, u*) without a handle and without allocating:
+ * the caller passes every input and output -- costs d_cost (B), candidates
+ * d_U (B, H, n), the FP64 mean d_mu and spread d_sigma (H, n, updated in
+ * place), and optionally d_elite (E) and d_ustar (n) -- and the intermediate
+ * results live in one fixed array in device memory that every GPU loading
+ * the library keeps until the process exits.  The paper has no counterpart;
+ * this is a deployment convenience.
+ *
+ * Limits: E <= MTP_NOALLOC_MAX_ELITES, H * n <= MTP_NOALLOC_MAX_HN, and B as
+ * for mtp_elite_update; larger requests return MTP_ERR_INVALID_ARG (text in
+ * mtp_last_error(NULL)).  The first call on each device looks up the array's
+ * device address and sets a kernel attribute; make that first call before
+ * any stream capture.  All calls share the one array, so calls whose work
+ * overlaps on the GPU (different streams, or threads without ordering) race
+ * and must be serialised by the caller.  No call allocates or frees memory. */
+#define MTP_NOALLOC_MAX_ELITES 2048
+#define MTP_NOALLOC_MAX_HN 4096
+mtp_status mtp_elite_update_noalloc(const float* d_cost, const float* d_U, int32_t B, int32_t E,
+                                    int32_t H, int32_t n, double lambda, double alpha,
+                                    double sigma_min, int32_t update_rule, double* d_mu,
+                                    double* d_sigma, int32_t* d_elite, float* d_ustar,
+                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void mtp::set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 struct mtp_handle {
   mtp_problem pr{};
   Dims dm{};

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 #include "mtp.h"
@@ -168,6 +170,7 @@ struct UpdateArgs {
 };
 
 // host-side launchers (defined in the .cu files)
+void set_thread_error(const std::string& msg);  // text for mtp_last_error(NULL)
 size_t candidates_smem_bytes(const CandArgs& a);
 cudaError_t init_candidate_attributes();
 cudaError_t init_select_attributes();

@@ -39,7 +39,7 @@ EXPORTS = [
     "mtp_get_buffers", "mtp_sample_tensor", "mtp_interpolate", "mtp_sample_local",
     "mtp_generate_candidates", "mtp_rollout_cost", "mtp_rollout_states", "mtp_elite_update",
     "mtp_plan_step", "mtp_plan_step_host", "mtp_shift", "mtp_get_state", "mtp_set_state",
-    "mtp_set_profiling", "mtp_stage_times",
+    "mtp_set_profiling", "mtp_stage_times", "mtp_elite_update_noalloc",
 ]
 
 
@@ -119,6 +119,8 @@ def load_library(path: str = LIB_PATH):
         "mtp_set_state": (i32, [vp, vp, vp, u32]),
         "mtp_set_profiling": (i32, [vp, i32]),
         "mtp_stage_times": (i32, [vp, vp, vp]),
+        "mtp_elite_update_noalloc": (i32, [vp, vp, i32, i32, i32, i32, C.c_double, C.c_double,
+                                           C.c_double, i32, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -405,3 +407,17 @@ def mtp_stage_times(h: Handle):
     n = C.c_int32()
     _check(load_library().mtp_stage_times(h.ptr, C.addressof(ms), C.addressof(n)), h.ptr)
     return [float(v) for v in ms], int(n.value)
+
+
+def mtp_elite_update_noalloc(cost, U, E: int, lam: float, alpha: float, sigma_min: float,
+                             update_rule: str, mu, sigma, elite=None, ustar=None, stream=None):
+    """The handle-free elite update: cost (B), U (B, H, n) float32; mu, sigma
+    (H, n) float64 CUDA tensors updated in place; elite (E) int32 and ustar
+    (n) float32 optional outputs.  Allocates nothing."""
+    import torch
+    B, H, n = U.shape
+    _check(load_library().mtp_elite_update_noalloc(
+        _dptr(cost, _f32(), B, "cost"), _dptr(U, _f32(), B * H * n, "U"), B, E, H, n,
+        float(lam), float(alpha), float(sigma_min), UPDATE[update_rule],
+        _dptr(mu, torch.float64, H * n, "mu"), _dptr(sigma, torch.float64, H * n, "sigma"),
+        _dptr(elite, _i32(), E, "elite"), _dptr(ustar, _f32(), n, "ustar"), _stream(stream)))
