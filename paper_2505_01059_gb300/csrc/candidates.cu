@@ -93,38 +93,56 @@ __global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
     __syncthreads();
 
     if (a.interp == MTP_INTERP_AKIMA) {
-      // Eqs. 6-7: per (path, dimension) piece coefficients (a, b, c, d).
+      // Eqs. 6-7 in three parallel passes over (path, dimension, knot):
+      // piece slopes m, knot slopes s, then piece coefficients (a, b, c, d).
       const float inv_h = a.inv_h;
-      for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
-        const int s = e / n, i = e - s * n;
-        const float* z = C + s * M * n + i;
-        auto slope = [&](int j) { return (z[(j + 1) * n] - z[j * n]) * inv_h; };
-        float* cf = coef + (size_t)(s * n + i) * (M - 1) * 4;
-        float s_left = akima_knot_slope(0, M, slope);
-        for (int k = 0; k < M - 1; ++k) {
-          const float s_right = akima_knot_slope(k + 1, M, slope);
-          const float mk = slope(k);
-          cf[4 * k + 0] = z[k * n];
-          cf[4 * k + 1] = s_left;
-          cf[4 * k + 2] = (3.f * mk - 2.f * s_left - s_right) * inv_h;
-          cf[4 * k + 3] = (s_left + s_right - 2.f * mk) * (inv_h * inv_h);
-          s_left = s_right;
-        }
+      const int K1 = M - 1;
+      float* mslope = coef + (size_t)SPB * n * K1 * 4;  // (nb, n, M-1)
+      float* kslope = mslope + (size_t)SPB * n * K1;    // (nb, n, M)
+      for (int e = threadIdx.x; e < nb * n * K1; e += blockDim.x) {
+        const int si = e / K1, k = e - si * K1;
+        const int sp = si / n, i = si - sp * n;
+        const float* z = C + sp * M * n + i;
+        mslope[e] = (z[(k + 1) * n] - z[k * n]) * inv_h;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < nb * n * M; e += blockDim.x) {
+        const int si = e / M, k = e - si * M;
+        const float* m = mslope + si * K1;
+        kslope[e] = akima_knot_slope(k, M, [&](int j) { return m[j]; });
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < nb * n * K1; e += blockDim.x) {
+        const int si = e / K1, k = e - si * K1;
+        const int sp = si / n, i = si - sp * n;
+        const float mk = mslope[e];
+        const float s_left = kslope[si * M + k], s_right = kslope[si * M + k + 1];
+        float* cf = coef + (size_t)e * 4;
+        cf[0] = C[(sp * M + k) * n + i];
+        cf[1] = s_left;
+        cf[2] = (3.f * mk - 2.f * s_left - s_right) * inv_h;
+        cf[3] = (s_left + s_right - 2.f * mk) * (inv_h * inv_h);
       }
       __syncthreads();
     }
 
-    // Interpolate and store rows b0 .. b0+nb-1 (coalesced over (t, i)).
+    // Interpolate and store rows b0 .. b0+nb-1 (coalesced over (t, i)); the
+    // (path, t, i) position of each thread advances by a fixed stride, so it
+    // is carried along instead of divided out.
     float* out = a.U_graph + (size_t)b0 * Hn;
-    for (int e = threadIdx.x; e < nb * Hn; e += blockDim.x) {
-      const int s = e / Hn, rem = e - s * Hn;
-      const int t = rem / n, i = rem - t * n;
+    const int total = nb * Hn;
+    int e = threadIdx.x;
+    int sp = e / Hn, rem = e - sp * Hn;
+    int t = rem / n, i = rem - t * n;
+    const int ds = blockDim.x / Hn, drem = blockDim.x - ds * Hn;
+    const int dt = drem / n, di = drem - dt * n;
+    for (; e < total; e += blockDim.x) {
       float u;
       if (a.interp == MTP_INTERP_BSPLINE) {
         // Def. 2: sum over the (p+1)-wide non-zero window of basis row t.
         const int f = a.bfirst[t];
         const float* brow = a.basis + (size_t)t * M;
-        const float* zc = C + s * M * n + i;
+        const float* zc = C + sp * M * n + i;
         u = 0.f;
         for (int q = 0; q <= a.degree; ++q) {
           const int m = f + q;
@@ -133,15 +151,27 @@ __global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
       } else if (a.interp == MTP_INTERP_AKIMA) {
         const int k = a.seg[t];
         const float dl = a.delta[t];
-        const float* cf = coef + ((size_t)(s * n + i) * (M - 1) + k) * 4;
+        const float* cf = coef + ((size_t)(sp * n + i) * (M - 1) + k) * 4;
         u = fmaf(fmaf(fmaf(cf[3], dl, cf[2]), dl, cf[1]), dl, cf[0]);
       } else {
         const int k = a.seg[t];
         const float w = fminf(a.delta[t] * a.inv_h, 1.f);
-        const float z0 = C[(s * M + k) * n + i], z1 = C[(s * M + k + 1) * n + i];
+        const float z0 = C[(sp * M + k) * n + i], z1 = C[(sp * M + k + 1) * n + i];
         u = fmaf(w, z1 - z0, z0);
       }
       out[e] = clamp_box(u, a.umin[i], a.umax[i]);
+      // advance (sp, t, i) by blockDim.x elements
+      sp += ds;
+      t += dt;
+      i += di;
+      if (i >= n) {
+        i -= n;
+        ++t;
+      }
+      if (t >= H) {
+        t -= H;
+        ++sp;
+      }
     }
     return;
   }
@@ -215,7 +245,8 @@ size_t candidates_smem_bytes(const CandArgs& a) {
   if (a.graph_blocks > 0) {
     if (!a.C_in) f += (size_t)d.M * d.N * d.n;
     f += (size_t)a.paths_per_block * d.M * d.n;
-    if (a.interp == MTP_INTERP_AKIMA) f += (size_t)a.paths_per_block * d.n * (d.M - 1) * 4;
+    if (a.interp == MTP_INTERP_AKIMA)  // coefficients, piece slopes, knot slopes
+      f += (size_t)a.paths_per_block * d.n * ((d.M - 1) * 5 + d.M);
   }
   return f * sizeof(float);
 }

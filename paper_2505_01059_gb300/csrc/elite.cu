@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   const int Bp = (B + 1) & ~1;
   uint32_t* keys = reinterpret_cast<uint32_t*>(sm_raw);
   unsigned long long* sel = reinterpret_cast<unsigned long long*>(keys + Bp);
-  __shared__ uint32_t hist[256];
+  __shared__ uint32_t hist[512];
   __shared__ uint32_t warp_tot[32];
   __shared__ uint32_t s_digit, s_below, s_lt;
   __shared__ double s_red[32];
@@ -42,23 +42,28 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   for (int b = tid; b < B; b += blockDim.x) keys[b] = order_key(a.cost[b]);
   __syncthreads();
 
-  // radix select of the E-th smallest key (rank 1-based)
+  // radix select of the E-th smallest key (rank 1-based); two histogram
+  // buffers alternate so each pass needs only two block barriers
   uint32_t prefix = 0, mask = 0;
   uint32_t rank = (uint32_t)E;
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
+  for (int i = tid; i < 512; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    uint32_t* cur = hist + 256 * (pass & 1);
+    uint32_t* nxt = hist + 256 * ((pass + 1) & 1);
     for (int b = tid; b < B; b += blockDim.x) {
       const uint32_t k = keys[b];
-      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+      if ((k & mask) == prefix) atomicAdd(&cur[(k >> shift) & 255u], 1u);
     }
+    for (int i = tid; i < 256; i += blockDim.x) nxt[i] = 0;
     __syncthreads();
     if (wid == 0) {
       // lane l owns digits 8l .. 8l+7
       uint32_t c[8], sum = 0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        c[q] = hist[lane * 8 + q];
+        c[q] = cur[lane * 8 + q];
         sum += c[q];
       }
       uint32_t incl = sum;
@@ -81,7 +86,6 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
     prefix |= s_digit << shift;
     mask |= 255u << shift;
     rank -= s_below;
-    __syncthreads();
   }
   const uint32_t T = prefix;       // the E-th smallest key
   const uint32_t need_eq = rank;   // how many keys equal to T are taken
