@@ -158,6 +158,26 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(seen)}
 
 
+def rank_spec(spec: dict, rank: int) -> dict:
+    """Each rank plans its own independent instance: same workload, own seed."""
+    return dict(spec, seed=spec["seed"] + 7919 * rank)
+
+
+def max_over_ranks(value: float, pg, device) -> float:
+    """The slowest rank's time (the contract's max over ranks)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds_max: float) -> float:
+    """Whole-job throughput: units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -254,7 +274,7 @@ def run_ours(args, spec, name):
         pg.barrier()
     mtp.load_library()
 
-    spec = dict(spec, seed=spec["seed"] + 7919 * rank)  # independent instance per rank
+    spec = rank_spec(spec, rank)  # independent instance per rank
     h = mtp.mtp_create(spec)
     s = h.sizes
     x0 = torch.tensor(spec["x0"], dtype=torch.float32, device=dev)
@@ -288,14 +308,10 @@ def run_ours(args, spec, name):
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     stage_ms, n_it = mtp.mtp_stage_times(h)
     mtp.mtp_set_profiling(h, False)
-    total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), pg, dev)
     steps_per_iter = s["B"] * s["H"]
-    value = world * steps_per_iter * args.steps / (total_ms / 1e3)
-    plan_steps = world * args.steps / (total_ms / 1e3)
+    value = job_rate(world, steps_per_iter * args.steps, total_ms / 1e3)
+    plan_steps = job_rate(world, args.steps, total_ms / 1e3)
 
     # same step through graph replay (reported alongside)
     g_start = torch.cuda.Event(enable_timing=True)
@@ -320,12 +336,8 @@ def run_ours(args, spec, name):
         t0 = time.perf_counter()
         mtp.mtp_plan_step_host(h, x0_h, 1, u_h)
         lat.append(time.perf_counter() - t0)
-    e2e_total = sum(lat)
-    if pg:
-        t = torch.tensor([e2e_total], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * steps_per_iter * n_e2e / e2e_total
+    e2e_total = max_over_ranks(sum(lat), pg, dev)
+    e2e_value = job_rate(world, steps_per_iter * n_e2e, e2e_total)
     lat_sorted = sorted(lat)
     p50 = 1e3 * lat_sorted[len(lat) // 2]
     p99 = 1e3 * lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
