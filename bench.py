@@ -255,6 +255,83 @@ def run_reference(args, spec, name):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batched vs plain on many uneven instances (one GPU): the plain form
+    plans each instance with its own launches, one after the other on one
+    stream; the batched form runs one CUDA graph per iteration for all."""
+    import numpy as np
+    import torch
+
+    from paper_2505_01059_gb300 import _build, mtp
+    from paper_2505_01059_gb300 import workloads as W
+    _build.build_library()
+    mtp.load_library()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    specs = W.batch(count=args.instances)
+    handles = [mtp.mtp_create(s) for s in specs]
+    b = mtp.mtp_batch_create(handles)
+    tiles = mtp.mtp_batch_autotune(b)
+    x0 = torch.tensor(np.concatenate([np.array(s["x0"], np.float32) for s in specs]), device=dev)
+    us = torch.empty(b.ustar_offset[-1], device=dev)
+    x0_each = [torch.tensor(s["x0"], dtype=torch.float32, device=dev) for s in specs]
+    u_each = [torch.empty(s["n"], device=dev) for s in specs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    steps_per_iter = sum(s["B"] * s["H"] for s in specs)
+    flops_per_iter = sum(flops_per_step(s) * s["B"] * s["H"] for s in specs)
+
+    def timed(fn, k):
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        for i in range(k):
+            flush.zero_()
+            st[i].record(stream)
+            fn()
+            en[i].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(c) for a, c in zip(st, en)) / k
+
+    def batched():
+        mtp.mtp_batch_plan_step(b, x0, 1, us)
+
+    def plain():
+        for h, xx, uu in zip(handles, x0_each, u_each):
+            mtp.mtp_plan_step(h, xx, 1, uu)
+
+    for _ in range(args.warmup):
+        batched()
+        plain()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        ms_b = timed(batched, args.steps)
+    ms_p = timed(plain, max(3, min(args.steps, 20)))
+    value = steps_per_iter / (ms_b / 1e3)
+    achieved = flops_per_iter / (ms_b / 1e3) / 1e12
+    peak = fp32_peak_tflops(peaks().get("sm_max_mhz", 2070.0))
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch of {len(specs)} uneven instances (point masses k 2..12, "
+                               f"chains 3..9 links, H 32..256, B 512..8192)",
+                   "l2": "flushed between steps (256 MB write)",
+                   "rollout_steps_per_iteration": steps_per_iter},
+        "plan_steps_per_s": len(specs) / (ms_b / 1e3),
+        "plain": {"ms_per_step": ms_p, "value": steps_per_iter / (ms_p / 1e3),
+                  "plan_steps_per_s": len(specs) / (ms_p / 1e3)},
+        "batched_over_plain": ms_p / ms_b,
+        "whole_step_fp32": {"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                            "frac": achieved / peak,
+                            "note": "rollout flops of all instances over the whole iteration time"},
+        "tiles": tiles, "clocks": clocks.summary(), "baseline_metric": BASELINE_METRIC,
+    }
+    print(json.dumps(line), flush=True)
+    mtp.mtp_batch_destroy(b)
+    for h in handles:
+        mtp.mtp_destroy(h)
+
+
 def run_ours(args, spec, name):
     import numpy as np
     import torch
@@ -404,13 +481,17 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="arm7", choices=["arm7", "pointmass2"])
+    ap.add_argument("--workload", default="arm7", choices=["arm7", "pointmass2", "batch"])
+    ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--reference-rows", type=int, default=512)
     ap.add_argument("--reference-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "batch":
+        run_batch(args)
+        return
     spec = workload(args.workload)
     if args.impl == "reference":
         run_reference(args, spec, args.workload)

@@ -227,6 +227,39 @@ mtp_status mtp_set_state(mtp_handle* h, const double* h_mu, const double* h_sigm
 mtp_status mtp_set_profiling(mtp_handle* h, int32_t enable);
 mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations);
 
+/* Batched planning over many handles (uneven sizes, point masses and chains
+ * mixed).  One iteration is one CUDA graph: the candidates of every instance
+ * in one launch, the rollouts grouped by (dynamics, control dimension) and
+ * run concurrently on their own streams, one selection block per instance,
+ * one update launch.  This is the GPU form of the paper's vectorised
+ * planning of many model instances (Sec. 3.3, Sec. 4 practical settings);
+ * each instance computes exactly what mtp_plan_step computes for it alone.
+ * The handles must stay alive while the batch exists; their states advance. */
+typedef struct mtp_batch mtp_batch;
+
+/* Builds the device tables of a batch over `count` distinct handles that
+ * live on the current device.  Errors: MTP_ERR_INVALID_ARG, MTP_ERR_CUDA,
+ * MTP_ERR_OUT_OF_MEMORY (text in mtp_last_error(NULL)). */
+mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch** out);
+mtp_status mtp_batch_destroy(mtp_batch* b);
+
+/* Packed layouts: x0_offset[i] .. x0_offset[i+1] is instance i's start state
+ * in the packed x0 vector, ustar_offset likewise for u*.  Each array has
+ * count + 1 entries (the last is the total length). */
+mtp_status mtp_batch_layout(const mtp_batch* b, int32_t* x0_offset, int32_t* ustar_offset);
+
+/* `iters` iterations of every instance from the packed start states d_x0;
+ * writes the packed last-iteration u* to d_ustar.  Stream-ordered. */
+mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, float* d_ustar,
+                               void* stream);
+
+/* Picks the rollout block size (candidates per block: 32, 64 or 128) of each
+ * (dynamics, dimension) group by timing one rollout launch of each choice.
+ * Writes (dynamics, dimension, block) triples to blocks_out (3 * groups
+ * entries, may be NULL) and the number of groups to n_groups.  Synchronous;
+ * overwrites the handles' cost buffers. */
+mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_groups, void* stream);
+
 /* Elite selection and update for callers that cannot allocate device memory.
  *
  * mtp_create allocates the handle's buffers with cudaMalloc.  Some callers

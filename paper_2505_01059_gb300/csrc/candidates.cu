@@ -43,16 +43,18 @@ __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& e0, 
   e1 = radius * sn;
 }
 
-__global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
-  extern __shared__ float smem[];
+// One block of candidate generation for one planning problem: block `bid`
+// of `nblocks` blocks that instance is given (graph blocks first).
+__device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, int bid,
+                                                int nblocks) {
   const Dims dm = a.dm;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
   const int H = dm.H, n = dm.n, M = dm.M, N = dm.N;
   const int Hn = H * n;
 
-  if ((int)blockIdx.x < a.graph_blocks) {
+  if (bid < a.graph_blocks) {
     const int SPB = a.paths_per_block;
-    const int b0 = blockIdx.x * SPB;
+    const int b0 = bid * SPB;
     const int nb = min(SPB, a.graph_rows - b0);
     float* Z = smem;
     float* C = Z + (a.C_in ? 0 : M * N * n);
@@ -179,8 +181,8 @@ __global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
   // Local rows: mu + sigma * eps, four elements of a row per generator call.
   const int G = (Hn + 3) >> 2;
   const int items = a.local_rows * G + (a.U_mean ? G : 0);
-  const int stride = (gridDim.x - a.graph_blocks) * blockDim.x;
-  for (int e = (blockIdx.x - a.graph_blocks) * blockDim.x + threadIdx.x; e < items; e += stride) {
+  const int stride = (nblocks - a.graph_blocks) * blockDim.x;
+  for (int e = (bid - a.graph_blocks) * blockDim.x + threadIdx.x; e < items; e += stride) {
     const int row = e / G;
     const int q = e - row * G;
     int i = (4 * q) % n;  // control dimension of element 4q, then advanced in place
@@ -208,6 +210,32 @@ __global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
+  extern __shared__ float smem[];
+  candidates_body(a, smem, blockIdx.x, gridDim.x);
+}
+
+// Many planning problems in one launch: block_start (count + 1 entries)
+// gives each instance's first block; each block copies its instance's
+// arguments into shared memory and runs the same body.
+__global__ void __launch_bounds__(kThreads) k_candidates_batch(const CandArgs* __restrict__ args,
+                                                               const int* __restrict__ block_start,
+                                                               int count) {
+  extern __shared__ float smem[];
+  __shared__ CandArgs sa;
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (block_start[mid] <= (int)blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  const int* src = reinterpret_cast<const int*>(args + lo);
+  int* dst = reinterpret_cast<int*>(&sa);
+  for (int w = threadIdx.x; w < (int)(sizeof(CandArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+  __syncthreads();
+  candidates_body(sa, smem, blockIdx.x - block_start[lo], block_start[lo + 1] - block_start[lo]);
 }
 
 // Def. 1 / Alg. 1 outputs for inspection: Z, I and C written to global memory.
@@ -254,8 +282,18 @@ size_t candidates_smem_bytes(const CandArgs& a) {
 // Opt in to large dynamic shared memory on the current device (called by
 // mtp_create, outside any stream capture).
 cudaError_t init_candidate_attributes() {
-  return cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_candidates_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               200 * 1024);
+}
+
+cudaError_t launch_candidates_batch(const CandArgs* d_args, const int* d_block_start, int count,
+                                    int total_blocks, size_t smem, cudaStream_t s) {
+  if (total_blocks <= 0) return cudaSuccess;
+  k_candidates_batch<<<total_blocks, kThreads, smem, s>>>(d_args, d_block_start, count);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t s) {

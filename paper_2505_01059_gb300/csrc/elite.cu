@@ -27,8 +27,7 @@ __device__ __forceinline__ int next_pow2(int v) {
   return p;
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+__device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* sm_raw) {
   const int B = a.B, E = a.E;
   const int Bp = (B + 1) & ~1;
   uint32_t* keys = reinterpret_cast<uint32_t*>(sm_raw);
@@ -212,17 +211,28 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  select_body(a, sm_raw);
+}
+
+// One block per planning problem.
+__global__ void __launch_bounds__(kSelThreads) k_select_batch(const SelectArgs* __restrict__ args) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const SelectArgs a = args[blockIdx.x];
+  select_body(a, sm_raw);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-__global__ void __launch_bounds__(128) k_update(const UpdateArgs a) {
+// Warp `gw` of `warps` warps given to one planning problem.
+__device__ __forceinline__ void update_body(const UpdateArgs& a, int gw, int warps) {
   constexpr int kHeld = 8;  // elites per lane kept in registers between the passes
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int Hn = a.H * a.n;
   const bool cem = a.update_rule == MTP_UPDATE_PLAIN_CEM;
   for (int e = gw; e < Hn; e += warps) {
@@ -278,7 +288,27 @@ __global__ void __launch_bounds__(128) k_update(const UpdateArgs a) {
       }
     }
   }
-  if (a.d_iter && blockIdx.x == 0 && threadIdx.x == 0) *a.d_iter += 1u;
+  if (a.d_iter && gw == 0 && lane == 0) *a.d_iter += 1u;
+}
+
+__global__ void __launch_bounds__(128) k_update(const UpdateArgs a) {
+  update_body(a, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+
+// Many planning problems: warp_start (count + 1 entries) holds each
+// instance's first warp.
+__global__ void __launch_bounds__(128) k_update_batch(const UpdateArgs* __restrict__ args,
+                                                      const int* __restrict__ warp_start, int count) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= __ldg(warp_start + count)) return;
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(warp_start + mid) <= gw) lo = mid;
+    else hi = mid;
+  }
+  const UpdateArgs a = args[lo];
+  update_body(a, gw - __ldg(warp_start + lo), __ldg(warp_start + lo + 1) - __ldg(warp_start + lo));
 }
 
 __global__ void k_shift(double* mu, double* sigma, float* mu_f, float* sigma_f, int H, int n,
@@ -305,7 +335,24 @@ size_t select_smem_bytes(int B, int E) {
 }
 
 cudaError_t init_select_attributes() {
-  return cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_select_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              200 * 1024);
+}
+
+cudaError_t launch_select_batch(const SelectArgs* d_args, int count, size_t smem, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_select_batch<<<count, kSelThreads, smem, s>>>(d_args);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_warp_start, int count,
+                                int total_warps, cudaStream_t s) {
+  if (total_warps <= 0) return cudaSuccess;
+  k_update_batch<<<(total_warps + 3) / 4, 128, 0, s>>>(d_args, d_warp_start, count);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {

@@ -3,6 +3,7 @@
 // "host precompute": B-spline basis of Def. 2 by the closed-form cardinal
 // B-spline, Akima / straight-line piece table of Def. 3), and the launch
 // sequence of one planner iteration (Alg. 2), replayed as a CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -274,22 +275,22 @@ RolloutArgs rollout_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_i
   return a;
 }
 
-cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
-  const mtp_problem& p = h->pr;
-  if (p.dyn == MTP_DYN_POINTMASS) {
-    PointMassModel m{};
-    for (int k = 0; k < p.ctrl_dim; ++k) m.target[k] = p.target[k];
-    m.w_target = p.w_target;
-    m.w_obs = p.w_obs;
-    m.w_ctrl = p.w_ctrl;
-    m.w_term = p.w_term;
-    m.n_obs = p.n_obstacles;
-    for (int o = 0; o < p.n_obstacles; ++o) {
-      for (int k = 0; k < p.ctrl_dim; ++k) m.obs_c[o][k] = p.obs_center[o][k];
-      m.obs_r[o] = p.obs_radius[o];
-    }
-    return launch_rollout_pointmass(a, m, s);
+PointMassModel pointmass_model(const mtp_problem& p) {
+  PointMassModel m{};
+  for (int k = 0; k < p.ctrl_dim; ++k) m.target[k] = p.target[k];
+  m.w_target = p.w_target;
+  m.w_obs = p.w_obs;
+  m.w_ctrl = p.w_ctrl;
+  m.w_term = p.w_term;
+  m.n_obs = p.n_obstacles;
+  for (int o = 0; o < p.n_obstacles; ++o) {
+    for (int k = 0; k < p.ctrl_dim; ++k) m.obs_c[o][k] = p.obs_center[o][k];
+    m.obs_r[o] = p.obs_radius[o];
   }
+  return m;
+}
+
+ChainModel chain_model(const mtp_problem& p) {
   ChainModel m{};
   for (int j = 0; j < p.n_links; ++j) {
     m.mass[j] = p.link_mass[j];
@@ -301,7 +302,13 @@ cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream
   m.w_target = p.w_target;
   m.w_ctrl = p.w_ctrl;
   m.w_term = p.w_term;
-  return launch_rollout_chain(a, m, p.n_links, s);
+  return m;
+}
+
+cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
+  const mtp_problem& p = h->pr;
+  if (p.dyn == MTP_DYN_POINTMASS) return launch_rollout_pointmass(a, pointmass_model(p), s);
+  return launch_rollout_chain(a, chain_model(p), p.n_links, s);
 }
 
 // One Alg. 2 iteration on the handle's own buffers, iteration from iter_dev.
@@ -681,6 +688,340 @@ mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations) {
   }
   if (iterations) *iterations = (int32_t)n_it;
   h->ev_used = 0;
+  return MTP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched planning over many handles
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct BatchGroup {
+  int dyn = 0, n = 0;
+  std::vector<int> members;
+  RolloutArgs* d_ra = nullptr;
+  void* d_model = nullptr;
+  int* d_row_start = nullptr;
+  int total_rows = 0;
+  int block = 128;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+}  // namespace
+
+struct mtp_batch {
+  std::vector<mtp_handle*> hs;
+  int device = 0;
+  CandArgs* d_cand = nullptr;
+  int* d_cand_start = nullptr;
+  int cand_blocks = 0;
+  size_t cand_smem = 0;
+  std::vector<BatchGroup> groups;
+  SelectArgs* d_sel = nullptr;
+  size_t sel_smem = 0;
+  UpdateArgs* d_upd = nullptr;
+  int* d_warp_start = nullptr;
+  int upd_warps = 0;
+  float** d_x0_dst = nullptr;
+  float** d_ustar_src = nullptr;
+  int* d_x0_off = nullptr;
+  int* d_us_off = nullptr;
+  std::vector<int> x0_off, us_off;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+  std::string err;
+};
+
+namespace {
+
+mtp_status batch_fail(mtp_batch* b, mtp_status st, const std::string& msg) {
+  if (b) b->err = msg;
+  g_create_error = msg;
+  return st;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (v.empty() ? 1 : v.size()));
+  if (e != cudaSuccess) return e;
+  return v.empty() ? cudaSuccess : cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+void free_batch(mtp_batch* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& g : b->groups) {
+    if (g.d_ra) cudaFree(g.d_ra);
+    if (g.d_model) cudaFree(g.d_model);
+    if (g.d_row_start) cudaFree(g.d_row_start);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    if (g.done) cudaEventDestroy(g.done);
+  }
+  void* ptrs[] = {b->d_cand, b->d_cand_start, b->d_sel, b->d_upd, b->d_warp_start,
+                  b->d_x0_dst, b->d_ustar_src, b->d_x0_off, b->d_us_off};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  delete b;
+}
+
+cudaError_t launch_group(const BatchGroup& g, int block, cudaStream_t s) {
+  if (g.dyn == MTP_DYN_POINTMASS)
+    return launch_rollout_pointmass_batch(g.d_ra, static_cast<const PointMassModel*>(g.d_model),
+                                          g.d_row_start, (int)g.members.size(), g.total_rows, g.n,
+                                          block, s);
+  return launch_rollout_chain_batch(g.d_ra, static_cast<const ChainModel*>(g.d_model),
+                                    g.d_row_start, (int)g.members.size(), g.total_rows, g.n,
+                                    block, s);
+}
+
+// One batched Alg. 2 iteration: candidates of all instances in one launch,
+// the rollouts of each (dynamics, dimension) group on its own stream, then
+// one selection block per instance and one update launch.
+cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
+  cudaError_t e;
+  const int count = (int)b->hs.size();
+  if ((e = launch_candidates_batch(b->d_cand, b->d_cand_start, count, b->cand_blocks, b->cand_smem, s)))
+    return e;
+  if ((e = cudaEventRecord(b->fork_ev, s))) return e;
+  for (auto& g : b->groups) {
+    if ((e = cudaStreamWaitEvent(g.stream, b->fork_ev, 0))) return e;
+    if ((e = launch_group(g, g.block, g.stream))) return e;
+    if ((e = cudaEventRecord(g.done, g.stream))) return e;
+  }
+  for (auto& g : b->groups)
+    if ((e = cudaStreamWaitEvent(s, g.done, 0))) return e;
+  if ((e = launch_select_batch(b->d_sel, count, b->sel_smem, s))) return e;
+  return launch_update_batch(b->d_upd, b->d_warp_start, count, b->upd_warps, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch** out) {
+  if (!handles || !out || count < 1) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: bad argument");
+  *out = nullptr;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < count; ++i) {
+    if (!handles[i]) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: null handle");
+    if (handles[i]->device != dev)
+      return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: handles must live on the current device");
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: repeated handle");
+  }
+  mtp_batch* b = new mtp_batch();
+  b->device = dev;
+  b->hs.assign(handles, handles + count);
+  auto err = [&](cudaError_t e, const char* where) {
+    mtp_status st = batch_fail(b, e == cudaErrorMemoryAllocation ? MTP_ERR_OUT_OF_MEMORY : MTP_ERR_CUDA,
+                               std::string(where) + ": " + cudaGetErrorString(e));
+    free_batch(b);
+    return st;
+  };
+  cudaError_t e;
+  // candidates: per-instance arguments and block ranges
+  std::vector<CandArgs> cand(count);
+  std::vector<int> cstart(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    mtp_handle* h = b->hs[i];
+    const Dims& dm = h->dm;
+    const size_t Hn = (size_t)dm.H * dm.n;
+    CandArgs c = cand_args(h, 0, h->iter_dev);
+    c.U_graph = h->U + Hn * dm.L;
+    c.graph_rows = dm.P;
+    c.graph_blocks = (dm.P + h->paths_per_block - 1) / h->paths_per_block;
+    c.U_local = h->U;
+    c.local_rows = dm.L;
+    c.U_mean = h->U + Hn * (dm.B - 1);
+    const long long items = ((long long)dm.L + 1) * (((long long)Hn + 3) / 4);
+    const int local_blocks = (int)std::max<long long>(1, (items + 1023) / 1024);
+    cand[i] = c;
+    cstart[i + 1] = cstart[i] + c.graph_blocks + local_blocks;
+    b->cand_smem = std::max(b->cand_smem, candidates_smem_bytes(c));
+  }
+  b->cand_blocks = cstart[count];
+  if ((e = upload(&b->d_cand, cand)) || (e = upload(&b->d_cand_start, cstart))) return err(e, "batch upload");
+  // rollout groups by (dynamics, dimension)
+  for (int i = 0; i < count; ++i) {
+    mtp_handle* h = b->hs[i];
+    const int key_n = h->pr.dyn == MTP_DYN_CHAIN ? h->pr.n_links : h->dm.n;
+    BatchGroup* g = nullptr;
+    for (auto& x : b->groups)
+      if (x.dyn == h->pr.dyn && x.n == key_n) g = &x;
+    if (!g) {
+      b->groups.emplace_back();
+      g = &b->groups.back();
+      g->dyn = h->pr.dyn;
+      g->n = key_n;
+    }
+    g->members.push_back(i);
+  }
+  for (auto& g : b->groups) {
+    std::vector<RolloutArgs> ra;
+    std::vector<int> rs(1, 0);
+    std::vector<PointMassModel> pms;
+    std::vector<ChainModel> cms;
+    for (int i : g.members) {
+      mtp_handle* h = b->hs[i];
+      ra.push_back(rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, h->dm.B, h->cost));
+      rs.push_back(rs.back() + ((h->dm.B + 31) / 32) * 32);  // whole warps per instance
+      if (g.dyn == MTP_DYN_POINTMASS) pms.push_back(pointmass_model(h->pr));
+      else cms.push_back(chain_model(h->pr));
+    }
+    g.total_rows = rs.back();
+    g.block = 128;
+    if ((e = upload(&g.d_ra, ra)) || (e = upload(&g.d_row_start, rs))) return err(e, "batch upload");
+    if (g.dyn == MTP_DYN_POINTMASS) {
+      PointMassModel* p = nullptr;
+      if ((e = upload(&p, pms))) return err(e, "batch upload");
+      g.d_model = p;
+    } else {
+      ChainModel* p = nullptr;
+      if ((e = upload(&p, cms))) return err(e, "batch upload");
+      g.d_model = p;
+    }
+    if ((e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming)))
+      return err(e, "batch streams");
+  }
+  // selection and update
+  std::vector<SelectArgs> sel(count);
+  std::vector<UpdateArgs> upd(count);
+  std::vector<int> wstart(count + 1, 0);
+  std::vector<float*> x0dst(count), usrc(count);
+  b->x0_off.assign(count + 1, 0);
+  b->us_off.assign(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    mtp_handle* h = b->hs[i];
+    const Dims& dm = h->dm;
+    sel[i] = SelectArgs{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
+                        h->elite, h->weight, h->ustar, nullptr, nullptr};
+    b->sel_smem = std::max(b->sel_smem, select_smem_bytes(dm.B, dm.E));
+    upd[i] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
+                        h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
+    wstart[i + 1] = wstart[i] + dm.H * dm.n;
+    x0dst[i] = h->x0;
+    usrc[i] = h->ustar;
+    b->x0_off[i + 1] = b->x0_off[i] + dm.d;
+    b->us_off[i + 1] = b->us_off[i] + dm.n;
+  }
+  b->upd_warps = wstart[count];
+  if ((e = upload(&b->d_sel, sel)) || (e = upload(&b->d_upd, upd)) ||
+      (e = upload(&b->d_warp_start, wstart)) || (e = upload(&b->d_x0_dst, x0dst)) ||
+      (e = upload(&b->d_ustar_src, usrc)) || (e = upload(&b->d_x0_off, b->x0_off)) ||
+      (e = upload(&b->d_us_off, b->us_off)))
+    return err(e, "batch upload");
+  if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) ||
+      (e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)))
+    return err(e, "batch streams");
+  *out = b;
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_destroy(mtp_batch* b) {
+  if (!b) return MTP_ERR_INVALID_ARG;
+  DeviceGuard g(b->device);
+  cudaDeviceSynchronize();
+  free_batch(b);
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_layout(const mtp_batch* b, int32_t* x0_offset, int32_t* ustar_offset) {
+  if (!b) return MTP_ERR_INVALID_ARG;
+  const size_t c = b->hs.size() + 1;
+  if (x0_offset) std::copy(b->x0_off.begin(), b->x0_off.begin() + c, x0_offset);
+  if (ustar_offset) std::copy(b->us_off.begin(), b->us_off.begin() + c, ustar_offset);
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, float* d_ustar,
+                               void* stream) {
+  if (!b || !d_x0 || !d_ustar || iters < 1)
+    return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_plan_step: bad argument");
+  DeviceGuard guard(b->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int count = (int)b->hs.size();
+  cudaError_t e = launch_scatter(d_x0, b->d_x0_dst, b->d_x0_off, count, s);
+  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch scatter: ") + cudaGetErrorString(e));
+  int left = iters;
+  while (left > 0) {
+    const int chunk = left > 64 ? 64 : left;
+    auto it = b->graphs.find(chunk);
+    if (it == b->graphs.end()) {
+      cudaGraph_t graph;
+      if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)))
+        return batch_fail(b, MTP_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+      for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = enqueue_batch_iteration(b, b->cap_stream);
+      cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess)
+        return batch_fail(b, MTP_ERR_CUDA, std::string("batch capture: ") +
+                                               cudaGetErrorString(e != cudaSuccess ? e : e2));
+      cudaGraphExec_t exec;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess)
+        return batch_fail(b, MTP_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+      it = b->graphs.emplace(chunk, exec).first;
+    }
+    if ((e = cudaGraphLaunch(it->second, s)))
+      return batch_fail(b, MTP_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    left -= chunk;
+  }
+  e = launch_gather(b->d_ustar_src, b->d_us_off, d_ustar, count, s);
+  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch gather: ") + cudaGetErrorString(e));
+  for (mtp_handle* h : b->hs) h->iter_host += (uint32_t)iters;
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_groups, void* stream) {
+  if (!b) return MTP_ERR_INVALID_ARG;
+  DeviceGuard guard(b->device);
+  (void)stream;
+  const int cand[3] = {32, 64, 128};  // the rollout kernels are bounded at 128 threads
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaError_t e = cudaSuccess;
+  for (auto& g : b->groups) {
+    float best = 1e30f;
+    int best_block = g.block;
+    for (int block : cand) {
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(t0, b->cap_stream);
+        e = launch_group(g, block, b->cap_stream);
+        cudaEventRecord(t1, b->cap_stream);
+        cudaEventSynchronize(t1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        ms_min = std::min(ms_min, ms);
+      }
+      if (ms_min < best) {
+        best = ms_min;
+        best_block = block;
+      }
+    }
+    g.block = best_block;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);  // tiles changed: recapture
+  b->graphs.clear();
+  if (n_groups) *n_groups = (int32_t)b->groups.size();
+  if (blocks_out)
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+      blocks_out[3 * i + 0] = b->groups[i].dyn;
+      blocks_out[3 * i + 1] = b->groups[i].n;
+      blocks_out[3 * i + 2] = b->groups[i].block;
+    }
   return MTP_OK;
 }
 

@@ -105,10 +105,8 @@ __device__ __forceinline__ float pm_state_cost(const PointMassModel& pm, const f
 }
 
 template <int K>
-__global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
-                                                         const PointMassModel pm) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.rows) return;
+__device__ __forceinline__ void rollout_pm_body(const RolloutArgs& a, const PointMassModel& pm,
+                                                int r) {
   const int b = a.row0 + r;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
   const float* Ub = a.U + (size_t)r * a.H * K;
@@ -200,10 +198,8 @@ __device__ __forceinline__ void chain_tip(const float (&len)[NL], const float (&
 }
 
 template <int NL>
-__global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
-                                                            const ChainModel cm) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.rows) return;
+__device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const ChainModel& cm,
+                                                   int r) {
   const int b = a.row0 + r;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
   const float* Ub = a.U + (size_t)r * a.H * NL;
@@ -396,6 +392,63 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
   a.cost[r] = cst;
 }
 
+// Instance of global row g in a batch: row_start (count + 1 entries) holds
+// each instance's first row, rows padded to whole warps.
+__device__ __forceinline__ int batch_instance(const int* __restrict__ row_start, int count, int g) {
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(row_start + mid) <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
+                                                         const PointMassModel pm) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.rows) return;
+  rollout_pm_body<K>(a, pm, r);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_rollout_pm_batch(const RolloutArgs* __restrict__ ra,
+                                                               const PointMassModel* __restrict__ pm,
+                                                               const int* __restrict__ row_start,
+                                                               int count) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= __ldg(row_start + count)) return;
+  const int i = batch_instance(row_start, count, g);
+  const RolloutArgs a = ra[i];
+  const int r = g - __ldg(row_start + i);
+  if (r >= a.rows) return;
+  rollout_pm_body<K>(a, pm[i], r);
+}
+
+template <int NL>
+__global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
+                                                            const ChainModel cm) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.rows) return;
+  rollout_chain_body<NL>(a, cm, r);
+}
+
+template <int NL>
+__global__ void __launch_bounds__(kThreads) k_rollout_chain_batch(const RolloutArgs* __restrict__ ra,
+                                                                  const ChainModel* __restrict__ cms,
+                                                                  const int* __restrict__ row_start,
+                                                                  int count) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= __ldg(row_start + count)) return;
+  const int i = batch_instance(row_start, count, g);
+  const RolloutArgs a = ra[i];
+  const ChainModel cm = cms[i];
+  const int r = g - __ldg(row_start + i);
+  if (r >= a.rows) return;
+  rollout_chain_body<NL>(a, cm, r);
+}
+
 template <int K>
 cudaError_t pm_dispatch(const RolloutArgs& a, const PointMassModel& m, int k, cudaStream_t s) {
   if constexpr (K <= 16) {
@@ -424,7 +477,50 @@ cudaError_t chain_dispatch(const RolloutArgs& a, const ChainModel& m, int links,
   }
 }
 
+template <int K>
+cudaError_t pm_batch_dispatch(const RolloutArgs* ra, const PointMassModel* pm, const int* row_start,
+                              int count, int total_rows, int k, int block, cudaStream_t s) {
+  if constexpr (K <= 16) {
+    if (k == K) {
+      k_rollout_pm_batch<K><<<(total_rows + block - 1) / block, block, 0, s>>>(ra, pm, row_start, count);
+      return cudaGetLastError();
+    }
+    return pm_batch_dispatch<K + 1>(ra, pm, row_start, count, total_rows, k, block, s);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <int NL>
+cudaError_t chain_batch_dispatch(const RolloutArgs* ra, const ChainModel* cm, const int* row_start,
+                                 int count, int total_rows, int links, int block, cudaStream_t s) {
+  if constexpr (NL <= 12) {
+    if (links == NL) {
+      k_rollout_chain_batch<NL><<<(total_rows + block - 1) / block, block, 0, s>>>(ra, cm, row_start,
+                                                                                 count);
+      return cudaGetLastError();
+    }
+    return chain_batch_dispatch<NL + 1>(ra, cm, row_start, count, total_rows, links, block, s);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_rollout_pointmass_batch(const RolloutArgs* d_ra, const PointMassModel* d_pm,
+                                           const int* d_row_start, int count, int total_rows,
+                                           int k, int block, cudaStream_t s) {
+  if (total_rows <= 0) return cudaSuccess;
+  return pm_batch_dispatch<1>(d_ra, d_pm, d_row_start, count, total_rows, k, block, s);
+}
+
+cudaError_t launch_rollout_chain_batch(const RolloutArgs* d_ra, const ChainModel* d_cm,
+                                       const int* d_row_start, int count, int total_rows,
+                                       int links, int block, cudaStream_t s) {
+  if (total_rows <= 0) return cudaSuccess;
+  return chain_batch_dispatch<1>(d_ra, d_cm, d_row_start, count, total_rows, links, block, s);
+}
 
 cudaError_t launch_rollout_pointmass(const RolloutArgs& a, const PointMassModel& m,
                                      cudaStream_t s) {

@@ -40,6 +40,8 @@ EXPORTS = [
     "mtp_generate_candidates", "mtp_rollout_cost", "mtp_rollout_states", "mtp_elite_update",
     "mtp_plan_step", "mtp_plan_step_host", "mtp_shift", "mtp_get_state", "mtp_set_state",
     "mtp_set_profiling", "mtp_stage_times", "mtp_elite_update_noalloc",
+    "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_layout", "mtp_batch_plan_step",
+    "mtp_batch_autotune",
 ]
 
 
@@ -121,6 +123,11 @@ def load_library(path: str = LIB_PATH):
         "mtp_stage_times": (i32, [vp, vp, vp]),
         "mtp_elite_update_noalloc": (i32, [vp, vp, i32, i32, i32, i32, C.c_double, C.c_double,
                                            C.c_double, i32, vp, vp, vp, vp, vp]),
+        "mtp_batch_create": (i32, [C.POINTER(vp), i32, C.POINTER(vp)]),
+        "mtp_batch_destroy": (i32, [vp]),
+        "mtp_batch_layout": (i32, [vp, vp, vp]),
+        "mtp_batch_plan_step": (i32, [vp, vp, i32, vp, vp]),
+        "mtp_batch_autotune": (i32, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -421,3 +428,57 @@ def mtp_elite_update_noalloc(cost, U, E: int, lam: float, alpha: float, sigma_mi
         float(lam), float(alpha), float(sigma_min), UPDATE[update_rule],
         _dptr(mu, torch.float64, H * n, "mu"), _dptr(sigma, torch.float64, H * n, "sigma"),
         _dptr(elite, _i32(), E, "elite"), _dptr(ustar, _f32(), n, "ustar"), _stream(stream)))
+
+
+class Batch:
+    """An mtp_batch* over handles (kept alive here) and its packed layout."""
+
+    def __init__(self, ptr: int, handles):
+        self.ptr = C.c_void_p(ptr)
+        self.handles = list(handles)
+        n = len(self.handles) + 1
+        x0 = (C.c_int32 * n)()
+        us = (C.c_int32 * n)()
+        _check(load_library().mtp_batch_layout(self.ptr, C.addressof(x0), C.addressof(us)))
+        self.x0_offset = list(x0)
+        self.ustar_offset = list(us)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            try:
+                load_library().mtp_batch_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = C.c_void_p(0)
+
+
+def mtp_batch_create(handles) -> Batch:
+    lib = load_library()
+    arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    out = C.c_void_p()
+    st = lib.mtp_batch_create(arr, len(handles), C.byref(out))
+    if st != MTP_OK:
+        raise MtpError(st, lib.mtp_last_error(None).decode())
+    return Batch(out.value, handles)
+
+
+def mtp_batch_destroy(b: Batch):
+    if b.ptr.value:
+        _check(load_library().mtp_batch_destroy(b.ptr))
+        b.ptr = C.c_void_p(0)
+
+
+def mtp_batch_plan_step(b: Batch, x0, iters: int, ustar, stream=None):
+    _check(load_library().mtp_batch_plan_step(
+        b.ptr, _dptr(x0, _f32(), b.x0_offset[-1], "x0"), iters,
+        _dptr(ustar, _f32(), b.ustar_offset[-1], "ustar"), _stream(stream)))
+
+
+def mtp_batch_autotune(b: Batch, stream=None):
+    """Returns [(dyn, dim, block), ...] per rollout group."""
+    groups = len(b.handles)
+    out = (C.c_int32 * (3 * groups))()
+    ng = C.c_int32()
+    _check(load_library().mtp_batch_autotune(b.ptr, C.addressof(out), C.addressof(ng),
+                                             _stream(stream)))
+    return [(out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i in range(ng.value)]

@@ -1,0 +1,81 @@
+"""Batched planning: each instance's result in the mix is bitwise the result
+it gets alone (random draws are keyed by (seed, iteration, index), never by
+the slot or launch shape), before and after the rollout tiles are tuned."""
+import numpy as np
+import pytest
+
+from paper_2505_01059_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def mtp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_01059_gb300 import _build, mtp as m
+    _build.build_library()
+    m.load_library()
+    torch.cuda.set_device(0)
+    return m
+
+
+def _specs():
+    specs = W.batch(seed=11, count=10)
+    specs.append(W.pointmass(B=512))
+    specs.append(W.chain(links=7, B=1000, E=50))
+    return specs
+
+
+def _run_alone(mtp, specs, x0s, iters):
+    out = []
+    for spec, x0 in zip(specs, x0s):
+        h = mtp.mtp_create(spec)
+        u = torch.empty(spec["n"], device=DEV)
+        mtp.mtp_plan_step(h, torch.tensor(x0, dtype=torch.float32, device=DEV), iters, u)
+        mu, sg, it = mtp.mtp_get_state(h)
+        buf = mtp.mtp_get_buffers(h)
+        cost = torch.as_tensor(buf["cost"], device=DEV).cpu().numpy().copy()
+        out.append((mu, sg, it, u.cpu().numpy(), cost))
+        mtp.mtp_destroy(h)
+    return out
+
+
+@pytest.mark.parametrize("tune", [False, True])
+def test_batch_matches_each_instance_alone(mtp, tune):
+    specs = _specs()
+    rng = np.random.default_rng(0)
+    x0s = [rng.uniform(-0.2, 0.2, size=s["d"]).astype(np.float32) for s in specs]
+    iters = 3
+    handles = [mtp.mtp_create(s) for s in specs]
+    b = mtp.mtp_batch_create(handles)
+    if tune:
+        tiles = mtp.mtp_batch_autotune(b)
+        assert all(blk in (32, 64, 128) for _, _, blk in tiles)
+    x0 = torch.tensor(np.concatenate(x0s), device=DEV)
+    us = torch.empty(b.ustar_offset[-1], device=DEV)
+    mtp.mtp_batch_plan_step(b, x0, 1, us)
+    mtp.mtp_batch_plan_step(b, x0, iters - 1, us)
+    torch.cuda.synchronize()
+    ref = _run_alone(mtp, specs, x0s, iters)
+    for i, (h, (mu, sg, it, u, cost)) in enumerate(zip(handles, ref)):
+        mu_b, sg_b, it_b = mtp.mtp_get_state(h)
+        assert it_b == it == iters
+        assert np.array_equal(mu_b, mu), i
+        assert np.array_equal(sg_b, sg), i
+        lo, hi = b.ustar_offset[i], b.ustar_offset[i + 1]
+        assert np.array_equal(us[lo:hi].cpu().numpy(), u), i
+        cost_b = torch.as_tensor(mtp.mtp_get_buffers(h)["cost"], device=DEV).cpu().numpy()
+        assert np.array_equal(cost_b, cost), i
+    mtp.mtp_batch_destroy(b)
+    for h in handles:
+        mtp.mtp_destroy(h)
+
+
+def test_batch_rejects_bad_input(mtp):
+    h = mtp.mtp_create(W.pointmass(B=64, E=8))
+    with pytest.raises(mtp.MtpError):
+        mtp.mtp_batch_create([h, h])
+    mtp.mtp_destroy(h)
