@@ -32,15 +32,18 @@ __device__ __forceinline__ float akima_knot_slope(int a, int M, SlopeFn slope) {
   return (w1 * mm1 + w2 * m0) / (w1 + w2);
 }
 
-// Standard normal pair by Box-Muller from two 32-bit words.
+// Standard normal pair by Box-Muller from two 32-bit words.  The angle
+// 2 pi u2 is evaluated as pi + x with x = 2 pi (u2 - 1/2) in [-pi, pi), where
+// the SFU sine / cosine have absolute error about 4e-7; the radius keeps the
+// accurate logarithm because it is ill-conditioned for u1 near 1.
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& e0, float& e1) {
   const float u1 = (float)((w0 >> 8) + 1u) * 5.9604644775390625e-8f;  // (0, 1]
   const float u2 = (float)(w1 >> 8) * 5.9604644775390625e-8f;         // [0, 1)
   const float radius = sqrtf(-2.f * logf(u1));
   float sn, cs;
-  sincospif(2.f * u2, &sn, &cs);
-  e0 = radius * cs;
-  e1 = radius * sn;
+  __sincosf(6.28318530717958648f * (u2 - 0.5f), &sn, &cs);
+  e0 = -radius * cs;
+  e1 = -radius * sn;
 }
 
 // One block of candidate generation for one planning problem: block `bid`
@@ -57,21 +60,25 @@ __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, 
     const int b0 = bid * SPB;
     const int nb = min(SPB, a.graph_rows - b0);
     float* Z = smem;
-    float* C = Z + (a.C_in ? 0 : M * N * n);
+    float* C = Z + ((a.C_in || a.Z_global) ? 0 : M * N * n);
     float* coef = C + SPB * M * n;
     if (a.C_in == nullptr) {
-      // Def. 1: Z[m][j][:] uniform over the box, four dimensions per call.
-      const int ng = (n + 3) >> 2;
-      for (int e = threadIdx.x; e < M * N * ng; e += blockDim.x) {
-        const int node = e / ng, g = e - node * ng;
-        const uint4 r = philox(make_uint4((uint32_t)node, (uint32_t)g, iter, kTagGraph), a.key);
+      const float* Zs = a.Z_global;
+      if (Zs == nullptr) {
+        // Def. 1: Z[m][j][:] uniform over the box, four dimensions per call.
+        const int ng = (n + 3) >> 2;
+        for (int e = threadIdx.x; e < M * N * ng; e += blockDim.x) {
+          const int node = e / ng, g = e - node * ng;
+          const uint4 r = philox(make_uint4((uint32_t)node, (uint32_t)g, iter, kTagGraph), a.key);
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int i = 4 * g + w;
-          if (i < n) Z[node * n + i] = fmaf(a.umax[i] - a.umin[i], unit24(pick(r, w)), a.umin[i]);
+          for (int w = 0; w < 4; ++w) {
+            const int i = 4 * g + w;
+            if (i < n) Z[node * n + i] = fmaf(a.umax[i] - a.umin[i], unit24(pick(r, w)), a.umin[i]);
+          }
         }
+        __syncthreads();
+        Zs = Z;
       }
-      __syncthreads();
       // Alg. 1: layer indices with replacement, then C = Z[m][I[b][m]][:].
       const int mg = (M + 3) >> 2;
       for (int e = threadIdx.x; e < nb * mg; e += blockDim.x) {
@@ -82,7 +89,7 @@ __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, 
           const int m = 4 * g + w;
           if (m < M) {
             const int j = index_of(pick(r, w), (uint32_t)N);
-            const float* src = Z + (m * N + j) * n;
+            const float* src = Zs + (m * N + j) * n;
             float* dst = C + (s * M + m) * n;
             for (int i = 0; i < n; ++i) dst[i] = src[i];
           }
@@ -238,6 +245,36 @@ __global__ void __launch_bounds__(kThreads) k_candidates_batch(const CandArgs* _
   candidates_body(sa, smem, blockIdx.x - block_start[lo], block_start[lo + 1] - block_start[lo]);
 }
 
+// Def. 1 for many planning problems: each instance's graph Z for its
+// current iteration, written once to global memory so that its graph
+// blocks gather from it instead of regenerating it.
+__global__ void __launch_bounds__(kThreads) k_graph_Z_batch(const CandArgs* __restrict__ args,
+                                                            float* const* __restrict__ Zs,
+                                                            const int* __restrict__ block_start,
+                                                            int count) {
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (block_start[mid] <= (int)blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  const CandArgs& a = args[lo];
+  const int M = a.dm.M, N = a.dm.N, n = a.dm.n;
+  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
+  const int ng = (n + 3) >> 2;
+  float* Z = Zs[lo];
+  for (int e = (blockIdx.x - block_start[lo]) * blockDim.x + threadIdx.x; e < M * N * ng;
+       e += (block_start[lo + 1] - block_start[lo]) * blockDim.x) {
+    const int node = e / ng, g = e - node * ng;
+    const uint4 r = philox(make_uint4((uint32_t)node, (uint32_t)g, iter, kTagGraph), a.key);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int i = 4 * g + w;
+      if (i < n) Z[node * n + i] = fmaf(a.umax[i] - a.umin[i], unit24(pick(r, w)), a.umin[i]);
+    }
+  }
+}
+
 // Def. 1 / Alg. 1 outputs for inspection: Z, I and C written to global memory.
 __global__ void k_sample_tensor(Dims dm, Key key, uint32_t iter, CandArgs box, float* Z,
                                 int32_t* I, float* C) {
@@ -271,7 +308,7 @@ size_t candidates_smem_bytes(const CandArgs& a) {
   const Dims& d = a.dm;
   size_t f = 0;
   if (a.graph_blocks > 0) {
-    if (!a.C_in) f += (size_t)d.M * d.N * d.n;
+    if (!a.C_in && !a.Z_global) f += (size_t)d.M * d.N * d.n;
     f += (size_t)a.paths_per_block * d.M * d.n;
     if (a.interp == MTP_INTERP_AKIMA)  // coefficients, piece slopes, knot slopes
       f += (size_t)a.paths_per_block * d.n * ((d.M - 1) * 5 + d.M);
@@ -300,6 +337,13 @@ cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t 
   const int grid = a.graph_blocks + local_blocks;
   if (grid <= 0) return cudaSuccess;
   k_candidates<<<grid, kThreads, candidates_smem_bytes(a), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_graph_Z_batch(const CandArgs* d_args, float* const* d_Z, const int* d_block_start,
+                                 int count, int total_blocks, cudaStream_t s) {
+  if (total_blocks <= 0) return cudaSuccess;
+  k_graph_Z_batch<<<total_blocks, kThreads, 0, s>>>(d_args, d_Z, d_block_start, count);
   return cudaGetLastError();
 }
 

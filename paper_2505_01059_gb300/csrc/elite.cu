@@ -223,51 +223,64 @@ __global__ void __launch_bounds__(kSelThreads) k_select_batch(const SelectArgs* 
   select_body(a, sm_raw);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+// G-lane reduction within aligned groups of a warp
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Warp `gw` of `warps` warps given to one planning problem.
-__device__ __forceinline__ void update_body(const UpdateArgs& a, int gw, int warps) {
+// Groups of G lanes each own one (t, i) element: lanes split the elites and
+// reduce with G-lane shuffles.  Thread `gt` of `threads` threads given to
+// one planning problem.  Many elements: G = 1 (no shuffles, fewest FP64 lane
+// operations); few elements: G = 32 (more lanes per element).
+template <int G>
+__device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int threads) {
   constexpr int kHeld = 8;  // elites per lane kept in registers between the passes
-  const int lane = threadIdx.x & 31;
+  const int sub = threadIdx.x & (G - 1);
   const int Hn = a.H * a.n;
   const bool cem = a.update_rule == MTP_UPDATE_PLAIN_CEM;
-  for (int e = gw; e < Hn; e += warps) {
+  // G == 1: thread gt owns elements gt, gt + threads, ... (no shuffles).
+  // G > 1: the loop runs warp-uniformly (threads is a multiple of 32) and
+  // groups past the end idle through the shuffles.
+  const int per_sweep = (G == 1) ? threads : (threads / 32) * (32 / G);
+  const int first = (G == 1) ? gt : (gt / 32) * (32 / G) + (threadIdx.x & 31) / G;
+  const int sweeps = (G == 1) ? 0 : (Hn - (gt / 32) * (32 / G) + per_sweep - 1) / per_sweep;
+  for (int it = 0, e = first; (G == 1) ? (e < Hn) : (it < sweeps); ++it, e += per_sweep) {
+    const bool valid = e < Hn;
     double held[kHeld];
     double m1 = 0.0;
 #pragma unroll
     for (int q = 0; q < kHeld; ++q) {
-      const int k = lane + 32 * q;
+      const int k = sub + G * q;
       held[q] = 0.0;
-      if (k < a.E) {
+      if (valid && k < a.E) {
         held[q] = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e);
         m1 += cem ? held[q] : a.weight[k] * held[q];
       }
     }
-    for (int k = lane + 32 * kHeld; k < a.E; k += 32) {
+    for (int k = sub + G * kHeld; valid && k < a.E; k += G) {
       const double u = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e);
       m1 += cem ? u : a.weight[k] * u;
     }
-    m1 = warp_sum(m1);
+    m1 = group_sum<G>(m1);
     if (cem) m1 /= (double)a.E;
     double v = 0.0;
 #pragma unroll
     for (int q = 0; q < kHeld; ++q) {
-      const int k = lane + 32 * q;
-      if (k < a.E) {
+      const int k = sub + G * q;
+      if (valid && k < a.E) {
         const double dlt = held[q] - m1;
         v += cem ? dlt * dlt : a.weight[k] * dlt * dlt;
       }
     }
-    for (int k = lane + 32 * kHeld; k < a.E; k += 32) {
+    for (int k = sub + G * kHeld; valid && k < a.E; k += G) {
       const double dlt = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - m1;
       v += cem ? dlt * dlt : a.weight[k] * dlt * dlt;
     }
-    v = warp_sum(v);
-    if (lane == 0) {
+    v = group_sum<G>(v);
+    if (valid && sub == 0) {
       if (cem) {
         const double s1 = a.E > 1 ? sqrt(v / (double)(a.E - 1)) : 0.0;
         const double mn = a.alpha * a.mu[e] + (1.0 - a.alpha) * m1;
@@ -288,27 +301,31 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int gw, int war
       }
     }
   }
-  if (a.d_iter && gw == 0 && lane == 0) *a.d_iter += 1u;
+  if (a.d_iter && gt == 0) *a.d_iter += 1u;
 }
 
+template <int G>
 __global__ void __launch_bounds__(128) k_update(const UpdateArgs a) {
-  update_body(a, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+  update_body<G>(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-// Many planning problems: warp_start (count + 1 entries) holds each
-// instance's first warp.
+// Many planning problems: thread_start (count + 1 entries) holds each
+// instance's first thread.
+template <int G>
 __global__ void __launch_bounds__(128) k_update_batch(const UpdateArgs* __restrict__ args,
-                                                      const int* __restrict__ warp_start, int count) {
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (gw >= __ldg(warp_start + count)) return;
+                                                      const int* __restrict__ thread_start,
+                                                      int count) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt >= __ldg(thread_start + count)) return;
   int lo = 0, hi = count;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (__ldg(warp_start + mid) <= gw) lo = mid;
+    if (__ldg(thread_start + mid) <= gt) lo = mid;
     else hi = mid;
   }
   const UpdateArgs a = args[lo];
-  update_body(a, gw - __ldg(warp_start + lo), __ldg(warp_start + lo + 1) - __ldg(warp_start + lo));
+  update_body<G>(a, gt - __ldg(thread_start + lo),
+                 __ldg(thread_start + lo + 1) - __ldg(thread_start + lo));
 }
 
 __global__ void k_shift(double* mu, double* sigma, float* mu_f, float* sigma_f, int H, int n,
@@ -348,10 +365,12 @@ cudaError_t launch_select_batch(const SelectArgs* d_args, int count, size_t smem
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_warp_start, int count,
-                                int total_warps, cudaStream_t s) {
-  if (total_warps <= 0) return cudaSuccess;
-  k_update_batch<<<(total_warps + 3) / 4, 128, 0, s>>>(d_args, d_warp_start, count);
+// Each instance gets Hn threads (one lane per element): the batch has many
+// elements, so the FP64 work needs no cross-lane reductions.
+cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_thread_start, int count,
+                                int total_threads, cudaStream_t s) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_update_batch<1><<<(total_threads + 127) / 128, 128, 0, s>>>(d_args, d_thread_start, count);
   return cudaGetLastError();
 }
 
@@ -360,12 +379,22 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Lanes per element: enough (t, i) elements fill the GPU with one lane each;
+// otherwise split the elites over up to a warp per element.
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   const int Hn = a.H * a.n;
-  int blocks = (Hn + 3) / 4;  // 4 warps per block, one warp per element
-  if (blocks > 2432) blocks = 2432;
-  if (blocks < 1) blocks = 1;
-  k_update<<<blocks, 128, 0, s>>>(a);
+  int G = 1;
+  while (G < 32 && Hn * G < 152 * 256) G <<= 1;
+  const long long threads = (long long)Hn * G;
+  const int blocks = (int)((threads + 127) / 128);
+  switch (G) {
+    case 1: k_update<1><<<blocks, 128, 0, s>>>(a); break;
+    case 2: k_update<2><<<blocks, 128, 0, s>>>(a); break;
+    case 4: k_update<4><<<blocks, 128, 0, s>>>(a); break;
+    case 8: k_update<8><<<blocks, 128, 0, s>>>(a); break;
+    case 16: k_update<16><<<blocks, 128, 0, s>>>(a); break;
+    default: k_update<32><<<blocks, 128, 0, s>>>(a); break;
+  }
   return cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ struct mtp_handle {
   double* weight = nullptr;
   float* ustar = nullptr;
   float* x0 = nullptr;
+  float* Z = nullptr;  // (M, N, n) graph of the current iteration (batched planning)
   // replay
   cudaStream_t cap_stream = nullptr;
   std::map<int, cudaGraphExec_t> graphs;
@@ -346,7 +347,7 @@ void free_handle(mtp_handle* h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->basis, h->bfirst, h->seg, h->delta, h->mu, h->sigma, h->mu_f, h->sigma_f,
                   h->iter_dev,
-                  h->U, h->cost, h->elite, h->weight, h->ustar, h->x0};
+                  h->U, h->cost, h->elite, h->weight, h->ustar, h->x0, h->Z};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -412,7 +413,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
       (e = dalloc(&h->iter_dev, 1)) || (e = dalloc(&h->U, rowsz * dm.B)) ||
       (e = dalloc(&h->cost, dm.B)) || (e = dalloc(&h->elite, dm.E)) ||
       (e = dalloc(&h->weight, dm.E)) || (e = dalloc(&h->ustar, dm.n)) ||
-      (e = dalloc(&h->x0, dm.d)))
+      (e = dalloc(&h->x0, dm.d)) || (e = dalloc(&h->Z, (size_t)dm.M * dm.N * dm.n)))
     return err(cuda_fail(h, e, "cudaMalloc"));
   std::vector<double> mu(rowsz, p.mu_init), sg(rowsz, p.sigma_init);
   std::vector<float> muf(rowsz, (float)p.mu_init), sgf(rowsz, (float)p.sigma_init);
@@ -716,6 +717,9 @@ struct BatchGroup {
 struct mtp_batch {
   std::vector<mtp_handle*> hs;
   int device = 0;
+  float** d_Z = nullptr;       // each instance's graph buffer
+  int* d_z_start = nullptr;    // blocks of the graph kernel per instance
+  int z_blocks = 0;
   CandArgs* d_cand = nullptr;
   int* d_cand_start = nullptr;
   int cand_blocks = 0;
@@ -761,7 +765,8 @@ void free_batch(mtp_batch* b) {
     if (g.stream) cudaStreamDestroy(g.stream);
     if (g.done) cudaEventDestroy(g.done);
   }
-  void* ptrs[] = {b->d_cand, b->d_cand_start, b->d_sel, b->d_upd, b->d_warp_start,
+  void* ptrs[] = {b->d_Z, b->d_z_start, b->d_cand, b->d_cand_start, b->d_sel, b->d_upd,
+                  b->d_warp_start,
                   b->d_x0_dst, b->d_ustar_src, b->d_x0_off, b->d_us_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -786,6 +791,7 @@ cudaError_t launch_group(const BatchGroup& g, int block, cudaStream_t s) {
 cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
   cudaError_t e;
   const int count = (int)b->hs.size();
+  if ((e = launch_graph_Z_batch(b->d_cand, b->d_Z, b->d_z_start, count, b->z_blocks, s))) return e;
   if ((e = launch_candidates_batch(b->d_cand, b->d_cand_start, count, b->cand_blocks, b->cand_smem, s)))
     return e;
   if ((e = cudaEventRecord(b->fork_ev, s))) return e;
@@ -828,7 +834,8 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
   cudaError_t e;
   // candidates: per-instance arguments and block ranges
   std::vector<CandArgs> cand(count);
-  std::vector<int> cstart(count + 1, 0);
+  std::vector<int> cstart(count + 1, 0), zstart(count + 1, 0);
+  std::vector<float*> zptr(count);
   for (int i = 0; i < count; ++i) {
     mtp_handle* h = b->hs[i];
     const Dims& dm = h->dm;
@@ -840,6 +847,9 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
     c.U_local = h->U;
     c.local_rows = dm.L;
     c.U_mean = h->U + Hn * (dm.B - 1);
+    c.Z_global = h->Z;
+    zptr[i] = h->Z;
+    zstart[i + 1] = zstart[i] + (dm.M * dm.N * ((dm.n + 3) / 4) + 255) / 256;
     const long long items = ((long long)dm.L + 1) * (((long long)Hn + 3) / 4);
     const int local_blocks = (int)std::max<long long>(1, (items + 1023) / 1024);
     cand[i] = c;
@@ -847,7 +857,10 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
     b->cand_smem = std::max(b->cand_smem, candidates_smem_bytes(c));
   }
   b->cand_blocks = cstart[count];
-  if ((e = upload(&b->d_cand, cand)) || (e = upload(&b->d_cand_start, cstart))) return err(e, "batch upload");
+  b->z_blocks = zstart[count];
+  if ((e = upload(&b->d_cand, cand)) || (e = upload(&b->d_cand_start, cstart)) ||
+      (e = upload(&b->d_Z, zptr)) || (e = upload(&b->d_z_start, zstart)))
+    return err(e, "batch upload");
   // rollout groups by (dynamics, dimension)
   for (int i = 0; i < count; ++i) {
     mtp_handle* h = b->hs[i];
@@ -906,7 +919,7 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
     b->sel_smem = std::max(b->sel_smem, select_smem_bytes(dm.B, dm.E));
     upd[i] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
                         h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
-    wstart[i + 1] = wstart[i] + dm.H * dm.n;
+    wstart[i + 1] = wstart[i] + dm.H * dm.n;  // one update thread per (t, i) element
     x0dst[i] = h->x0;
     usrc[i] = h->ustar;
     b->x0_off[i + 1] = b->x0_off[i] + dm.d;

@@ -98,6 +98,8 @@ struct CandArgs {
   const float* delta;      // (H) offset of step t from the piece's left knot
   // graph rows
   const float* C_in;       // (P, M, n) given waypoints, or null to sample them
+  const float* Z_global;   // (M, N, n) graph already in global memory, or null to
+                           // regenerate it in each block's shared memory
   float* U_graph;          // output rows of the graph paths (graph_rows, H, n)
   int32_t graph_rows;
   int32_t graph_blocks;    // blocks [0, graph_blocks) make graph rows
@@ -186,6 +188,8 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 size_t select_smem_bytes(int B, int E);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 // batched forms: one launch over many planning problems
+cudaError_t launch_graph_Z_batch(const CandArgs* d_args, float* const* d_Z, const int* d_block_start,
+                                 int count, int total_blocks, cudaStream_t s);
 cudaError_t launch_candidates_batch(const CandArgs* d_args, const int* d_block_start, int count,
                                     int total_blocks, size_t smem, cudaStream_t s);
 cudaError_t launch_rollout_pointmass_batch(const RolloutArgs* d_ra, const PointMassModel* d_pm,

@@ -142,7 +142,8 @@ def test_sample_local(mtp, spec):
     UL = orc.local_samples(spec, it, mu, sigma)
     ref = np.clip(UL, lo, hi)
     eps = (UL - mu) / sigma
-    tol = 2e-6 * (np.abs(mu) + sigma * (1 + np.abs(eps))) + 1e-7
+    # FP32 Box-Muller with the SFU angle: |d eps| <= ~4e-7 x radius (radius < 6 here)
+    tol = 2e-6 * (np.abs(mu) + sigma * (1 + np.abs(eps))) + 3e-6 * sigma + 1e-7
     assert np.all(np.abs(Ug[:s["L"]] - ref) <= tol)
     assert np.allclose(Ug[-1], np.clip(mu, lo, hi), rtol=1e-7, atol=1e-7)
     mtp.mtp_destroy(h)
