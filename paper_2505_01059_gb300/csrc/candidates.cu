@@ -46,6 +46,47 @@ __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& e0, 
   e1 = -radius * sn;
 }
 
+// Local rows (Alg. 2 local sampling) and the mean row: block `lb` of
+// `nlb` blocks given to them; mu + sigma * eps, four elements of a row per
+// generator call.
+__device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int nlb) {
+  const Dims dm = a.dm;
+  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
+  const int n = dm.n;
+  const int Hn = dm.H * n;
+  const int G = (Hn + 3) >> 2;
+  const int items = a.local_rows * G + (a.U_mean ? G : 0);
+  const int stride = nlb * blockDim.x;
+  for (int e = lb * blockDim.x + threadIdx.x; e < items; e += stride) {
+    const int row = e / G;
+    const int q = e - row * G;
+    int i = (4 * q) % n;  // control dimension of element 4q, then advanced in place
+    if (row < a.local_rows) {
+      const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
+      float eps[4];
+      box_muller(r.x, r.y, eps[0], eps[1]);
+      box_muller(r.z, r.w, eps[2], eps[3]);
+      float* dst = a.U_local + (size_t)row * Hn;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int el = 4 * q + w;
+        if (el < Hn) {
+          const float u = fmaf(a.sigma[el], eps[w], a.mu[el]);
+          dst[el] = clamp_box(u, a.umin[i], a.umax[i]);
+        }
+        if (++i == n) i = 0;
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int el = 4 * q + w;
+        if (el < Hn) a.U_mean[el] = clamp_box(a.mu[el], a.umin[i], a.umax[i]);
+        if (++i == n) i = 0;
+      }
+    }
+  }
+}
+
 // One block of candidate generation for one planning problem: block `bid`
 // of `nblocks` blocks that instance is given (graph blocks first).
 __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, int bid,
@@ -185,38 +226,7 @@ __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, 
     return;
   }
 
-  // Local rows: mu + sigma * eps, four elements of a row per generator call.
-  const int G = (Hn + 3) >> 2;
-  const int items = a.local_rows * G + (a.U_mean ? G : 0);
-  const int stride = (nblocks - a.graph_blocks) * blockDim.x;
-  for (int e = (bid - a.graph_blocks) * blockDim.x + threadIdx.x; e < items; e += stride) {
-    const int row = e / G;
-    const int q = e - row * G;
-    int i = (4 * q) % n;  // control dimension of element 4q, then advanced in place
-    if (row < a.local_rows) {
-      const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
-      float eps[4];
-      box_muller(r.x, r.y, eps[0], eps[1]);
-      box_muller(r.z, r.w, eps[2], eps[3]);
-      float* dst = a.U_local + (size_t)row * Hn;
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int el = 4 * q + w;
-        if (el < Hn) {
-          const float u = fmaf(a.sigma[el], eps[w], a.mu[el]);
-          dst[el] = clamp_box(u, a.umin[i], a.umax[i]);
-        }
-        if (++i == n) i = 0;
-      }
-    } else {
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int el = 4 * q + w;
-        if (el < Hn) a.U_mean[el] = clamp_box(a.mu[el], a.umin[i], a.umax[i]);
-        if (++i == n) i = 0;
-      }
-    }
-  }
+  local_rows_body(a, bid - a.graph_blocks, nblocks - a.graph_blocks);
 }
 
 __global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
@@ -243,6 +253,21 @@ __global__ void __launch_bounds__(kThreads) k_candidates_batch(const CandArgs* _
   for (int w = threadIdx.x; w < (int)(sizeof(CandArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
   __syncthreads();
   candidates_body(sa, smem, blockIdx.x - block_start[lo], block_start[lo + 1] - block_start[lo]);
+}
+
+// Local rows of many planning problems (no shared memory, so the blocks
+// pack densely); local_start (count + 1 entries) gives each instance's
+// first local block.
+__global__ void __launch_bounds__(kThreads) k_local_batch(const CandArgs* __restrict__ args,
+                                                          const int* __restrict__ local_start,
+                                                          int count) {
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (local_start[mid] <= (int)blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  local_rows_body(args[lo], blockIdx.x - local_start[lo], local_start[lo + 1] - local_start[lo]);
 }
 
 // Def. 1 for many planning problems: each instance's graph Z for its
@@ -337,6 +362,13 @@ cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t 
   const int grid = a.graph_blocks + local_blocks;
   if (grid <= 0) return cudaSuccess;
   k_candidates<<<grid, kThreads, candidates_smem_bytes(a), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_batch(const CandArgs* d_args, const int* d_local_start, int count,
+                               int total_blocks, cudaStream_t s) {
+  if (total_blocks <= 0) return cudaSuccess;
+  k_local_batch<<<total_blocks, kThreads, 0, s>>>(d_args, d_local_start, count);
   return cudaGetLastError();
 }
 

@@ -359,42 +359,38 @@ cudaError_t init_select_attributes() {
                               200 * 1024);
 }
 
+// Every update, alone or batched, gives each (t, i) element kUpdateLanes
+// lanes, so an instance's FP64 reduction order -- and its result -- does not
+// depend on what it is launched with.
+constexpr int kUpdateLanes = 4;
+
 cudaError_t launch_select_batch(const SelectArgs* d_args, int count, size_t smem, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_select_batch<<<count, kSelThreads, smem, s>>>(d_args);
   return cudaGetLastError();
 }
 
-// Each instance gets Hn threads (one lane per element): the batch has many
-// elements, so the FP64 work needs no cross-lane reductions.
+// thread_start gives each instance a whole number of warps (see
+// update_threads), so no warp straddles two instances.
 cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_thread_start, int count,
                                 int total_threads, cudaStream_t s) {
   if (total_threads <= 0) return cudaSuccess;
-  k_update_batch<1><<<(total_threads + 127) / 128, 128, 0, s>>>(d_args, d_thread_start, count);
+  k_update_batch<kUpdateLanes><<<(total_threads + 127) / 128, 128, 0, s>>>(d_args, d_thread_start,
+                                                                          count);
   return cudaGetLastError();
 }
+
+int update_threads(int H, int n) { return ((H * n * kUpdateLanes + 31) / 32) * 32; }
 
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
   k_select<<<1, kSelThreads, select_smem_bytes(a.B, a.E), s>>>(a);
   return cudaGetLastError();
 }
 
-// Lanes per element: enough (t, i) elements fill the GPU with one lane each;
-// otherwise split the elites over up to a warp per element.
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
-  const int Hn = a.H * a.n;
-  int G = 1;
-  while (G < 32 && Hn * G < 152 * 256) G <<= 1;
-  const long long threads = (long long)Hn * G;
+  const long long threads = (long long)a.H * a.n * kUpdateLanes;
   const int blocks = (int)((threads + 127) / 128);
-  switch (G) {
-    case 1: k_update<1><<<blocks, 128, 0, s>>>(a); break;
-    case 2: k_update<2><<<blocks, 128, 0, s>>>(a); break;
-    case 4: k_update<4><<<blocks, 128, 0, s>>>(a); break;
-    case 8: k_update<8><<<blocks, 128, 0, s>>>(a); break;
-    case 16: k_update<16><<<blocks, 128, 0, s>>>(a); break;
-    default: k_update<32><<<blocks, 128, 0, s>>>(a); break;
-  }
+  k_update<kUpdateLanes><<<blocks, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -721,7 +721,9 @@ struct mtp_batch {
   int* d_z_start = nullptr;    // blocks of the graph kernel per instance
   int z_blocks = 0;
   CandArgs* d_cand = nullptr;
-  int* d_cand_start = nullptr;
+  int* d_cand_start = nullptr;  // graph blocks per instance
+  int* d_local_start = nullptr;  // local-row blocks per instance
+  int local_blocks = 0;
   int cand_blocks = 0;
   size_t cand_smem = 0;
   std::vector<BatchGroup> groups;
@@ -765,7 +767,8 @@ void free_batch(mtp_batch* b) {
     if (g.stream) cudaStreamDestroy(g.stream);
     if (g.done) cudaEventDestroy(g.done);
   }
-  void* ptrs[] = {b->d_Z, b->d_z_start, b->d_cand, b->d_cand_start, b->d_sel, b->d_upd,
+  void* ptrs[] = {b->d_Z, b->d_z_start, b->d_cand, b->d_cand_start, b->d_local_start, b->d_sel,
+                  b->d_upd,
                   b->d_warp_start,
                   b->d_x0_dst, b->d_ustar_src, b->d_x0_off, b->d_us_off};
   for (void* p : ptrs)
@@ -794,6 +797,7 @@ cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
   if ((e = launch_graph_Z_batch(b->d_cand, b->d_Z, b->d_z_start, count, b->z_blocks, s))) return e;
   if ((e = launch_candidates_batch(b->d_cand, b->d_cand_start, count, b->cand_blocks, b->cand_smem, s)))
     return e;
+  if ((e = launch_local_batch(b->d_cand, b->d_local_start, count, b->local_blocks, s))) return e;
   if ((e = cudaEventRecord(b->fork_ev, s))) return e;
   for (auto& g : b->groups) {
     if ((e = cudaStreamWaitEvent(g.stream, b->fork_ev, 0))) return e;
@@ -834,7 +838,7 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
   cudaError_t e;
   // candidates: per-instance arguments and block ranges
   std::vector<CandArgs> cand(count);
-  std::vector<int> cstart(count + 1, 0), zstart(count + 1, 0);
+  std::vector<int> cstart(count + 1, 0), zstart(count + 1, 0), lstart(count + 1, 0);
   std::vector<float*> zptr(count);
   for (int i = 0; i < count; ++i) {
     mtp_handle* h = b->hs[i];
@@ -853,12 +857,15 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
     const long long items = ((long long)dm.L + 1) * (((long long)Hn + 3) / 4);
     const int local_blocks = (int)std::max<long long>(1, (items + 1023) / 1024);
     cand[i] = c;
-    cstart[i + 1] = cstart[i] + c.graph_blocks + local_blocks;
+    cstart[i + 1] = cstart[i] + c.graph_blocks;  // graph blocks only: local rows run apart
+    lstart[i + 1] = lstart[i] + local_blocks;
     b->cand_smem = std::max(b->cand_smem, candidates_smem_bytes(c));
   }
   b->cand_blocks = cstart[count];
   b->z_blocks = zstart[count];
+  b->local_blocks = lstart[count];
   if ((e = upload(&b->d_cand, cand)) || (e = upload(&b->d_cand_start, cstart)) ||
+      (e = upload(&b->d_local_start, lstart)) ||
       (e = upload(&b->d_Z, zptr)) || (e = upload(&b->d_z_start, zstart)))
     return err(e, "batch upload");
   // rollout groups by (dynamics, dimension)
@@ -919,7 +926,7 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
     b->sel_smem = std::max(b->sel_smem, select_smem_bytes(dm.B, dm.E));
     upd[i] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
                         h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
-    wstart[i + 1] = wstart[i] + dm.H * dm.n;  // one update thread per (t, i) element
+    wstart[i + 1] = wstart[i] + update_threads(dm.H, dm.n);
     x0dst[i] = h->x0;
     usrc[i] = h->ustar;
     b->x0_off[i + 1] = b->x0_off[i] + dm.d;

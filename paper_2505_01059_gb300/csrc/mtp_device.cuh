@@ -188,6 +188,8 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 size_t select_smem_bytes(int B, int E);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 // batched forms: one launch over many planning problems
+cudaError_t launch_local_batch(const CandArgs* d_args, const int* d_local_start, int count,
+                               int total_blocks, cudaStream_t s);
 cudaError_t launch_graph_Z_batch(const CandArgs* d_args, float* const* d_Z, const int* d_block_start,
                                  int count, int total_blocks, cudaStream_t s);
 cudaError_t launch_candidates_batch(const CandArgs* d_args, const int* d_block_start, int count,
@@ -199,8 +201,9 @@ cudaError_t launch_rollout_chain_batch(const RolloutArgs* d_ra, const ChainModel
                                        const int* d_row_start, int count, int total_rows,
                                        int links, int block, cudaStream_t s);
 cudaError_t launch_select_batch(const SelectArgs* d_args, int count, size_t smem, cudaStream_t s);
-cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_warp_start, int count,
-                                int total_warps, cudaStream_t s);
+cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_thread_start, int count,
+                                int total_threads, cudaStream_t s);
+int update_threads(int H, int n);  // threads one instance's update gets in a batch
 cudaError_t launch_scatter(const float* packed, float* const* d_dst, const int* d_off, int count,
                            cudaStream_t s);
 cudaError_t launch_gather(const float* const* d_src, const int* d_off, float* packed, int count,
