@@ -223,21 +223,36 @@ __global__ void __launch_bounds__(kSelThreads) k_select_batch(const SelectArgs* 
   select_body(a, sm_raw);
 }
 
-// G-lane reduction within aligned groups of a warp
+// The FP64 sums over elites follow one canonical order for every launch
+// shape: elite k feeds virtual lane k mod 32 (in increasing k), and the 32
+// virtual lanes are combined by the butterfly o = 16, 8, 4, 2, 1.  A group of
+// G physical lanes gives each lane the 32 / G virtual lanes v = sub + G j; the
+// butterfly steps o >= G pair virtual lanes held by the same lane and run in
+// registers, the steps o < G run as shuffles.  Every pairwise add is the same
+// (a + b == b + a), so the result is bit-identical for any G.
 template <int G>
-__device__ __forceinline__ double group_sum(double v) {
+__device__ __forceinline__ double canonical_sum(double (&part)[32 / G]) {
+  constexpr int P = 32 / G;
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o >= G && o >= 1; o >>= 1) {
+    constexpr int dummy = 0;
+    (void)dummy;
+    const int sj = o / G;
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      if ((j & sj) == 0) part[j] = part[j] + part[j ^ sj];
+  }
+  double v = part[0];
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = v + __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Groups of G lanes each own one (t, i) element: lanes split the elites and
-// reduce with G-lane shuffles.  Thread `gt` of `threads` threads given to
-// one planning problem.  Many elements: G = 1 (no shuffles, fewest FP64 lane
-// operations); few elements: G = 32 (more lanes per element).
+// Groups of G lanes each own one (t, i) element.  Thread `gt` of `threads`
+// threads given to one planning problem.
 template <int G>
 __device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int threads) {
-  constexpr int kHeld = 8;  // elites per lane kept in registers between the passes
+  constexpr int P = 32 / G;
   const int sub = threadIdx.x & (G - 1);
   const int Hn = a.H * a.n;
   const bool cem = a.update_rule == MTP_UPDATE_PLAIN_CEM;
@@ -249,37 +264,28 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int thr
   const int sweeps = (G == 1) ? 0 : (Hn - (gt / 32) * (32 / G) + per_sweep - 1) / per_sweep;
   for (int it = 0, e = first; (G == 1) ? (e < Hn) : (it < sweeps); ++it, e += per_sweep) {
     const bool valid = e < Hn;
-    double held[kHeld];
-    double m1 = 0.0;
+    double part[P];
 #pragma unroll
-    for (int q = 0; q < kHeld; ++q) {
-      const int k = sub + G * q;
-      held[q] = 0.0;
-      if (valid && k < a.E) {
-        held[q] = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e);
-        m1 += cem ? held[q] : a.weight[k] * held[q];
-      }
+    for (int j = 0; j < P; ++j) {
+      part[j] = 0.0;
+      if (valid)
+        for (int k = sub + G * j; k < a.E; k += 32) {
+          const double u = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e);
+          part[j] = cem ? part[j] + u : fma(a.weight[k], u, part[j]);
+        }
     }
-    for (int k = sub + G * kHeld; valid && k < a.E; k += G) {
-      const double u = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e);
-      m1 += cem ? u : a.weight[k] * u;
-    }
-    m1 = group_sum<G>(m1);
+    double m1 = canonical_sum<G>(part);
     if (cem) m1 /= (double)a.E;
-    double v = 0.0;
 #pragma unroll
-    for (int q = 0; q < kHeld; ++q) {
-      const int k = sub + G * q;
-      if (valid && k < a.E) {
-        const double dlt = held[q] - m1;
-        v += cem ? dlt * dlt : a.weight[k] * dlt * dlt;
-      }
+    for (int j = 0; j < P; ++j) {
+      part[j] = 0.0;
+      if (valid)
+        for (int k = sub + G * j; k < a.E; k += 32) {
+          const double dlt = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - m1;
+          part[j] = cem ? fma(dlt, dlt, part[j]) : fma(a.weight[k] * dlt, dlt, part[j]);
+        }
     }
-    for (int k = sub + G * kHeld; valid && k < a.E; k += G) {
-      const double dlt = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - m1;
-      v += cem ? dlt * dlt : a.weight[k] * dlt * dlt;
-    }
-    v = group_sum<G>(v);
+    const double v = canonical_sum<G>(part);
     if (valid && sub == 0) {
       if (cem) {
         const double s1 = a.E > 1 ? sqrt(v / (double)(a.E - 1)) : 0.0;
@@ -359,38 +365,42 @@ cudaError_t init_select_attributes() {
                               200 * 1024);
 }
 
-// Every update, alone or batched, gives each (t, i) element kUpdateLanes
-// lanes, so an instance's FP64 reduction order -- and its result -- does not
-// depend on what it is launched with.
-constexpr int kUpdateLanes = 4;
-
 cudaError_t launch_select_batch(const SelectArgs* d_args, int count, size_t smem, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_select_batch<<<count, kSelThreads, smem, s>>>(d_args);
   return cudaGetLastError();
 }
 
-// thread_start gives each instance a whole number of warps (see
-// update_threads), so no warp straddles two instances.
+// Batches have many (t, i) elements: one lane each, no cross-lane sums.
 cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_thread_start, int count,
                                 int total_threads, cudaStream_t s) {
   if (total_threads <= 0) return cudaSuccess;
-  k_update_batch<kUpdateLanes><<<(total_threads + 127) / 128, 128, 0, s>>>(d_args, d_thread_start,
-                                                                          count);
+  k_update_batch<1><<<(total_threads + 127) / 128, 128, 0, s>>>(d_args, d_thread_start, count);
   return cudaGetLastError();
 }
 
-int update_threads(int H, int n) { return ((H * n * kUpdateLanes + 31) / 32) * 32; }
+int update_threads(int H, int n) { return H * n; }
 
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
   k_select<<<1, kSelThreads, select_smem_bytes(a.B, a.E), s>>>(a);
   return cudaGetLastError();
 }
 
+// Lanes per element: as many as keep roughly 38K threads busy, up to a warp.
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
-  const long long threads = (long long)a.H * a.n * kUpdateLanes;
+  const int Hn = a.H * a.n;
+  int G = 1;
+  while (G < 32 && (long long)Hn * G < 152 * 256) G <<= 1;
+  const long long threads = (long long)Hn * G;
   const int blocks = (int)((threads + 127) / 128);
-  k_update<kUpdateLanes><<<blocks, 128, 0, s>>>(a);
+  switch (G) {
+    case 1: k_update<1><<<blocks, 128, 0, s>>>(a); break;
+    case 2: k_update<2><<<blocks, 128, 0, s>>>(a); break;
+    case 4: k_update<4><<<blocks, 128, 0, s>>>(a); break;
+    case 8: k_update<8><<<blocks, 128, 0, s>>>(a); break;
+    case 16: k_update<16><<<blocks, 128, 0, s>>>(a); break;
+    default: k_update<32><<<blocks, 128, 0, s>>>(a); break;
+  }
   return cudaGetLastError();
 }
 
