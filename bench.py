@@ -42,6 +42,8 @@ def workload(name: str) -> dict:
         return W.chain()
     if name == "pointmass2":
         return W.pointmass()
+    if name == "legged16":
+        return W.legged()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -65,6 +67,18 @@ def flops_per_step(spec: dict) -> int:
         solves = 2 * L * L
         integrate = 4 * L
         return cost + rhs + mass_matrix + velocity + chol + solves + integrate
+    if spec["dyn"] == "legged":
+        L = spec["n_links"]
+        pairs = L * (L - 1) // 2
+        cost = 2 * (L - 1) + 14                 # base height / pitch / velocity, torque penalty
+        forces = 3 * L + 4 * L                  # torque and gravity terms; tip position / velocity
+        contact_walk = 10 * L                   # back-walk of the contact points and their moments
+        velocity = 21 * L                       # prefix / suffix velocity terms
+        schur = 6 * L + 4 * pairs               # Schur right-hand side and matrix
+        chol = L * (L - 1) + sum((L - 1 - j) * (2 * j + 1) for j in range(L))
+        solves = 2 * L * L
+        integrate = 4 * L + 4 * L + 8
+        return cost + forces + contact_walk + velocity + schur + chol + solves + integrate
     if spec["dyn"] == "pointmass":
         k = spec["n"]
         return 9 * k + 8 + len(spec.get("obs_c", [])) * (3 * k + 3)
@@ -428,7 +442,10 @@ def run_ours(args, spec, name):
     peak_mhz = pk.get("sm_max_mhz", 2070.0)
     peak = fp32_peak_tflops(peak_mhz)
     kernel_file = "rollout.cu"
-    summary = {"chain": "rollout_chain7_arm_B4096.txt", "pointmass": "rollout_pointmass2_B512.txt"}[spec["dyn"]]
+    summary = {"chain": "rollout_chain7_arm_B4096.txt", "pointmass": "rollout_pointmass2_B512.txt",
+               "legged": "rollout_legged16_B16384.txt"}[spec["dyn"]]
+    if spec["dyn"] == "legged":
+        kernel_file = "legged.cu"
     traffic = profiled_traffic(kernel_file, summary)
     share = {st: ms / max(sum(stage_ms), 1e-12) for st, ms in
              zip(("generate", "rollout", "select", "update"), stage_ms)}
@@ -481,7 +498,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="arm7", choices=["arm7", "pointmass2", "batch"])
+    ap.add_argument("--workload", default="arm7", choices=["arm7", "pointmass2", "legged16", "batch"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--reference-rows", type=int, default=512)

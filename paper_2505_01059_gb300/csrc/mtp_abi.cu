@@ -133,7 +133,13 @@ mtp_status validate(const mtp_problem& p) {
     for (int j = 0; j < p.n_links; ++j)
       if (!(p.link_mass[j] > 0.f) || !(p.link_length[j] > 0.f)) return bad("chain: link mass/length must be > 0");
   } else if (p.dyn == MTP_DYN_LEGGED) {
-    return fail(nullptr, MTP_ERR_UNSUPPORTED, "legged dynamics are not built into this library yet");
+    if (p.n_links < 2 || p.n_links > 16) return bad("legged: n_links must be in 2..16");
+    if (p.ctrl_dim != p.n_links - 1 || p.state_dim != 2 * (p.n_links + 2))
+      return bad("legged: ctrl_dim must be n_links-1 and state_dim 2*(n_links+2)");
+    for (int j = 0; j < p.n_links; ++j)
+      if (!(p.link_mass[j] > 0.f) || !(p.link_length[j] > 0.f)) return bad("legged: link mass/length must be > 0");
+    if (!(p.k_contact >= 0.f) || !(p.c_contact >= 0.f) || !(p.mu_friction >= 0.f) || !(p.v_slip > 0.f))
+      return bad("legged: need k, c, friction >= 0 and v_slip > 0");
   } else {
     return bad("unknown dyn");
   }
@@ -306,9 +312,30 @@ ChainModel chain_model(const mtp_problem& p) {
   return m;
 }
 
+LeggedModel legged_model(const mtp_problem& p) {
+  LeggedModel m{};
+  for (int j = 0; j < p.n_links; ++j) {
+    m.mass[j] = p.link_mass[j];
+    m.length[j] = p.link_length[j];
+  }
+  m.gravity = p.gravity;
+  m.k_contact = p.k_contact;
+  m.c_contact = p.c_contact;
+  m.mu_friction = p.mu_friction;
+  m.inv_v_slip = 1.f / p.v_slip;
+  for (int i = 0; i < 3; ++i) m.target[i] = p.target[i];
+  m.w_height = p.w_height;
+  m.w_vel = p.w_vel;
+  m.w_pitch = p.w_pitch;
+  m.w_ctrl = p.w_ctrl;
+  m.w_term = p.w_term;
+  return m;
+}
+
 cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
   const mtp_problem& p = h->pr;
   if (p.dyn == MTP_DYN_POINTMASS) return launch_rollout_pointmass(a, pointmass_model(p), s);
+  if (p.dyn == MTP_DYN_LEGGED) return launch_rollout_legged(a, legged_model(p), p.n_links, s);
   return launch_rollout_chain(a, chain_model(p), p.n_links, s);
 }
 
@@ -783,6 +810,9 @@ cudaError_t launch_group(const BatchGroup& g, int block, cudaStream_t s) {
     return launch_rollout_pointmass_batch(g.d_ra, static_cast<const PointMassModel*>(g.d_model),
                                           g.d_row_start, (int)g.members.size(), g.total_rows, g.n,
                                           block, s);
+  if (g.dyn == MTP_DYN_LEGGED)  // fixed 64-thread blocks (shared-memory staging)
+    return launch_rollout_legged_batch(g.d_ra, static_cast<const LeggedModel*>(g.d_model),
+                                       g.d_row_start, (int)g.members.size(), g.total_rows, g.n, s);
   return launch_rollout_chain_batch(g.d_ra, static_cast<const ChainModel*>(g.d_model),
                                     g.d_row_start, (int)g.members.size(), g.total_rows, g.n,
                                     block, s);
@@ -871,7 +901,7 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
   // rollout groups by (dynamics, dimension)
   for (int i = 0; i < count; ++i) {
     mtp_handle* h = b->hs[i];
-    const int key_n = h->pr.dyn == MTP_DYN_CHAIN ? h->pr.n_links : h->dm.n;
+    const int key_n = h->pr.dyn == MTP_DYN_POINTMASS ? h->dm.n : h->pr.n_links;
     BatchGroup* g = nullptr;
     for (auto& x : b->groups)
       if (x.dyn == h->pr.dyn && x.n == key_n) g = &x;
@@ -888,11 +918,13 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
     std::vector<int> rs(1, 0);
     std::vector<PointMassModel> pms;
     std::vector<ChainModel> cms;
+    std::vector<LeggedModel> lms;
     for (int i : g.members) {
       mtp_handle* h = b->hs[i];
       ra.push_back(rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, h->dm.B, h->cost));
       rs.push_back(rs.back() + ((h->dm.B + 31) / 32) * 32);  // whole warps per instance
       if (g.dyn == MTP_DYN_POINTMASS) pms.push_back(pointmass_model(h->pr));
+      else if (g.dyn == MTP_DYN_LEGGED) lms.push_back(legged_model(h->pr));
       else cms.push_back(chain_model(h->pr));
     }
     g.total_rows = rs.back();
@@ -901,6 +933,10 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
     if (g.dyn == MTP_DYN_POINTMASS) {
       PointMassModel* p = nullptr;
       if ((e = upload(&p, pms))) return err(e, "batch upload");
+      g.d_model = p;
+    } else if (g.dyn == MTP_DYN_LEGGED) {
+      LeggedModel* p = nullptr;
+      if ((e = upload(&p, lms))) return err(e, "batch upload");
       g.d_model = p;
     } else {
       ChainModel* p = nullptr;

@@ -144,6 +144,14 @@ struct ChainModel {
   float w_target, w_ctrl, w_term;
 };
 
+struct LeggedModel {
+  float mass[16], length[16];
+  float gravity;
+  float k_contact, c_contact, mu_friction, inv_v_slip;
+  float target[3];  // height, forward velocity, pitch
+  float w_height, w_vel, w_pitch, w_ctrl, w_term;
+};
+
 struct SelectArgs {
   const float* cost;  // (B)
   const float* U;     // (B, H, n)
@@ -184,6 +192,11 @@ cudaError_t launch_rollout_pointmass(const RolloutArgs& a, const PointMassModel&
                                      cudaStream_t s);
 cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int links,
                                  cudaStream_t s);
+cudaError_t launch_rollout_legged(const RolloutArgs& a, const LeggedModel& m, int links,
+                                  cudaStream_t s);
+cudaError_t launch_rollout_legged_batch(const RolloutArgs* d_ra, const LeggedModel* d_lm,
+                                        const int* d_row_start, int count, int total_rows,
+                                        int links, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 size_t select_smem_bytes(int B, int E);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);

@@ -13,63 +13,13 @@
 // g l_j beta_j cos(phi_j) and generalised forces tau_j - tau_{j+1}; the
 // SPD system is solved by an unrolled Cholesky.  Semi-implicit Euler in
 // (phi, w) equals semi-implicit Euler in the relative joint coordinates.
-#include "mtp_device.cuh"
+#include "rollout_common.cuh"
 
 namespace mtp {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kPrefetch = 4;  // control steps requested ahead of use
 
-
-// Compile-time loop: calls f(IC<i>) for i in [B, E), so every array index
-// derived from i is a constant and the arrays stay in registers.
-template <int V>
-struct IC {
-  static constexpr int value = V;
-};
-template <int B, int E>
-struct Unroll {
-  template <class F>
-  static __device__ __forceinline__ void run(F&& f) {
-    if constexpr (B < E) {
-      f(IC<B>{});
-      Unroll<B + 1, E>::run(f);
-    }
-  }
-};
-
-// Model scales of slots 0..S-1 for one model unit, four slots per generator
-// call (the same words draw() returns one at a time).
-template <int S>
-__device__ __forceinline__ void dr_scales(const RolloutArgs& a, uint32_t iter, uint32_t unit,
-                                          float (&out)[S]) {
-  if (a.dr_mode == MTP_DR_NONE) {
-#pragma unroll
-    for (int j = 0; j < S; ++j) out[j] = 1.f;
-    return;
-  }
-  const uint32_t tag = (a.dr_mode == MTP_DR_SHARED) ? kTagParamModel : kTagParamSample;
-  const float span = a.dr_hi - a.dr_lo;
-#pragma unroll
-  for (int g = 0; g < (S + 3) / 4; ++g) {
-    const uint4 r = philox(make_uint4(unit, (uint32_t)g, iter, tag), a.key);
-    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (4 * g + q < S) out[4 * g + q] = fmaf(span, unit24(w[q]), a.dr_lo);
-  }
-}
-
-// sin and cos of an absolute link angle: Cody-Waite reduction of x by 2 pi
-// (a two-term split of 2 pi) to [-pi, pi], then the SFU sine / cosine, whose
-// absolute error on that interval is about 4e-7.
-__device__ __forceinline__ void sincos_reduced(float x, float* s, float* c) {
-  const float k = rintf(x * 0.15915494309189535f);
-  float r = fmaf(-k, 6.28318548202514648f, x);
-  r = fmaf(-k, -1.7484556e-07f, r);
-  __sincosf(r, s, c);
-}
 
 // Threads per block: fill as many SMs as the batch allows (one thread per
 // candidate; small batches get one warp per block).
@@ -179,12 +129,6 @@ __device__ __forceinline__ void rollout_pm_body(const RolloutArgs& a, const Poin
 // ---------------------------------------------------------------------------
 // Planar serial chain under joint torques.
 // ---------------------------------------------------------------------------
-template <int NL>
-struct Tri {
-  static constexpr int size = NL * (NL + 1) / 2;
-  static __device__ __forceinline__ constexpr int at(int i, int j) { return i * (i + 1) / 2 + j; }
-};
-
 template <int NL>
 __device__ __forceinline__ void chain_tip(const float (&len)[NL], const float (&c)[NL],
                                           const float (&s)[NL], float& x, float& y) {
@@ -390,18 +334,6 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
   float cst = total / (float)models;
   if (!isfinite(cst)) cst = __int_as_float(0x7f800000);
   a.cost[r] = cst;
-}
-
-// Instance of global row g in a batch: row_start (count + 1 entries) holds
-// each instance's first row, rows padded to whole warps.
-__device__ __forceinline__ int batch_instance(const int* __restrict__ row_start, int count, int g) {
-  int lo = 0, hi = count;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(row_start + mid) <= g) lo = mid;
-    else hi = mid;
-  }
-  return lo;
 }
 
 template <int K>

@@ -451,3 +451,60 @@ def test_invalid_calls_rejected(mtp):
     with pytest.raises(ValueError):
         mtp.mtp_rollout_cost(h, 0, x0.cpu(), U, cost)
     mtp.mtp_destroy(h)
+
+
+# ----------------------------------------------------------------------------
+# Floating-base legged chain with ground contact
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("links,B,H,dr", [(16, 96, 256, "per_sample"), (5, 64, 200, "per_sample"),
+                                          (2, 32, 100, "none"), (9, 64, 64, "shared")])
+def test_legged_rollout_cost(mtp, links, B, H, dr):
+    spec = W.legged(links=links, B=B, H=H, E=4, dr_mode=dr, R=3)
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    U32 = _rand_U(spec, s["B"], links)
+    x0 = np.array(spec["x0"], np.float32)
+    cost = torch.empty(s["B"], device=DEV)
+    mtp.mtp_rollout_cost(h, 2, _t(x0), _t(U32), cost)
+    ref = orc.rollout_costs(spec, 2, x0.astype(np.float64), U32.astype(np.float64))
+    assert np.all(np.isfinite(ref))
+    assert _cost_close(_np(cost), ref) <= COST_RTOL
+    mtp.mtp_destroy(h)
+
+
+@pytest.mark.parametrize("links", [3, 16])
+def test_legged_states(mtp, links):
+    spec = W.legged(links=links, B=8, H=120, E=2)
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    rng = np.random.default_rng(links)
+    U = rng.uniform(-5, 5, size=(120, s["n"])).astype(np.float32)
+    x0 = np.array(spec["x0"], np.float32)
+    X = torch.empty(121, s["d"], device=DEV)
+    c = torch.empty(1, device=DEV)
+    mtp.mtp_rollout_states(h, 1, _t(x0), _t(U), 3, X, c)
+    Xr, Jr = orc.rollout_states(spec, 1, x0.astype(np.float64), U.astype(np.float64), 3)
+    assert np.abs(_np(X) - Xr).max() <= 1e-3 * max(1.0, np.abs(Xr).max())
+    assert _cost_close(_np(c), [Jr]) <= COST_RTOL
+    mtp.mtp_destroy(h)
+
+
+def test_legged_plan_step_teacher_forced(mtp):
+    spec = W.legged(links=6, B=256, H=64, M=6, N=16, E=16)
+    h = mtp.mtp_create(spec)
+    x0 = np.array(spec["x0"], np.float64)
+    u = torch.empty(h.sizes["n"], device=DEV)
+    buf = mtp.mtp_get_buffers(h)
+    for k in range(2):
+        mu, sigma, it = mtp.mtp_get_state(h)
+        mtp.mtp_plan_step(h, _t(x0), 1, u)
+        torch.cuda.synchronize()
+        Ug = _np(torch.as_tensor(buf["U"], device=DEV))
+        cg = _np(torch.as_tensor(buf["cost"], device=DEV))
+        eg = _np(torch.as_tensor(buf["elite"], device=DEV), np.int32)
+        ref = orc.plan_iteration(spec, k, x0, mu, sigma)
+        assert np.abs(Ug - ref["U"]).max() <= 2e-5 * _range(spec).max()
+        assert _cost_close(cg, orc.rollout_costs(spec, k, x0, Ug)) <= COST_RTOL
+        assert np.array_equal(eg, orc.top_e(cg.astype(np.float64), h.sizes["E"]))
+    mtp.mtp_destroy(h)
