@@ -492,14 +492,84 @@ def run_ours(args, spec, name):
         pg.destroy_process_group()
 
 
+def run_serve(args):
+    """The re-plan server under closed-loop load: every robot resubmits as
+    soon as its previous control arrives (host state in, u* out through the
+    C ABI), so cycles of up to --max-batch robots keep two in flight."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2505_01059_gb300 import _build, mtp
+    from paper_2505_01059_gb300 import workloads as W
+    _build.build_library()
+    mtp.load_library()
+    torch.cuda.set_device(0)
+    specs = W.robots(count=args.instances)
+    srv = mtp.mtp_server_create(max_batch=args.max_batch, iters_per_request=1, shift_after=1,
+                                max_queue=2, max_robots=len(specs))
+    ids = [mtp.mtp_server_register(srv, s) for s in specs]
+    rng = np.random.default_rng(7)
+    x0 = [(np.asarray(s["x0"]) + rng.uniform(-0.1, 0.1, size=s["d"])).astype(np.float32)
+          for s in specs]
+    outs = [np.empty(s["n"], dtype=np.float32) for s in specs]
+    rounds = max(3, min(args.steps, 400))
+
+    def closed_loop(k):
+        tickets = [mtp.mtp_submit(srv, r, x0[r]) for r in ids]
+        for _ in range(k - 1):
+            for r in ids:
+                if mtp.mtp_poll(srv, tickets[r], outs[r], 60.0) != 0:
+                    raise RuntimeError("serving request timed out")
+                tickets[r] = mtp.mtp_submit(srv, r, x0[r])
+        for r in ids:
+            if mtp.mtp_poll(srv, tickets[r], outs[r], 60.0) != 0:
+                raise RuntimeError("serving request timed out")
+
+    closed_loop(args.warmup)
+    s0 = mtp.mtp_server_get_stats(srv)
+    with ClockSampler(0) as clocks:
+        t0 = time.perf_counter()
+        closed_loop(rounds)
+        dt = time.perf_counter() - t0
+    s1 = mtp.mtp_server_get_stats(srv)
+    n_req = s1["completed"] - s0["completed"]
+    cycles = s1["cycles"] - s0["cycles"]
+    steps_per_round = sum(s["B"] * s["H"] for s in specs)
+    value = steps_per_round * rounds / dt
+    bytes_in = sum(4 * s["d"] for s in specs)
+    bytes_out = sum(4 * s["n"] for s in specs)
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": rounds,
+        "warmup": args.warmup, "ms_per_step": dt / rounds * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"re-plan server, {len(specs)} robots (2-D point masses and "
+                               f"3..9-link arms, H 64..128, B 1024..4096), 1 iteration + shift "
+                               f"per request, max_batch {args.max_batch}, closed loop",
+                   "l2": "not flushed: the working set of all robots (U tensors) exceeds L2",
+                   "step": "one request per robot"},
+        "requests_per_s": n_req / dt,
+        "latency_p50_ms": s1["p50_latency_s"] * 1e3,
+        "latency_p99_ms": s1["p99_latency_s"] * 1e3,
+        "mean_robots_per_cycle": n_req / max(cycles, 1),
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": bytes_in,
+                "d2h_bytes_per_step": bytes_out},
+        "clocks": clocks.summary(), "baseline_metric": BASELINE_METRIC,
+    }
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="arm7", choices=["arm7", "pointmass2", "legged16", "batch"])
+    ap.add_argument("--workload", default="arm7", choices=["arm7", "pointmass2", "legged16", "batch", "serve"])
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--max-batch", type=int, default=128)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--reference-rows", type=int, default=512)
     ap.add_argument("--reference-seconds", type=float, default=90.0)
@@ -508,6 +578,9 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     spec = workload(args.workload)
     if args.impl == "reference":

@@ -45,7 +45,7 @@ typedef enum {
   MTP_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
   MTP_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed */
   MTP_ERR_CUDA = 3,          /* a CUDA runtime call failed (text in mtp_last_error) */
-  MTP_ERR_ADMISSION = 4,     /* serving: the request does not fit the memory budget */
+  MTP_ERR_ADMISSION = 4,     /* serving: over the memory budget, robot count or queue depth */
   MTP_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
   MTP_ERR_NOT_READY = 6,     /* serving: the result is not there yet */
   MTP_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
@@ -248,8 +248,22 @@ mtp_status mtp_batch_destroy(mtp_batch* b);
  * count + 1 entries (the last is the total length). */
 mtp_status mtp_batch_layout(const mtp_batch* b, int32_t* x0_offset, int32_t* ustar_offset);
 
+/* A batch with device tables for up to `capacity` instances and none filled
+ * yet: mtp_batch_fill gives it its instances, as often as needed, without
+ * allocating.  Errors as mtp_batch_create. */
+mtp_status mtp_batch_reserve(int32_t capacity, mtp_batch** out);
+
+/* Replaces the batch's instances by `count` (1 .. capacity) distinct handles
+ * on the batch's device: one host-to-device copy of the packed tables on
+ * `stream`.  The handles must stay alive while they are in the batch.  Work
+ * of this batch enqueued before the fill must be on `stream` too (or have
+ * finished).  Errors: MTP_ERR_INVALID_ARG, MTP_ERR_CUDA. */
+mtp_status mtp_batch_fill(mtp_batch* b, mtp_handle* const* handles, int32_t count, void* stream);
+
 /* `iters` iterations of every instance from the packed start states d_x0;
- * writes the packed last-iteration u* to d_ustar.  Stream-ordered. */
+ * writes the packed last-iteration u* to d_ustar.  Stream-ordered.  The
+ * first call after a fill launches its kernels directly; later calls with
+ * the same instances replay a captured CUDA graph. */
 mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, float* d_ustar,
                                void* stream);
 
@@ -259,6 +273,78 @@ mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, f
  * entries, may be NULL) and the number of groups to n_groups.  Synchronous;
  * overwrites the handles' cost buffers. */
 mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_groups, void* stream);
+
+/* mtp_shift(h, k) of every instance of the batch in one launch. */
+mtp_status mtp_batch_shift(mtp_batch* b, int32_t k, void* stream);
+
+/* Device bytes mtp_create requests for `problem`, each allocation rounded up
+ * to 512 bytes (the candidate tensor U dominates: B * H * n floats).  The serving layer admits
+ * robots against a memory budget with it.  MTP_ERR_INVALID_ARG when the
+ * problem does not validate. */
+mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes);
+
+/* Re-planning server (continuous batching).  Robots are registered with
+ * their planning problem; a client submits a robot's current state and polls
+ * for its control.  A worker thread gathers up to max_batch robots that have
+ * a queued request and no request in flight (a robot's next plan starts from
+ * the state its previous one left), oldest request first, and runs them as
+ * one batched planner cycle: iters_per_request iterations (Alg. 2), u* back
+ * to pinned host memory, then the warm-start shift.  Two cycles may be in
+ * flight on separate streams with disjoint robots.  Each request's u*, and
+ * each robot's planner state after it, are exactly what mtp_plan_step
+ * (and mtp_shift) give on the robot's handle alone. */
+typedef struct mtp_server mtp_server;
+
+typedef struct mtp_server_config {
+  int32_t max_batch;          /* robots per cycle (>= 1) */
+  int32_t iters_per_request;  /* planner iterations per request (>= 1) */
+  int32_t shift_after;        /* warm-start shift k after each request (>= 0) */
+  int32_t max_queue;          /* queued requests per robot before submits are refused (>= 1) */
+  int32_t max_robots;         /* registrations before they are refused (>= 1) */
+  uint64_t memory_budget;     /* device bytes the robots may take; 0: 90% of the
+                                 free device memory when the server is created */
+} mtp_server_config;
+
+typedef struct mtp_server_stats {
+  uint64_t submitted, completed, cycles, planned;  /* planned: robot-plans run */
+  int32_t queued, in_flight, robots, failed;       /* failed: 1 after a device error */
+  uint64_t bytes_admitted;
+  double p50_latency_s, p99_latency_s;  /* submit -> result ready, completed requests */
+} mtp_server_stats;
+
+/* Creates the server on the current device and starts its worker thread.
+ * Allocates everything a cycle needs now (tables, pinned staging).  Errors:
+ * MTP_ERR_INVALID_ARG, MTP_ERR_OUT_OF_MEMORY, MTP_ERR_CUDA (text in
+ * mtp_last_error(NULL)). */
+mtp_status mtp_server_create(const mtp_server_config* cfg, mtp_server** out);
+
+/* Stops the worker after the cycles in flight, drops queued requests and
+ * frees everything, the robots' handles included. */
+mtp_status mtp_server_destroy(mtp_server* srv);
+
+/* Admits a robot: creates its planner handle when its footprint
+ * (mtp_problem_device_bytes) fits the remaining budget and the robot count
+ * is below max_robots; otherwise MTP_ERR_ADMISSION and nothing is
+ * allocated.  Writes the robot's id (0, 1, ...). */
+mtp_status mtp_server_register(mtp_server* srv, const mtp_problem* problem, int32_t* robot);
+
+/* Queues a plan request for `robot` from host state h_x0 (state_dim
+ * floats, copied) and writes its ticket (> 0).  MTP_ERR_ADMISSION when the
+ * robot already has max_queue requests queued; MTP_ERR_CUDA after a device
+ * error; MTP_ERR_INVALID_ARG for an unknown robot. */
+mtp_status mtp_submit(mtp_server* srv, int32_t robot, const float* h_x0, uint64_t* ticket);
+
+/* Result of a ticket: copies u* (ctrl_dim floats) to h_ustar and releases
+ * the ticket (MTP_OK).  When it is not ready: waits up to timeout_s
+ * seconds, then MTP_ERR_NOT_READY (timeout_s == 0) or MTP_ERR_TIMEOUT.
+ * MTP_ERR_INVALID_ARG for a ticket never issued or already released;
+ * MTP_ERR_CUDA if the server failed. */
+mtp_status mtp_poll(mtp_server* srv, uint64_t ticket, float* h_ustar, double timeout_s);
+
+mtp_status mtp_server_get_stats(mtp_server* srv, mtp_server_stats* out);
+
+/* Text of the server's last error (worker or call). */
+const char* mtp_server_last_error(const mtp_server* srv);
 
 /* Elite selection and update for callers that cannot allocate device memory.
  *

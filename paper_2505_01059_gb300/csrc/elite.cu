@@ -334,12 +334,10 @@ __global__ void __launch_bounds__(128) k_update_batch(const UpdateArgs* __restri
                  __ldg(thread_start + lo + 1) - __ldg(thread_start + lo));
 }
 
-__global__ void k_shift(double* mu, double* sigma, float* mu_f, float* sigma_f, int H, int n,
-                        int k) {
-  // one thread per dimension walks the horizon forward (in place is safe:
-  // row t reads row t+k >= t)
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// Warm start: one thread per control dimension walks the horizon forward (in
+// place is safe: row t reads row t+k >= t); the last row repeats.
+__device__ __forceinline__ void shift_body(double* mu, double* sigma, float* mu_f, float* sigma_f,
+                                           int H, int n, int k, int i) {
   for (int t = 0; t < H; ++t) {
     const int src = t + k < H ? t + k : H - 1;
     mu[t * n + i] = mu[src * n + i];
@@ -347,6 +345,19 @@ __global__ void k_shift(double* mu, double* sigma, float* mu_f, float* sigma_f, 
     mu_f[t * n + i] = (float)mu[t * n + i];
     sigma_f[t * n + i] = (float)sigma[t * n + i];
   }
+}
+
+__global__ void k_shift(double* mu, double* sigma, float* mu_f, float* sigma_f, int H, int n,
+                        int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) shift_body(mu, sigma, mu_f, sigma_f, H, n, k, i);
+}
+
+// one block per instance of a batch
+__global__ void k_shift_batch(const UpdateArgs* __restrict__ args, int k) {
+  const UpdateArgs& a = args[blockIdx.x];
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x)
+    shift_body(a.mu, a.sigma, a.mu_f, a.sigma_f, a.H, a.n, k, i);
 }
 
 }  // namespace
@@ -401,6 +412,12 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
     case 16: k_update<16><<<blocks, 128, 0, s>>>(a); break;
     default: k_update<32><<<blocks, 128, 0, s>>>(a); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift_batch(const UpdateArgs* d_args, int count, int k, cudaStream_t s) {
+  if (count <= 0 || k <= 0) return cudaSuccess;
+  k_shift_batch<<<count, 32, 0, s>>>(d_args, k);
   return cudaGetLastError();
 }
 

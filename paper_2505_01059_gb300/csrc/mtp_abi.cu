@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "mtp_device.cuh"
@@ -458,6 +459,22 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   return MTP_OK;
 }
 
+mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes) {
+  if (!problem || !bytes) return fail(nullptr, MTP_ERR_INVALID_ARG, "null argument");
+  mtp_status st = validate(*problem);
+  if (st != MTP_OK) return st;
+  const mtp_problem& p = *problem;
+  const uint64_t rowsz = (uint64_t)p.horizon * p.ctrl_dim;
+  auto r = [](uint64_t b) { return (b + 511) & ~uint64_t(511); };  // allocation granularity
+  *bytes = r((uint64_t)p.horizon * p.M * 4) + 3 * r((uint64_t)p.horizon * 4)  // tables
+           + 2 * r(rowsz * 8) + 2 * r(rowsz * 4) + r(4)                       // mean, spread
+           + r(rowsz * p.B * 4) + r((uint64_t)p.B * 4)                        // U, cost
+           + r((uint64_t)p.E * 4) + r((uint64_t)p.E * 8)                      // elites, weights
+           + r((uint64_t)p.ctrl_dim * 4) + r((uint64_t)p.state_dim * 4)
+           + r((uint64_t)p.M * p.N * p.ctrl_dim * 4);                         // graph Z
+  return MTP_OK;
+}
+
 mtp_status mtp_destroy(mtp_handle* h) {
   if (!h) return MTP_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
@@ -729,44 +746,95 @@ namespace {
 
 struct BatchGroup {
   int dyn = 0, n = 0;
-  std::vector<int> members;
-  RolloutArgs* d_ra = nullptr;
-  void* d_model = nullptr;
-  int* d_row_start = nullptr;
+  int first = 0, count = 0;   // instances [first, first + count) of the sorted order
+  int model_first = 0;        // first model of this group in its dynamics' table
+  int rows_first = 0;         // offset of this group's row_start segment
   int total_rows = 0;
   int block = 128;
-  cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
 };
 
-}  // namespace
+constexpr int kMaxGroups = 64;
 
-struct mtp_batch {
-  std::vector<mtp_handle*> hs;
-  int device = 0;
-  float** d_Z = nullptr;       // each instance's graph buffer
-  int* d_z_start = nullptr;    // blocks of the graph kernel per instance
-  int z_blocks = 0;
+// Device tables of a batch, packed into one device block that is refilled in
+// place from a pinned host mirror with one copy.  The layout depends on the
+// instance count, so the pointers are set on every fill.
+struct BatchTables {
+  int cap = 0;
+  size_t block_bytes = 0;
+  unsigned char* d_block = nullptr;
+  unsigned char* h_block = nullptr;  // pinned mirror
+  cudaEvent_t copied = nullptr;      // the mirror's last copy has been read
   CandArgs* d_cand = nullptr;
-  int* d_cand_start = nullptr;  // graph blocks per instance
-  int* d_local_start = nullptr;  // local-row blocks per instance
-  int local_blocks = 0;
-  int cand_blocks = 0;
-  size_t cand_smem = 0;
-  std::vector<BatchGroup> groups;
+  int* d_cand_start = nullptr;
+  int* d_local_start = nullptr;
+  float** d_Z = nullptr;
+  int* d_z_start = nullptr;
+  RolloutArgs* d_ra = nullptr;  // in group order
+  PointMassModel* d_pm = nullptr;
+  ChainModel* d_cm = nullptr;
+  LeggedModel* d_lm = nullptr;
+  int* d_row_start = nullptr;  // one segment of (members + 1) entries per group
   SelectArgs* d_sel = nullptr;
-  size_t sel_smem = 0;
   UpdateArgs* d_upd = nullptr;
   int* d_warp_start = nullptr;
-  int upd_warps = 0;
   float** d_x0_dst = nullptr;
   float** d_ustar_src = nullptr;
   int* d_x0_off = nullptr;
   int* d_us_off = nullptr;
+};
+
+// Packs the tables of `count` instances (n_pm point masses, n_cm chains,
+// n_lm legged robots, `groups` rollout groups) at 64-byte boundaries; with
+// `base` null it only returns the size.
+size_t layout_tables(BatchTables* t, unsigned char* base, int count, int n_pm, int n_cm, int n_lm,
+                     int groups) {
+  size_t off = 0;
+  auto take = [&](auto** field, size_t n) {
+    using T = std::remove_pointer_t<std::remove_reference_t<decltype(*field)>>;
+    off = (off + 63) & ~size_t(63);
+    if (base) *field = reinterpret_cast<T*>(base + off);
+    off += sizeof(T) * n;
+  };
+  BatchTables dummy;
+  BatchTables* d = t ? t : &dummy;
+  take(&d->d_cand, count);
+  take(&d->d_cand_start, count + 1);
+  take(&d->d_local_start, count + 1);
+  take(&d->d_Z, count);
+  take(&d->d_z_start, count + 1);
+  take(&d->d_ra, count);
+  take(&d->d_pm, n_pm);
+  take(&d->d_cm, n_cm);
+  take(&d->d_lm, n_lm);
+  take(&d->d_row_start, count + groups);
+  take(&d->d_sel, count);
+  take(&d->d_upd, count);
+  take(&d->d_warp_start, count + 1);
+  take(&d->d_x0_dst, count);
+  take(&d->d_ustar_src, count);
+  take(&d->d_x0_off, count + 1);
+  take(&d->d_us_off, count + 1);
+  return off;
+}
+
+}  // namespace
+
+struct mtp_batch {
+  std::vector<mtp_handle*> hs;  // in the caller's order
+  int device = 0;
+  BatchTables t;
+  int count = 0;
+  int cand_blocks = 0, local_blocks = 0, z_blocks = 0, upd_warps = 0;
+  size_t cand_smem = 0, sel_smem = 0;
+  std::vector<BatchGroup> groups;
+  std::map<std::pair<int, int>, int> tuned;  // (dyn, n) -> block chosen by the autotuner
   std::vector<int> x0_off, us_off;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t fork_ev = nullptr;
+  cudaStream_t group_stream[kMaxGroups] = {};
+  cudaEvent_t group_done[kMaxGroups] = {};
   std::map<int, cudaGraphExec_t> graphs;
+  int runs_since_fill = 0;
   std::string err;
 };
 
@@ -778,100 +846,96 @@ mtp_status batch_fail(mtp_batch* b, mtp_status st, const std::string& msg) {
   return st;
 }
 
-template <class T>
-cudaError_t upload(T** dst, const std::vector<T>& v) {
-  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (v.empty() ? 1 : v.size()));
-  if (e != cudaSuccess) return e;
-  return v.empty() ? cudaSuccess : cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+void drop_graphs(mtp_batch* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
 }
 
 void free_batch(mtp_batch* b) {
-  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
-  for (auto& g : b->groups) {
-    if (g.d_ra) cudaFree(g.d_ra);
-    if (g.d_model) cudaFree(g.d_model);
-    if (g.d_row_start) cudaFree(g.d_row_start);
-    if (g.stream) cudaStreamDestroy(g.stream);
-    if (g.done) cudaEventDestroy(g.done);
+  drop_graphs(b);
+  if (b->t.d_block) cudaFree(b->t.d_block);
+  if (b->t.h_block) cudaFreeHost(b->t.h_block);
+  if (b->t.copied) cudaEventDestroy(b->t.copied);
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (b->group_stream[g]) cudaStreamDestroy(b->group_stream[g]);
+    if (b->group_done[g]) cudaEventDestroy(b->group_done[g]);
   }
-  void* ptrs[] = {b->d_Z, b->d_z_start, b->d_cand, b->d_cand_start, b->d_local_start, b->d_sel,
-                  b->d_upd,
-                  b->d_warp_start,
-                  b->d_x0_dst, b->d_ustar_src, b->d_x0_off, b->d_us_off};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   delete b;
 }
 
-cudaError_t launch_group(const BatchGroup& g, int block, cudaStream_t s) {
-  if (g.dyn == MTP_DYN_POINTMASS)
-    return launch_rollout_pointmass_batch(g.d_ra, static_cast<const PointMassModel*>(g.d_model),
-                                          g.d_row_start, (int)g.members.size(), g.total_rows, g.n,
-                                          block, s);
-  if (g.dyn == MTP_DYN_LEGGED)  // fixed 64-thread blocks (shared-memory staging)
-    return launch_rollout_legged_batch(g.d_ra, static_cast<const LeggedModel*>(g.d_model),
-                                       g.d_row_start, (int)g.members.size(), g.total_rows, g.n, s);
-  return launch_rollout_chain_batch(g.d_ra, static_cast<const ChainModel*>(g.d_model),
-                                    g.d_row_start, (int)g.members.size(), g.total_rows, g.n,
-                                    block, s);
-}
-
-// One batched Alg. 2 iteration: candidates of all instances in one launch,
-// the rollouts of each (dynamics, dimension) group on its own stream, then
-// one selection block per instance and one update launch.
-cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
+cudaError_t alloc_batch(mtp_batch* b, int cap) {
+  BatchTables& t = b->t;
+  t.cap = cap;
+  // every instance could be of any dynamics and every one its own group
+  t.block_bytes = layout_tables(nullptr, nullptr, cap, cap, cap, cap, std::min(cap, kMaxGroups));
   cudaError_t e;
-  const int count = (int)b->hs.size();
-  if ((e = launch_graph_Z_batch(b->d_cand, b->d_Z, b->d_z_start, count, b->z_blocks, s))) return e;
-  if ((e = launch_candidates_batch(b->d_cand, b->d_cand_start, count, b->cand_blocks, b->cand_smem, s)))
+  if ((e = cudaMalloc((void**)&t.d_block, t.block_bytes)) ||
+      (e = cudaMallocHost((void**)&t.h_block, t.block_bytes)) ||
+      (e = cudaEventCreateWithFlags(&t.copied, cudaEventDisableTiming)) ||
+      (e = cudaEventRecord(t.copied, 0)) ||
+      (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) ||
+      (e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)))
     return e;
-  if ((e = launch_local_batch(b->d_cand, b->d_local_start, count, b->local_blocks, s))) return e;
-  if ((e = cudaEventRecord(b->fork_ev, s))) return e;
-  for (auto& g : b->groups) {
-    if ((e = cudaStreamWaitEvent(g.stream, b->fork_ev, 0))) return e;
-    if ((e = launch_group(g, g.block, g.stream))) return e;
-    if ((e = cudaEventRecord(g.done, g.stream))) return e;
-  }
-  for (auto& g : b->groups)
-    if ((e = cudaStreamWaitEvent(s, g.done, 0))) return e;
-  if ((e = launch_select_batch(b->d_sel, count, b->sel_smem, s))) return e;
-  return launch_update_batch(b->d_upd, b->d_warp_start, count, b->upd_warps, s);
+  return cudaSuccess;
 }
 
-}  // namespace
+int group_key_n(const mtp_handle* h) {
+  return h->pr.dyn == MTP_DYN_POINTMASS ? h->dm.n : h->pr.n_links;
+}
 
-extern "C" {
-
-mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch** out) {
-  if (!handles || !out || count < 1) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: bad argument");
-  *out = nullptr;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  for (int i = 0; i < count; ++i) {
-    if (!handles[i]) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: null handle");
-    if (handles[i]->device != dev)
-      return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: handles must live on the current device");
-    for (int j = 0; j < i; ++j)
-      if (handles[j] == handles[i]) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: repeated handle");
-  }
-  mtp_batch* b = new mtp_batch();
-  b->device = dev;
-  b->hs.assign(handles, handles + count);
-  auto err = [&](cudaError_t e, const char* where) {
-    mtp_status st = batch_fail(b, e == cudaErrorMemoryAllocation ? MTP_ERR_OUT_OF_MEMORY : MTP_ERR_CUDA,
-                               std::string(where) + ": " + cudaGetErrorString(e));
-    free_batch(b);
-    return st;
-  };
+// Fills the batch's tables for `handles` (at most the capacity, distinct,
+// on the batch's device) with one host-to-device copy on `s`.  Instances are
+// grouped by (dynamics, dimension) for the rollouts; everything else keeps
+// the caller's order.  Captured graphs are dropped: their launches baked in
+// the previous layout.
+cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cudaStream_t s) {
+  BatchTables& t = b->t;
   cudaError_t e;
-  // candidates: per-instance arguments and block ranges
-  std::vector<CandArgs> cand(count);
-  std::vector<int> cstart(count + 1, 0), zstart(count + 1, 0), lstart(count + 1, 0);
-  std::vector<float*> zptr(count);
+  if ((e = cudaEventSynchronize(t.copied))) return e;  // the mirror is free again
+  drop_graphs(b);
+  b->runs_since_fill = 0;
+  b->count = 0;  // unusable until this fill has succeeded
+  b->hs.clear();
+  // rollout groups: sorted by (dynamics, dimension), stable in the caller's order
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const int dx = handles[x]->pr.dyn, dy = handles[y]->pr.dyn;
+    if (dx != dy) return dx < dy;
+    return group_key_n(handles[x]) < group_key_n(handles[y]);
+  });
+  b->groups.clear();
+  int n_dyn[3] = {0, 0, 0};
+  for (int pos = 0; pos < count; ++pos) {
+    const mtp_handle* h = handles[order[pos]];
+    const int dyn = h->pr.dyn, n = group_key_n(h);
+    if (b->groups.empty() || b->groups.back().dyn != dyn || b->groups.back().n != n) {
+      if ((int)b->groups.size() == kMaxGroups) return cudaErrorInvalidValue;
+      BatchGroup g;
+      g.dyn = dyn;
+      g.n = n;
+      g.first = pos;
+      g.model_first = n_dyn[dyn];
+      auto it = b->tuned.find({dyn, n});
+      g.block = it != b->tuned.end() ? it->second : 128;
+      b->groups.push_back(g);
+    }
+    ++b->groups.back().count;
+    ++n_dyn[dyn];
+  }
+  layout_tables(&t, t.h_block, count, n_dyn[MTP_DYN_POINTMASS], n_dyn[MTP_DYN_CHAIN],
+                n_dyn[MTP_DYN_LEGGED], (int)b->groups.size());
+  // host views of the mirror (same offsets as the device block)
+  BatchTables hv = t;
+  const size_t used = layout_tables(&t, t.d_block, count, n_dyn[MTP_DYN_POINTMASS],
+                                    n_dyn[MTP_DYN_CHAIN], n_dyn[MTP_DYN_LEGGED], (int)b->groups.size());
+  // candidates
+  hv.d_cand_start[0] = hv.d_z_start[0] = hv.d_local_start[0] = 0;
+  b->cand_smem = 0;
   for (int i = 0; i < count; ++i) {
-    mtp_handle* h = b->hs[i];
+    mtp_handle* h = handles[i];
     const Dims& dm = h->dm;
     const size_t Hn = (size_t)dm.H * dm.n;
     CandArgs c = cand_args(h, 0, h->iter_dev);
@@ -882,101 +946,209 @@ mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch
     c.local_rows = dm.L;
     c.U_mean = h->U + Hn * (dm.B - 1);
     c.Z_global = h->Z;
-    zptr[i] = h->Z;
-    zstart[i + 1] = zstart[i] + (dm.M * dm.N * ((dm.n + 3) / 4) + 255) / 256;
+    hv.d_Z[i] = h->Z;
+    hv.d_z_start[i + 1] = hv.d_z_start[i] + (dm.M * dm.N * ((dm.n + 3) / 4) + 255) / 256;
     const long long items = ((long long)dm.L + 1) * (((long long)Hn + 3) / 4);
-    const int local_blocks = (int)std::max<long long>(1, (items + 1023) / 1024);
-    cand[i] = c;
-    cstart[i + 1] = cstart[i] + c.graph_blocks;  // graph blocks only: local rows run apart
-    lstart[i + 1] = lstart[i] + local_blocks;
+    hv.d_cand[i] = c;
+    hv.d_cand_start[i + 1] = hv.d_cand_start[i] + c.graph_blocks;  // local rows run apart
+    hv.d_local_start[i + 1] = hv.d_local_start[i] + (int)std::max<long long>(1, (items + 1023) / 1024);
     b->cand_smem = std::max(b->cand_smem, candidates_smem_bytes(c));
   }
-  b->cand_blocks = cstart[count];
-  b->z_blocks = zstart[count];
-  b->local_blocks = lstart[count];
-  if ((e = upload(&b->d_cand, cand)) || (e = upload(&b->d_cand_start, cstart)) ||
-      (e = upload(&b->d_local_start, lstart)) ||
-      (e = upload(&b->d_Z, zptr)) || (e = upload(&b->d_z_start, zstart)))
-    return err(e, "batch upload");
-  // rollout groups by (dynamics, dimension)
-  for (int i = 0; i < count; ++i) {
-    mtp_handle* h = b->hs[i];
-    const int key_n = h->pr.dyn == MTP_DYN_POINTMASS ? h->dm.n : h->pr.n_links;
-    BatchGroup* g = nullptr;
-    for (auto& x : b->groups)
-      if (x.dyn == h->pr.dyn && x.n == key_n) g = &x;
-    if (!g) {
-      b->groups.emplace_back();
-      g = &b->groups.back();
-      g->dyn = h->pr.dyn;
-      g->n = key_n;
-    }
-    g->members.push_back(i);
-  }
+  b->cand_blocks = hv.d_cand_start[count];
+  b->z_blocks = hv.d_z_start[count];
+  b->local_blocks = hv.d_local_start[count];
+  // rollouts, in group order; whole warps per instance
+  int rs = 0;
   for (auto& g : b->groups) {
-    std::vector<RolloutArgs> ra;
-    std::vector<int> rs(1, 0);
-    std::vector<PointMassModel> pms;
-    std::vector<ChainModel> cms;
-    std::vector<LeggedModel> lms;
-    for (int i : g.members) {
-      mtp_handle* h = b->hs[i];
-      ra.push_back(rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, h->dm.B, h->cost));
-      rs.push_back(rs.back() + ((h->dm.B + 31) / 32) * 32);  // whole warps per instance
-      if (g.dyn == MTP_DYN_POINTMASS) pms.push_back(pointmass_model(h->pr));
-      else if (g.dyn == MTP_DYN_LEGGED) lms.push_back(legged_model(h->pr));
-      else cms.push_back(chain_model(h->pr));
+    g.rows_first = rs;
+    int* row = hv.d_row_start + rs;
+    row[0] = 0;
+    for (int j = 0; j < g.count; ++j) {
+      mtp_handle* h = handles[order[g.first + j]];
+      hv.d_ra[g.first + j] = rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, h->dm.B, h->cost);
+      const int m = g.model_first + j;
+      if (g.dyn == MTP_DYN_POINTMASS) hv.d_pm[m] = pointmass_model(h->pr);
+      else if (g.dyn == MTP_DYN_LEGGED) hv.d_lm[m] = legged_model(h->pr);
+      else hv.d_cm[m] = chain_model(h->pr);
+      row[j + 1] = row[j] + ((h->dm.B + 31) / 32) * 32;
     }
-    g.total_rows = rs.back();
-    g.block = 128;
-    if ((e = upload(&g.d_ra, ra)) || (e = upload(&g.d_row_start, rs))) return err(e, "batch upload");
-    if (g.dyn == MTP_DYN_POINTMASS) {
-      PointMassModel* p = nullptr;
-      if ((e = upload(&p, pms))) return err(e, "batch upload");
-      g.d_model = p;
-    } else if (g.dyn == MTP_DYN_LEGGED) {
-      LeggedModel* p = nullptr;
-      if ((e = upload(&p, lms))) return err(e, "batch upload");
-      g.d_model = p;
-    } else {
-      ChainModel* p = nullptr;
-      if ((e = upload(&p, cms))) return err(e, "batch upload");
-      g.d_model = p;
-    }
-    if ((e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking)) ||
-        (e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming)))
-      return err(e, "batch streams");
+    g.total_rows = row[g.count];
+    rs += g.count + 1;
   }
-  // selection and update
-  std::vector<SelectArgs> sel(count);
-  std::vector<UpdateArgs> upd(count);
-  std::vector<int> wstart(count + 1, 0);
-  std::vector<float*> x0dst(count), usrc(count);
+  // selection, update, packing of x0 and u*
   b->x0_off.assign(count + 1, 0);
   b->us_off.assign(count + 1, 0);
+  hv.d_warp_start[0] = 0;
+  b->sel_smem = 0;
   for (int i = 0; i < count; ++i) {
-    mtp_handle* h = b->hs[i];
+    mtp_handle* h = handles[i];
     const Dims& dm = h->dm;
-    sel[i] = SelectArgs{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
-                        h->elite, h->weight, h->ustar, nullptr, nullptr};
+    hv.d_sel[i] = SelectArgs{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
+                             h->elite, h->weight, h->ustar, nullptr, nullptr};
     b->sel_smem = std::max(b->sel_smem, select_smem_bytes(dm.B, dm.E));
-    upd[i] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
-                        h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
-    wstart[i + 1] = wstart[i] + update_threads(dm.H, dm.n);
-    x0dst[i] = h->x0;
-    usrc[i] = h->ustar;
+    hv.d_upd[i] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
+                             h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
+    hv.d_warp_start[i + 1] = hv.d_warp_start[i] + update_threads(dm.H, dm.n);
+    hv.d_x0_dst[i] = h->x0;
+    hv.d_ustar_src[i] = h->ustar;
     b->x0_off[i + 1] = b->x0_off[i] + dm.d;
     b->us_off[i + 1] = b->us_off[i] + dm.n;
+    hv.d_x0_off[i + 1] = b->x0_off[i + 1];
+    hv.d_us_off[i + 1] = b->us_off[i + 1];
   }
-  b->upd_warps = wstart[count];
-  if ((e = upload(&b->d_sel, sel)) || (e = upload(&b->d_upd, upd)) ||
-      (e = upload(&b->d_warp_start, wstart)) || (e = upload(&b->d_x0_dst, x0dst)) ||
-      (e = upload(&b->d_ustar_src, usrc)) || (e = upload(&b->d_x0_off, b->x0_off)) ||
-      (e = upload(&b->d_us_off, b->us_off)))
-    return err(e, "batch upload");
-  if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) ||
-      (e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)))
-    return err(e, "batch streams");
+  hv.d_x0_off[0] = hv.d_us_off[0] = 0;
+  b->upd_warps = hv.d_warp_start[count];
+  if ((e = cudaMemcpyAsync(t.d_block, t.h_block, used, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaEventRecord(t.copied, s)))
+    return e;
+  b->hs.assign(handles, handles + count);
+  b->count = count;
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    if (!b->group_stream[g]) {
+      if ((e = cudaStreamCreateWithFlags(&b->group_stream[g], cudaStreamNonBlocking)) ||
+          (e = cudaEventCreateWithFlags(&b->group_done[g], cudaEventDisableTiming)))
+        return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_group(const mtp_batch* b, const BatchGroup& g, int block, cudaStream_t s) {
+  const BatchTables& t = b->t;
+  const RolloutArgs* ra = t.d_ra + g.first;
+  const int* rs = t.d_row_start + g.rows_first;
+  if (g.dyn == MTP_DYN_POINTMASS)
+    return launch_rollout_pointmass_batch(ra, t.d_pm + g.model_first, rs, g.count, g.total_rows, g.n, block, s);
+  if (g.dyn == MTP_DYN_LEGGED)  // fixed 64-thread blocks (shared-memory staging)
+    return launch_rollout_legged_batch(ra, t.d_lm + g.model_first, rs, g.count, g.total_rows, g.n, s);
+  return launch_rollout_chain_batch(ra, t.d_cm + g.model_first, rs, g.count, g.total_rows, g.n, block, s);
+}
+
+// One batched Alg. 2 iteration: graphs, graph paths and local rows of all
+// instances, the rollouts of each (dynamics, dimension) group on its own
+// stream, then one selection block per instance and one update launch.
+cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
+  cudaError_t e;
+  const BatchTables& t = b->t;
+  const int count = b->count;
+  if ((e = launch_graph_Z_batch(t.d_cand, t.d_Z, t.d_z_start, count, b->z_blocks, s))) return e;
+  if ((e = launch_candidates_batch(t.d_cand, t.d_cand_start, count, b->cand_blocks, b->cand_smem, s)))
+    return e;
+  if ((e = launch_local_batch(t.d_cand, t.d_local_start, count, b->local_blocks, s))) return e;
+  if ((e = cudaEventRecord(b->fork_ev, s))) return e;
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    if ((e = cudaStreamWaitEvent(b->group_stream[g], b->fork_ev, 0))) return e;
+    if ((e = launch_group(b, b->groups[g], b->groups[g].block, b->group_stream[g]))) return e;
+    if ((e = cudaEventRecord(b->group_done[g], b->group_stream[g]))) return e;
+  }
+  for (size_t g = 0; g < b->groups.size(); ++g)
+    if ((e = cudaStreamWaitEvent(s, b->group_done[g], 0))) return e;
+  if ((e = launch_select_batch(t.d_sel, count, b->sel_smem, s))) return e;
+  return launch_update_batch(t.d_upd, t.d_warp_start, count, b->upd_warps, s);
+}
+
+// scatter x0 -> iterations -> gather u*.  The first run after a fill
+// launches eagerly; later runs over the same layout replay captured graphs.
+cudaError_t run_batch(mtp_batch* b, const float* d_x0, int iters, float* d_ustar, cudaStream_t s) {
+  const bool graphs = b->runs_since_fill++ > 0;
+  cudaError_t e = launch_scatter(d_x0, b->t.d_x0_dst, b->t.d_x0_off, b->count, s);
+  if (e != cudaSuccess) return e;
+  if (!graphs) {
+    for (int k = 0; k < iters; ++k)
+      if ((e = enqueue_batch_iteration(b, s))) return e;
+  } else {
+    int left = iters;
+    while (left > 0) {
+      const int chunk = left > 64 ? 64 : left;
+      auto it = b->graphs.find(chunk);
+      if (it == b->graphs.end()) {
+        cudaGraph_t graph;
+        if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal))) return e;
+        for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = enqueue_batch_iteration(b, b->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (e != cudaSuccess) return e;
+        if (e2 != cudaSuccess) return e2;
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return e;
+        it = b->graphs.emplace(chunk, exec).first;
+      }
+      if ((e = cudaGraphLaunch(it->second, s))) return e;
+      left -= chunk;
+    }
+  }
+  e = launch_gather(b->t.d_ustar_src, b->t.d_us_off, d_ustar, b->count, s);
+  if (e != cudaSuccess) return e;
+  for (mtp_handle* h : b->hs) h->iter_host += (uint32_t)iters;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+static mtp_status check_batch_handles(mtp_handle* const* handles, int32_t count, int dev) {
+  for (int i = 0; i < count; ++i) {
+    if (!handles[i]) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch: null handle");
+    if (handles[i]->device != dev)
+      return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch: handles must live on the batch's device");
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch: repeated handle");
+  }
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_reserve(int32_t capacity, mtp_batch** out) {
+  if (!out || capacity < 1) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_reserve: bad argument");
+  *out = nullptr;
+  mtp_batch* b = new mtp_batch();
+  cudaGetDevice(&b->device);
+  cudaError_t e = init_candidate_attributes();
+  if (e == cudaSuccess) e = init_select_attributes();
+  if (e == cudaSuccess) e = alloc_batch(b, capacity);
+  if (e != cudaSuccess) {
+    mtp_status st = batch_fail(nullptr, e == cudaErrorMemoryAllocation ? MTP_ERR_OUT_OF_MEMORY : MTP_ERR_CUDA,
+                               std::string("batch_reserve: ") + cudaGetErrorString(e));
+    free_batch(b);
+    return st;
+  }
+  *out = b;
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_fill(mtp_batch* b, mtp_handle* const* handles, int32_t count, void* stream) {
+  if (!b || !handles || count < 1 || count > b->t.cap)
+    return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_fill: bad argument (count must be 1 .. capacity)");
+  mtp_status st = check_batch_handles(handles, count, b->device);
+  if (st != MTP_OK) return batch_fail(b, st, g_create_error);
+  DeviceGuard guard(b->device);
+  cudaError_t e = fill_batch(b, handles, count, (cudaStream_t)stream);
+  if (e == cudaErrorInvalidValue)
+    return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_fill: more than 64 (dynamics, dimension) groups");
+  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch_fill: ") + cudaGetErrorString(e));
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch** out) {
+  if (!handles || !out || count < 1) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: bad argument");
+  *out = nullptr;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  mtp_status st = check_batch_handles(handles, count, dev);
+  if (st != MTP_OK) return st;
+  mtp_batch* b = nullptr;
+  if ((st = mtp_batch_reserve(count, &b)) != MTP_OK) return st;
+  if ((st = mtp_batch_fill(b, handles, count, b->cap_stream)) != MTP_OK) {
+    g_create_error = b->err;
+    free_batch(b);
+    return st;
+  }
+  cudaError_t e = cudaStreamSynchronize(b->cap_stream);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return batch_fail(nullptr, MTP_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
+  }
   *out = b;
   return MTP_OK;
 }
@@ -990,7 +1162,7 @@ mtp_status mtp_batch_destroy(mtp_batch* b) {
 }
 
 mtp_status mtp_batch_layout(const mtp_batch* b, int32_t* x0_offset, int32_t* ustar_offset) {
-  if (!b) return MTP_ERR_INVALID_ARG;
+  if (!b || b->count < 1) return MTP_ERR_INVALID_ARG;
   const size_t c = b->hs.size() + 1;
   if (x0_offset) std::copy(b->x0_off.begin(), b->x0_off.begin() + c, x0_offset);
   if (ustar_offset) std::copy(b->us_off.begin(), b->us_off.begin() + c, ustar_offset);
@@ -999,60 +1171,42 @@ mtp_status mtp_batch_layout(const mtp_batch* b, int32_t* x0_offset, int32_t* ust
 
 mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, float* d_ustar,
                                void* stream) {
-  if (!b || !d_x0 || !d_ustar || iters < 1)
-    return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_plan_step: bad argument");
+  if (!b || !d_x0 || !d_ustar || iters < 1 || b->count < 1)
+    return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_plan_step: bad argument (or batch never filled)");
   DeviceGuard guard(b->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  const int count = (int)b->hs.size();
-  cudaError_t e = launch_scatter(d_x0, b->d_x0_dst, b->d_x0_off, count, s);
-  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch scatter: ") + cudaGetErrorString(e));
-  int left = iters;
-  while (left > 0) {
-    const int chunk = left > 64 ? 64 : left;
-    auto it = b->graphs.find(chunk);
-    if (it == b->graphs.end()) {
-      cudaGraph_t graph;
-      if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)))
-        return batch_fail(b, MTP_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
-      for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = enqueue_batch_iteration(b, b->cap_stream);
-      cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
-      if (e != cudaSuccess || e2 != cudaSuccess)
-        return batch_fail(b, MTP_ERR_CUDA, std::string("batch capture: ") +
-                                               cudaGetErrorString(e != cudaSuccess ? e : e2));
-      cudaGraphExec_t exec;
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess)
-        return batch_fail(b, MTP_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
-      it = b->graphs.emplace(chunk, exec).first;
-    }
-    if ((e = cudaGraphLaunch(it->second, s)))
-      return batch_fail(b, MTP_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
-    left -= chunk;
-  }
-  e = launch_gather(b->d_ustar_src, b->d_us_off, d_ustar, count, s);
-  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch gather: ") + cudaGetErrorString(e));
-  for (mtp_handle* h : b->hs) h->iter_host += (uint32_t)iters;
+  cudaError_t e = run_batch(b, d_x0, iters, d_ustar, (cudaStream_t)stream);
+  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch_plan_step: ") + cudaGetErrorString(e));
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_shift(mtp_batch* b, int32_t k, void* stream) {
+  if (!b || k < 0 || b->count < 1) return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_shift: bad argument");
+  DeviceGuard guard(b->device);
+  cudaError_t e = launch_shift_batch(b->t.d_upd, b->count, k, (cudaStream_t)stream);
+  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch_shift: ") + cudaGetErrorString(e));
   return MTP_OK;
 }
 
 mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_groups, void* stream) {
   if (!b) return MTP_ERR_INVALID_ARG;
+  if (b->count < 1) return batch_fail(b, MTP_ERR_INVALID_ARG, "autotune: batch never filled");
   DeviceGuard guard(b->device);
   (void)stream;
+  cudaEventSynchronize(b->t.copied);  // the tables may have been filled on another stream
   const int cand[3] = {32, 64, 128};  // the rollout kernels are bounded at 128 threads
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
   cudaError_t e = cudaSuccess;
   for (auto& g : b->groups) {
+    if (g.dyn == MTP_DYN_LEGGED) continue;  // fixed block size
     float best = 1e30f;
     int best_block = g.block;
     for (int block : cand) {
       float ms_min = 1e30f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         cudaEventRecord(t0, b->cap_stream);
-        e = launch_group(g, block, b->cap_stream);
+        e = launch_group(b, g, block, b->cap_stream);
         cudaEventRecord(t1, b->cap_stream);
         cudaEventSynchronize(t1);
         float ms = 0.f;
@@ -1065,6 +1219,7 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_grou
       }
     }
     g.block = best_block;
+    b->tuned[{g.dyn, g.n}] = best_block;
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);

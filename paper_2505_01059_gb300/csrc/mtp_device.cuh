@@ -221,6 +221,7 @@ cudaError_t launch_scatter(const float* packed, float* const* d_dst, const int* 
                            cudaStream_t s);
 cudaError_t launch_gather(const float* const* d_src, const int* d_off, float* packed, int count,
                           cudaStream_t s);
+cudaError_t launch_shift_batch(const UpdateArgs* d_args, int count, int k, cudaStream_t s);
 cudaError_t launch_shift(double* mu, double* sigma, float* mu_f, float* sigma_f, int H, int n, int k,
                          cudaStream_t s);
 

@@ -41,7 +41,9 @@ EXPORTS = [
     "mtp_plan_step", "mtp_plan_step_host", "mtp_shift", "mtp_get_state", "mtp_set_state",
     "mtp_set_profiling", "mtp_stage_times", "mtp_elite_update_noalloc",
     "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_layout", "mtp_batch_plan_step",
-    "mtp_batch_autotune",
+    "mtp_batch_autotune", "mtp_batch_reserve", "mtp_batch_fill", "mtp_batch_shift",
+    "mtp_problem_device_bytes", "mtp_server_create", "mtp_server_destroy", "mtp_server_register",
+    "mtp_submit", "mtp_poll", "mtp_server_get_stats", "mtp_server_last_error",
 ]
 
 
@@ -87,6 +89,19 @@ class MtpBuffers(C.Structure):
                 ("ustar", C.c_void_p), ("iter", C.c_void_p)]
 
 
+class MtpServerConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("iters_per_request", C.c_int32),
+                ("shift_after", C.c_int32), ("max_queue", C.c_int32), ("max_robots", C.c_int32),
+                ("memory_budget", C.c_uint64)]
+
+
+class MtpServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("cycles", C.c_uint64),
+                ("planned", C.c_uint64), ("queued", C.c_int32), ("in_flight", C.c_int32),
+                ("robots", C.c_int32), ("failed", C.c_int32), ("bytes_admitted", C.c_uint64),
+                ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double)]
+
+
 _lib = None
 
 
@@ -128,6 +143,17 @@ def load_library(path: str = LIB_PATH):
         "mtp_batch_layout": (i32, [vp, vp, vp]),
         "mtp_batch_plan_step": (i32, [vp, vp, i32, vp, vp]),
         "mtp_batch_autotune": (i32, [vp, vp, vp, vp]),
+        "mtp_batch_reserve": (i32, [i32, C.POINTER(vp)]),
+        "mtp_batch_fill": (i32, [vp, C.POINTER(vp), i32, vp]),
+        "mtp_batch_shift": (i32, [vp, i32, vp]),
+        "mtp_problem_device_bytes": (i32, [C.POINTER(MtpProblem), C.POINTER(C.c_uint64)]),
+        "mtp_server_create": (i32, [C.POINTER(MtpServerConfig), C.POINTER(vp)]),
+        "mtp_server_destroy": (i32, [vp]),
+        "mtp_server_register": (i32, [vp, C.POINTER(MtpProblem), C.POINTER(i32)]),
+        "mtp_submit": (i32, [vp, i32, vp, C.POINTER(C.c_uint64)]),
+        "mtp_poll": (i32, [vp, C.c_uint64, vp, C.c_double]),
+        "mtp_server_get_stats": (i32, [vp, C.POINTER(MtpServerStats)]),
+        "mtp_server_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -435,6 +461,13 @@ class Batch:
 
     def __init__(self, ptr: int, handles):
         self.ptr = C.c_void_p(ptr)
+        self.handles = []
+        self.x0_offset = [0]
+        self.ustar_offset = [0]
+        if handles:
+            self._set(handles)
+
+    def _set(self, handles):
         self.handles = list(handles)
         n = len(self.handles) + 1
         x0 = (C.c_int32 * n)()
@@ -452,14 +485,50 @@ class Batch:
             self.ptr = C.c_void_p(0)
 
 
+def _handle_array(handles):
+    return (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+
+
 def mtp_batch_create(handles) -> Batch:
     lib = load_library()
-    arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
     out = C.c_void_p()
-    st = lib.mtp_batch_create(arr, len(handles), C.byref(out))
+    st = lib.mtp_batch_create(_handle_array(handles), len(handles), C.byref(out))
     if st != MTP_OK:
         raise MtpError(st, lib.mtp_last_error(None).decode())
     return Batch(out.value, handles)
+
+
+def mtp_batch_reserve(capacity: int) -> Batch:
+    lib = load_library()
+    out = C.c_void_p()
+    st = lib.mtp_batch_reserve(int(capacity), C.byref(out))
+    if st != MTP_OK:
+        raise MtpError(st, lib.mtp_last_error(None).decode())
+    return Batch(out.value, [])
+
+
+def mtp_batch_fill(b: Batch, handles, stream=None):
+    lib = load_library()
+    st = lib.mtp_batch_fill(b.ptr, _handle_array(handles), len(handles), _stream(stream))
+    if st != MTP_OK:
+        raise MtpError(st, lib.mtp_last_error(None).decode())
+    b._set(handles)
+
+
+def mtp_batch_shift(b: Batch, k: int, stream=None):
+    st = load_library().mtp_batch_shift(b.ptr, int(k), _stream(stream))
+    if st != MTP_OK:
+        raise MtpError(st, load_library().mtp_last_error(None).decode())
+
+
+def mtp_problem_device_bytes(spec_or_problem) -> int:
+    lib = load_library()
+    pr = spec_or_problem if isinstance(spec_or_problem, MtpProblem) else problem_from_spec(spec_or_problem)
+    out = C.c_uint64()
+    st = lib.mtp_problem_device_bytes(C.byref(pr), C.byref(out))
+    if st != MTP_OK:
+        raise MtpError(st, lib.mtp_last_error(None).decode())
+    return out.value
 
 
 def mtp_batch_destroy(b: Batch):
@@ -482,3 +551,81 @@ def mtp_batch_autotune(b: Batch, stream=None):
     _check(load_library().mtp_batch_autotune(b.ptr, C.addressof(out), C.addressof(ng),
                                              _stream(stream)))
     return [(out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i in range(ng.value)]
+
+
+# ----------------------------------------------------------------------------
+# re-plan server
+# ----------------------------------------------------------------------------
+
+class Server:
+    """An mtp_server*: robots registered with their problems, requests
+    submitted with host start states, results polled by ticket."""
+
+    def __init__(self, ptr: int):
+        self.ptr = C.c_void_p(ptr)
+
+    def _err(self):
+        return load_library().mtp_server_last_error(self.ptr).decode()
+
+    def close(self):
+        if self.ptr.value:
+            _check(load_library().mtp_server_destroy(self.ptr))
+            self.ptr = C.c_void_p(0)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            try:
+                load_library().mtp_server_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = C.c_void_p(0)
+
+
+def mtp_server_create(max_batch: int = 64, iters_per_request: int = 1, shift_after: int = 1,
+                      max_queue: int = 4, max_robots: int = 1024, memory_budget: int = 0) -> Server:
+    lib = load_library()
+    cfg = MtpServerConfig(int(max_batch), int(iters_per_request), int(shift_after), int(max_queue),
+                          int(max_robots), int(memory_budget))
+    out = C.c_void_p()
+    st = lib.mtp_server_create(C.byref(cfg), C.byref(out))
+    if st != MTP_OK:
+        raise MtpError(st, lib.mtp_last_error(None).decode())
+    return Server(out.value)
+
+
+def mtp_server_destroy(srv: Server):
+    srv.close()
+
+
+def mtp_server_register(srv: Server, spec_or_problem) -> int:
+    pr = spec_or_problem if isinstance(spec_or_problem, MtpProblem) else problem_from_spec(spec_or_problem)
+    rid = C.c_int32()
+    st = load_library().mtp_server_register(srv.ptr, C.byref(pr), C.byref(rid))
+    if st != MTP_OK:
+        raise MtpError(st, srv._err())
+    return rid.value
+
+
+def mtp_submit(srv: Server, robot: int, x0: np.ndarray) -> int:
+    x = np.ascontiguousarray(x0, dtype=np.float32)
+    t = C.c_uint64()
+    st = load_library().mtp_submit(srv.ptr, int(robot), x.ctypes.data, C.byref(t))
+    if st != MTP_OK:
+        raise MtpError(st, srv._err())
+    return t.value
+
+
+def mtp_poll(srv: Server, ticket: int, out: np.ndarray, timeout_s: float = 0.0) -> int:
+    """Returns the status: MTP_OK (u* in `out`), NOT_READY (6) or TIMEOUT (5);
+    raises for the other errors."""
+    assert out.dtype == np.float32 and out.flags.c_contiguous
+    st = load_library().mtp_poll(srv.ptr, C.c_uint64(int(ticket)), out.ctypes.data, float(timeout_s))
+    if st not in (MTP_OK, 5, 6):
+        raise MtpError(st, srv._err())
+    return st
+
+
+def mtp_server_get_stats(srv: Server) -> dict:
+    s = MtpServerStats()
+    _check(load_library().mtp_server_get_stats(srv.ptr, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in MtpServerStats._fields_}

@@ -79,3 +79,39 @@ def test_batch_rejects_bad_input(mtp):
     with pytest.raises(mtp.MtpError):
         mtp.mtp_batch_create([h, h])
     mtp.mtp_destroy(h)
+
+
+def test_batch_refill_in_place_and_shift(mtp):
+    """A reserved batch refilled with different instance sets (legged robots
+    included) and shifted in one launch gives every instance exactly what
+    mtp_plan_step + mtp_shift give it alone, cycle after cycle."""
+    specs = _specs() + [W.legged(links=4, B=256, H=32, M=6, N=16, E=16)]
+    handles = [mtp.mtp_create(s) for s in specs]
+    twins = [mtp.mtp_create(s) for s in specs]
+    b = mtp.mtp_batch_reserve(8)
+    rng = np.random.default_rng(5)
+    for sel in ([0, 1, 2, 3, 4, 5], [6, 7, 8, 9, 10, 11, 12], [12, 0, 3]):
+        mtp.mtp_batch_fill(b, [handles[i] for i in sel])
+        # start states near each spec's own (the legged robot stands on the ground)
+        x0s = [(np.asarray(specs[i]["x0"]) + (0.0 if specs[i]["dyn"] == "legged" else
+                rng.uniform(-0.2, 0.2, size=specs[i]["d"]))).astype(np.float32) for i in sel]
+        us = torch.empty(b.ustar_offset[-1], device=DEV)
+        mtp.mtp_batch_plan_step(b, torch.tensor(np.concatenate(x0s), device=DEV), 2, us)
+        mtp.mtp_batch_shift(b, 1)
+        torch.cuda.synchronize()
+        for j, i in enumerate(sel):
+            u = torch.empty(specs[i]["n"], device=DEV)
+            mtp.mtp_plan_step(twins[i], torch.tensor(x0s[j], device=DEV), 2, u)
+            mtp.mtp_shift(twins[i], 1)
+            lo, hi = b.ustar_offset[j], b.ustar_offset[j + 1]
+            assert np.array_equal(us[lo:hi].cpu().numpy(), u.cpu().numpy()), (sel, i)
+    for i, (h, t) in enumerate(zip(handles, twins)):
+        mu_b, sg_b, it_b = mtp.mtp_get_state(h)
+        mu_t, sg_t, it_t = mtp.mtp_get_state(t)
+        assert it_b == it_t and np.array_equal(mu_b, mu_t) and np.array_equal(sg_b, sg_t), i
+    with pytest.raises(mtp.MtpError) as ei:
+        mtp.mtp_batch_fill(b, handles[:9])  # over capacity
+    assert ei.value.status == 1
+    mtp.mtp_batch_destroy(b)
+    for h in handles + twins:
+        mtp.mtp_destroy(h)
