@@ -492,10 +492,24 @@ def run_ours(args, spec, name):
         pg.destroy_process_group()
 
 
+def _advance(x, u, dt):
+    """Host stand-in for the robots' true motion between re-plans: one control
+    step of a double integrator per controlled coordinate (point masses: the
+    position; arms: the joint angles, unit inertia), FP64."""
+    import numpy as np
+    half = x.shape[0] // 2
+    v = x[half:] + dt * u[:half]
+    return np.concatenate([x[:half] + dt * v, v])
+
+
 def run_serve(args):
-    """The re-plan server under closed-loop load: every robot resubmits as
-    soon as its previous control arrives (host state in, u* out through the
-    C ABI), so cycles of up to --max-batch robots keep two in flight."""
+    """The re-plan server under the fleet workload: every robot is an
+    independent Poisson process of re-plan requests at --rate-hz (open loop),
+    its next start state the previous one advanced on the host with the
+    returned control.  Reports completed re-plans/s, rollout-steps/s and the
+    submit -> poll-success latency; then the saturation capacity (closed
+    loop, every robot resubmits at once) and the plain path's capacity (one
+    request at a time through mtp_plan_step_host on its own handle)."""
     import time
 
     import numpy as np
@@ -507,58 +521,133 @@ def run_serve(args):
     mtp.load_library()
     torch.cuda.set_device(0)
     specs = W.robots(count=args.instances)
+    R = len(specs)
     srv = mtp.mtp_server_create(max_batch=args.max_batch, iters_per_request=1, shift_after=1,
-                                max_queue=2, max_robots=len(specs))
-    ids = [mtp.mtp_server_register(srv, s) for s in specs]
-    rng = np.random.default_rng(7)
-    x0 = [(np.asarray(s["x0"]) + rng.uniform(-0.1, 0.1, size=s["d"])).astype(np.float32)
-          for s in specs]
-    outs = [np.empty(s["n"], dtype=np.float32) for s in specs]
-    rounds = max(3, min(args.steps, 400))
+                                max_queue=4, max_robots=R)
+    ids = np.array([mtp.mtp_server_register(srv, s) for s in specs], dtype=np.int32)
+    d = np.array([s["d"] for s in specs])
+    n = np.array([s["n"] for s in specs])
+    steps_of = np.array([s["B"] * s["H"] for s in specs], dtype=np.float64)
+    rng = np.random.default_rng(4)
+    state = [np.asarray(s["x0"], np.float64) + rng.uniform(-0.1, 0.1, size=s["d"]) for s in specs]
+    dts = [s["dt"] for s in specs]
 
-    def closed_loop(k):
-        tickets = [mtp.mtp_submit(srv, r, x0[r]) for r in ids]
-        for _ in range(k - 1):
-            for r in ids:
-                if mtp.mtp_poll(srv, tickets[r], outs[r], 60.0) != 0:
-                    raise RuntimeError("serving request timed out")
-                tickets[r] = mtp.mtp_submit(srv, r, x0[r])
-        for r in ids:
-            if mtp.mtp_poll(srv, tickets[r], outs[r], 60.0) != 0:
-                raise RuntimeError("serving request timed out")
+    def open_loop(seconds, record):
+        """Poisson arrivals; returns (completed, rollout steps, latencies)."""
+        t0 = time.perf_counter()
+        next_t = t0 + rng.exponential(1.0 / args.rate_hz, size=R)
+        out_t, out_r, out_sub = [], [], []  # outstanding tickets, robots, submit times
+        done = 0
+        steps = 0.0
+        lat = []
+        while True:
+            now = time.perf_counter()
+            if now - t0 >= seconds and not out_t:
+                break
+            if now - t0 < seconds:
+                due = np.nonzero(next_t <= now)[0]
+                if len(due):
+                    x0 = np.concatenate([state[r] for r in due]).astype(np.float32)
+                    ts = mtp.mtp_submit_many(srv, ids[due], x0)
+                    out_t.extend(ts.tolist())
+                    out_r.extend(due.tolist())
+                    out_sub.extend([now] * len(due))
+                    next_t[due] += rng.exponential(1.0 / args.rate_hz, size=len(due))
+            if out_t:
+                status, u, ready = mtp.mtp_poll_many(srv, np.array(out_t, np.uint64), 32, 0.0)
+                if ready:
+                    t_obs = time.perf_counter()
+                    keep_t, keep_r, keep_s = [], [], []
+                    for k, st in enumerate(status):
+                        r = out_r[k]
+                        if st == 0:
+                            state[r] = _advance(state[r], u[k, :n[r]].astype(np.float64), dts[r])
+                            done += 1
+                            steps += steps_of[r]
+                            if record:
+                                lat.append(t_obs - out_sub[k])
+                        elif st in (5, 6):
+                            keep_t.append(out_t[k])
+                            keep_r.append(r)
+                            keep_s.append(out_sub[k])
+                        else:
+                            raise RuntimeError(f"serving poll failed: status {st}")
+                    out_t, out_r, out_sub = keep_t, keep_r, keep_s
+                    continue
+            time.sleep(100e-6)
+        return done, steps, lat
 
-    closed_loop(args.warmup)
+    open_loop(args.serve_warmup, False)
     s0 = mtp.mtp_server_get_stats(srv)
     with ClockSampler(0) as clocks:
         t0 = time.perf_counter()
-        closed_loop(rounds)
-        dt = time.perf_counter() - t0
+        done, steps, lat = open_loop(args.serve_seconds, True)
+        wall = time.perf_counter() - t0
     s1 = mtp.mtp_server_get_stats(srv)
-    n_req = s1["completed"] - s0["completed"]
+    lat_ms = np.sort(np.array(lat)) * 1e3
+    value = steps / wall
     cycles = s1["cycles"] - s0["cycles"]
-    steps_per_round = sum(s["B"] * s["H"] for s in specs)
-    value = steps_per_round * rounds / dt
-    bytes_in = sum(4 * s["d"] for s in specs)
-    bytes_out = sum(4 * s["n"] for s in specs)
+
+    # saturation: all robots resubmit at once, several rounds
+    def closed_loop(k):
+        t0 = time.perf_counter()
+        for _ in range(k):
+            ts = mtp.mtp_submit_many(srv, ids, np.concatenate([state[r] for r in range(R)]).astype(np.float32))
+            status, _, ready = mtp.mtp_poll_many(srv, ts, 32, 60.0)
+            if ready != R:
+                raise RuntimeError("serving request timed out")
+        return time.perf_counter() - t0
+
+    closed_loop(2)
+    k_sat = 10
+    t_sat = closed_loop(k_sat)
+    srv.close()
+    # the plain path: one request at a time on its own handle
+    sample = list(range(0, R, max(1, R // 64)))
+    hs = {r: mtp.mtp_create(specs[r]) for r in sample}
+    u = np.empty(32, np.float32)
+    for r in sample:
+        mtp.mtp_plan_step_host(hs[r], state[r].astype(np.float32), 1, u)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        for r in sample:
+            mtp.mtp_plan_step_host(hs[r], state[r].astype(np.float32), 1, u)
+            mtp.mtp_shift(hs[r], 1)
+    t_plain = (time.perf_counter() - t0) / (3 * len(sample))
+    torch.cuda.synchronize()
+    for h in hs.values():
+        mtp.mtp_destroy(h)
+    sat_rps = R * k_sat / t_sat
+    plain_rps = 1.0 / t_plain
+    mean_steps = float(steps_of.mean())
     line = {
-        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": rounds,
-        "warmup": args.warmup, "ms_per_step": dt / rounds * 1e3, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": done,
+        "warmup": args.warmup, "ms_per_step": wall / max(done, 1) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"re-plan server, {len(specs)} robots (2-D point masses and "
-                               f"3..9-link arms, H 64..128, B 1024..4096), 1 iteration + shift "
-                               f"per request, max_batch {args.max_batch}, closed loop",
-                   "l2": "not flushed: the working set of all robots (U tensors) exceeds L2",
-                   "step": "one request per robot"},
-        "requests_per_s": n_req / dt,
-        "latency_p50_ms": s1["p50_latency_s"] * 1e3,
-        "latency_p99_ms": s1["p99_latency_s"] * 1e3,
-        "mean_robots_per_cycle": n_req / max(cycles, 1),
-        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": bytes_in,
-                "d2h_bytes_per_step": bytes_out},
+        "config": {"workload": f"re-plan server, {R} robots (2-D point masses and 3..9-link arms, "
+                               f"H 64..128, B 1024..4096), each a Poisson process at "
+                               f"{args.rate_hz:g} Hz; 1 iteration + shift per request; "
+                               f"max_batch {args.max_batch}; {args.serve_seconds:g} s after "
+                               f"{args.serve_warmup:g} s warm-up",
+                   "l2": "not flushed: the robots' candidate tensors together exceed L2",
+                   "step": "one completed re-plan"},
+        "offered_requests_per_s": R * args.rate_hz,
+        "requests_per_s": done / wall,
+        "latency_p50_ms": float(lat_ms[len(lat_ms) // 2]) if len(lat_ms) else None,
+        "latency_p99_ms": float(lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]) if len(lat_ms) else None,
+        "latency": "mtp_submit -> mtp_poll success, host wall time, polled every ~0.1 ms",
+        "mean_robots_per_cycle": (s1["planned"] - s0["planned"]) / max(cycles, 1),
+        "saturation": {"requests_per_s": sat_rps, "rollout_steps_per_s": sat_rps * mean_steps,
+                       "note": "closed loop: all robots resubmit together"},
+        "plain": {"requests_per_s": plain_rps, "rollout_steps_per_s": plain_rps * mean_steps,
+                  "latency_ms": t_plain * 1e3,
+                  "note": f"mtp_plan_step_host + mtp_shift one request at a time, {len(sample)} robots"},
+        "served_over_plain_capacity": sat_rps / plain_rps,
+        "e2e": {"value": value, "unit": METRIC,
+                "h2d_bytes_per_step": float(4 * d.mean()), "d2h_bytes_per_step": float(4 * n.mean())},
         "clocks": clocks.summary(), "baseline_metric": BASELINE_METRIC,
     }
     print(json.dumps(line), flush=True)
-    srv.close()
 
 
 def main():
@@ -568,14 +657,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="arm7", choices=["arm7", "pointmass2", "legged16", "batch", "serve"])
-    ap.add_argument("--instances", type=int, default=256)
-    ap.add_argument("--max-batch", type=int, default=128)
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batch: instances (256); serve: robots (1024)")
+    ap.add_argument("--max-batch", type=int, default=256)
+    ap.add_argument("--rate-hz", type=float, default=50.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-warmup", type=float, default=2.0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--reference-rows", type=int, default=512)
     ap.add_argument("--reference-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.instances is None:
+        args.instances = 1024 if args.workload == "serve" else 256
     if args.workload == "batch":
         run_batch(args)
         return

@@ -341,6 +341,21 @@ mtp_status mtp_submit(mtp_server* srv, int32_t robot, const float* h_x0, uint64_
  * MTP_ERR_CUDA if the server failed. */
 mtp_status mtp_poll(mtp_server* srv, uint64_t ticket, float* h_ustar, double timeout_s);
 
+/* mtp_submit for `count` requests in order: robots[i]'s start state follows
+ * the previous request's in h_x0 (state_dim floats each).  Stops at the first
+ * request refused; *accepted (may be NULL) is the number queued, whose
+ * tickets are in tickets[0 .. accepted).  Returns that refusal's status, or
+ * MTP_OK. */
+mtp_status mtp_submit_many(mtp_server* srv, int32_t count, const int32_t* robots, const float* h_x0,
+                           uint64_t* tickets, int32_t* accepted);
+
+/* mtp_poll for `count` tickets, sharing one deadline timeout_s seconds
+ * away: status[i] is ticket i's mtp_poll status and its u* goes to
+ * h_ustar + i * stride (stride >= its ctrl_dim).  *ready (may be NULL) is
+ * the number of MTP_OK entries.  Returns MTP_OK unless an argument is bad. */
+mtp_status mtp_poll_many(mtp_server* srv, int32_t count, const uint64_t* tickets, float* h_ustar,
+                         int32_t stride, double timeout_s, int32_t* status, int32_t* ready);
+
 mtp_status mtp_server_get_stats(mtp_server* srv, mtp_server_stats* out);
 
 /* Text of the server's last error (worker or call). */

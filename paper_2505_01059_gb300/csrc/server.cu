@@ -11,6 +11,7 @@
 // robots that are not in flight.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -208,6 +209,19 @@ mtp_status server_fail(mtp_server* S, mtp_status st, const std::string& msg) {
   return st;
 }
 
+// One ticket: at most n_max values of its u* go to `out`.
+mtp_status poll_one(mtp_server* S, uint64_t ticket, float* out, int n_max, double wait_s) {
+  switch (S->sched.poll(ticket, out, n_max, wait_s)) {
+    case mtp_sched::kReady:
+      return MTP_OK;
+    case mtp_sched::kUnknown:
+      return server_fail(S, MTP_ERR_INVALID_ARG, "poll: unknown or already collected ticket");
+    default:
+      if (S->failed.load()) return server_fail(S, MTP_ERR_CUDA, "poll: the server failed");
+      return wait_s == 0.0 ? MTP_ERR_NOT_READY : MTP_ERR_TIMEOUT;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -306,15 +320,48 @@ mtp_status mtp_submit(mtp_server* S, int32_t robot, const float* h_x0, uint64_t*
 
 mtp_status mtp_poll(mtp_server* S, uint64_t ticket, float* h_ustar, double timeout_s) {
   if (!S || !h_ustar || !(timeout_s >= 0.0)) return server_fail(S, MTP_ERR_INVALID_ARG, "poll: bad argument");
-  switch (S->sched.poll(ticket, h_ustar, MTP_MAX_CTRL, timeout_s)) {
-    case mtp_sched::kReady:
-      return MTP_OK;
-    case mtp_sched::kUnknown:
-      return server_fail(S, MTP_ERR_INVALID_ARG, "poll: unknown or already collected ticket");
-    default:
-      if (S->failed.load()) return server_fail(S, MTP_ERR_CUDA, "poll: the server failed");
-      return timeout_s == 0.0 ? MTP_ERR_NOT_READY : MTP_ERR_TIMEOUT;
+  return poll_one(S, ticket, h_ustar, MTP_MAX_CTRL, timeout_s);
+}
+
+mtp_status mtp_submit_many(mtp_server* S, int32_t count, const int32_t* robots, const float* h_x0,
+                           uint64_t* tickets, int32_t* accepted) {
+  if (accepted) *accepted = 0;
+  if (!S || count < 0 || (count > 0 && (!robots || !h_x0 || !tickets)))
+    return server_fail(S, MTP_ERR_INVALID_ARG, "submit_many: bad argument");
+  size_t off = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    int d = 0;
+    {
+      std::lock_guard<std::mutex> lock(S->reg_mu);
+      if (robots[i] < 0 || robots[i] >= (int32_t)S->robots.size())
+        return server_fail(S, MTP_ERR_INVALID_ARG, "submit_many: unknown robot");
+      d = S->robot_d[robots[i]];
+    }
+    const mtp_status st = mtp_submit(S, robots[i], h_x0 + off, tickets + i);
+    if (st != MTP_OK) return st;
+    off += (size_t)d;
+    if (accepted) *accepted = i + 1;
   }
+  return MTP_OK;
+}
+
+mtp_status mtp_poll_many(mtp_server* S, int32_t count, const uint64_t* tickets, float* h_ustar,
+                         int32_t stride, double timeout_s, int32_t* status, int32_t* ready) {
+  if (ready) *ready = 0;
+  if (!S || count < 0 || stride < 1 || !(timeout_s >= 0.0) ||
+      (count > 0 && (!tickets || !h_ustar || !status)))
+    return server_fail(S, MTP_ERR_INVALID_ARG, "poll_many: bad argument");
+  const double deadline = mtp_sched::now_seconds() + timeout_s;
+  int32_t n_ok = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    const double left = timeout_s > 0.0 ? std::max(0.0, deadline - mtp_sched::now_seconds()) : 0.0;
+    mtp_status st = poll_one(S, tickets[i], h_ustar + (size_t)i * stride, stride, left);
+    if (st == MTP_ERR_NOT_READY && timeout_s > 0.0) st = MTP_ERR_TIMEOUT;  // the shared deadline passed
+    status[i] = st;
+    if (st == MTP_OK) ++n_ok;
+  }
+  if (ready) *ready = n_ok;
+  return MTP_OK;
 }
 
 mtp_status mtp_server_get_stats(mtp_server* S, mtp_server_stats* out) {

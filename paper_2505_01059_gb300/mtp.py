@@ -44,6 +44,7 @@ EXPORTS = [
     "mtp_batch_autotune", "mtp_batch_reserve", "mtp_batch_fill", "mtp_batch_shift",
     "mtp_problem_device_bytes", "mtp_server_create", "mtp_server_destroy", "mtp_server_register",
     "mtp_submit", "mtp_poll", "mtp_server_get_stats", "mtp_server_last_error",
+    "mtp_submit_many", "mtp_poll_many",
 ]
 
 
@@ -154,6 +155,8 @@ def load_library(path: str = LIB_PATH):
         "mtp_poll": (i32, [vp, C.c_uint64, vp, C.c_double]),
         "mtp_server_get_stats": (i32, [vp, C.POINTER(MtpServerStats)]),
         "mtp_server_last_error": (C.c_char_p, [vp]),
+        "mtp_submit_many": (i32, [vp, i32, vp, vp, vp, vp]),
+        "mtp_poll_many": (i32, [vp, i32, vp, vp, i32, C.c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -629,3 +632,32 @@ def mtp_server_get_stats(srv: Server) -> dict:
     s = MtpServerStats()
     _check(load_library().mtp_server_get_stats(srv.ptr, C.byref(s)))
     return {k: getattr(s, k) for k, _ in MtpServerStats._fields_}
+
+
+def mtp_submit_many(srv: Server, robots: np.ndarray, x0_packed: np.ndarray) -> np.ndarray:
+    """Queues one request per entry of `robots` (start states packed in
+    order); returns the tickets.  Raises on the first refusal, after the
+    requests before it were queued (their tickets are in the error's
+    `tickets` attribute)."""
+    r = np.ascontiguousarray(robots, dtype=np.int32)
+    x = np.ascontiguousarray(x0_packed, dtype=np.float32)
+    t = np.zeros(len(r), dtype=np.uint64)
+    acc = C.c_int32()
+    st = load_library().mtp_submit_many(srv.ptr, len(r), r.ctypes.data, x.ctypes.data,
+                                        t.ctypes.data, C.byref(acc))
+    if st != MTP_OK:
+        err = MtpError(st, srv._err())
+        err.tickets = t[:acc.value]
+        raise err
+    return t
+
+
+def mtp_poll_many(srv: Server, tickets: np.ndarray, stride: int, timeout_s: float = 0.0):
+    """Returns (status per ticket, u* rows (count, stride), number ready)."""
+    t = np.ascontiguousarray(tickets, dtype=np.uint64)
+    out = np.zeros((len(t), stride), dtype=np.float32)
+    status = np.zeros(len(t), dtype=np.int32)
+    ready = C.c_int32()
+    _check(load_library().mtp_poll_many(srv.ptr, len(t), t.ctypes.data, out.ctypes.data, int(stride),
+                                        float(timeout_s), status.ctypes.data, C.byref(ready)))
+    return status, out, ready.value

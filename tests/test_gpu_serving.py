@@ -143,3 +143,34 @@ def test_memory_budget_admission(mtp):
         mtp.mtp_server_register(srv, dict(small, E=10 ** 6))  # does not validate
     assert ei.value.status == 1
     srv.close()
+
+
+def test_submit_many_poll_many_match_single_calls(mtp):
+    specs = _fleet()
+    srv = mtp.mtp_server_create(max_batch=4, iters_per_request=1, shift_after=1, max_queue=2,
+                                max_robots=16)
+    ids = np.array([mtp.mtp_server_register(srv, s) for s in specs], dtype=np.int32)
+    twins = [mtp.mtp_create(s) for s in specs]
+    rng = np.random.default_rng(3)
+    for _ in range(2):
+        x0s = [_x0(s, rng) for s in specs]
+        tickets = mtp.mtp_submit_many(srv, ids, np.concatenate(x0s))
+        assert len(set(tickets.tolist())) == len(specs) and (tickets > 0).all()
+        status, out, ready = mtp.mtp_poll_many(srv, tickets, 32, timeout_s=30.0)
+        assert ready == len(specs) and (status == OK).all()
+        for r, s in enumerate(specs):
+            want = torch.empty(s["n"], device=DEV)
+            mtp.mtp_plan_step(twins[r], torch.tensor(x0s[r], device=DEV), 1, want)
+            mtp.mtp_shift(twins[r], 1)
+            assert np.array_equal(out[r, :s["n"]], want.cpu().numpy()), r
+        status, _, ready = mtp.mtp_poll_many(srv, tickets, 32, 0.0)  # all collected now
+        assert ready == 0 and (status == 1).all()
+    # a refusal part-way: the requests before it are queued
+    with pytest.raises(mtp.MtpError) as ei:
+        mtp.mtp_submit_many(srv, np.array([0, 99], dtype=np.int32), np.zeros(64, np.float32))
+    assert ei.value.status == 1 and len(ei.value.tickets) == 1
+    status, _, ready = mtp.mtp_poll_many(srv, ei.value.tickets, 32, 30.0)
+    assert ready == 1
+    srv.close()
+    for t in twins:
+        mtp.mtp_destroy(t)
