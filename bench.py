@@ -523,7 +523,7 @@ def run_serve(args):
     specs = W.robots(count=args.instances)
     R = len(specs)
     srv = mtp.mtp_server_create(max_batch=args.max_batch, iters_per_request=1, shift_after=1,
-                                max_queue=4, max_robots=R)
+                                max_queue=8, max_robots=R)
     ids = np.array([mtp.mtp_server_register(srv, s) for s in specs], dtype=np.int32)
     d = np.array([s["d"] for s in specs])
     n = np.array([s["n"] for s in specs])
@@ -531,6 +531,8 @@ def run_serve(args):
     rng = np.random.default_rng(4)
     state = [np.asarray(s["x0"], np.float64) + rng.uniform(-0.1, 0.1, size=s["d"]) for s in specs]
     dts = [s["dt"] for s in specs]
+
+    refused = [0]
 
     def open_loop(seconds, record):
         """Poisson arrivals; returns (completed, rollout steps, latencies)."""
@@ -547,12 +549,22 @@ def run_serve(args):
             if now - t0 < seconds:
                 due = np.nonzero(next_t <= now)[0]
                 if len(due):
-                    x0 = np.concatenate([state[r] for r in due]).astype(np.float32)
-                    ts = mtp.mtp_submit_many(srv, ids[due], x0)
-                    out_t.extend(ts.tolist())
-                    out_r.extend(due.tolist())
-                    out_sub.extend([now] * len(due))
                     next_t[due] += rng.exponential(1.0 / args.rate_hz, size=len(due))
+                while len(due):
+                    x0 = np.concatenate([state[r] for r in due]).astype(np.float32)
+                    try:
+                        ts = mtp.mtp_submit_many(srv, ids[due], x0)
+                        skip = 0
+                    except mtp.MtpError as e:  # a full queue drops that arrival
+                        if e.status != 4:
+                            raise
+                        ts, skip = e.tickets, 1
+                        refused[0] += record
+                    k = len(ts)
+                    out_t.extend(ts.tolist())
+                    out_r.extend(due[:k].tolist())
+                    out_sub.extend([now] * k)
+                    due = due[k + skip:]
             if out_t:
                 status, u, ready = mtp.mtp_poll_many(srv, np.array(out_t, np.uint64), 32, 0.0)
                 if ready:
@@ -632,6 +644,7 @@ def run_serve(args):
                    "l2": "not flushed: the robots' candidate tensors together exceed L2",
                    "step": "one completed re-plan"},
         "offered_requests_per_s": R * args.rate_hz,
+        "refused": refused[0],
         "requests_per_s": done / wall,
         "latency_p50_ms": float(lat_ms[len(lat_ms) // 2]) if len(lat_ms) else None,
         "latency_p99_ms": float(lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]) if len(lat_ms) else None,
