@@ -36,6 +36,10 @@ SMS = 152
 FP32_LANES_PER_SM = 128
 
 
+ROLLOUT_KERNEL = {"pointmass": "k_rollout_pm", "chain": "k_rollout_chain",
+                  "legged": "k_rollout_legged"}
+
+
 def workload(name: str) -> dict:
     from paper_2505_01059_gb300 import workloads as W
     if name == "arm7":
@@ -471,7 +475,7 @@ def run_ours(args, spec, name):
             "stage_ms_per_step": dict(zip(("generate", "rollout", "select", "update"),
                                           [v / max(n_it, 1) for v in stage_ms])),
             "stage_share": share,
-            "roofline": {"bound": "alu", "kernel": f"k_rollout_{spec['dyn']}",
+            "roofline": {"bound": "alu", "kernel": ROLLOUT_KERNEL[spec["dyn"]],
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "flops_per_launch": fl,
@@ -480,7 +484,7 @@ def run_ours(args, spec, name):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 4 * s["d"],
                     "d2h_bytes_per_step": 4 * s["n"]},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": s["kernels_per_iteration"] * args.steps,
             "clocks": clk,
             "baseline_metric": BASELINE_METRIC,
             "wall_s_timed": t_wall,

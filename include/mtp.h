@@ -117,6 +117,7 @@ typedef struct mtp_problem {
 
 typedef struct mtp_sizes {
   int32_t B, P, L, E, H, n, d, M, N;
+  int32_t kernels_per_iteration; /* kernel launches of one mtp_plan_step iteration */
 } mtp_sizes;
 
 /* Device buffers owned by a handle (valid until mtp_destroy).  After

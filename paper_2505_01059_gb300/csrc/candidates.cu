@@ -57,6 +57,11 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
   const int G = (Hn + 3) >> 2;
   const int items = a.local_rows * G + (a.U_mean ? G : 0);
   const int stride = nlb * blockDim.x;
+  // whole 16-byte groups: one vector load of mu and sigma and one vector
+  // store per generator call (rows of a 16-byte aligned tensor stay aligned)
+  const bool vec = (Hn & 3) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(a.U_local) | reinterpret_cast<uintptr_t>(a.mu) |
+                     reinterpret_cast<uintptr_t>(a.sigma)) & 15) == 0;
   for (int e = lb * blockDim.x + threadIdx.x; e < items; e += stride) {
     const int row = e / G;
     const int q = e - row * G;
@@ -67,6 +72,19 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
       box_muller(r.x, r.y, eps[0], eps[1]);
       box_muller(r.z, r.w, eps[2], eps[3]);
       float* dst = a.U_local + (size_t)row * Hn;
+      if (vec) {
+        const float4 s4 = __ldg(reinterpret_cast<const float4*>(a.sigma) + q);
+        const float4 m4 = __ldg(reinterpret_cast<const float4*>(a.mu) + q);
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w}, mv[4] = {m4.x, m4.y, m4.z, m4.w};
+        float o[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          o[w] = clamp_box(fmaf(sv[w], eps[w], mv[w]), a.umin[i], a.umax[i]);
+          if (++i == n) i = 0;
+        }
+        reinterpret_cast<float4*>(dst)[q] = make_float4(o[0], o[1], o[2], o[3]);
+        continue;
+      }
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
         const int el = 4 * q + w;
@@ -270,6 +288,29 @@ __global__ void __launch_bounds__(kThreads) k_local_batch(const CandArgs* __rest
   local_rows_body(args[lo], blockIdx.x - local_start[lo], local_start[lo + 1] - local_start[lo]);
 }
 
+// Def. 1: the graph Z of the current iteration written to global memory,
+// block `blk` of `nblk` given to it, four dimensions per generator call.
+__device__ __forceinline__ void graph_Z_body(const CandArgs& a, float* Z, int blk, int nblk) {
+  const int M = a.dm.M, N = a.dm.N, n = a.dm.n;
+  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
+  const int ng = (n + 3) >> 2;
+  for (int e = blk * blockDim.x + threadIdx.x; e < M * N * ng; e += nblk * blockDim.x) {
+    const int node = e / ng, g = e - node * ng;
+    const uint4 r = philox(make_uint4((uint32_t)node, (uint32_t)g, iter, kTagGraph), a.key);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int i = 4 * g + w;
+      if (i < n) Z[node * n + i] = fmaf(a.umax[i] - a.umin[i], unit24(pick(r, w)), a.umin[i]);
+    }
+  }
+}
+
+// One planning problem whose graph is too large to regenerate in every
+// block's shared memory: Z once per iteration, its graph blocks gather from it.
+__global__ void __launch_bounds__(kThreads) k_graph_Z(const CandArgs a, float* Z) {
+  graph_Z_body(a, Z, blockIdx.x, gridDim.x);
+}
+
 // Def. 1 for many planning problems: each instance's graph Z for its
 // current iteration, written once to global memory so that its graph
 // blocks gather from it instead of regenerating it.
@@ -283,21 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_graph_Z_batch(const CandArgs* __re
     if (block_start[mid] <= (int)blockIdx.x) lo = mid;
     else hi = mid;
   }
-  const CandArgs& a = args[lo];
-  const int M = a.dm.M, N = a.dm.N, n = a.dm.n;
-  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
-  const int ng = (n + 3) >> 2;
-  float* Z = Zs[lo];
-  for (int e = (blockIdx.x - block_start[lo]) * blockDim.x + threadIdx.x; e < M * N * ng;
-       e += (block_start[lo + 1] - block_start[lo]) * blockDim.x) {
-    const int node = e / ng, g = e - node * ng;
-    const uint4 r = philox(make_uint4((uint32_t)node, (uint32_t)g, iter, kTagGraph), a.key);
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const int i = 4 * g + w;
-      if (i < n) Z[node * n + i] = fmaf(a.umax[i] - a.umin[i], unit24(pick(r, w)), a.umin[i]);
-    }
-  }
+  graph_Z_body(args[lo], Zs[lo], blockIdx.x - block_start[lo], block_start[lo + 1] - block_start[lo]);
 }
 
 // Def. 1 / Alg. 1 outputs for inspection: Z, I and C written to global memory.
@@ -362,6 +389,15 @@ cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t 
   const int grid = a.graph_blocks + local_blocks;
   if (grid <= 0) return cudaSuccess;
   k_candidates<<<grid, kThreads, candidates_smem_bytes(a), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_graph_Z(const CandArgs& a, float* Z, cudaStream_t s) {
+  const int items = a.dm.M * a.dm.N * ((a.dm.n + 3) / 4);
+  int blocks = (items + kThreads - 1) / kThreads;
+  if (blocks > 152) blocks = 152;
+  if (blocks <= 0) return cudaSuccess;
+  k_graph_Z<<<blocks, kThreads, 0, s>>>(a, Z);
   return cudaGetLastError();
 }
 

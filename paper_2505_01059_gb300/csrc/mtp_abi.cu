@@ -49,6 +49,7 @@ struct mtp_handle {
   float* delta = nullptr;
   float inv_h = 1.f;
   int paths_per_block = 1;
+  bool global_Z = false;  // Z written once per iteration instead of per graph block
   // planner state
   double* mu = nullptr;
   double* sigma = nullptr;
@@ -333,6 +334,18 @@ LeggedModel legged_model(const mtp_problem& p) {
   return m;
 }
 
+// Candidate generation of one handle (graph rows, local rows, mean row as
+// `c` asks), with the graph written first when it is not regenerated per block.
+cudaError_t launch_generate(const mtp_handle* h, CandArgs& c, cudaStream_t s) {
+  if (c.graph_blocks > 0 && h->global_Z && !c.C_in) {
+    c.Z_global = h->Z;
+    cudaError_t e = launch_graph_Z(c, h->Z, s);
+    if (e != cudaSuccess) return e;
+  }
+  const int local_blocks = c.U_local ? local_blocks_for(h, (long long)c.local_rows + 1) : 0;
+  return launch_candidates(c, local_blocks, s);
+}
+
 cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
   const mtp_problem& p = h->pr;
   if (p.dyn == MTP_DYN_POINTMASS) return launch_rollout_pointmass(a, pointmass_model(p), s);
@@ -353,7 +366,7 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev) {
   c.U_local = h->U;
   c.local_rows = dm.L;
   c.U_mean = h->U + Hn * (dm.B - 1);
-  if ((e = launch_candidates(c, local_blocks_for(h, (long long)dm.L + 1), s)) != cudaSuccess) return e;
+  if ((e = launch_generate(h, c, s)) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
   RolloutArgs r = rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, dm.B, h->cost);
   if ((e = launch_rollout(h, r, s)) != cudaSuccess) return e;
@@ -412,6 +425,9 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   // paths for Akima so its per-(path, dimension) coefficient pass is wide;
   // shrunk until the block's shared memory fits
   const long long Hn = (long long)dm.H * dm.n;
+  // a graph larger than 16 KB is written once per iteration rather than
+  // regenerated in every graph block's shared memory
+  h->global_Z = (long long)dm.M * dm.N * dm.n > 4096;
   int spb = (int)((4096 + Hn - 1) / Hn);
   if (p.interp == MTP_INTERP_AKIMA && spb < 16) spb = 16;
   if (spb < 1) spb = 1;
@@ -422,6 +438,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
     probe.interp = p.interp;
     probe.graph_blocks = 1;
     probe.paths_per_block = spb;
+    probe.Z_global = h->global_Z ? reinterpret_cast<float*>(16) : nullptr;  // only tested for null
     if (candidates_smem_bytes(probe) <= kMaxSmem || spb == 1) break;
     spb /= 2;
   }
@@ -490,7 +507,8 @@ const char* mtp_last_error(const mtp_handle* h) {
 mtp_status mtp_get_sizes(const mtp_handle* h, mtp_sizes* out) {
   if (!h || !out) return MTP_ERR_INVALID_ARG;
   const Dims& d = h->dm;
-  *out = mtp_sizes{d.B, d.P, d.L, d.E, d.H, d.n, d.d, d.M, d.N};
+  // candidates (+ graph when written once), rollout, select, update
+  *out = mtp_sizes{d.B, d.P, d.L, d.E, d.H, d.n, d.d, d.M, d.N, h->global_Z && d.P > 0 ? 5 : 4};
   return MTP_OK;
 }
 
@@ -532,7 +550,7 @@ mtp_status mtp_sample_local(mtp_handle* h, uint32_t iter, float* d_U, void* stre
   c.U_local = d_U;
   c.local_rows = h->dm.L;
   c.U_mean = d_U + Hn * (h->dm.B - 1);
-  cudaError_t e = launch_candidates(c, local_blocks_for(h, (long long)h->dm.L + 1), (cudaStream_t)stream);
+  cudaError_t e = launch_generate(h, c, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "sample_local");
   return MTP_OK;
 }
@@ -549,7 +567,7 @@ mtp_status mtp_generate_candidates(mtp_handle* h, uint32_t iter, float* d_U, voi
   c.U_local = d_U;
   c.local_rows = dm.L;
   c.U_mean = d_U + Hn * (dm.B - 1);
-  cudaError_t e = launch_candidates(c, local_blocks_for(h, (long long)dm.L + 1), (cudaStream_t)stream);
+  cudaError_t e = launch_generate(h, c, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "generate_candidates");
   return MTP_OK;
 }

@@ -201,6 +201,7 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 size_t select_smem_bytes(int B, int E);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 // batched forms: one launch over many planning problems
+cudaError_t launch_graph_Z(const CandArgs& a, float* Z, cudaStream_t s);
 cudaError_t launch_local_batch(const CandArgs* d_args, const int* d_local_start, int count,
                                int total_blocks, cudaStream_t s);
 cudaError_t launch_graph_Z_batch(const CandArgs* d_args, float* const* d_Z, const int* d_block_start,

@@ -81,7 +81,8 @@ class MtpProblem(C.Structure):
 
 
 class MtpSizes(C.Structure):
-    _fields_ = [(k, C.c_int32) for k in ("B", "P", "L", "E", "H", "n", "d", "M", "N")]
+    _fields_ = [(k, C.c_int32) for k in ("B", "P", "L", "E", "H", "n", "d", "M", "N",
+                                         "kernels_per_iteration")]
 
 
 class MtpBuffers(C.Structure):
