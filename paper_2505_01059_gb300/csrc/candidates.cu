@@ -46,10 +46,23 @@ __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& e0, 
   e1 = -radius * sn;
 }
 
+// The control box copied to shared memory once per block: reading it from
+// the kernel parameters with a run-time dimension index goes through the
+// constant cache's indexed path, whose throughput bounded the whole kernel.
+__device__ __forceinline__ void stage_box(const CandArgs& a, float* lo, float* hi) {
+  for (int i = threadIdx.x; i < a.dm.n; i += blockDim.x) {
+    lo[i] = a.umin[i];
+    hi[i] = a.umax[i];
+  }
+  __syncthreads();
+}
+
 // Local rows (Alg. 2 local sampling) and the mean row: block `lb` of
 // `nlb` blocks given to them; mu + sigma * eps, four elements of a row per
 // generator call.
 __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int nlb) {
+  __shared__ float box_lo[MTP_MAX_CTRL], box_hi[MTP_MAX_CTRL];
+  stage_box(a, box_lo, box_hi);
   const Dims dm = a.dm;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
   const int n = dm.n;
@@ -79,7 +92,7 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
         float o[4];
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-          o[w] = clamp_box(fmaf(sv[w], eps[w], mv[w]), a.umin[i], a.umax[i]);
+          o[w] = clamp_box(fmaf(sv[w], eps[w], mv[w]), box_lo[i], box_hi[i]);
           if (++i == n) i = 0;
         }
         reinterpret_cast<float4*>(dst)[q] = make_float4(o[0], o[1], o[2], o[3]);
@@ -90,7 +103,7 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
         const int el = 4 * q + w;
         if (el < Hn) {
           const float u = fmaf(a.sigma[el], eps[w], a.mu[el]);
-          dst[el] = clamp_box(u, a.umin[i], a.umax[i]);
+          dst[el] = clamp_box(u, box_lo[i], box_hi[i]);
         }
         if (++i == n) i = 0;
       }
@@ -98,7 +111,7 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
         const int el = 4 * q + w;
-        if (el < Hn) a.U_mean[el] = clamp_box(a.mu[el], a.umin[i], a.umax[i]);
+        if (el < Hn) a.U_mean[el] = clamp_box(a.mu[el], box_lo[i], box_hi[i]);
         if (++i == n) i = 0;
       }
     }
@@ -115,6 +128,8 @@ __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, 
   const int Hn = H * n;
 
   if (bid < a.graph_blocks) {
+    __shared__ float box_lo[MTP_MAX_CTRL], box_hi[MTP_MAX_CTRL];
+    stage_box(a, box_lo, box_hi);
     const int SPB = a.paths_per_block;
     const int b0 = bid * SPB;
     const int nb = min(SPB, a.graph_rows - b0);
@@ -132,7 +147,7 @@ __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, 
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             const int i = 4 * g + w;
-            if (i < n) Z[node * n + i] = fmaf(a.umax[i] - a.umin[i], unit24(pick(r, w)), a.umin[i]);
+            if (i < n) Z[node * n + i] = fmaf(box_hi[i] - box_lo[i], unit24(pick(r, w)), box_lo[i]);
           }
         }
         __syncthreads();
@@ -227,7 +242,7 @@ __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, 
         const float z0 = C[(sp * M + k) * n + i], z1 = C[(sp * M + k + 1) * n + i];
         u = fmaf(w, z1 - z0, z0);
       }
-      out[e] = clamp_box(u, a.umin[i], a.umax[i]);
+      out[e] = clamp_box(u, box_lo[i], box_hi[i]);
       // advance (sp, t, i) by blockDim.x elements
       sp += ds;
       t += dt;
@@ -291,6 +306,8 @@ __global__ void __launch_bounds__(kThreads) k_local_batch(const CandArgs* __rest
 // Def. 1: the graph Z of the current iteration written to global memory,
 // block `blk` of `nblk` given to it, four dimensions per generator call.
 __device__ __forceinline__ void graph_Z_body(const CandArgs& a, float* Z, int blk, int nblk) {
+  __shared__ float box_lo[MTP_MAX_CTRL], box_hi[MTP_MAX_CTRL];
+  stage_box(a, box_lo, box_hi);
   const int M = a.dm.M, N = a.dm.N, n = a.dm.n;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
   const int ng = (n + 3) >> 2;
@@ -300,7 +317,7 @@ __device__ __forceinline__ void graph_Z_body(const CandArgs& a, float* Z, int bl
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const int i = 4 * g + w;
-      if (i < n) Z[node * n + i] = fmaf(a.umax[i] - a.umin[i], unit24(pick(r, w)), a.umin[i]);
+      if (i < n) Z[node * n + i] = fmaf(box_hi[i] - box_lo[i], unit24(pick(r, w)), box_lo[i]);
     }
   }
 }
