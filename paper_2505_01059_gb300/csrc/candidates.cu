@@ -275,17 +275,18 @@ __global__ void __launch_bounds__(kThreads) k_candidates_batch(const CandArgs* _
                                                                int count) {
   extern __shared__ float smem[];
   __shared__ CandArgs sa;
+  const int blk = block_start[0] + (int)blockIdx.x;  // block_start holds absolute block numbers
   int lo = 0, hi = count;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (block_start[mid] <= (int)blockIdx.x) lo = mid;
+    if (block_start[mid] <= blk) lo = mid;
     else hi = mid;
   }
   const int* src = reinterpret_cast<const int*>(args + lo);
   int* dst = reinterpret_cast<int*>(&sa);
   for (int w = threadIdx.x; w < (int)(sizeof(CandArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
   __syncthreads();
-  candidates_body(sa, smem, blockIdx.x - block_start[lo], block_start[lo + 1] - block_start[lo]);
+  candidates_body(sa, smem, blk - block_start[lo], block_start[lo + 1] - block_start[lo]);
 }
 
 // Local rows of many planning problems (no shared memory, so the blocks
@@ -294,13 +295,14 @@ __global__ void __launch_bounds__(kThreads) k_candidates_batch(const CandArgs* _
 __global__ void __launch_bounds__(kThreads) k_local_batch(const CandArgs* __restrict__ args,
                                                           const int* __restrict__ local_start,
                                                           int count) {
+  const int blk = local_start[0] + (int)blockIdx.x;  // local_start holds absolute block numbers
   int lo = 0, hi = count;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (local_start[mid] <= (int)blockIdx.x) lo = mid;
+    if (local_start[mid] <= blk) lo = mid;
     else hi = mid;
   }
-  local_rows_body(args[lo], blockIdx.x - local_start[lo], local_start[lo + 1] - local_start[lo]);
+  local_rows_body(args[lo], blk - local_start[lo], local_start[lo + 1] - local_start[lo]);
 }
 
 // Def. 1: the graph Z of the current iteration written to global memory,
@@ -335,13 +337,14 @@ __global__ void __launch_bounds__(kThreads) k_graph_Z_batch(const CandArgs* __re
                                                             float* const* __restrict__ Zs,
                                                             const int* __restrict__ block_start,
                                                             int count) {
+  const int blk = block_start[0] + (int)blockIdx.x;  // block_start holds absolute block numbers
   int lo = 0, hi = count;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (block_start[mid] <= (int)blockIdx.x) lo = mid;
+    if (block_start[mid] <= blk) lo = mid;
     else hi = mid;
   }
-  graph_Z_body(args[lo], Zs[lo], blockIdx.x - block_start[lo], block_start[lo + 1] - block_start[lo]);
+  graph_Z_body(args[lo], Zs[lo], blk - block_start[lo], block_start[lo + 1] - block_start[lo]);
 }
 
 // Def. 1 / Alg. 1 outputs for inspection: Z, I and C written to global memory.

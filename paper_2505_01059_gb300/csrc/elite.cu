@@ -321,7 +321,8 @@ template <int G>
 __global__ void __launch_bounds__(128) k_update_batch(const UpdateArgs* __restrict__ args,
                                                       const int* __restrict__ thread_start,
                                                       int count) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  // thread_start holds absolute thread numbers; this launch starts at thread_start[0]
+  const int gt = __ldg(thread_start) + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (gt >= __ldg(thread_start + count)) return;
   int lo = 0, hi = count;
   while (hi - lo > 1) {

@@ -769,9 +769,13 @@ struct BatchGroup {
   int rows_first = 0;         // offset of this group's row_start segment
   int total_rows = 0;
   int block = 128;
+  // this group's share of the generation, selection and update launches
+  int z_blocks = 0, cand_blocks = 0, local_blocks = 0, upd_threads = 0;
+  size_t cand_smem = 0, sel_smem = 0;
 };
 
 constexpr int kMaxGroups = 64;
+constexpr size_t kBatchGraphSmem = 40 * 1024;  // four graph blocks per SM
 
 // Device tables of a batch, packed into one device block that is refilled in
 // place from a pinned host mirror with one copy.  The layout depends on the
@@ -842,8 +846,6 @@ struct mtp_batch {
   int device = 0;
   BatchTables t;
   int count = 0;
-  int cand_blocks = 0, local_blocks = 0, z_blocks = 0, upd_warps = 0;
-  size_t cand_smem = 0, sel_smem = 0;
   std::vector<BatchGroup> groups;
   std::map<std::pair<int, int>, int> tuned;  // (dyn, n) -> block chosen by the autotuner
   std::vector<int> x0_off, us_off;
@@ -949,32 +951,51 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
   BatchTables hv = t;
   const size_t used = layout_tables(&t, t.d_block, count, n_dyn[MTP_DYN_POINTMASS],
                                     n_dyn[MTP_DYN_CHAIN], n_dyn[MTP_DYN_LEGGED], (int)b->groups.size());
-  // candidates
-  hv.d_cand_start[0] = hv.d_z_start[0] = hv.d_local_start[0] = 0;
-  b->cand_smem = 0;
-  for (int i = 0; i < count; ++i) {
-    mtp_handle* h = handles[i];
+  // candidate generation, selection and update tables in group order, so
+  // that each group's stream launches them over a contiguous range
+  hv.d_cand_start[0] = hv.d_z_start[0] = hv.d_local_start[0] = hv.d_warp_start[0] = 0;
+  for (int pos = 0; pos < count; ++pos) {
+    mtp_handle* h = handles[order[pos]];
     const Dims& dm = h->dm;
     const size_t Hn = (size_t)dm.H * dm.n;
     CandArgs c = cand_args(h, 0, h->iter_dev);
     c.U_graph = h->U + Hn * dm.L;
     c.graph_rows = dm.P;
-    c.graph_blocks = (dm.P + h->paths_per_block - 1) / h->paths_per_block;
     c.U_local = h->U;
     c.local_rows = dm.L;
     c.U_mean = h->U + Hn * (dm.B - 1);
     c.Z_global = h->Z;
-    hv.d_Z[i] = h->Z;
-    hv.d_z_start[i + 1] = hv.d_z_start[i] + (dm.M * dm.N * ((dm.n + 3) / 4) + 255) / 256;
+    // one launch gives every block the largest instance's shared memory, so
+    // paths per block shrink until the instance fits kBatchGraphSmem (a
+    // path's values do not depend on how paths are grouped into blocks)
+    c.paths_per_block = h->paths_per_block;
+    c.graph_blocks = 1;  // counts the graph part in candidates_smem_bytes
+    while (c.paths_per_block > 1 && candidates_smem_bytes(c) > kBatchGraphSmem) c.paths_per_block /= 2;
+    c.graph_blocks = (dm.P + c.paths_per_block - 1) / c.paths_per_block;
+    hv.d_Z[pos] = h->Z;
+    hv.d_z_start[pos + 1] = hv.d_z_start[pos] + (dm.M * dm.N * ((dm.n + 3) / 4) + 255) / 256;
     const long long items = ((long long)dm.L + 1) * (((long long)Hn + 3) / 4);
-    hv.d_cand[i] = c;
-    hv.d_cand_start[i + 1] = hv.d_cand_start[i] + c.graph_blocks;  // local rows run apart
-    hv.d_local_start[i + 1] = hv.d_local_start[i] + (int)std::max<long long>(1, (items + 1023) / 1024);
-    b->cand_smem = std::max(b->cand_smem, candidates_smem_bytes(c));
+    hv.d_cand[pos] = c;
+    hv.d_cand_start[pos + 1] = hv.d_cand_start[pos] + c.graph_blocks;  // local rows run apart
+    hv.d_local_start[pos + 1] = hv.d_local_start[pos] + (int)std::max<long long>(1, (items + 1023) / 1024);
+    hv.d_sel[pos] = SelectArgs{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
+                               h->elite, h->weight, h->ustar, nullptr, nullptr};
+    hv.d_upd[pos] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
+                               h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
+    hv.d_warp_start[pos + 1] = hv.d_warp_start[pos] + update_threads(dm.H, dm.n);
   }
-  b->cand_blocks = hv.d_cand_start[count];
-  b->z_blocks = hv.d_z_start[count];
-  b->local_blocks = hv.d_local_start[count];
+  for (auto& g : b->groups) {
+    const int a0 = g.first, a1 = g.first + g.count;
+    g.z_blocks = hv.d_z_start[a1] - hv.d_z_start[a0];
+    g.cand_blocks = hv.d_cand_start[a1] - hv.d_cand_start[a0];
+    g.local_blocks = hv.d_local_start[a1] - hv.d_local_start[a0];
+    g.upd_threads = hv.d_warp_start[a1] - hv.d_warp_start[a0];
+    g.cand_smem = g.sel_smem = 0;
+    for (int pos = a0; pos < a1; ++pos) {
+      g.cand_smem = std::max(g.cand_smem, candidates_smem_bytes(hv.d_cand[pos]));
+      g.sel_smem = std::max(g.sel_smem, select_smem_bytes(hv.d_sel[pos].B, hv.d_sel[pos].E));
+    }
+  }
   // rollouts, in group order; whole warps per instance
   int rs = 0;
   for (auto& g : b->groups) {
@@ -993,29 +1014,19 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
     g.total_rows = row[g.count];
     rs += g.count + 1;
   }
-  // selection, update, packing of x0 and u*
+  // packing of x0 and u*, in the caller's order
   b->x0_off.assign(count + 1, 0);
   b->us_off.assign(count + 1, 0);
-  hv.d_warp_start[0] = 0;
-  b->sel_smem = 0;
+  hv.d_x0_off[0] = hv.d_us_off[0] = 0;
   for (int i = 0; i < count; ++i) {
     mtp_handle* h = handles[i];
-    const Dims& dm = h->dm;
-    hv.d_sel[i] = SelectArgs{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
-                             h->elite, h->weight, h->ustar, nullptr, nullptr};
-    b->sel_smem = std::max(b->sel_smem, select_smem_bytes(dm.B, dm.E));
-    hv.d_upd[i] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
-                             h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
-    hv.d_warp_start[i + 1] = hv.d_warp_start[i] + update_threads(dm.H, dm.n);
     hv.d_x0_dst[i] = h->x0;
     hv.d_ustar_src[i] = h->ustar;
-    b->x0_off[i + 1] = b->x0_off[i] + dm.d;
-    b->us_off[i + 1] = b->us_off[i] + dm.n;
+    b->x0_off[i + 1] = b->x0_off[i] + h->dm.d;
+    b->us_off[i + 1] = b->us_off[i] + h->dm.n;
     hv.d_x0_off[i + 1] = b->x0_off[i + 1];
     hv.d_us_off[i + 1] = b->us_off[i + 1];
   }
-  hv.d_x0_off[0] = hv.d_us_off[0] = 0;
-  b->upd_warps = hv.d_warp_start[count];
   if ((e = cudaMemcpyAsync(t.d_block, t.h_block, used, cudaMemcpyHostToDevice, s)) ||
       (e = cudaEventRecord(t.copied, s)))
     return e;
@@ -1042,27 +1053,32 @@ cudaError_t launch_group(const mtp_batch* b, const BatchGroup& g, int block, cud
   return launch_rollout_chain_batch(ra, t.d_cm + g.model_first, rs, g.count, g.total_rows, g.n, block, s);
 }
 
-// One batched Alg. 2 iteration: graphs, graph paths and local rows of all
-// instances, the rollouts of each (dynamics, dimension) group on its own
-// stream, then one selection block per instance and one update launch.
+// One batched Alg. 2 iteration.  Each (dynamics, dimension) group runs its
+// whole iteration on its own stream: graphs, graph paths and local rows of
+// its instances, its rollouts, one selection block per instance, the update.
+// Groups overlap one another (one group's generation fills the issue slots
+// that the others' latency-bound rollouts leave idle).
 cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
   cudaError_t e;
   const BatchTables& t = b->t;
-  const int count = b->count;
-  if ((e = launch_graph_Z_batch(t.d_cand, t.d_Z, t.d_z_start, count, b->z_blocks, s))) return e;
-  if ((e = launch_candidates_batch(t.d_cand, t.d_cand_start, count, b->cand_blocks, b->cand_smem, s)))
-    return e;
-  if ((e = launch_local_batch(t.d_cand, t.d_local_start, count, b->local_blocks, s))) return e;
   if ((e = cudaEventRecord(b->fork_ev, s))) return e;
-  for (size_t g = 0; g < b->groups.size(); ++g) {
-    if ((e = cudaStreamWaitEvent(b->group_stream[g], b->fork_ev, 0))) return e;
-    if ((e = launch_group(b, b->groups[g], b->groups[g].block, b->group_stream[g]))) return e;
-    if ((e = cudaEventRecord(b->group_done[g], b->group_stream[g]))) return e;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const BatchGroup& g = b->groups[gi];
+    cudaStream_t gs = b->group_stream[gi];
+    const int f = g.first;
+    if ((e = cudaStreamWaitEvent(gs, b->fork_ev, 0))) return e;
+    if ((e = launch_graph_Z_batch(t.d_cand + f, t.d_Z + f, t.d_z_start + f, g.count, g.z_blocks, gs))) return e;
+    if ((e = launch_candidates_batch(t.d_cand + f, t.d_cand_start + f, g.count, g.cand_blocks, g.cand_smem, gs)))
+      return e;
+    if ((e = launch_local_batch(t.d_cand + f, t.d_local_start + f, g.count, g.local_blocks, gs))) return e;
+    if ((e = launch_group(b, g, g.block, gs))) return e;
+    if ((e = launch_select_batch(t.d_sel + f, g.count, g.sel_smem, gs))) return e;
+    if ((e = launch_update_batch(t.d_upd + f, t.d_warp_start + f, g.count, g.upd_threads, gs))) return e;
+    if ((e = cudaEventRecord(b->group_done[gi], gs))) return e;
   }
-  for (size_t g = 0; g < b->groups.size(); ++g)
-    if ((e = cudaStreamWaitEvent(s, b->group_done[g], 0))) return e;
-  if ((e = launch_select_batch(t.d_sel, count, b->sel_smem, s))) return e;
-  return launch_update_batch(t.d_upd, t.d_warp_start, count, b->upd_warps, s);
+  for (size_t gi = 0; gi < b->groups.size(); ++gi)
+    if ((e = cudaStreamWaitEvent(s, b->group_done[gi], 0))) return e;
+  return cudaSuccess;
 }
 
 // scatter x0 -> iterations -> gather u*.  The first run after a fill
