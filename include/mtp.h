@@ -202,7 +202,7 @@ mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U
 /* `iters` full planner iterations (Alg. 2 loop body) from start state d_x0
  * (d) using and advancing the handle's iteration counter; writes the last
  * iteration's u* to d_ustar (n).  Replays a captured CUDA graph unless
- * MTP_FLAG_NO_GRAPH is set or profiling is on. */
+ * MTP_FLAG_NO_GRAPH is set. */
 mtp_status mtp_plan_step(mtp_handle* h, const float* d_x0, int32_t iters, float* d_ustar,
                          void* stream);
 
@@ -222,9 +222,11 @@ mtp_status mtp_set_state(mtp_handle* h, const double* h_mu, const double* h_sigm
                          uint32_t iter);
 
 /* Per-stage device time: with profiling on, mtp_plan_step records CUDA
- * events around each stage.  mtp_stage_times synchronises on them and
- * returns the summed milliseconds of [generate, rollout, select, update]
- * and the number of iterations recorded since the last read, then resets. */
+ * events around each stage (generate, rollout, select, update), inside the
+ * captured graph unless MTP_FLAG_NO_GRAPH is set, and then waits for the
+ * step so the events can be read.  mtp_stage_times returns the summed
+ * milliseconds of the four stages and the number of iterations recorded
+ * since the last read, then resets. */
 mtp_status mtp_set_profiling(mtp_handle* h, int32_t enable);
 mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations);
 

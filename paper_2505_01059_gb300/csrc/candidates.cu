@@ -75,10 +75,14 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
   const bool vec = (Hn & 3) == 0 &&
                    ((reinterpret_cast<uintptr_t>(a.U_local) | reinterpret_cast<uintptr_t>(a.mu) |
                      reinterpret_cast<uintptr_t>(a.sigma)) & 15) == 0;
-  for (int e = lb * blockDim.x + threadIdx.x; e < items; e += stride) {
-    const int row = e / G;
-    const int q = e - row * G;
-    int i = (4 * q) % n;  // control dimension of element 4q, then advanced in place
+  // (row, group q, dimension of element 4q) of this thread's item, advanced
+  // by the grid stride without dividing (4G is a multiple of n when Hn is)
+  int e = lb * blockDim.x + threadIdx.x;
+  int row = e / G, q = e - row * G;
+  int i0 = (4 * q) % n;
+  const int srow = stride / G, sq = stride - srow * G, si = (4 * sq) % n;
+  for (; e < items; e += stride) {
+    int i = i0;  // advanced in place over the group's four elements
     if (row < a.local_rows) {
       const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
       float eps[4];
@@ -96,16 +100,16 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
           if (++i == n) i = 0;
         }
         reinterpret_cast<float4*>(dst)[q] = make_float4(o[0], o[1], o[2], o[3]);
-        continue;
-      }
+      } else {
 #pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int el = 4 * q + w;
-        if (el < Hn) {
-          const float u = fmaf(a.sigma[el], eps[w], a.mu[el]);
-          dst[el] = clamp_box(u, box_lo[i], box_hi[i]);
+        for (int w = 0; w < 4; ++w) {
+          const int el = 4 * q + w;
+          if (el < Hn) {
+            const float u = fmaf(a.sigma[el], eps[w], a.mu[el]);
+            dst[el] = clamp_box(u, box_lo[i], box_hi[i]);
+          }
+          if (++i == n) i = 0;
         }
-        if (++i == n) i = 0;
       }
     } else {
 #pragma unroll
@@ -114,6 +118,15 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
         if (el < Hn) a.U_mean[el] = clamp_box(a.mu[el], box_lo[i], box_hi[i]);
         if (++i == n) i = 0;
       }
+    }
+    row += srow;
+    q += sq;
+    i0 += si;
+    if (i0 >= n) i0 -= n;
+    if (q >= G) {
+      q -= G;
+      ++row;
+      if ((Hn & 3) != 0) i0 = (4 * q) % n;  // 4G = Hn + padding: recompute
     }
   }
 }

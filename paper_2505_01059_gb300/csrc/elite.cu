@@ -38,22 +38,50 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   __shared__ double s_red[32];
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int b = tid; b < B; b += blockDim.x) keys[b] = order_key(a.cost[b]);
-  __syncthreads();
-
-  // radix select of the E-th smallest key (rank 1-based); two histogram
-  // buffers alternate so each pass needs only two block barriers
-  uint32_t prefix = 0, mask = 0;
-  uint32_t rank = (uint32_t)E;
+  __shared__ uint32_t s_kmin[32], s_kmax[32];
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
+  for (int b = tid; b < B; b += blockDim.x) {
+    const uint32_t k = order_key(a.cost[b]);
+    keys[b] = k;
+    kmin = min(kmin, k);
+    kmax = max(kmax, k);
+  }
   for (int i = tid; i < 512; i += blockDim.x) hist[i] = 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  }
+  if (lane == 0) {
+    s_kmin[wid] = kmin;
+    s_kmax[wid] = kmax;
+  }
   __syncthreads();
-  for (int pass = 0; pass < 4; ++pass) {
-    const int shift = 24 - 8 * pass;
+  kmin = s_kmin[0];
+  kmax = s_kmax[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+    kmin = min(kmin, s_kmin[w]);
+    kmax = max(kmax, s_kmax[w]);
+  }
+
+  // radix select of the E-th smallest key (rank 1-based), 8-bit digits from
+  // the highest bit where the keys differ down (the bits above it are
+  // common to all keys, and a digit over them would put every key in one
+  // histogram bin); two histogram buffers alternate so each pass needs only
+  // two block barriers
+  const int top = kmin == kmax ? 0 : 32 - __clz(kmin ^ kmax);  // bits that still differ
+  const int passes = (top + 7) >> 3;
+  uint32_t mask = top >= 32 ? 0u : ~((1u << top) - 1u);
+  uint32_t prefix = kmin & mask;
+  uint32_t rank = (uint32_t)E;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = max(top - 8 * (pass + 1), 0);
+    const uint32_t dmask = (1u << (top - 8 * pass - shift)) - 1u;  // 8 bits, fewer at the bottom
     uint32_t* cur = hist + 256 * (pass & 1);
     uint32_t* nxt = hist + 256 * ((pass + 1) & 1);
     for (int b = tid; b < B; b += blockDim.x) {
       const uint32_t k = keys[b];
-      if ((k & mask) == prefix) atomicAdd(&cur[(k >> shift) & 255u], 1u);
+      if ((k & mask) == prefix) atomicAdd(&cur[(k >> shift) & dmask], 1u);
     }
     for (int i = tid; i < 256; i += blockDim.x) nxt[i] = 0;
     __syncthreads();
@@ -83,7 +111,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
     }
     __syncthreads();
     prefix |= s_digit << shift;
-    mask |= 255u << shift;
+    mask |= dmask << shift;
     rank -= s_below;
   }
   const uint32_t T = prefix;       // the E-th smallest key
@@ -179,7 +207,11 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   const double best = (double)a.cost[(int)(sel[0] & 0xffffffffu)];
   const bool uniform = (a.update_rule == MTP_UPDATE_PLAIN_CEM) || !(best < INFINITY);
   double part = 0.0;
-  for (int k = tid; k < E; k += blockDim.x) {
+  // elite k goes to lane k / nw of warp k % nw: the FP64 exponentials spread
+  // over all warps (and so all four SM sub-partitions) instead of the first two
+  const int nw = blockDim.x >> 5;
+  const int k0 = wid + nw * lane;
+  for (int k = k0; k < E; k += blockDim.x) {
     const int idx = (int)(sel[k] & 0xffffffffu);
     a.elite[k] = idx;
     if (a.elite_out) a.elite_out[k] = idx;
@@ -194,14 +226,14 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   if (lane == 0) s_red[wid] = part;
   __syncthreads();
   if (wid == 0) {
-    double v = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0.0;
+    double v = lane < nw ? s_red[lane] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) s_red[0] = 1.0 / v;
   }
   __syncthreads();
   const double inv_total = s_red[0];
-  for (int k = tid; k < E; k += blockDim.x) a.weight[k] = a.weight[k] * inv_total;
+  for (int k = k0; k < E; k += blockDim.x) a.weight[k] = a.weight[k] * inv_total;
   // u* = U[elite[0], 0, :]
   const int best_row = (int)(sel[0] & 0xffffffffu);
   for (int i = tid; i < a.n; i += blockDim.x) {
@@ -264,31 +296,32 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int thr
   const int sweeps = (G == 1) ? 0 : (Hn - (gt / 32) * (32 / G) + per_sweep - 1) / per_sweep;
   for (int it = 0, e = first; (G == 1) ? (e < Hn) : (it < sweeps); ++it, e += per_sweep) {
     const bool valid = e < Hn;
-    double part[P];
+    // one pass over the elites: sums of d = u - c and d^2 with the shift c =
+    // the best elite's value, so that the variance S2 - S1^2 does not cancel
+    // (the spread of the elites is small next to their mean late in a run)
+    const double c = valid ? (double)__ldg(a.U + (size_t)__ldg(a.elite) * Hn + e) : 0.0;
+    double p1[P], p2[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      part[j] = 0.0;
+      p1[j] = 0.0;
+      p2[j] = 0.0;
       if (valid)
         for (int k = sub + G * j; k < a.E; k += 32) {
-          const double u = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e);
-          part[j] = cem ? part[j] + u : fma(a.weight[k], u, part[j]);
+          const double d = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - c;
+          const double wd = cem ? d : a.weight[k] * d;
+          p1[j] = p1[j] + wd;
+          p2[j] = fma(wd, d, p2[j]);
         }
     }
-    double m1 = canonical_sum<G>(part);
-    if (cem) m1 /= (double)a.E;
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      part[j] = 0.0;
-      if (valid)
-        for (int k = sub + G * j; k < a.E; k += 32) {
-          const double dlt = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - m1;
-          part[j] = cem ? fma(dlt, dlt, part[j]) : fma(a.weight[k] * dlt, dlt, part[j]);
-        }
-    }
-    const double v = canonical_sum<G>(part);
+    const double S1 = canonical_sum<G>(p1);
+    const double S2 = canonical_sum<G>(p2);
     if (valid && sub == 0) {
       if (cem) {
-        const double s1 = a.E > 1 ? sqrt(v / (double)(a.E - 1)) : 0.0;
+        // Sec. 2.1 CEM update: mean and unbiased variance of the elites
+        const double E = (double)a.E;
+        const double m1 = c + S1 / E;
+        const double ss = fmax(S2 - S1 * (S1 / E), 0.0);
+        const double s1 = a.E > 1 ? sqrt(ss / (E - 1.0)) : 0.0;
         const double mn = a.alpha * a.mu[e] + (1.0 - a.alpha) * m1;
         const double sn = a.alpha * a.sigma[e] + (1.0 - a.alpha) * s1;
         a.mu[e] = mn;
@@ -296,7 +329,9 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int thr
         a.mu_f[e] = (float)mn;
         a.sigma_f[e] = (float)sn;
       } else {
-        double s1 = sqrt(v);
+        // Alg. 2: weighted mean and standard deviation (weights sum to one)
+        const double m1 = c + S1;
+        double s1 = sqrt(fmax(S2 - S1 * S1, 0.0));
         if (s1 < a.sigma_min) s1 = a.sigma_min;
         const double mn = m1 + a.alpha * (a.mu[e] - m1);
         const double sn = s1 + a.alpha * (a.sigma[e] - s1);

@@ -70,8 +70,12 @@ struct mtp_handle {
   std::map<int, cudaGraphExec_t> graphs;
   // profiling
   bool profiling = false;
-  std::vector<cudaEvent_t> events;
+  std::vector<cudaEvent_t> events;  // eager launches: 5 per iteration, read by mtp_stage_times
   size_t ev_used = 0;
+  std::vector<cudaEvent_t> gevents;            // inside profiled graphs: 5 per iteration of a chunk
+  std::map<int, cudaGraphExec_t> pgraphs;      // graphs with the stage events captured
+  double stage_acc[4] = {0, 0, 0, 0};          // read from gevents after each profiled replay
+  int64_t stage_iters = 0;
   std::string err;
 };
 
@@ -385,6 +389,8 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev) {
 void free_handle(mtp_handle* h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->gevents) cudaEventDestroy(e);
+  for (auto& kv : h->pgraphs) cudaGraphExecDestroy(kv.second);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->basis, h->bfirst, h->seg, h->delta, h->mu, h->sigma, h->mu_f, h->sigma_f,
                   h->iter_dev,
@@ -421,7 +427,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   dm.N = p.N;
   h->key.k0 = (uint32_t)(p.seed & 0xffffffffu);
   h->key.k1 = (uint32_t)(p.seed >> 32);
-  // graph paths per block: ~4K output elements per block, and at least 16
+  // graph paths per block: ~4K output elements per block, and at least 8
   // paths for Akima so its per-(path, dimension) coefficient pass is wide;
   // shrunk until the block's shared memory fits
   const long long Hn = (long long)dm.H * dm.n;
@@ -429,7 +435,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   // regenerated in every graph block's shared memory
   h->global_Z = (long long)dm.M * dm.N * dm.n > 4096;
   int spb = (int)((4096 + Hn - 1) / Hn);
-  if (p.interp == MTP_INTERP_AKIMA && spb < 16) spb = 16;
+  if (p.interp == MTP_INTERP_AKIMA && spb < 8) spb = 8;
   if (spb < 1) spb = 1;
   if (spb > 32) spb = 32;
   for (;;) {
@@ -616,7 +622,7 @@ mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U
 
 static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
   cudaError_t e;
-  const bool use_graph = !(h->pr.flags & MTP_FLAG_NO_GRAPH) && !h->profiling;
+  const bool use_graph = !(h->pr.flags & MTP_FLAG_NO_GRAPH);
   if (!use_graph) {
     for (int k = 0; k < iters; ++k) {
       cudaEvent_t* ev = nullptr;
@@ -633,17 +639,29 @@ static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
     }
     return MTP_OK;
   }
-  // one captured graph per distinct iteration count (at most 64 iterations each)
+  // one captured graph per distinct iteration count (at most 64 iterations
+  // each); with profiling on, a second set of graphs also records the stage
+  // events, and each replay is waited for and its stage times accumulated
+  constexpr int kChunk = 64;
+  if (h->profiling) {
+    while (h->gevents.size() < 5 * kChunk) {
+      cudaEvent_t x;
+      if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+      h->gevents.push_back(x);
+    }
+  }
+  auto& cache = h->profiling ? h->pgraphs : h->graphs;
   int left = iters;
   while (left > 0) {
-    const int chunk = left > 64 ? 64 : left;
-    auto it = h->graphs.find(chunk);
-    if (it == h->graphs.end()) {
+    const int chunk = left > kChunk ? kChunk : left;
+    auto it = cache.find(chunk);
+    if (it == cache.end()) {
       cudaGraph_t graph;
       if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(h, e, "cudaStreamBeginCapture");
       for (int k = 0; k < chunk; ++k) {
-        if ((e = enqueue_iteration(h, h->cap_stream, nullptr)) != cudaSuccess) {
+        cudaEvent_t* ev = h->profiling ? h->gevents.data() + 5 * k : nullptr;
+        if ((e = enqueue_iteration(h, h->cap_stream, ev)) != cudaSuccess) {
           cudaStreamEndCapture(h->cap_stream, &graph);
           return cuda_fail(h, e, "capture");
         }
@@ -654,9 +672,20 @@ static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
       e = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-      it = h->graphs.emplace(chunk, exec).first;
+      it = cache.emplace(chunk, exec).first;
     }
     if ((e = cudaGraphLaunch(it->second, s)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    if (h->profiling) {
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "profiled replay");
+      for (int k = 0; k < chunk; ++k)
+        for (int st = 0; st < 4; ++st) {
+          float ms = 0.f;
+          if ((e = cudaEventElapsedTime(&ms, h->gevents[5 * k + st], h->gevents[5 * k + st + 1])) != cudaSuccess)
+            return cuda_fail(h, e, "cudaEventElapsedTime");
+          h->stage_acc[st] += ms;
+        }
+      h->stage_iters += chunk;
+    }
     left -= chunk;
   }
   return MTP_OK;
@@ -733,13 +762,18 @@ mtp_status mtp_set_profiling(mtp_handle* h, int32_t enable) {
   if (!h) return MTP_ERR_INVALID_ARG;
   h->profiling = enable != 0;
   h->ev_used = 0;
+  for (int i = 0; i < 4; ++i) h->stage_acc[i] = 0.0;
+  h->stage_iters = 0;
   return MTP_OK;
 }
 
 mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations) {
   if (!h || !ms4) return MTP_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
-  for (int i = 0; i < 4; ++i) ms4[i] = 0.0;
+  for (int i = 0; i < 4; ++i) ms4[i] = h->stage_acc[i];
+  const int64_t g_it = h->stage_iters;
+  for (int i = 0; i < 4; ++i) h->stage_acc[i] = 0.0;
+  h->stage_iters = 0;
   const size_t n_it = h->ev_used / 5;
   if (n_it > 0) MTP_CUDA(h, cudaEventSynchronize(h->events[h->ev_used - 1]));
   for (size_t k = 0; k < n_it; ++k) {
@@ -749,7 +783,7 @@ mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations) {
       ms4[st] += ms;
     }
   }
-  if (iterations) *iterations = (int32_t)n_it;
+  if (iterations) *iterations = (int32_t)(n_it + g_it);
   h->ev_used = 0;
   return MTP_OK;
 }
