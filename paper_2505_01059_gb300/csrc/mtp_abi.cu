@@ -357,12 +357,19 @@ cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream
   return launch_rollout_chain(a, chain_model(p), p.n_links, s);
 }
 
+// Stage event: inside a stream capture it must be an external event record
+// node to be timed afterwards (a plain record there only orders streams).
+inline void stage_event(cudaEvent_t ev, cudaStream_t s, bool captured) {
+  if (captured) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+  else cudaEventRecord(ev, s);
+}
+
 // One Alg. 2 iteration on the handle's own buffers, iteration from iter_dev.
-cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev, bool captured = false) {
   cudaError_t e;
   const Dims& dm = h->dm;
   const size_t Hn = (size_t)dm.H * dm.n;
-  if (ev) cudaEventRecord(ev[0], s);
+  if (ev) stage_event(ev[0], s, captured);
   CandArgs c = cand_args(h, 0, h->iter_dev);
   c.U_graph = h->U + Hn * dm.L;
   c.graph_rows = dm.P;
@@ -371,18 +378,18 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev) {
   c.local_rows = dm.L;
   c.U_mean = h->U + Hn * (dm.B - 1);
   if ((e = launch_generate(h, c, s)) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[1], s);
+  if (ev) stage_event(ev[1], s, captured);
   RolloutArgs r = rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, dm.B, h->cost);
   if ((e = launch_rollout(h, r, s)) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[2], s);
+  if (ev) stage_event(ev[2], s, captured);
   SelectArgs sa{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
                 h->elite, h->weight, h->ustar, nullptr, nullptr};
   if ((e = launch_select(sa, s)) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[3], s);
+  if (ev) stage_event(ev[3], s, captured);
   UpdateArgs ua{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
                 h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
   if ((e = launch_update(ua, s)) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[4], s);
+  if (ev) stage_event(ev[4], s, captured);
   return cudaSuccess;
 }
 
@@ -661,7 +668,7 @@ static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
         return cuda_fail(h, e, "cudaStreamBeginCapture");
       for (int k = 0; k < chunk; ++k) {
         cudaEvent_t* ev = h->profiling ? h->gevents.data() + 5 * k : nullptr;
-        if ((e = enqueue_iteration(h, h->cap_stream, ev)) != cudaSuccess) {
+        if ((e = enqueue_iteration(h, h->cap_stream, ev, true)) != cudaSuccess) {
           cudaStreamEndCapture(h->cap_stream, &graph);
           return cuda_fail(h, e, "capture");
         }

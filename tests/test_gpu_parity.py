@@ -393,6 +393,29 @@ def test_graph_replay_equals_eager(mtp):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("flags", [0, 2])
+def test_profiled_plan_step_same_result_and_stage_times(mtp, flags):
+    """Profiling (stage events inside the graph, or between eager launches)
+    changes no result and reports four positive stage times per iteration."""
+    spec = dict(W.chain(links=5, B=2048, H=64), flags=flags)
+    outs = []
+    for prof in (False, True):
+        h = mtp.mtp_create(spec)
+        mtp.mtp_set_profiling(h, prof)
+        x0 = _t(np.array(spec["x0"]))
+        u = torch.empty(h.sizes["n"], device=DEV)
+        mtp.mtp_plan_step(h, x0, 3, u)
+        mtp.mtp_plan_step(h, x0, 2, u)
+        if prof:
+            ms, n_it = mtp.mtp_stage_times(h)
+            assert n_it == 5 and all(v > 0 for v in ms)
+            assert mtp.mtp_stage_times(h)[1] == 0  # read and reset
+        outs.append((*mtp.mtp_get_state(h), _np(u)))
+        mtp.mtp_destroy(h)
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
 def test_plan_step_host_and_resume(mtp):
     spec = W.pointmass(B=1024)
     h1 = mtp.mtp_create(spec)
