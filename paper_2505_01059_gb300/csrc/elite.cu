@@ -57,11 +57,13 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
     s_kmax[wid] = kmax;
   }
   __syncthreads();
-  kmin = s_kmin[0];
-  kmax = s_kmax[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-    kmin = min(kmin, s_kmin[w]);
-    kmax = max(kmax, s_kmax[w]);
+  // every warp reduces the per-warp extremes itself (no second barrier)
+  kmin = lane < (int)(blockDim.x >> 5) ? s_kmin[lane] : 0xffffffffu;
+  kmax = lane < (int)(blockDim.x >> 5) ? s_kmax[lane] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
   }
 
   // radix select of the E-th smallest key (rank 1-based), 8-bit digits from
@@ -207,10 +209,10 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   const double best = (double)a.cost[(int)(sel[0] & 0xffffffffu)];
   const bool uniform = (a.update_rule == MTP_UPDATE_PLAIN_CEM) || !(best < INFINITY);
   double part = 0.0;
-  // elite k goes to lane k / nw of warp k % nw: the FP64 exponentials spread
-  // over all warps (and so all four SM sub-partitions) instead of the first two
+  // elites on consecutive threads: the FP64 pipe is occupied per warp
+  // instruction, so full warps do the exponentials at the least cost
   const int nw = blockDim.x >> 5;
-  const int k0 = wid + nw * lane;
+  const int k0 = tid;
   for (int k = k0; k < E; k += blockDim.x) {
     const int idx = (int)(sel[k] & 0xffffffffu);
     a.elite[k] = idx;
@@ -305,14 +307,22 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int thr
     for (int j = 0; j < P; ++j) {
       p1[j] = 0.0;
       p2[j] = 0.0;
-      if (valid)
-        for (int k = sub + G * j; k < a.E; k += 32) {
-          const double d = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - c;
-          const double wd = cem ? d : a.weight[k] * d;
-          p1[j] = p1[j] + wd;
-          p2[j] = fma(wd, d, p2[j]);
-        }
     }
+    // virtual lane v = sub + G j takes elites v, v + 32, ... in that order;
+    // the P gathers of one round are independent and issued together
+    if (valid)
+      for (int k0 = 0; k0 < a.E; k0 += 32) {
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const int k = k0 + sub + G * j;
+          if (k < a.E) {
+            const double d = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - c;
+            const double wd = cem ? d : a.weight[k] * d;
+            p1[j] = p1[j] + wd;
+            p2[j] = fma(wd, d, p2[j]);
+          }
+        }
+      }
     const double S1 = canonical_sum<G>(p1);
     const double S2 = canonical_sum<G>(p2);
     if (valid && sub == 0) {
@@ -436,8 +446,11 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
 // Lanes per element: as many as keep roughly 38K threads busy, up to a warp.
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   const int Hn = a.H * a.n;
+  // lanes per element: enough threads to spread the gathers over the GPU,
+  // but at most 8, because every lane of a group repeats the FP64 butterfly
+  // and the final square root, and FP64 issue is scarce on this GPU
   int G = 1;
-  while (G < 32 && (long long)Hn * G < 152 * 256) G <<= 1;
+  while (G < 8 && (long long)Hn * G < 152 * 256) G <<= 1;
   const long long threads = (long long)Hn * G;
   const int blocks = (int)((threads + 127) / 128);
   switch (G) {
