@@ -446,11 +446,12 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
 // Lanes per element: as many as keep roughly 38K threads busy, up to a warp.
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   const int Hn = a.H * a.n;
-  // lanes per element: enough threads to spread the gathers over the GPU,
-  // but at most 8, because every lane of a group repeats the FP64 butterfly
-  // and the final square root, and FP64 issue is scarce on this GPU
+  // lanes per element: enough threads to spread the gathers over the GPU.
+  // The kernel is latency-bound (elite index, then row gather), so more
+  // lanes win even though each lane repeats the FP64 butterfly (8 lanes per
+  // element measured slower than 32 on the 7-link arm workload)
   int G = 1;
-  while (G < 8 && (long long)Hn * G < 152 * 256) G <<= 1;
+  while (G < 32 && (long long)Hn * G < 152 * 256) G <<= 1;
   const long long threads = (long long)Hn * G;
   const int blocks = (int)((threads + 127) / 128);
   switch (G) {
