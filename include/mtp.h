@@ -71,8 +71,12 @@ typedef enum { MTP_DR_NONE = 0, MTP_DR_PER_SAMPLE = 1, MTP_DR_SHARED = 2 } mtp_d
 /* flags */
 #define MTP_FLAG_NO_KAHAN 0x1u    /* plain FP32 cost sums instead of compensated ones */
 #define MTP_FLAG_NO_GRAPH 0x2u    /* mtp_plan_step launches eagerly, no CUDA graph */
-#define MTP_FLAG_BF16_BASIS 0x4u  /* B-spline contraction with a BF16 basis and BF16
-                                     knots on the tensor cores, FP32 accumulation */
+#define MTP_FLAG_BF16_BASIS 0x4u  /* B-spline contraction with BF16 operands: basis
+                                     values and knots rounded to the nearest bfloat16
+                                     (ties to even), exact products, FP32 sums.  B-spline
+                                     only (MTP_ERR_UNSUPPORTED otherwise).  Runs on the
+                                     FP32 pipe: the contraction stores 4 bytes per p+1
+                                     products, so tensor cores would not shorten it */
 
 /* One planning problem (Sec. 2.1 problem statement, Alg. 2 inputs, Table 3
  * hyper-parameters).  Plain data; mtp_create copies it. */

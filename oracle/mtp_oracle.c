@@ -79,6 +79,10 @@ typedef struct {
   /* legged ground contact */
   double k_contact, c_contact, mu_friction, v_slip;
   double w_height, w_pitch, w_vel;
+  /* precision of the B-spline contraction: 0 FP64; 1 operands (basis value
+   * and knot, each first rounded to FP32) rounded to BF16, products and sums
+   * exact here (the GPU sums in FP32) */
+  int32_t bf16_basis;
 } or_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -203,6 +207,20 @@ void or_bspline_basis(int M, int p, int H, int mapping, double* Bmat) {
   free(knots);
 }
 
+/* bfloat16 rounding: the nearest number with an 8-bit significand (the
+ * exponent range of FP32), ties to the even significand.  Written from that
+ * definition: x = f * 2^e with f in [0.5, 1); f * 2^8 is rounded to an integer
+ * by rint (round-half-even in the default rounding mode). */
+double or_bf16_round(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  int e;
+  double f = frexp(x, &e);
+  return ldexp(rint(ldexp(f, 8)), e - 8);
+}
+
+/* An operand of the BF16 contraction: the value as FP32, then to BF16. */
+static double bf16_operand(double x) { return or_bf16_round((double)(float)x); }
+
 /* Def. 2: U = einsum over the M layers of Bmat and C, U[b][j][i]. */
 void or_interp_bspline(const or_problem* pr, const double* C, int32_t P, double* U) {
   double* Bmat = (double*)malloc(sizeof(double) * (size_t)pr->M * pr->H);
@@ -211,8 +229,15 @@ void or_interp_bspline(const or_problem* pr, const double* C, int32_t P, double*
     for (int j = 0; j < pr->H; ++j)
       for (int i = 0; i < pr->n; ++i) {
         double acc = 0.0;
-        for (int m = 0; m < pr->M; ++m)
-          acc += Bmat[(size_t)m * pr->H + j] * C[((size_t)b * pr->M + m) * pr->n + i];
+        for (int m = 0; m < pr->M; ++m) {
+          double bm = Bmat[(size_t)m * pr->H + j];
+          double cm = C[((size_t)b * pr->M + m) * pr->n + i];
+          if (pr->bf16_basis) {
+            bm = bf16_operand(bm);
+            cm = bf16_operand(cm);
+          }
+          acc += bm * cm;
+        }
         U[((size_t)b * pr->H + j) * pr->n + i] = acc;
       }
   free(Bmat);

@@ -57,6 +57,7 @@ class OrProblem(C.Structure):
         ("k_contact", C.c_double), ("c_contact", C.c_double), ("mu_friction", C.c_double),
         ("v_slip", C.c_double),
         ("w_height", C.c_double), ("w_pitch", C.c_double), ("w_vel", C.c_double),
+        ("bf16_basis", C.c_int32),
     ]
 
 
@@ -91,6 +92,7 @@ def _load():
             "or_bspline_time": (C.c_double, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
             "or_bspline_basis": (None, [C.c_int, C.c_int, C.c_int, C.c_int, dp]),
             "or_interp_bspline": (None, [pp, dp, C.c_int32, dp]),
+            "or_bf16_round": (C.c_double, [C.c_double]),
             "or_akima_knot": (C.c_double, [C.c_int, C.c_int, C.c_int]),
             "or_akima_time": (C.c_double, [C.c_int, C.c_int, C.c_int]),
             "or_akima_coeffs": (None, [C.c_int, dp, dp, dp]),
@@ -200,6 +202,7 @@ def make_problem(spec: dict) -> OrProblem:
     pr.w_height = spec.get("w_height", 0.0)
     pr.w_pitch = spec.get("w_pitch", 0.0)
     pr.w_vel = spec.get("w_vel", 0.0)
+    pr.bf16_basis = 1 if (spec.get("flags", 0) & 0x4) else 0
     return pr
 
 
@@ -278,6 +281,13 @@ def akima_eval(tk, coef, t: float) -> float:
     tk = _f64(tk)
     coef = _f64(coef)
     return float(_load().or_akima_eval(tk.shape[0], _dp(tk), _dp(coef), float(t)))
+
+
+def bf16_round(x) -> np.ndarray:
+    """bfloat16 rounding of each value (the oracle's definition, FP64 in/out)."""
+    x = np.ascontiguousarray(np.atleast_1d(x), dtype=np.float64)
+    lib = _load()
+    return np.array([lib.or_bf16_round(float(v)) for v in x.ravel()]).reshape(x.shape)
 
 
 def interpolate(spec, Cc, kind: str | None = None) -> np.ndarray:

@@ -10,6 +10,8 @@
 // waypoints and interpolates them with coalesced row-major stores.  The other
 // blocks stream the local Gaussian rows and the mean row, four elements per
 // generator call.
+#include <cuda_bf16.h>
+
 #include "mtp_device.cuh"
 
 namespace mtp {
@@ -187,6 +189,13 @@ __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, 
       for (int e = threadIdx.x; e < nb * M * n; e += blockDim.x) C[e] = src[e];
     }
     __syncthreads();
+    if (a.bf16 && a.interp == MTP_INTERP_BSPLINE) {
+      // BF16 operands: each knot rounded to the nearest bfloat16 (ties to
+      // even); its products with the BF16 basis are exact in FP32
+      for (int e = threadIdx.x; e < nb * M * n; e += blockDim.x)
+        C[e] = __bfloat162float(__float2bfloat16_rn(C[e]));
+      __syncthreads();
+    }
 
     if (a.interp == MTP_INTERP_AKIMA) {
       // Eqs. 6-7 in three parallel passes over (path, dimension, knot):

@@ -173,7 +173,8 @@ mtp_status validate(const mtp_problem& p) {
   if (p.dr_mode != MTP_DR_NONE && !(p.dr_lo > 0.f && p.dr_lo <= p.dr_hi)) return bad("need 0 < dr_lo <= dr_hi");
   if ((size_t)p.M * p.N * p.ctrl_dim * 4 > 160 * 1024) return bad("graph M*N*n too large for one block's shared memory");
   if (select_smem_bytes(p.B, p.E) > kMaxSmem) return bad("B and E too large for the single-block elite selection");
-  if (p.flags & MTP_FLAG_BF16_BASIS) return fail(nullptr, MTP_ERR_UNSUPPORTED, "BF16 basis path not built yet");
+  if ((p.flags & MTP_FLAG_BF16_BASIS) && p.interp != MTP_INTERP_BSPLINE)
+    return fail(nullptr, MTP_ERR_UNSUPPORTED, "the BF16 basis applies to B-spline interpolation only");
   return MTP_OK;
 }
 
@@ -182,8 +183,23 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
 }
 
+// Nearest bfloat16 of a finite float, ties to even, as a float: the low 16
+// bits of the IEEE-754 encoding are rounded away (adding 0x7fff plus the
+// lowest kept bit carries into the kept bits exactly when the dropped part
+// is above one half, or exactly one half with an odd kept part).
+float round_bf16(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  u &= 0xffff0000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
 mtp_status build_tables(mtp_handle* h) {
   const mtp_problem& p = h->pr;
+  const bool bf16 = (p.flags & MTP_FLAG_BF16_BASIS) != 0;
   const int H = p.horizon, M = p.M;
   std::vector<float> basis((size_t)H * M, 0.f);
   std::vector<int32_t> bfirst(H, 0), seg(H, 0);
@@ -203,7 +219,7 @@ mtp_status build_tables(mtp_handle* h) {
       int first = -1;
       for (int m = 0; m < M; ++m) {
         const double v = cardinal_bspline(deg, x - m, left);
-        basis[(size_t)j * M + m] = (float)v;
+        basis[(size_t)j * M + m] = bf16 ? round_bf16((float)v) : (float)v;
         if (v != 0.0 && first < 0) first = m;
       }
       if (first < 0) first = 0;
@@ -242,6 +258,7 @@ CandArgs cand_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter) {
   a.d_iter = d_iter;
   a.interp = h->pr.interp;
   a.degree = h->pr.bspline_degree;
+  a.bf16 = (h->pr.flags & MTP_FLAG_BF16_BASIS) ? 1 : 0;
   a.inv_h = h->inv_h;
   a.basis = h->basis;
   a.bfirst = h->bfirst;

@@ -91,6 +91,8 @@ struct CandArgs {
   const uint32_t* d_iter;  // when set, the iteration is read from here
   int32_t interp;          // mtp_interp
   int32_t degree;          // B-spline degree p
+  int32_t bf16;            // B-spline contraction with BF16 operands (the basis table is
+                           // rounded on the host, the knots as they are gathered)
   float inv_h;             // reciprocal knot spacing of the Akima / linear knots
   const float* basis;      // (H, M) B-spline basis, row t
   const int32_t* bfirst;   // (H) first non-zero basis column of row t

@@ -122,6 +122,46 @@ def test_interpolate(mtp, interp, p, mapping, M, H, n, P):
     mtp.mtp_destroy(h)
 
 
+@pytest.mark.parametrize("p,M,H,n,P", [(3, 4, 64, 2, 256), (2, 16, 256, 15, 300), (2, 8, 128, 7, 77)])
+def test_interpolate_bf16_basis(mtp, p, M, H, n, P):
+    """BF16 operands, FP32 sums: against the oracle's BF16 mode up to FP32
+    summation, and within 1e-2 of the full-precision contraction."""
+    spec = W.pointmass(k=n, M=M, N=8, H=H, B=P + 1, E=1, beta=1.0, degree=p,
+                       u_min=[-2.0] * n, u_max=[3.0] * n, flags=0x4)
+    h = mtp.mtp_create(spec)
+    rng = np.random.default_rng(P)
+    C32 = rng.uniform(-2.0, 3.0, size=(P, M, n)).astype(np.float32)
+    U = torch.empty(P, H, n, device=DEV)
+    mtp.mtp_interpolate(h, _t(C32), U)
+    ug = _np(U)
+    ref16 = np.clip(orc.interpolate(spec, C32.astype(np.float64)), -2.0, 3.0)
+    ref64 = np.clip(orc.interpolate(dict(spec, flags=0), C32.astype(np.float64)), -2.0, 3.0)
+    scale = np.abs(ref64).max()
+    assert np.abs(ug - ref16).max() <= 2e-6 * scale
+    assert np.abs(ug - ref64).max() <= 1e-2 * scale
+    assert np.abs(ug - ref64).max() > 1e-5 * scale  # the operands really are BF16
+    mtp.mtp_destroy(h)
+
+
+def test_bf16_basis_plan_step_and_rejections(mtp):
+    spec = W.pointmass(flags=0x4)
+    h = mtp.mtp_create(spec)
+    it = 0
+    U = torch.empty(spec["B"], spec["H"], spec["n"], device=DEV)
+    mtp.mtp_generate_candidates(h, it, U)
+    mu, sg = W.initial_distribution(spec)
+    ref = orc.plan_iteration(spec, it, spec["x0"], mu, sg)["U"]
+    L = spec["B"] - orc.num_graph_samples(spec["beta"], spec["B"]) - 1
+    assert np.abs(_np(U)[L:-1] - ref[L:-1]).max() <= 2e-6 * np.abs(ref).max()
+    u = torch.empty(spec["n"], device=DEV)
+    mtp.mtp_plan_step(h, _t(np.array(spec["x0"])), 3, u)
+    assert torch.isfinite(u).all()
+    mtp.mtp_destroy(h)
+    with pytest.raises(mtp.MtpError) as ei:
+        mtp.mtp_create(W.chain(flags=0x4))  # Akima: the flag applies to B-splines only
+    assert ei.value.status == 7
+
+
 # ----------------------------------------------------------------------------
 # Local Gaussian samples and the mean row
 # ----------------------------------------------------------------------------

@@ -198,3 +198,62 @@ def test_linear_interpolation(orc):
     U = orc.interpolate(spec, z[None, :, None])
     ts = np.linspace(0, 1, H)
     np.testing.assert_allclose(U[0, :, 0], np.interp(ts, np.linspace(0, 1, M), z), atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# BF16 operands of the B-spline contraction
+# ----------------------------------------------------------------------------
+
+def _bf16_bits(x):
+    """Independent reference: round float32 values to bfloat16 through their
+    IEEE-754 encoding (keep the high 16 bits, round half to even)."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_round_known_values(orc):
+    # published bfloat16 encodings: pi = 0x4049, 0.1 = 0x3DCD
+    assert orc.bf16_round(np.pi)[0] == 3.140625
+    assert orc.bf16_round(0.1)[0] == 0.10009765625
+    # ties go to the even significand (ulp of [1, 2) is 2^-7)
+    assert orc.bf16_round(1 + 2.0 ** -8)[0] == 1.0
+    assert orc.bf16_round(1 + 3 * 2.0 ** -8)[0] == 1 + 2.0 ** -6
+    assert orc.bf16_round(-(1 + 3 * 2.0 ** -8))[0] == -(1 + 2.0 ** -6)
+    assert orc.bf16_round(65408.0)[0] == 65536.0  # 255.5 * 256 -> 256 * 256
+    assert orc.bf16_round(0.0)[0] == 0.0
+
+
+def test_bf16_round_matches_bit_rounding(orc):
+    rng = np.random.default_rng(7)
+    x = (rng.standard_normal(4000) * 10.0 ** rng.uniform(-6, 6, 4000)).astype(np.float32)
+    assert np.array_equal(orc.bf16_round(x.astype(np.float64)), _bf16_bits(x))
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_bf16_bspline_within_operand_rounding(orc, p):
+    """Each operand moves by at most 2^-8 of itself (the unit roundoff of an
+    8-bit significand), so with a non-negative basis summing to one the
+    result moves by at most ~2^-7 max|C|."""
+    spec = W.pointmass(k=3, M=8, H=64, degree=p)
+    rng = np.random.default_rng(p)
+    Cc = rng.uniform(-1, 1, size=(40, spec["M"], 3))
+    U64 = orc.interpolate(spec, Cc)
+    U16 = orc.interpolate(dict(spec, flags=0x4), Cc)
+    err = np.abs(U16 - U64).max()
+    assert 0 < err <= 2.0 ** -7 * np.abs(Cc).max() * 1.01
+    assert np.abs(U16 - U64).max() / np.abs(U64).max() < 1e-2
+
+
+def test_bf16_bspline_exact_when_operands_are_bf16(orc):
+    """Degree 1, M = 5, H = 9 (valid span) samples the piecewise-linear
+    interpolant at the knots and the midpoints (basis values 0, 1/2, 1); with
+    knots on a 2^-6 grid every BF16 operand is exact, so the result is the
+    closed form exactly (the FP64 basis itself is only within 1e-16 of 1/2)."""
+    spec = W.pointmass(k=2, M=5, H=9, degree=1)
+    rng = np.random.default_rng(3)
+    Cc = rng.integers(-64, 65, size=(7, 5, 2)) / 64.0
+    want = np.empty((7, 9, 2))
+    want[:, 0::2] = Cc
+    want[:, 1::2] = 0.5 * (Cc[:, :-1] + Cc[:, 1:])
+    assert np.array_equal(orc.interpolate(dict(spec, flags=0x4), Cc), want)
