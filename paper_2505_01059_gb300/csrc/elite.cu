@@ -27,6 +27,30 @@ __device__ __forceinline__ int next_pow2(int v) {
   return p;
 }
 
+// Bins with at most this many keys end the radix passes early.
+constexpr int kBoundaryMax = 64;
+
+// Ascending bitonic sort of 64 values held two per lane (v0 = element lane,
+// v1 = element lane + 32) in one warp.
+__device__ __forceinline__ void warp_sort64(unsigned long long& v0, unsigned long long& v1, int lane) {
+  for (int k = 2; k <= 64; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {  // partner is the lane's other element (k == 64, ascending)
+        const unsigned long long lo = v0 < v1 ? v0 : v1, hi = v0 < v1 ? v1 : v0;
+        v0 = lo;
+        v1 = hi;
+      } else {
+        const bool lower = (lane & j) == 0;
+        const unsigned long long o0 = __shfl_xor_sync(0xffffffffu, v0, j);
+        const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, v1, j);
+        const bool up0 = (lane & k) == 0, up1 = ((lane + 32) & k) == 0;
+        v0 = (lower == up0) ? (v0 < o0 ? v0 : o0) : (v0 < o0 ? o0 : v0);
+        v1 = (lower == up1) ? (v1 < o1 ? v1 : o1) : (v1 < o1 ? o1 : v1);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* sm_raw) {
   const int B = a.B, E = a.E;
   const int Bp = (B + 1) & ~1;
@@ -34,7 +58,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   unsigned long long* sel = reinterpret_cast<unsigned long long*>(keys + Bp);
   __shared__ uint32_t hist[512];
   __shared__ uint32_t warp_tot[32];
-  __shared__ uint32_t s_digit, s_below, s_lt;
+  __shared__ uint32_t s_digit, s_below, s_lt, s_cnt, s_nb;
   __shared__ double s_red[32];
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -76,6 +100,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   uint32_t mask = top >= 32 ? 0u : ~((1u << top) - 1u);
   uint32_t prefix = kmin & mask;
   uint32_t rank = (uint32_t)E;
+  bool boundary = false;
   for (int pass = 0; pass < passes; ++pass) {
     const int shift = max(top - 8 * (pass + 1), 0);
     const uint32_t dmask = (1u << (top - 8 * pass - shift)) - 1u;  // 8 bits, fewer at the bottom
@@ -107,6 +132,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
         if (run < rank && rank <= run + c[q]) {
           s_digit = (uint32_t)(lane * 8 + q);
           s_below = run;
+          s_cnt = c[q];
         }
         run += c[q];
       }
@@ -115,7 +141,41 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
     prefix |= s_digit << shift;
     mask |= dmask << shift;
     rank -= s_below;
+    if (s_cnt <= kBoundaryMax) {  // block-uniform: read after the barrier
+      boundary = true;
+      break;
+    }
   }
+  const int Ep = next_pow2(E);
+  if (boundary) {
+    // The bin holding the E-th key has at most kBoundaryMax keys: every key
+    // below the bin is an elite, and the bin's keys are sorted by
+    // (key, index) in one warp to take the `rank` still needed.
+    unsigned long long* bnd = sel + Ep;
+    if (tid == 0) {
+      s_lt = 0;
+      s_nb = 0;
+    }
+    __syncthreads();
+    for (int b = tid; b < B; b += blockDim.x) {
+      const uint32_t k = keys[b];
+      const uint32_t km = k & mask;
+      if (km < prefix) sel[atomicAdd(&s_lt, 1u)] = ((unsigned long long)k << 32) | (uint32_t)b;
+      else if (km == prefix) bnd[atomicAdd(&s_nb, 1u)] = ((unsigned long long)k << 32) | (uint32_t)b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      const int nb = (int)s_nb;
+      unsigned long long v0 = lane < nb ? bnd[lane] : ~0ull;
+      unsigned long long v1 = lane + 32 < nb ? bnd[lane + 32] : ~0ull;
+      warp_sort64(v0, v1, lane);
+      const uint32_t base = (uint32_t)E - rank;  // == s_lt
+      if ((uint32_t)lane < rank) sel[base + lane] = v0;
+      if ((uint32_t)(lane + 32) < rank) sel[base + lane + 32] = v1;
+    }
+    for (int i = E + tid; i < Ep; i += blockDim.x) sel[i] = ~0ull;
+    __syncthreads();
+  } else {
   const uint32_t T = prefix;       // the E-th smallest key
   const uint32_t need_eq = rank;   // how many keys equal to T are taken
 
@@ -156,9 +216,9 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
       ++eq_rank;
     }
   }
-  const int Ep = next_pow2(E);
   for (int i = E + tid; i < Ep; i += blockDim.x) sel[i] = ~0ull;
   __syncthreads();
+  }
 
   // bitonic sort of the E selected (key, index) pairs, ascending: in the
   // registers of one warp for E <= 64, through shared memory otherwise
@@ -166,22 +226,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
     if (wid == 0) {
       unsigned long long v0 = lane < Ep ? sel[lane] : ~0ull;
       unsigned long long v1 = lane + 32 < Ep ? sel[lane + 32] : ~0ull;
-      for (int k = 2; k <= 64; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          if (j == 32) {  // partner is the lane's other element (k == 64, ascending)
-            const unsigned long long lo = v0 < v1 ? v0 : v1, hi = v0 < v1 ? v1 : v0;
-            v0 = lo;
-            v1 = hi;
-          } else {
-            const bool lower = (lane & j) == 0;
-            const unsigned long long o0 = __shfl_xor_sync(0xffffffffu, v0, j);
-            const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, v1, j);
-            const bool up0 = (lane & k) == 0, up1 = ((lane + 32) & k) == 0;
-            v0 = (lower == up0) ? (v0 < o0 ? v0 : o0) : (v0 < o0 ? o0 : v0);
-            v1 = (lower == up1) ? (v1 < o1 ? v1 : o1) : (v1 < o1 ? o1 : v1);
-          }
-        }
-      }
+      warp_sort64(v0, v1, lane);
       if (lane < Ep) sel[lane] = v0;
       if (lane + 32 < Ep) sel[lane + 32] = v1;
     }
@@ -411,7 +456,8 @@ __global__ void k_shift_batch(const UpdateArgs* __restrict__ args, int k) {
 size_t select_smem_bytes(int B, int E) {
   int Ep = 1;
   while (Ep < E) Ep <<= 1;
-  return (size_t)((B + 1) & ~1) * 4 + (size_t)Ep * 8;
+  // keys, the selected pairs, the boundary bin's pairs
+  return (size_t)((B + 1) & ~1) * 4 + (size_t)Ep * 8 + (size_t)kBoundaryMax * 8;
 }
 
 cudaError_t init_select_attributes() {

@@ -312,6 +312,8 @@ def test_chain_states(mtp, links):
     (1, 1, "rand"), (2, 2, "ties"), (33, 5, "ties"), (512, 32, "rand"), (1000, 1000, "ties"),
     (4096, 64, "rand"), (4096, 64, "ties"), (4096, 4096, "rand"), (16384, 64, "special"),
     (16384, 16384, "ties"), (777, 300, "special"),
+    # the radix passes stop at a bin of <= 64 keys, which one warp sorts
+    (4096, 100, "rand"), (2000, 64, "special"), (64, 64, "rand"), (65, 64, "ties"), (8192, 7, "rand"),
 ])
 def test_top_e(mtp, B, E, kind):
     spec = W.pointmass(k=1, H=2, B=B, E=E, beta=0.0)
