@@ -73,16 +73,15 @@ def flops_per_step(spec: dict) -> int:
         return cost + rhs + mass_matrix + velocity + chol + solves + integrate
     if spec["dyn"] == "legged":
         L = spec["n_links"]
-        pairs = L * (L - 1) // 2
         cost = 2 * (L - 1) + 14                 # base height / pitch / velocity, torque penalty
         forces = 3 * L + 4 * L                  # torque and gravity terms; tip position / velocity
         contact_walk = 10 * L                   # back-walk of the contact points and their moments
         velocity = 21 * L                       # prefix / suffix velocity terms
-        schur = 6 * L + 4 * pairs               # Schur right-hand side and matrix
-        chol = L * (L - 1) + sum((L - 1 - j) * (2 * j + 1) for j in range(L))
-        solves = 2 * L * L
+        schur_rhs = 6 * L                       # Schur right-hand side
+        factor = 24 * L                         # semiseparable Cholesky: 2 x 2 recursion per link
+        solves = 18 * L                         # forward and backward solves with running 2-vectors
         integrate = 4 * L + 4 * L + 8
-        return cost + forces + contact_walk + velocity + schur + chol + solves + integrate
+        return cost + forces + contact_walk + velocity + schur_rhs + factor + solves + integrate
     if spec["dyn"] == "pointmass":
         k = spec["n"]
         return 9 * k + 8 + len(spec.get("obs_c", [])) * (3 * k + 3)

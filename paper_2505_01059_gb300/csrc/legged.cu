@@ -184,56 +184,49 @@ __device__ __forceinline__ void rollout_legged_body(const RolloutArgs& a, const 
 #pragma unroll
       for (int j = 0; j < NL; ++j)
         rhs[j] = fmaf(-LB[j * BD] * invm, fmaf(-SN[j * BD], Rx, CS[j * BD] * Ry), rhs[j]);
-      // Schur matrix (lower triangle) and Cholesky
-      using T = Tri<NL>;
-      float A[T::size];  // lower triangle; after the factorisation the diagonal holds 1 / L_jj
+      // Schur system S phi'' = rhs.  Below the diagonal S_jk = u_j . v_k with
+      // u_j = lb_j (cos phi_j, sin phi_j) and v_k = WV_k (cos phi_k, sin phi_k):
+      // a rank-2 semiseparable matrix plus its diagonal SD.  Its Cholesky
+      // factor has the same form, L_jk = u_j . w_k below the diagonal, built
+      // link by link with the running 2 x 2 matrix M = sum_{i<k} w_i w_i^T:
+      //   d_k^2 = SD_k - u_k^T M u_k,  w_k = (v_k - M u_k) / d_k,  M += w_k w_k^T.
+      // Then L y = rhs and L^T phi'' = y with running 2-vectors: O(NL) in
+      // all, against O(NL^3) for the dense factorisation of the same matrix.
+      float u1[NL], u2[NL], w1[NL], w2[NL], dinv[NL];
+      {
+        float m11 = 0.f, m12 = 0.f, m22 = 0.f;
 #pragma unroll
-      for (int j = 0; j < NL; ++j) A[T::at(j, j)] = SD[j * BD];
-      Unroll<1, NL>::run([&](auto Jc) {
-        constexpr int j = decltype(Jc)::value;
-        const float sj = SN[j * BD], cj = CS[j * BD], lbj = LB[j * BD];
-        Unroll<0, j>::run([&](auto Kc) {
-          constexpr int k = decltype(Kc)::value;
-          A[T::at(j, k)] = (lbj * WV[k * BD]) * fmaf(cj, CS[k * BD], sj * SN[k * BD]);
-        });
-      });
-      Unroll<0, NL>::run([&](auto Jc) {
-        constexpr int j = decltype(Jc)::value;
-        float d = A[T::at(j, j)];
-        Unroll<0, j>::run([&](auto Kc) {
-          constexpr int k = decltype(Kc)::value;
-          d = fmaf(-A[T::at(j, k)], A[T::at(j, k)], d);
-        });
-        const float invj = rsqrtf(d);
-        A[T::at(j, j)] = invj;
-        Unroll<j + 1, NL>::run([&](auto Ic) {
-          constexpr int i = decltype(Ic)::value;
-          float v = A[T::at(i, j)];
-          Unroll<0, j>::run([&](auto Kc) {
-            constexpr int k = decltype(Kc)::value;
-            v = fmaf(-A[T::at(i, k)], A[T::at(j, k)], v);
-          });
-          A[T::at(i, j)] = v * invj;
-        });
-      });
-      Unroll<0, NL>::run([&](auto Ic) {
-        constexpr int i = decltype(Ic)::value;
-        float v = rhs[i];
-        Unroll<0, i>::run([&](auto Kc) {
-          constexpr int k = decltype(Kc)::value;
-          v = fmaf(-A[T::at(i, k)], rhs[k], v);
-        });
-        rhs[i] = v * A[T::at(i, i)];
-      });
-      Unroll<0, NL>::run([&](auto Ic) {
-        constexpr int i = NL - 1 - decltype(Ic)::value;
-        float v = rhs[i];
-        Unroll<i + 1, NL>::run([&](auto Kc) {
-          constexpr int k = decltype(Kc)::value;
-          v = fmaf(-A[T::at(k, i)], rhs[k], v);
-        });
-        rhs[i] = v * A[T::at(i, i)];
-      });
+        for (int k = 0; k < NL; ++k) {
+          const float ck = CS[k * BD], sk = SN[k * BD], lbk = LB[k * BD], wvk = WV[k * BD];
+          u1[k] = lbk * ck;
+          u2[k] = lbk * sk;
+          const float mu1 = fmaf(m11, u1[k], m12 * u2[k]);
+          const float mu2 = fmaf(m12, u1[k], m22 * u2[k]);
+          const float inv = rsqrtf(SD[k * BD] - fmaf(u1[k], mu1, u2[k] * mu2));
+          dinv[k] = inv;
+          w1[k] = fmaf(wvk, ck, -mu1) * inv;
+          w2[k] = fmaf(wvk, sk, -mu2) * inv;
+          m11 = fmaf(w1[k], w1[k], m11);
+          m12 = fmaf(w1[k], w2[k], m12);
+          m22 = fmaf(w2[k], w2[k], m22);
+        }
+      }
+      {
+        float z1 = 0.f, z2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          rhs[j] = (rhs[j] - fmaf(u1[j], z1, u2[j] * z2)) * dinv[j];
+          z1 = fmaf(w1[j], rhs[j], z1);
+          z2 = fmaf(w2[j], rhs[j], z2);
+        }
+        float r1 = 0.f, r2 = 0.f;
+#pragma unroll
+        for (int k = NL - 1; k >= 0; --k) {
+          rhs[k] = (rhs[k] - fmaf(w1[k], r1, w2[k] * r2)) * dinv[k];
+          r1 = fmaf(u1[k], rhs[k], r1);
+          r2 = fmaf(u2[k], rhs[k], r2);
+        }
+      }
       // base acceleration, then semi-implicit Euler
       float ax = Rx, ay = Ry;
 #pragma unroll
