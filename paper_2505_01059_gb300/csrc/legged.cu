@@ -39,7 +39,7 @@ __device__ __forceinline__ void rollout_legged_body(const RolloutArgs& a, const 
   float* SD = my + 6 * NL * BD;
   float* SA = my + 7 * NL * BD;  // velocity-term suffix sums
   float* SB = my + 8 * NL * BD;
-  float* TN = my + 9 * NL * BD;  // the next step's torques (prefetched)
+  float* TN = my + 9 * NL * BD;  // torques of steps t and t + 1 (two slots of NC)
 
   const int b = a.row0 + r;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
@@ -87,16 +87,24 @@ __device__ __forceinline__ void rollout_legged_body(const RolloutArgs& a, const 
       for (int k = 0; k < 2 * NQ; ++k) a.X[k] = a.x0[k];
     }
     KahanSum J;
+    // the torques of step t + 1 are copied into shared memory asynchronously
+    // while step t is computed (a plain load stored to shared memory would
+    // stall at the store until the load returned)
 #pragma unroll
-    for (int j = 0; j < NC; ++j) TN[j * BD] = __ldg(Ub + j);
+    for (int j = 0; j < NC; ++j) copy_async_f32(TN + j * BD, Ub + j);
+    copy_async_commit();
     for (int t = 0; t < a.H; ++t) {
-      float tau[NC];
-      const int tn = min(t + 1, a.H - 1);
+      float* slot = TN + (t & 1) * NC * BD;
+      copy_async_wait_all();  // step t's torques (issued one step ago)
+      if (t + 1 < a.H) {
+        float* next = TN + ((t + 1) & 1) * NC * BD;
 #pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        tau[j] = TN[j * BD];
-        TN[j * BD] = __ldg(Ub + tn * NC + j);  // one step ahead
+        for (int j = 0; j < NC; ++j) copy_async_f32(next + j * BD, Ub + (size_t)(t + 1) * NC + j);
+        copy_async_commit();
       }
+      float tau[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) tau[j] = slot[j * BD];
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
         float sj, cj;
@@ -273,7 +281,7 @@ __device__ __forceinline__ void rollout_legged_body(const RolloutArgs& a, const 
 template <int NL>
 __global__ void __launch_bounds__(kLegThreads) k_rollout_legged(const RolloutArgs a,
                                                                 const LeggedModel lm) {
-  __shared__ float sh[10 * NL * kLegThreads];
+  __shared__ float sh[(9 * NL + 2 * (NL - 1)) * kLegThreads];
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.rows) return;
   rollout_legged_body<NL>(a, lm, r, sh + threadIdx.x);
@@ -283,7 +291,7 @@ template <int NL>
 __global__ void __launch_bounds__(kLegThreads) k_rollout_legged_batch(
     const RolloutArgs* __restrict__ ra, const LeggedModel* __restrict__ lms,
     const int* __restrict__ row_start, int count) {
-  __shared__ float sh[10 * NL * kLegThreads];
+  __shared__ float sh[(9 * NL + 2 * (NL - 1)) * kLegThreads];
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= __ldg(row_start + count)) return;
   const int i = batch_instance(row_start, count, g);

@@ -59,6 +59,15 @@ __device__ __forceinline__ void sincos_reduced(float x, float* s, float* c) {
   __sincosf(r, s, c);
 }
 
+// Asynchronous 4-byte global-to-shared copy (cp.async, cached at L1), its
+// commit, and the wait for all of the thread's committed copies.
+__device__ __forceinline__ void copy_async_f32(float* smem_dst, const float* gmem_src) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void copy_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void copy_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <int NL>
 struct Tri {
   static constexpr int size = NL * (NL + 1) / 2;
