@@ -40,16 +40,22 @@ __device__ __forceinline__ float pm_state_cost(const PointMassModel& pm, const f
     const float e = p[k] - pm.target[k];
     dist2 = fmaf(e, e, dist2);
   }
+  // unrolled to the maximum obstacle count so every model index is a
+  // constant (a run-time index into the kernel parameters goes through the
+  // constant cache's slow indexed path)
   float pen = 0.f;
-  for (int o = 0; o < pm.n_obs; ++o) {
-    float d2 = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float e = p[k] - pm.obs_c[o][k];
-      d2 = fmaf(e, e, d2);
+  for (int o = 0; o < MTP_MAX_OBSTACLES; ++o) {
+    if (o < pm.n_obs) {
+      float d2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float e = p[k] - pm.obs_c[o][k];
+        d2 = fmaf(e, e, d2);
+      }
+      const float depth = pm.obs_r[o] - sqrtf(d2);
+      pen += depth > 0.f ? depth : 0.f;
     }
-    const float depth = pm.obs_r[o] - sqrtf(d2);
-    pen += depth > 0.f ? depth : 0.f;
   }
   return fmaf(pm.w_target, dist2, pm.w_obs * pen);
 }
