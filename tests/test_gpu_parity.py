@@ -377,10 +377,19 @@ def _boundary_ok(cost, E):
     return (b - a) > 2 * COST_RTOL * max(abs(a), 1.0)
 
 
-@pytest.mark.parametrize("spec,iters", [(W.pointmass(), 10), (W.chain(), 3),
-                                        (W.chain(links=4, B=1024, interp="bspline", M=6,
-                                                 beta=0.25), 3)])
-def test_plan_step_teacher_forced(mtp, spec, iters):
+@pytest.mark.parametrize("spec,iters,min_checked", [
+    (W.pointmass(), 10, 1), (W.chain(), 3, 1),
+    (W.chain(links=4, B=1024, interp="bspline", M=6, beta=0.25), 3, 1),
+    # degenerate and extreme shapes (min_checked: iterations whose E-th cost
+    # gap is clear enough to compare elite sets with the oracle's own costs)
+    (W.pointmass(B=1, E=1), 2, 1),                                  # the mean row alone
+    (W.pointmass(B=2, E=1, beta=1.0), 2, 1),                        # one graph path + the mean
+    (W.pointmass(k=16, B=300, H=1, E=7, M=4, degree=3), 2, 0),      # widest point mass, one step
+    (W.chain(links=12, B=256, H=16, M=3, N=1, E=8, beta=0.1), 2, 1),  # longest chain, one node per layer
+    (W.chain(links=1, B=64, H=8, M=2, interp="linear", E=4), 4, 1),   # one link, straight lines
+    (W.legged(links=2, B=128, H=16, M=4, N=8, E=4), 2, 1),          # shortest legged robot
+])
+def test_plan_step_teacher_forced(mtp, spec, iters, min_checked):
     h = mtp.mtp_create(spec)
     s = h.sizes
     x0 = np.array(spec["x0"], np.float64)
@@ -414,7 +423,7 @@ def test_plan_step_teacher_forced(mtp, spec, iters):
         np.testing.assert_allclose(mu_g, mu_r, rtol=1e-9, atol=1e-12)
         np.testing.assert_allclose(sg_g, sg_r, rtol=1e-9, atol=1e-12)
         assert np.array_equal(_np(ustar), us_r)
-    assert checked >= 1
+    assert checked >= min_checked
     mtp.mtp_destroy(h)
 
 
@@ -535,6 +544,28 @@ def test_legged_rollout_cost(mtp, links, B, H, dr):
     ref = orc.rollout_costs(spec, 2, x0.astype(np.float64), U32.astype(np.float64))
     assert np.all(np.isfinite(ref))
     assert _cost_close(_np(cost), ref) <= COST_RTOL
+    mtp.mtp_destroy(h)
+
+
+def test_legged_full_workload_sampled(mtp):
+    """The 16-link legged workload at full size (16384 candidates x 256 steps,
+    per-sample randomisation) in the launch configuration of the plan step:
+    sampled local, graph and mean rows against the oracle one by one."""
+    spec = W.legged()
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    U = torch.empty(s["B"], s["H"], s["n"], device=DEV)
+    mtp.mtp_generate_candidates(h, 0, U)
+    cost = torch.empty(s["B"], device=DEV)
+    x0 = np.array(spec["x0"], np.float32)
+    mtp.mtp_rollout_cost(h, 0, _t(x0), U, cost)
+    rows = np.unique(np.concatenate([np.random.default_rng(9).integers(0, s["B"], 40),
+                                     [0, s["L"] - 1, s["L"], s["B"] - 2, s["B"] - 1]]))
+    Un = _np(U)
+    cg = _np(cost)
+    for r in rows:
+        ref = orc.rollout_costs(spec, 0, x0.astype(np.float64), Un[r:r + 1], row0=int(r))
+        assert _cost_close(cg[r:r + 1], ref) <= COST_RTOL, r
     mtp.mtp_destroy(h)
 
 
