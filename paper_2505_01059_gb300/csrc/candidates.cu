@@ -286,7 +286,6 @@ __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, 
 
 __global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
   extern __shared__ float smem[];
-  griddep_sync();
   candidates_body(a, smem, blockIdx.x, gridDim.x);
 }
 
@@ -350,7 +349,6 @@ __device__ __forceinline__ void graph_Z_body(const CandArgs& a, float* Z, int bl
 // One planning problem whose graph is too large to regenerate in every
 // block's shared memory: Z once per iteration, its graph blocks gather from it.
 __global__ void __launch_bounds__(kThreads) k_graph_Z(const CandArgs a, float* Z) {
-  griddep_sync();
   graph_Z_body(a, Z, blockIdx.x, gridDim.x);
 }
 
@@ -429,18 +427,20 @@ cudaError_t launch_candidates_batch(const CandArgs* d_args, const int* d_block_s
   return cudaGetLastError();
 }
 
-cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t s, bool pdl) {
+cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t s) {
   const int grid = a.graph_blocks + local_blocks;
   if (grid <= 0) return cudaSuccess;
-  return launch_k(k_candidates, grid, kThreads, candidates_smem_bytes(a), s, pdl, a);
+  k_candidates<<<grid, kThreads, candidates_smem_bytes(a), s>>>(a);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_graph_Z(const CandArgs& a, float* Z, cudaStream_t s, bool pdl) {
+cudaError_t launch_graph_Z(const CandArgs& a, float* Z, cudaStream_t s) {
   const int items = a.dm.M * a.dm.N * ((a.dm.n + 3) / 4);
   int blocks = (items + kThreads - 1) / kThreads;
   if (blocks > 152) blocks = 152;
   if (blocks <= 0) return cudaSuccess;
-  return launch_k(k_graph_Z, blocks, kThreads, 0, s, pdl, a, Z);
+  k_graph_Z<<<blocks, kThreads, 0, s>>>(a, Z);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_local_batch(const CandArgs* d_args, const int* d_local_start, int count,

@@ -292,7 +292,6 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
 
 __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  griddep_sync();
   select_body(a, sm_raw);
 }
 
@@ -403,7 +402,6 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int thr
 
 template <int G>
 __global__ void __launch_bounds__(128) k_update(const UpdateArgs a) {
-  griddep_sync();
   update_body<G>(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
@@ -486,11 +484,13 @@ cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_thread_st
 
 int update_threads(int H, int n) { return H * n; }
 
-cudaError_t launch_select(const SelectArgs& a, cudaStream_t s, bool pdl) {
-  return launch_k(k_select, 1, kSelThreads, select_smem_bytes(a.B, a.E), s, pdl, a);
+cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
+  k_select<<<1, kSelThreads, select_smem_bytes(a.B, a.E), s>>>(a);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s, bool pdl) {
+// Lanes per element: as many as keep roughly 38K threads busy, up to a warp.
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   const int Hn = a.H * a.n;
   // lanes per element: enough threads to spread the gathers over the GPU.
   // The kernel is latency-bound (elite index, then row gather), so more
@@ -501,13 +501,14 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s, bool pdl) {
   const long long threads = (long long)Hn * G;
   const int blocks = (int)((threads + 127) / 128);
   switch (G) {
-    case 1: return launch_k(k_update<1>, blocks, 128, 0, s, pdl, a);
-    case 2: return launch_k(k_update<2>, blocks, 128, 0, s, pdl, a);
-    case 4: return launch_k(k_update<4>, blocks, 128, 0, s, pdl, a);
-    case 8: return launch_k(k_update<8>, blocks, 128, 0, s, pdl, a);
-    case 16: return launch_k(k_update<16>, blocks, 128, 0, s, pdl, a);
-    default: return launch_k(k_update<32>, blocks, 128, 0, s, pdl, a);
+    case 1: k_update<1><<<blocks, 128, 0, s>>>(a); break;
+    case 2: k_update<2><<<blocks, 128, 0, s>>>(a); break;
+    case 4: k_update<4><<<blocks, 128, 0, s>>>(a); break;
+    case 8: k_update<8><<<blocks, 128, 0, s>>>(a); break;
+    case 16: k_update<16><<<blocks, 128, 0, s>>>(a); break;
+    default: k_update<32><<<blocks, 128, 0, s>>>(a); break;
   }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_shift_batch(const UpdateArgs* d_args, int count, int k, cudaStream_t s) {

@@ -282,7 +282,6 @@ template <int NL>
 __global__ void __launch_bounds__(kLegThreads) k_rollout_legged(const RolloutArgs a,
                                                                 const LeggedModel lm) {
   __shared__ float sh[(9 * NL + 2 * (NL - 1)) * kLegThreads];
-  griddep_sync();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.rows) return;
   rollout_legged_body<NL>(a, lm, r, sh + threadIdx.x);
@@ -303,14 +302,13 @@ __global__ void __launch_bounds__(kLegThreads) k_rollout_legged_batch(
 }
 
 template <int NL>
-cudaError_t legged_dispatch(const RolloutArgs& a, const LeggedModel& m, int links, cudaStream_t s,
-                            bool pdl) {
+cudaError_t legged_dispatch(const RolloutArgs& a, const LeggedModel& m, int links, cudaStream_t s) {
   if constexpr (NL <= 16) {
     if (links == NL) {
-      return launch_k(k_rollout_legged<NL>, (a.rows + kLegThreads - 1) / kLegThreads, kLegThreads, 0,
-                      s, pdl, a, m);
+      k_rollout_legged<NL><<<(a.rows + kLegThreads - 1) / kLegThreads, kLegThreads, 0, s>>>(a, m);
+      return cudaGetLastError();
     }
-    return legged_dispatch<NL + 1>(a, m, links, s, pdl);
+    return legged_dispatch<NL + 1>(a, m, links, s);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -334,9 +332,9 @@ cudaError_t legged_batch_dispatch(const RolloutArgs* ra, const LeggedModel* lm, 
 }  // namespace
 
 cudaError_t launch_rollout_legged(const RolloutArgs& a, const LeggedModel& m, int links,
-                                  cudaStream_t s, bool pdl) {
+                                  cudaStream_t s) {
   if (a.rows <= 0) return cudaSuccess;
-  return legged_dispatch<2>(a, m, links, s, pdl);
+  return legged_dispatch<2>(a, m, links, s);
 }
 
 cudaError_t launch_rollout_legged_batch(const RolloutArgs* d_ra, const LeggedModel* d_lm,

@@ -357,23 +357,21 @@ LeggedModel legged_model(const mtp_problem& p) {
 
 // Candidate generation of one handle (graph rows, local rows, mean row as
 // `c` asks), with the graph written first when it is not regenerated per block.
-cudaError_t launch_generate(const mtp_handle* h, CandArgs& c, cudaStream_t s, bool pdl_first = false,
-                            bool pdl = false) {
+cudaError_t launch_generate(const mtp_handle* h, CandArgs& c, cudaStream_t s) {
   if (c.graph_blocks > 0 && h->global_Z && !c.C_in) {
     c.Z_global = h->Z;
-    cudaError_t e = launch_graph_Z(c, h->Z, s, pdl_first);
+    cudaError_t e = launch_graph_Z(c, h->Z, s);
     if (e != cudaSuccess) return e;
-    pdl_first = pdl;
   }
   const int local_blocks = c.U_local ? local_blocks_for(h, (long long)c.local_rows + 1) : 0;
-  return launch_candidates(c, local_blocks, s, pdl_first);
+  return launch_candidates(c, local_blocks, s);
 }
 
-cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s, bool pdl = false) {
+cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
   const mtp_problem& p = h->pr;
-  if (p.dyn == MTP_DYN_POINTMASS) return launch_rollout_pointmass(a, pointmass_model(p), s, pdl);
-  if (p.dyn == MTP_DYN_LEGGED) return launch_rollout_legged(a, legged_model(p), p.n_links, s, pdl);
-  return launch_rollout_chain(a, chain_model(p), p.n_links, s, pdl);
+  if (p.dyn == MTP_DYN_POINTMASS) return launch_rollout_pointmass(a, pointmass_model(p), s);
+  if (p.dyn == MTP_DYN_LEGGED) return launch_rollout_legged(a, legged_model(p), p.n_links, s);
+  return launch_rollout_chain(a, chain_model(p), p.n_links, s);
 }
 
 // Stage event: inside a stream capture it must be an external event record
@@ -384,12 +382,7 @@ inline void stage_event(cudaEvent_t ev, cudaStream_t s, bool captured) {
 }
 
 // One Alg. 2 iteration on the handle's own buffers, iteration from iter_dev.
-// Without stage events its kernels use programmatic dependent launch (each
-// may start while its predecessor drains); `pdl_first` extends that to the
-// iteration's first kernel when a kernel of this handle precedes it.
-cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev, bool captured = false,
-                              bool pdl_first = false) {
-  const bool pdl = ev == nullptr;
+cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev, bool captured = false) {
   cudaError_t e;
   const Dims& dm = h->dm;
   const size_t Hn = (size_t)dm.H * dm.n;
@@ -401,18 +394,18 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev, bo
   c.U_local = h->U;
   c.local_rows = dm.L;
   c.U_mean = h->U + Hn * (dm.B - 1);
-  if ((e = launch_generate(h, c, s, pdl && pdl_first, pdl)) != cudaSuccess) return e;
+  if ((e = launch_generate(h, c, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[1], s, captured);
   RolloutArgs r = rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, dm.B, h->cost);
-  if ((e = launch_rollout(h, r, s, pdl)) != cudaSuccess) return e;
+  if ((e = launch_rollout(h, r, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[2], s, captured);
   SelectArgs sa{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
                 h->elite, h->weight, h->ustar, nullptr, nullptr};
-  if ((e = launch_select(sa, s, pdl)) != cudaSuccess) return e;
+  if ((e = launch_select(sa, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[3], s, captured);
   UpdateArgs ua{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
                 h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
-  if ((e = launch_update(ua, s, pdl)) != cudaSuccess) return e;
+  if ((e = launch_update(ua, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[4], s, captured);
   return cudaSuccess;
 }
@@ -666,7 +659,7 @@ static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
         ev = h->events.data() + h->ev_used;
         h->ev_used += 5;
       }
-      if ((e = enqueue_iteration(h, s, ev, false, k > 0)) != cudaSuccess) return cuda_fail(h, e, "plan_step");
+      if ((e = enqueue_iteration(h, s, ev)) != cudaSuccess) return cuda_fail(h, e, "plan_step");
     }
     return MTP_OK;
   }
@@ -692,7 +685,7 @@ static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
         return cuda_fail(h, e, "cudaStreamBeginCapture");
       for (int k = 0; k < chunk; ++k) {
         cudaEvent_t* ev = h->profiling ? h->gevents.data() + 5 * k : nullptr;
-        if ((e = enqueue_iteration(h, h->cap_stream, ev, true, k > 0)) != cudaSuccess) {
+        if ((e = enqueue_iteration(h, h->cap_stream, ev, true)) != cudaSuccess) {
           cudaStreamEndCapture(h->cap_stream, &graph);
           return cuda_fail(h, e, "capture");
         }

@@ -4,7 +4,6 @@
 
 #include <cstdint>
 #include <string>
-#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -187,50 +186,24 @@ void set_thread_error(const std::string& msg);  // text for mtp_last_error(NULL)
 size_t candidates_smem_bytes(const CandArgs& a);
 cudaError_t init_candidate_attributes();
 cudaError_t init_select_attributes();
-// Programmatic dependent launch.  A kernel launched with `pdl` may start
-// while the previous kernel on its stream is still running: every kernel
-// here first lets its own dependents launch, then waits for its
-// prerequisite grids (and their memory) before reading anything they wrote.
-// Without the launch attribute the wait returns at once.
-__device__ __forceinline__ void griddep_sync() {
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-}
-
-template <typename... KArgs, typename... Args>
-cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                     bool pdl, Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
-cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t s, bool pdl = false);
+cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t s);
 cudaError_t launch_sample_tensor(const Dims& dm, Key key, uint32_t iter, const float* umin,
                                  const float* umax, float* Z, int32_t* I, float* C,
                                  cudaStream_t s);
 cudaError_t launch_rollout_pointmass(const RolloutArgs& a, const PointMassModel& m,
-                                     cudaStream_t s, bool pdl = false);
+                                     cudaStream_t s);
 cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int links,
-                                 cudaStream_t s, bool pdl = false);
+                                 cudaStream_t s);
 cudaError_t launch_rollout_legged(const RolloutArgs& a, const LeggedModel& m, int links,
-                                  cudaStream_t s, bool pdl = false);
+                                  cudaStream_t s);
 cudaError_t launch_rollout_legged_batch(const RolloutArgs* d_ra, const LeggedModel* d_lm,
                                         const int* d_row_start, int count, int total_rows,
                                         int links, cudaStream_t s);
-cudaError_t launch_select(const SelectArgs& a, cudaStream_t s, bool pdl = false);
+cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 size_t select_smem_bytes(int B, int E);
-cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s, bool pdl = false);
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 // batched forms: one launch over many planning problems
-cudaError_t launch_graph_Z(const CandArgs& a, float* Z, cudaStream_t s, bool pdl = false);
+cudaError_t launch_graph_Z(const CandArgs& a, float* Z, cudaStream_t s);
 cudaError_t launch_local_batch(const CandArgs* d_args, const int* d_local_start, int count,
                                int total_blocks, cudaStream_t s);
 cudaError_t launch_graph_Z_batch(const CandArgs* d_args, float* const* d_Z, const int* d_block_start,

@@ -345,7 +345,6 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
 template <int K>
 __global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
                                                          const PointMassModel pm) {
-  griddep_sync();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.rows) return;
   rollout_pm_body<K>(a, pm, r);
@@ -368,7 +367,6 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm_batch(const RolloutArgs
 template <int NL>
 __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
                                                             const ChainModel cm) {
-  griddep_sync();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.rows) return;
   rollout_chain_body<NL>(a, cm, r);
@@ -390,28 +388,28 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain_batch(const RolloutA
 }
 
 template <int K>
-cudaError_t pm_dispatch(const RolloutArgs& a, const PointMassModel& m, int k, cudaStream_t s,
-                        bool pdl) {
+cudaError_t pm_dispatch(const RolloutArgs& a, const PointMassModel& m, int k, cudaStream_t s) {
   if constexpr (K <= 16) {
     if (k == K) {
       const int bd = rollout_block(a.rows);
-      return launch_k(k_rollout_pm<K>, (a.rows + bd - 1) / bd, bd, 0, s, pdl, a, m);
+      k_rollout_pm<K><<<(a.rows + bd - 1) / bd, bd, 0, s>>>(a, m);
+      return cudaGetLastError();
     }
-    return pm_dispatch<K + 1>(a, m, k, s, pdl);
+    return pm_dispatch<K + 1>(a, m, k, s);
   } else {
     return cudaErrorInvalidValue;
   }
 }
 
 template <int NL>
-cudaError_t chain_dispatch(const RolloutArgs& a, const ChainModel& m, int links, cudaStream_t s,
-                           bool pdl) {
+cudaError_t chain_dispatch(const RolloutArgs& a, const ChainModel& m, int links, cudaStream_t s) {
   if constexpr (NL <= 12) {
     if (links == NL) {
       const int bd = rollout_block(a.rows);
-      return launch_k(k_rollout_chain<NL>, (a.rows + bd - 1) / bd, bd, 0, s, pdl, a, m);
+      k_rollout_chain<NL><<<(a.rows + bd - 1) / bd, bd, 0, s>>>(a, m);
+      return cudaGetLastError();
     }
-    return chain_dispatch<NL + 1>(a, m, links, s, pdl);
+    return chain_dispatch<NL + 1>(a, m, links, s);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -463,15 +461,15 @@ cudaError_t launch_rollout_chain_batch(const RolloutArgs* d_ra, const ChainModel
 }
 
 cudaError_t launch_rollout_pointmass(const RolloutArgs& a, const PointMassModel& m,
-                                     cudaStream_t s, bool pdl) {
+                                     cudaStream_t s) {
   if (a.rows <= 0) return cudaSuccess;
-  return pm_dispatch<1>(a, m, a.n, s, pdl);
+  return pm_dispatch<1>(a, m, a.n, s);
 }
 
 cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int links,
-                                 cudaStream_t s, bool pdl) {
+                                 cudaStream_t s) {
   if (a.rows <= 0) return cudaSuccess;
-  return chain_dispatch<1>(a, m, links, s, pdl);
+  return chain_dispatch<1>(a, m, links, s);
 }
 
 }  // namespace mtp
