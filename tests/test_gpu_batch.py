@@ -26,6 +26,7 @@ def _specs():
     specs = W.batch(seed=11, count=10)
     specs.append(W.pointmass(B=512))
     specs.append(W.chain(links=7, B=1000, E=50))
+    specs.append(W.pointmass(k=3, B=600, flags=0x4))  # BF16 basis operands
     return specs
 
 
