@@ -350,18 +350,31 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
   rollout_pm_body<K>(a, pm, r);
 }
 
+// Rows are padded to whole warps, so a warp belongs to one instance: each
+// warp copies its instance's model (goal, obstacles) to shared memory once.
+// Read from global memory, the obstacle data cost about 6K + 9 loads per
+// step through L1; the standalone kernel reads it as constant operands.
 template <int K>
 __global__ void __launch_bounds__(kThreads) k_rollout_pm_batch(const RolloutArgs* __restrict__ ra,
                                                                const PointMassModel* __restrict__ pm,
                                                                const int* __restrict__ row_start,
                                                                int count) {
+  __shared__ PointMassModel models[kThreads / 32];
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= __ldg(row_start + count)) return;
+  if (g >= __ldg(row_start + count)) return;  // whole warps: the total is padded to warps
   const int i = batch_instance(row_start, count, g);
+  PointMassModel& m = models[threadIdx.x >> 5];
+  {
+    const int* src = reinterpret_cast<const int*>(pm + i);
+    int* dst = reinterpret_cast<int*>(&m);
+    for (int w = threadIdx.x & 31; w < (int)(sizeof(PointMassModel) / sizeof(int)); w += 32)
+      dst[w] = __ldg(src + w);
+    __syncwarp();
+  }
   const RolloutArgs a = ra[i];
   const int r = g - __ldg(row_start + i);
   if (r >= a.rows) return;
-  rollout_pm_body<K>(a, pm[i], r);
+  rollout_pm_body<K>(a, m, r);
 }
 
 template <int NL>
