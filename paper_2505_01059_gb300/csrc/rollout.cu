@@ -53,7 +53,11 @@ __device__ __forceinline__ float pm_state_cost(const PointMassModel& pm, const f
         const float e = p[k] - pm.obs_c[o][k];
         d2 = fmaf(e, e, d2);
       }
-      const float depth = pm.obs_r[o] - sqrtf(d2);
+      // distance as d2 * rsqrt(d2): one SFU operation and a multiply instead
+      // of the correctly rounded square root's fix-up sequence (relative
+      // error ~1e-7, far inside the cost tolerance)
+      const float dist = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+      const float depth = pm.obs_r[o] - dist;
       pen += depth > 0.f ? depth : 0.f;
     }
   }
