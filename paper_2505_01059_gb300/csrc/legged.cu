@@ -23,6 +23,14 @@ namespace {
 
 constexpr int kLegThreads = 64;
 
+// tanh(x) = 1 - 2 / (exp(2x) + 1) with the SFU exponential and an
+// approximate division: the smoothed Coulomb friction direction.  Exact at
+// both limits (exp overflows to inf, or underflows to 0); absolute error
+// about 1e-7 elsewhere, which scales a friction force of at most mu * fn.
+__device__ __forceinline__ float smooth_sign(float x) {
+  return 1.f - __fdividef(2.f, __expf(2.f * x) + 1.f);
+}
+
 template <int NL>
 __device__ __forceinline__ void rollout_legged_body(const RolloutArgs& a, const LeggedModel& lm,
                                                     int r, float* my) {
@@ -144,11 +152,12 @@ __device__ __forceinline__ void rollout_legged_body(const RolloutArgs& a, const 
       float Fx = 0.f, Fy = 0.f;
 #pragma unroll
       for (int c = NL; c >= 0; --c) {
-        if (cy < 0.f) {
-          const float fn = fmaxf(fmaf(-lm.k_contact, cy, -lm.c_contact * cvy), 0.f);
-          Fx = fmaf(-mu_s * fn, tanhf(cvx * lm.inv_v_slip), Fx);
-          Fy += fn;
-        }
+        // branch-free: a point above the ground gets a zero normal force (a
+        // divergent branch per point cost more than the arithmetic it skipped)
+        const float fn_in = fmaxf(fmaf(-lm.k_contact, cy, -lm.c_contact * cvy), 0.f);
+        const float fn = cy < 0.f ? fn_in : 0.f;
+        Fx = fmaf(-mu_s * fn, smooth_sign(cvx * lm.inv_v_slip), Fx);
+        Fy += fn;
         if (c >= 1) {
           const int j = c - 1;
           const float l = lm.length[j], w = OMG[j * BD];
