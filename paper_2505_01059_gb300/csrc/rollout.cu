@@ -64,7 +64,7 @@ __device__ __forceinline__ float pm_state_cost(const PointMassModel& pm, const f
   return fmaf(pm.w_target, dist2, pm.w_obs * pen);
 }
 
-template <int K>
+template <int K, int PF>
 __device__ __forceinline__ void rollout_pm_body(const RolloutArgs& a, const PointMassModel& pm,
                                                 int r) {
   const int b = a.row0 + r;
@@ -91,21 +91,21 @@ __device__ __forceinline__ void rollout_pm_body(const RolloutArgs& a, const Poin
       }
     }
     KahanSum J;
-    // controls are requested kPrefetch steps ahead into a rotating register
-    // buffer (the time loop is unrolled by kPrefetch so slots are constants)
-    float ubuf[kPrefetch][K];
+    // controls are requested PF steps ahead into a rotating register buffer
+    // (the time loop is unrolled by PF so slots are constants)
+    float ubuf[PF][K];
 #pragma unroll
-    for (int q = 0; q < kPrefetch; ++q)
+    for (int q = 0; q < PF; ++q)
 #pragma unroll
       for (int k = 0; k < K; ++k) ubuf[q][k] = __ldg(Ub + min(q, a.H - 1) * K + k);
-    for (int t0 = 0; t0 < a.H; t0 += kPrefetch) {
-      Unroll<0, kPrefetch>::run([&](auto Q) {
+    for (int t0 = 0; t0 < a.H; t0 += PF) {
+      Unroll<0, PF>::run([&](auto Q) {
         constexpr int q = decltype(Q)::value;
         const int t = t0 + q;
         if (t < a.H) {
           float u[K];
           float uu = 0.f;
-          const int tn = min(t + kPrefetch, a.H - 1);
+          const int tn = min(t + PF, a.H - 1);
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             u[k] = ubuf[q][k];
@@ -151,7 +151,7 @@ __device__ __forceinline__ void chain_tip(const float (&len)[NL], const float (&
   }
 }
 
-template <int NL>
+template <int NL, int PF>
 __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const ChainModel& cm,
                                                    int r) {
   const int b = a.row0 + r;
@@ -202,22 +202,22 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
       }
     }
     KahanSum J;
-    float ubuf[kPrefetch][NL];
+    float ubuf[PF][NL];
 #pragma unroll
-    for (int q = 0; q < kPrefetch; ++q)
+    for (int q = 0; q < PF; ++q)
 #pragma unroll
       for (int j = 0; j < NL; ++j) ubuf[q][j] = __ldg(Ub + min(q, a.H - 1) * NL + j);
-    for (int t0 = 0; t0 < a.H; t0 += kPrefetch) {
-     Unroll<0, kPrefetch>::run([&](auto Q) {
+    for (int t0 = 0; t0 < a.H; t0 += PF) {
+     Unroll<0, PF>::run([&](auto Q) {
       constexpr int q = decltype(Q)::value;
       const int t = t0 + q;
       if (t >= a.H) return;
       float c[NL], s[NL], tau[NL];
-      const int tn = min(t + kPrefetch, a.H - 1);
+      const int tn = min(t + PF, a.H - 1);
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
         tau[j] = ubuf[q][j];
-        ubuf[q][j] = __ldg(Ub + tn * NL + j);  // kPrefetch steps ahead
+        ubuf[q][j] = __ldg(Ub + tn * NL + j);  // PF steps ahead
         sincos_reduced(phi[j], &s[j], &c[j]);
       }
       // stage cost c(x_t, u_t): reach error of the tip and torque penalty
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
                                                          const PointMassModel pm) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.rows) return;
-  rollout_pm_body<K>(a, pm, r);
+  rollout_pm_body<K, kPrefetchAlone>(a, pm, r);
 }
 
 // Rows are padded to whole warps, so a warp belongs to one instance: each
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm_batch(const RolloutArgs
   const RolloutArgs a = ra[i];
   const int r = g - __ldg(row_start + i);
   if (r >= a.rows) return;
-  rollout_pm_body<K>(a, m, r);
+  rollout_pm_body<K, kPrefetchBatch>(a, m, r);
 }
 
 template <int NL>
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
                                                             const ChainModel cm) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.rows) return;
-  rollout_chain_body<NL>(a, cm, r);
+  rollout_chain_body<NL, kPrefetchAlone>(a, cm, r);
 }
 
 template <int NL>
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain_batch(const RolloutA
   const ChainModel cm = cms[i];
   const int r = g - __ldg(row_start + i);
   if (r >= a.rows) return;
-  rollout_chain_body<NL>(a, cm, r);
+  rollout_chain_body<NL, kPrefetchBatch>(a, cm, r);
 }
 
 template <int K>

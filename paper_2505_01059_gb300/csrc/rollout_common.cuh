@@ -8,7 +8,13 @@
 namespace mtp {
 namespace {
 
-constexpr int kPrefetch = 4;  // control steps requested ahead of use
+// Control steps requested ahead of use by the point-mass and chain rollouts.
+// Measured on GB300 (depths 1 / 2 / 3 / 4): a lone instance, which has one
+// warp per SM sub-partition at most, is fastest at 2 (7-link arm 118 / 105 /
+// 105 / 109 us per step); a batch, where registers set how many warps are
+// resident, at 1 (256 instances 4.06 / 4.16 / 4.25 / 4.37 ms per iteration).
+constexpr int kPrefetchAlone = 2;
+constexpr int kPrefetchBatch = 1;
 
 // Compile-time loop: calls f(IC<i>) for i in [B, E), so every array index
 // derived from i is a constant and the arrays stay in registers.
