@@ -489,16 +489,15 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Lanes per element: as many as keep roughly 38K threads busy, up to a warp.
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   const int Hn = a.H * a.n;
-  // lanes per element: enough threads to spread the gathers over the GPU,
-  // at most 16.  The kernel is latency-bound (elite index, then row gather),
-  // but every lane of an element repeats the FP64 butterfly and the final
-  // square root.  Measured on the 7-link arm workload: a cap of 8 lanes
-  // slowed the kernel (10.6 -> 12.5 us against 32), a cap of 16 shortened
-  // the whole plan step (105.1 -> 103.1 us)
+  // lanes per element: enough threads to spread the gathers over the GPU.
+  // The kernel is latency-bound (elite index, then row gather), so more
+  // lanes win even though each lane repeats the FP64 butterfly (8 lanes per
+  // element measured slower than 32 on the 7-link arm workload)
   int G = 1;
-  while (G < 16 && (long long)Hn * G < 152 * 256) G <<= 1;
+  while (G < 32 && (long long)Hn * G < 152 * 256) G <<= 1;
   const long long threads = (long long)Hn * G;
   const int blocks = (int)((threads + 127) / 128);
   switch (G) {
@@ -506,7 +505,8 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
     case 2: k_update<2><<<blocks, 128, 0, s>>>(a); break;
     case 4: k_update<4><<<blocks, 128, 0, s>>>(a); break;
     case 8: k_update<8><<<blocks, 128, 0, s>>>(a); break;
-    default: k_update<16><<<blocks, 128, 0, s>>>(a); break;
+    case 16: k_update<16><<<blocks, 128, 0, s>>>(a); break;
+    default: k_update<32><<<blocks, 128, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }
