@@ -128,7 +128,7 @@ __device__ __forceinline__ void rollout_legged_body(const RolloutArgs& a, const 
         for (int j = 0; j < NC; ++j) tt = fmaf(tau[j], tau[j], tt);
         const float dh = py - lm.target[0], dv = vx - lm.target[1], dp = PHI[0] - lm.target[2];
         const float state = fmaf(lm.w_height, dh * dh, fmaf(lm.w_pitch, dp * dp, lm.w_vel * dv * dv));
-        J.add(fmaf(lm.w_ctrl, tt, state), a.kahan);
+        J.add_branch_free(fmaf(lm.w_ctrl, tt, state), a.kahan);
       }
       // generalised forces of the torques and gravity on the link angles
       float rhs[NL];
@@ -278,7 +278,7 @@ __device__ __forceinline__ void rollout_legged_body(const RolloutArgs& a, const 
     {
       const float dh = py - lm.target[0], dv = vx - lm.target[1], dp = PHI[0] - lm.target[2];
       const float state = fmaf(lm.w_height, dh * dh, fmaf(lm.w_pitch, dp * dp, lm.w_vel * dv * dv));
-      J.add(lm.w_term * state, a.kahan);
+      J.add_branch_free(lm.w_term * state, a.kahan);
     }
     total += J.s;
   }
