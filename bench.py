@@ -100,18 +100,30 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+KERNEL_HEADERS = ("paper_2505_01059_gb300/csrc/rollout_common.cuh",
+                  "paper_2505_01059_gb300/csrc/mtp_device.cuh", "include/mtp.h")
+
+
+def source_digest(kernel_file: str) -> str:
+    """sha256 over a rollout kernel's source file and the headers it is
+    compiled with, so that a change to either retires its profile."""
+    h = hashlib.sha256()
+    for rel in ("paper_2505_01059_gb300/csrc/" + kernel_file,) + KERNEL_HEADERS:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def profiled_traffic(kernel_file: str, summary: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current source of the kernel (else None)."""
-    src = os.path.join(ROOT, "paper_2505_01059_gb300", "csrc", kernel_file)
+    the current sources of the kernel (else None)."""
     prof = os.path.join(ROOT, "profiles", summary)
-    if not (os.path.exists(src) and os.path.exists(prof)):
+    if not os.path.exists(prof):
         return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     text = open(prof).read()
     m_hash = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     m_bytes = re.search(r"dram_bytes_per_launch_full_workload:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != digest:
+    if not m_hash or not m_bytes or m_hash.group(1) != source_digest(kernel_file):
         return None
     return float(m_bytes.group(1))
 
