@@ -326,7 +326,9 @@ typedef struct mtp_server_stats {
 mtp_status mtp_server_create(const mtp_server_config* cfg, mtp_server** out);
 
 /* Stops the worker after the cycles in flight, drops queued requests and
- * frees everything, the robots' handles included. */
+ * frees everything, the robots' handles included.  No other thread may call
+ * into the server during or after this call.  Every other server call may be
+ * made from any thread. */
 mtp_status mtp_server_destroy(mtp_server* srv);
 
 /* Admits a robot: creates its planner handle when its footprint

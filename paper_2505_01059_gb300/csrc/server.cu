@@ -57,7 +57,8 @@ struct mtp_server {
   std::mutex reg_mu;  // guards the robot tables and the admitted bytes
   std::vector<mtp_handle*> robots;
   std::vector<int32_t> robot_d, robot_n;
-  uint64_t bytes_admitted = 0;
+  uint64_t bytes_admitted = 0;  // robots admitted, and registrations in progress
+  int registering = 0;          // registrations between admission and their handle
   Slot slots[kSlots];
   std::thread worker;
   std::atomic<bool> stop{false};
@@ -283,22 +284,35 @@ mtp_status mtp_server_register(mtp_server* S, const mtp_problem* problem, int32_
   uint64_t bytes = 0;
   mtp_status st = mtp_problem_device_bytes(problem, &bytes);
   if (st != MTP_OK) return server_fail(S, st, std::string("register: ") + mtp_last_error(nullptr));
-  std::lock_guard<std::mutex> lock(S->reg_mu);
-  if ((int)S->robots.size() >= S->cfg.max_robots)
-    return server_fail(S, MTP_ERR_ADMISSION, "register: max_robots reached");
-  if (S->bytes_admitted + bytes > S->budget)
-    return server_fail(S, MTP_ERR_ADMISSION,
-                       "register: " + std::to_string(bytes) + " bytes do not fit the remaining budget of " +
-                           std::to_string(S->budget - S->bytes_admitted));
-  DeviceScope g(S->device);
+  // admission is decided and reserved under the lock; the handle (device
+  // allocations, synchronous copies) is created outside it, so cycles that
+  // start meanwhile are not held up
+  {
+    std::lock_guard<std::mutex> lock(S->reg_mu);
+    if ((int)S->robots.size() + S->registering >= S->cfg.max_robots)
+      return server_fail(S, MTP_ERR_ADMISSION, "register: max_robots reached");
+    if (S->bytes_admitted + bytes > S->budget)
+      return server_fail(S, MTP_ERR_ADMISSION,
+                         "register: " + std::to_string(bytes) + " bytes do not fit the remaining budget of " +
+                             std::to_string(S->budget - S->bytes_admitted));
+    S->bytes_admitted += bytes;
+    ++S->registering;
+  }
   mtp_handle* h = nullptr;
-  if ((st = mtp_create(problem, &h)) != MTP_OK)
+  {
+    DeviceScope g(S->device);
+    st = mtp_create(problem, &h);
+  }
+  std::lock_guard<std::mutex> lock(S->reg_mu);
+  --S->registering;
+  if (st != MTP_OK) {
+    S->bytes_admitted -= bytes;  // the reservation is returned
     return server_fail(S, st, std::string("register: ") + mtp_last_error(nullptr));
+  }
   *robot = (int32_t)S->robots.size();
   S->robots.push_back(h);
   S->robot_d.push_back(problem->state_dim);
   S->robot_n.push_back(problem->ctrl_dim);
-  S->bytes_admitted += bytes;
   return MTP_OK;
 }
 
