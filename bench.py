@@ -418,7 +418,9 @@ def run_ours(args, spec, name):
 
     # stage pass over the same number of steps (at most 500): the same
     # kernels launched directly with CUDA events between them on the launch
-    # stream, for the per-stage times and the rollout kernel's duration
+    # stream, for the per-stage times and the rollout kernel's duration; a
+    # pipelined handle's preparation of the next iteration is timed on its
+    # own stream (it overlaps the rollout)
     hp = mtp.mtp_create(dict(spec, flags=spec.get("flags", 0) | mtp.FLAG_NO_GRAPH))
     for _ in range(3):
         mtp.mtp_plan_step(hp, x0, 1, ustar)
@@ -428,7 +430,8 @@ def run_ours(args, spec, name):
         flush.zero_()
         mtp.mtp_plan_step(hp, x0, 1, ustar)
     torch.cuda.synchronize()
-    stage_ms, n_it = mtp.mtp_stage_times(hp)
+    stage5, n_it = mtp.mtp_stage_times5(hp)
+    stage_ms, prep_ms = stage5[:4], stage5[4]
     mtp.mtp_destroy(hp)
 
     # end to end through the host-pointer entry point: pinned x0 in, u* out
@@ -486,6 +489,8 @@ def run_ours(args, spec, name):
             "stage_ms_per_step": dict(zip(("generate", "rollout", "select", "update"),
                                           [v / max(n_it, 1) for v in stage_ms])),
             "stage_share": share,
+            "pipelined": bool(s["pipelined"]),
+            "prepare_overlapped_ms_per_step": prep_ms / max(n_it, 1),
             "roofline": {"bound": "alu", "kernel": ROLLOUT_KERNEL[spec["dyn"]],
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,

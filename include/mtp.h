@@ -77,6 +77,10 @@ typedef enum { MTP_DR_NONE = 0, MTP_DR_PER_SAMPLE = 1, MTP_DR_SHARED = 2 } mtp_d
                                      only (MTP_ERR_UNSUPPORTED otherwise).  Runs on the
                                      FP32 pipe: the contraction stores 4 bytes per p+1
                                      products, so tensor cores would not shorten it */
+#define MTP_FLAG_NO_PIPELINE 0x8u /* mtp_plan_step makes each iteration's candidates in
+                                     full on the critical path instead of preparing the
+                                     next iteration's graph rows and draws during the
+                                     rollout (results are the same bits either way) */
 
 /* One planning problem (Sec. 2.1 problem statement, Alg. 2 inputs, Table 3
  * hyper-parameters).  Plain data; mtp_create copies it. */
@@ -121,11 +125,17 @@ typedef struct mtp_problem {
 
 typedef struct mtp_sizes {
   int32_t B, P, L, E, H, n, d, M, N;
-  int32_t kernels_per_iteration; /* kernel launches of one mtp_plan_step iteration */
+  int32_t kernels_per_iteration; /* kernel launches of one mtp_plan_step iteration (after
+                                    the first, when pipelined) */
+  int32_t pipelined;             /* 1: mtp_plan_step prepares each next iteration's graph
+                                    rows and draws on the SMs its rollout leaves idle */
 } mtp_sizes;
 
 /* Device buffers owned by a handle (valid until mtp_destroy).  After
- * mtp_plan_step they hold the last iteration's candidates and results. */
+ * mtp_plan_step they hold the last iteration's candidates and results.  A
+ * pipelined handle alternates between two candidate buffers, so U is the
+ * buffer of the latest iteration as of this call: query it again after each
+ * mtp_plan_step. */
 typedef struct mtp_buffers {
   float* U;        /* (B, H, n) */
   float* cost;     /* (B) */
@@ -206,7 +216,12 @@ mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U
 /* `iters` full planner iterations (Alg. 2 loop body) from start state d_x0
  * (d) using and advancing the handle's iteration counter; writes the last
  * iteration's u* to d_ustar (n).  Replays a captured CUDA graph unless
- * MTP_FLAG_NO_GRAPH is set. */
+ * MTP_FLAG_NO_GRAPH is set.  On a pipelined handle (mtp_sizes.pipelined)
+ * each iteration also prepares the next iteration's graph rows and local
+ * draws on a second stream, on the SMs the rollout leaves idle, and the next
+ * iteration (in this call or the next, unless mtp_set_state or a batch run
+ * changed the iteration counter in between) only finishes its local rows and
+ * mean row.  The results are the same bits as without the pipeline. */
 mtp_status mtp_plan_step(mtp_handle* h, const float* d_x0, int32_t iters, float* d_ustar,
                          void* stream);
 
@@ -230,9 +245,14 @@ mtp_status mtp_set_state(mtp_handle* h, const double* h_mu, const double* h_sigm
  * captured graph unless MTP_FLAG_NO_GRAPH is set, and then waits for the
  * step so the events can be read.  mtp_stage_times returns the summed
  * milliseconds of the four stages and the number of iterations recorded
- * since the last read, then resets. */
+ * since the last read, then resets.  On a pipelined handle "generate" is the
+ * part on the critical path (finishing the local rows and the mean row, or
+ * the whole generation when the draws were not prepared); mtp_stage_times5
+ * adds, fifth, the time of the next iteration's preparation, which runs on a
+ * second stream during the rollout (0 when not pipelined). */
 mtp_status mtp_set_profiling(mtp_handle* h, int32_t enable);
 mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations);
+mtp_status mtp_stage_times5(mtp_handle* h, double* ms5, int32_t* iterations);
 
 /* Batched planning over many handles (uneven sizes, point masses and chains
  * mixed).  One iteration is one CUDA graph: the candidates of every instance

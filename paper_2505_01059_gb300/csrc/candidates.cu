@@ -18,6 +18,7 @@ namespace mtp {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kPrepThreads = 1024;
 
 // Eq. 6 with the end rules stated under it, 0-based knot a of M knots.
 // slope(j) is the slope of piece j (between knots j and j+1).
@@ -61,16 +62,18 @@ __device__ __forceinline__ void stage_box(const CandArgs& a, float* lo, float* h
 
 // Local rows (Alg. 2 local sampling) and the mean row: block `lb` of
 // `nlb` blocks given to them; mu + sigma * eps, four elements of a row per
-// generator call.
+// generator call.  MODE (LocalMode) selects whether the draws, the finished
+// samples from stored draws, or both in one pass are made.
+template <int MODE>
 __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int nlb) {
   __shared__ float box_lo[MTP_MAX_CTRL], box_hi[MTP_MAX_CTRL];
   stage_box(a, box_lo, box_hi);
   const Dims dm = a.dm;
-  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
+  const uint32_t iter = (a.d_iter ? *a.d_iter : a.iter) + a.iter_offset;
   const int n = dm.n;
   const int Hn = dm.H * n;
   const int G = (Hn + 3) >> 2;
-  const int items = a.local_rows * G + (a.U_mean ? G : 0);
+  const int items = a.local_rows * G + ((MODE != kLocalNoise && a.U_mean) ? G : 0);
   const int stride = nlb * blockDim.x;
   // whole 16-byte groups: one vector load of mu and sigma and one vector
   // store per generator call (rows of a 16-byte aligned tensor stay aligned)
@@ -86,12 +89,33 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
   for (; e < items; e += stride) {
     int i = i0;  // advanced in place over the group's four elements
     if (row < a.local_rows) {
-      const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
-      float eps[4];
-      box_muller(r.x, r.y, eps[0], eps[1]);
-      box_muller(r.z, r.w, eps[2], eps[3]);
       float* dst = a.U_local + (size_t)row * Hn;
-      if (vec) {
+      float eps[4];
+      if constexpr (MODE == kLocalFinish) {
+        if (vec) {
+          const float4 e4 = reinterpret_cast<const float4*>(dst)[q];
+          eps[0] = e4.x;
+          eps[1] = e4.y;
+          eps[2] = e4.z;
+          eps[3] = e4.w;
+        } else {
+#pragma unroll
+          for (int w = 0; w < 4; ++w) eps[w] = (4 * q + w < Hn) ? dst[4 * q + w] : 0.f;
+        }
+      } else {
+        const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
+        box_muller(r.x, r.y, eps[0], eps[1]);
+        box_muller(r.z, r.w, eps[2], eps[3]);
+      }
+      if constexpr (MODE == kLocalNoise) {
+        if (vec) {
+          reinterpret_cast<float4*>(dst)[q] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+        } else {
+#pragma unroll
+          for (int w = 0; w < 4; ++w)
+            if (4 * q + w < Hn) dst[4 * q + w] = eps[w];
+        }
+      } else if (vec) {
         const float4 s4 = __ldg(reinterpret_cast<const float4*>(a.sigma) + q);
         const float4 m4 = __ldg(reinterpret_cast<const float4*>(a.mu) + q);
         const float sv[4] = {s4.x, s4.y, s4.z, s4.w}, mv[4] = {m4.x, m4.y, m4.z, m4.w};
@@ -133,155 +157,171 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
   }
 }
 
+// Def. 1: Z[m][j][:] uniform over the box, four dimensions per call, written
+// by the whole block into Z (shared memory).
+__device__ __forceinline__ void regenerate_Z(const CandArgs& a, float* Z, uint32_t iter,
+                                             const float* box_lo, const float* box_hi) {
+  const int M = a.dm.M, N = a.dm.N, n = a.dm.n;
+  const int ng = (n + 3) >> 2;
+  for (int e = threadIdx.x; e < M * N * ng; e += blockDim.x) {
+    const int node = e / ng, g = e - node * ng;
+    const uint4 r = philox(make_uint4((uint32_t)node, (uint32_t)g, iter, kTagGraph), a.key);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int i = 4 * g + w;
+      if (i < n) Z[node * n + i] = fmaf(box_hi[i] - box_lo[i], unit24(pick(r, w)), box_lo[i]);
+    }
+  }
+}
+
+// Graph rows of graph block `bid` (Alg. 1 and the interpolation): its paths'
+// layer indices, their waypoints gathered from the graph Zs (shared or
+// global memory) into C (shared memory, followed by the Akima scratch), and
+// the interpolated, clamped rows.  Every path is computed on its own, so the
+// grouping of paths into blocks does not change any value.
+__device__ __forceinline__ void graph_paths_body(const CandArgs& a, const float* Zs, float* C,
+                                                 int bid, uint32_t iter, const float* box_lo,
+                                                 const float* box_hi) {
+  const Dims dm = a.dm;
+  const int H = dm.H, n = dm.n, M = dm.M, N = dm.N;
+  const int Hn = H * n;
+  const int SPB = a.paths_per_block;
+  const int b0 = bid * SPB;
+  const int nb = min(SPB, a.graph_rows - b0);
+  float* coef = C + SPB * M * n;
+  if (a.C_in == nullptr) {
+    // Alg. 1: layer indices with replacement, then C = Z[m][I[b][m]][:].
+    const int mg = (M + 3) >> 2;
+    for (int e = threadIdx.x; e < nb * mg; e += blockDim.x) {
+      const int s = e / mg, g = e - s * mg;
+      const uint4 r = philox(make_uint4((uint32_t)(b0 + s), (uint32_t)g, iter, kTagPath), a.key);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int m = 4 * g + w;
+        if (m < M) {
+          const int j = index_of(pick(r, w), (uint32_t)N);
+          const float* src = Zs + (m * N + j) * n;
+          float* dst = C + (s * M + m) * n;
+          for (int i = 0; i < n; ++i) dst[i] = src[i];
+        }
+      }
+    }
+  } else {
+    const float* src = a.C_in + (size_t)b0 * M * n;
+    for (int e = threadIdx.x; e < nb * M * n; e += blockDim.x) C[e] = src[e];
+  }
+  __syncthreads();
+  if (a.bf16 && a.interp == MTP_INTERP_BSPLINE) {
+    // BF16 operands: each knot rounded to the nearest bfloat16 (ties to
+    // even); its products with the BF16 basis are exact in FP32
+    for (int e = threadIdx.x; e < nb * M * n; e += blockDim.x)
+      C[e] = __bfloat162float(__float2bfloat16_rn(C[e]));
+    __syncthreads();
+  }
+
+  if (a.interp == MTP_INTERP_AKIMA) {
+    // Eqs. 6-7 in three parallel passes over (path, dimension, knot):
+    // piece slopes m, knot slopes s, then piece coefficients (a, b, c, d).
+    const float inv_h = a.inv_h;
+    const int K1 = M - 1;
+    float* mslope = coef + (size_t)SPB * n * K1 * 4;  // (nb, n, M-1)
+    float* kslope = mslope + (size_t)SPB * n * K1;    // (nb, n, M)
+    for (int e = threadIdx.x; e < nb * n * K1; e += blockDim.x) {
+      const int si = e / K1, k = e - si * K1;
+      const int sp = si / n, i = si - sp * n;
+      const float* z = C + sp * M * n + i;
+      mslope[e] = (z[(k + 1) * n] - z[k * n]) * inv_h;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * n * M; e += blockDim.x) {
+      const int si = e / M, k = e - si * M;
+      const float* m = mslope + si * K1;
+      kslope[e] = akima_knot_slope(k, M, [&](int j) { return m[j]; });
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * n * K1; e += blockDim.x) {
+      const int si = e / K1, k = e - si * K1;
+      const int sp = si / n, i = si - sp * n;
+      const float mk = mslope[e];
+      const float s_left = kslope[si * M + k], s_right = kslope[si * M + k + 1];
+      float* cf = coef + (size_t)e * 4;
+      cf[0] = C[(sp * M + k) * n + i];
+      cf[1] = s_left;
+      cf[2] = (3.f * mk - 2.f * s_left - s_right) * inv_h;
+      cf[3] = (s_left + s_right - 2.f * mk) * (inv_h * inv_h);
+    }
+    __syncthreads();
+  }
+
+  // Interpolate and store rows b0 .. b0+nb-1 (coalesced over (t, i)); the
+  // (path, t, i) position of each thread advances by a fixed stride, so it
+  // is carried along instead of divided out.
+  float* out = a.U_graph + (size_t)b0 * Hn;
+  const int total = nb * Hn;
+  int e = threadIdx.x;
+  int sp = e / Hn, rem = e - sp * Hn;
+  int t = rem / n, i = rem - t * n;
+  const int ds = blockDim.x / Hn, drem = blockDim.x - ds * Hn;
+  const int dt = drem / n, di = drem - dt * n;
+  for (; e < total; e += blockDim.x) {
+    float u;
+    if (a.interp == MTP_INTERP_BSPLINE) {
+      // Def. 2: sum over the (p+1)-wide non-zero window of basis row t.
+      const int f = a.bfirst[t];
+      const float* brow = a.basis + (size_t)t * M;
+      const float* zc = C + sp * M * n + i;
+      u = 0.f;
+      for (int q = 0; q <= a.degree; ++q) {
+        const int m = f + q;
+        if (m < M) u = fmaf(brow[m], zc[m * n], u);
+      }
+    } else if (a.interp == MTP_INTERP_AKIMA) {
+      const int k = a.seg[t];
+      const float dl = a.delta[t];
+      const float* cf = coef + ((size_t)(sp * n + i) * (M - 1) + k) * 4;
+      u = fmaf(fmaf(fmaf(cf[3], dl, cf[2]), dl, cf[1]), dl, cf[0]);
+    } else {
+      const int k = a.seg[t];
+      const float w = fminf(a.delta[t] * a.inv_h, 1.f);
+      const float z0 = C[(sp * M + k) * n + i], z1 = C[(sp * M + k + 1) * n + i];
+      u = fmaf(w, z1 - z0, z0);
+    }
+    out[e] = clamp_box(u, box_lo[i], box_hi[i]);
+    // advance (sp, t, i) by blockDim.x elements
+    sp += ds;
+    t += dt;
+    i += di;
+    if (i >= n) {
+      i -= n;
+      ++t;
+    }
+    if (t >= H) {
+      t -= H;
+      ++sp;
+    }
+  }
+}
+
 // One block of candidate generation for one planning problem: block `bid`
 // of `nblocks` blocks that instance is given (graph blocks first).
 __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, int bid,
                                                 int nblocks) {
-  const Dims dm = a.dm;
-  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
-  const int H = dm.H, n = dm.n, M = dm.M, N = dm.N;
-  const int Hn = H * n;
-
   if (bid < a.graph_blocks) {
     __shared__ float box_lo[MTP_MAX_CTRL], box_hi[MTP_MAX_CTRL];
     stage_box(a, box_lo, box_hi);
-    const int SPB = a.paths_per_block;
-    const int b0 = bid * SPB;
-    const int nb = min(SPB, a.graph_rows - b0);
+    const uint32_t iter = (a.d_iter ? *a.d_iter : a.iter) + a.iter_offset;
     float* Z = smem;
-    float* C = Z + ((a.C_in || a.Z_global) ? 0 : M * N * n);
-    float* coef = C + SPB * M * n;
-    if (a.C_in == nullptr) {
-      const float* Zs = a.Z_global;
-      if (Zs == nullptr) {
-        // Def. 1: Z[m][j][:] uniform over the box, four dimensions per call.
-        const int ng = (n + 3) >> 2;
-        for (int e = threadIdx.x; e < M * N * ng; e += blockDim.x) {
-          const int node = e / ng, g = e - node * ng;
-          const uint4 r = philox(make_uint4((uint32_t)node, (uint32_t)g, iter, kTagGraph), a.key);
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const int i = 4 * g + w;
-            if (i < n) Z[node * n + i] = fmaf(box_hi[i] - box_lo[i], unit24(pick(r, w)), box_lo[i]);
-          }
-        }
-        __syncthreads();
-        Zs = Z;
-      }
-      // Alg. 1: layer indices with replacement, then C = Z[m][I[b][m]][:].
-      const int mg = (M + 3) >> 2;
-      for (int e = threadIdx.x; e < nb * mg; e += blockDim.x) {
-        const int s = e / mg, g = e - s * mg;
-        const uint4 r = philox(make_uint4((uint32_t)(b0 + s), (uint32_t)g, iter, kTagPath), a.key);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int m = 4 * g + w;
-          if (m < M) {
-            const int j = index_of(pick(r, w), (uint32_t)N);
-            const float* src = Zs + (m * N + j) * n;
-            float* dst = C + (s * M + m) * n;
-            for (int i = 0; i < n; ++i) dst[i] = src[i];
-          }
-        }
-      }
-    } else {
-      const float* src = a.C_in + (size_t)b0 * M * n;
-      for (int e = threadIdx.x; e < nb * M * n; e += blockDim.x) C[e] = src[e];
-    }
-    __syncthreads();
-    if (a.bf16 && a.interp == MTP_INTERP_BSPLINE) {
-      // BF16 operands: each knot rounded to the nearest bfloat16 (ties to
-      // even); its products with the BF16 basis are exact in FP32
-      for (int e = threadIdx.x; e < nb * M * n; e += blockDim.x)
-        C[e] = __bfloat162float(__float2bfloat16_rn(C[e]));
+    float* C = Z + ((a.C_in || a.Z_global) ? 0 : a.dm.M * a.dm.N * a.dm.n);
+    const float* Zs = a.Z_global;
+    if (a.C_in == nullptr && Zs == nullptr) {
+      regenerate_Z(a, Z, iter, box_lo, box_hi);
       __syncthreads();
+      Zs = Z;
     }
-
-    if (a.interp == MTP_INTERP_AKIMA) {
-      // Eqs. 6-7 in three parallel passes over (path, dimension, knot):
-      // piece slopes m, knot slopes s, then piece coefficients (a, b, c, d).
-      const float inv_h = a.inv_h;
-      const int K1 = M - 1;
-      float* mslope = coef + (size_t)SPB * n * K1 * 4;  // (nb, n, M-1)
-      float* kslope = mslope + (size_t)SPB * n * K1;    // (nb, n, M)
-      for (int e = threadIdx.x; e < nb * n * K1; e += blockDim.x) {
-        const int si = e / K1, k = e - si * K1;
-        const int sp = si / n, i = si - sp * n;
-        const float* z = C + sp * M * n + i;
-        mslope[e] = (z[(k + 1) * n] - z[k * n]) * inv_h;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < nb * n * M; e += blockDim.x) {
-        const int si = e / M, k = e - si * M;
-        const float* m = mslope + si * K1;
-        kslope[e] = akima_knot_slope(k, M, [&](int j) { return m[j]; });
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < nb * n * K1; e += blockDim.x) {
-        const int si = e / K1, k = e - si * K1;
-        const int sp = si / n, i = si - sp * n;
-        const float mk = mslope[e];
-        const float s_left = kslope[si * M + k], s_right = kslope[si * M + k + 1];
-        float* cf = coef + (size_t)e * 4;
-        cf[0] = C[(sp * M + k) * n + i];
-        cf[1] = s_left;
-        cf[2] = (3.f * mk - 2.f * s_left - s_right) * inv_h;
-        cf[3] = (s_left + s_right - 2.f * mk) * (inv_h * inv_h);
-      }
-      __syncthreads();
-    }
-
-    // Interpolate and store rows b0 .. b0+nb-1 (coalesced over (t, i)); the
-    // (path, t, i) position of each thread advances by a fixed stride, so it
-    // is carried along instead of divided out.
-    float* out = a.U_graph + (size_t)b0 * Hn;
-    const int total = nb * Hn;
-    int e = threadIdx.x;
-    int sp = e / Hn, rem = e - sp * Hn;
-    int t = rem / n, i = rem - t * n;
-    const int ds = blockDim.x / Hn, drem = blockDim.x - ds * Hn;
-    const int dt = drem / n, di = drem - dt * n;
-    for (; e < total; e += blockDim.x) {
-      float u;
-      if (a.interp == MTP_INTERP_BSPLINE) {
-        // Def. 2: sum over the (p+1)-wide non-zero window of basis row t.
-        const int f = a.bfirst[t];
-        const float* brow = a.basis + (size_t)t * M;
-        const float* zc = C + sp * M * n + i;
-        u = 0.f;
-        for (int q = 0; q <= a.degree; ++q) {
-          const int m = f + q;
-          if (m < M) u = fmaf(brow[m], zc[m * n], u);
-        }
-      } else if (a.interp == MTP_INTERP_AKIMA) {
-        const int k = a.seg[t];
-        const float dl = a.delta[t];
-        const float* cf = coef + ((size_t)(sp * n + i) * (M - 1) + k) * 4;
-        u = fmaf(fmaf(fmaf(cf[3], dl, cf[2]), dl, cf[1]), dl, cf[0]);
-      } else {
-        const int k = a.seg[t];
-        const float w = fminf(a.delta[t] * a.inv_h, 1.f);
-        const float z0 = C[(sp * M + k) * n + i], z1 = C[(sp * M + k + 1) * n + i];
-        u = fmaf(w, z1 - z0, z0);
-      }
-      out[e] = clamp_box(u, box_lo[i], box_hi[i]);
-      // advance (sp, t, i) by blockDim.x elements
-      sp += ds;
-      t += dt;
-      i += di;
-      if (i >= n) {
-        i -= n;
-        ++t;
-      }
-      if (t >= H) {
-        t -= H;
-        ++sp;
-      }
-    }
+    graph_paths_body(a, Zs, C, bid, iter, box_lo, box_hi);
     return;
   }
-
-  local_rows_body(a, bid - a.graph_blocks, nblocks - a.graph_blocks);
+  local_rows_body<kLocalFull>(a, bid - a.graph_blocks, nblocks - a.graph_blocks);
 }
 
 __global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
@@ -324,7 +364,7 @@ __global__ void __launch_bounds__(kThreads) k_local_batch(const CandArgs* __rest
     if (local_start[mid] <= blk) lo = mid;
     else hi = mid;
   }
-  local_rows_body(args[lo], blk - local_start[lo], local_start[lo + 1] - local_start[lo]);
+  local_rows_body<kLocalFull>(args[lo], blk - local_start[lo], local_start[lo + 1] - local_start[lo]);
 }
 
 // Def. 1: the graph Z of the current iteration written to global memory,
@@ -333,7 +373,7 @@ __device__ __forceinline__ void graph_Z_body(const CandArgs& a, float* Z, int bl
   __shared__ float box_lo[MTP_MAX_CTRL], box_hi[MTP_MAX_CTRL];
   stage_box(a, box_lo, box_hi);
   const int M = a.dm.M, N = a.dm.N, n = a.dm.n;
-  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
+  const uint32_t iter = (a.d_iter ? *a.d_iter : a.iter) + a.iter_offset;
   const int ng = (n + 3) >> 2;
   for (int e = blk * blockDim.x + threadIdx.x; e < M * N * ng; e += nblk * blockDim.x) {
     const int node = e / ng, g = e - node * ng;
@@ -367,6 +407,54 @@ __global__ void __launch_bounds__(kThreads) k_graph_Z_batch(const CandArgs* __re
     else hi = mid;
   }
   graph_Z_body(args[lo], Zs[lo], blk - block_start[lo], block_start[lo + 1] - block_start[lo]);
+}
+
+// The next iteration's candidates, made while the current iteration's
+// rollout runs: `gridDim.x` persistent blocks, each on an SM of its own (the
+// launch asks for the whole of an SM's shared memory, so no block of another
+// kernel can share the SM and slow that kernel's warps).  Each block makes
+// the graph Z of iteration d_iter + iter_offset once in shared memory, then
+// the graph rows of graph blocks blockIdx.x, blockIdx.x + gridDim.x, ...,
+// then its grid-stride share of the local rows' standard normal draws.  The
+// mean and spread are not read: the finishing pass applies them once they
+// are known.
+__global__ void __launch_bounds__(kPrepThreads, 1) k_prepare(const CandArgs a) {
+  extern __shared__ float smem[];
+  if (a.graph_blocks > 0) {
+    __shared__ float box_lo[MTP_MAX_CTRL], box_hi[MTP_MAX_CTRL];
+    stage_box(a, box_lo, box_hi);
+    const uint32_t iter = (a.d_iter ? *a.d_iter : a.iter) + a.iter_offset;
+    float* Z = smem;
+    regenerate_Z(a, Z, iter, box_lo, box_hi);
+    float* C = Z + a.dm.M * a.dm.N * a.dm.n;
+    for (int vb = blockIdx.x; vb < a.graph_blocks; vb += gridDim.x) {
+      __syncthreads();  // Z complete; the previous paths' scratch no longer read
+      graph_paths_body(a, Z, C, vb, iter, box_lo, box_hi);
+    }
+  }
+  if (a.U_local && a.local_rows > 0) local_rows_body<kLocalNoise>(a, blockIdx.x, gridDim.x);
+}
+
+// Asks the L2 to fetch [p, p + bytes) from device memory; no data comes back
+// to the SM.  p and bytes are multiples of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Local rows from their stored draws, clamp(mu + sigma * eps), and the mean
+// row.  The graph rows, made during the previous iteration and possibly
+// evicted from L2 since, are prefetched back into L2 for the rollout that
+// follows (16 KB per request, the 16-byte aligned interior of the rows).
+__global__ void __launch_bounds__(kThreads) k_finish(const CandArgs a) {
+  if (threadIdx.x == 0 && a.U_graph && a.graph_rows > 0) {
+    const uintptr_t b = reinterpret_cast<uintptr_t>(a.U_graph);
+    const uintptr_t lo = (b + 15) & ~uintptr_t(15);
+    const uintptr_t hi = (b + (size_t)a.graph_rows * a.dm.H * a.dm.n * sizeof(float)) & ~uintptr_t(15);
+    constexpr uintptr_t kChunk = 16384;
+    for (uintptr_t p = lo + (uintptr_t)blockIdx.x * kChunk; p < hi; p += (uintptr_t)gridDim.x * kChunk)
+      prefetch_l2_bulk(reinterpret_cast<const void*>(p), (uint32_t)(hi - p < kChunk ? hi - p : kChunk));
+  }
+  local_rows_body<kLocalFinish>(a, blockIdx.x, gridDim.x);
 }
 
 // Def. 1 / Alg. 1 outputs for inspection: Z, I and C written to global memory.
@@ -440,6 +528,47 @@ cudaError_t launch_graph_Z(const CandArgs& a, float* Z, cudaStream_t s) {
   if (blocks > 152) blocks = 152;
   if (blocks <= 0) return cudaSuccess;
   k_graph_Z<<<blocks, kThreads, 0, s>>>(a, Z);
+  return cudaGetLastError();
+}
+
+size_t prepare_smem_need(const CandArgs& a) {
+  const Dims& d = a.dm;
+  size_t f = 0;
+  if (a.graph_blocks > 0) {
+    f += (size_t)d.M * d.N * d.n + (size_t)a.paths_per_block * d.M * d.n;
+    if (a.interp == MTP_INTERP_AKIMA)
+      f += (size_t)a.paths_per_block * d.n * ((d.M - 1) * 5 + d.M);
+  }
+  return f * sizeof(float);
+}
+
+// The dynamic shared memory that makes one k_prepare block fill an SM: the
+// per-block opt-in limit less the kernel's static shared memory.
+cudaError_t init_prepare_attributes(size_t* dyn_smem) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return e;
+  cudaFuncAttributes fa{};
+  if ((e = cudaFuncGetAttributes(&fa, k_prepare)) != cudaSuccess) return e;
+  const size_t dyn = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  if ((e = cudaFuncSetAttribute(k_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) !=
+      cudaSuccess)
+    return e;
+  *dyn_smem = dyn;
+  return cudaSuccess;
+}
+
+cudaError_t launch_prepare(const CandArgs& a, int grid, size_t dyn_smem, cudaStream_t s) {
+  if (grid <= 0) return cudaSuccess;
+  k_prepare<<<grid, kPrepThreads, dyn_smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const CandArgs& a, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  k_finish<<<blocks, kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,23 @@ struct mtp_handle {
   uint32_t* iter_dev = nullptr;
   uint32_t iter_host = 0;
   // scratch of one iteration
-  float* U = nullptr;
+  float* U = nullptr;  // candidates of the latest iteration: Ubuf[cur]
+  // Pipelined generation.  Everything costly in an iteration's candidates
+  // (the graph rows and the local rows' standard normal draws) depends only
+  // on the key and the iteration number, not on the mean and spread.  When
+  // the rollout leaves SMs idle, a single-instance iteration therefore
+  // makes the next iteration's graph rows and draws on those SMs while its
+  // rollout runs (on `side`), into the other candidate buffer; the next
+  // iteration then only finishes its local rows and mean row.
+  bool pipeline = false;
+  float* Ubuf[2] = {nullptr, nullptr};
+  int cur = 0;                // Ubuf[cur] holds the latest iteration's candidates
+  bool prep_valid = false;    // Ubuf[cur ^ 1] holds the draws and graph rows of prep_iter
+  uint32_t prep_iter = 0;
+  int prep_grid = 0;          // SMs the rollout leaves free
+  size_t prep_smem = 0;       // dynamic shared memory of a k_prepare block (a whole SM)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   float* cost = nullptr;
   int32_t* elite = nullptr;
   double* weight = nullptr;
@@ -67,14 +83,14 @@ struct mtp_handle {
   float* Z = nullptr;  // (M, N, n) graph of the current iteration (batched planning)
   // replay
   cudaStream_t cap_stream = nullptr;
-  std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, cudaGraphExec_t> graphs;  // key: graph_key(iterations, cur, first prepared)
   // profiling
   bool profiling = false;
-  std::vector<cudaEvent_t> events;  // eager launches: 5 per iteration, read by mtp_stage_times
+  std::vector<cudaEvent_t> events;  // eager launches: kEvPerIter per iteration, read by mtp_stage_times
   size_t ev_used = 0;
-  std::vector<cudaEvent_t> gevents;            // inside profiled graphs: 5 per iteration of a chunk
+  std::vector<cudaEvent_t> gevents;            // inside profiled graphs: kEvPerIter per iteration
   std::map<int, cudaGraphExec_t> pgraphs;      // graphs with the stage events captured
-  double stage_acc[4] = {0, 0, 0, 0};          // read from gevents after each profiled replay
+  double stage_acc[5] = {0, 0, 0, 0, 0};       // read from gevents after each profiled replay
   int64_t stage_iters = 0;
   std::string err;
 };
@@ -381,32 +397,167 @@ inline void stage_event(cudaEvent_t ev, cudaStream_t s, bool captured) {
   else cudaEventRecord(ev, s);
 }
 
-// One Alg. 2 iteration on the handle's own buffers, iteration from iter_dev.
-cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, cudaEvent_t* ev, bool captured = false) {
-  cudaError_t e;
+// Stage events per iteration: generate, rollout, select, update on the
+// launch stream (five marks), and the overlapped preparation on the side
+// stream (two marks).
+constexpr int kEvPerIter = 7;
+
+// The candidate-generation arguments of the handle's own iteration, writing
+// the (B, H, n) tensor U.
+CandArgs own_cand_args(const mtp_handle* h, float* U) {
   const Dims& dm = h->dm;
   const size_t Hn = (size_t)dm.H * dm.n;
-  if (ev) stage_event(ev[0], s, captured);
   CandArgs c = cand_args(h, 0, h->iter_dev);
-  c.U_graph = h->U + Hn * dm.L;
+  c.U_graph = U + Hn * dm.L;
   c.graph_rows = dm.P;
   c.graph_blocks = (dm.P + h->paths_per_block - 1) / h->paths_per_block;
-  c.U_local = h->U;
+  c.U_local = U;
   c.local_rows = dm.L;
-  c.U_mean = h->U + Hn * (dm.B - 1);
-  if ((e = launch_generate(h, c, s)) != cudaSuccess) return e;
+  c.U_mean = U + Hn * (dm.B - 1);
+  return c;
+}
+
+// How an iteration gets its candidates.
+enum class Gen { kFull, kFinish };
+
+// One Alg. 2 iteration on the handle's own buffers, iteration from iter_dev,
+// candidates in Ubuf[work].  kFinish: Ubuf[work] already holds this
+// iteration's graph rows and local draws.  With the pipeline on, the next
+// iteration's graph rows and draws are made into Ubuf[work ^ 1] on the side
+// stream while this iteration's rollout runs; the update, which advances
+// iter_dev, waits for them.
+cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, int work, Gen gen, cudaEvent_t* ev,
+                              bool captured = false) {
+  cudaError_t e;
+  const Dims& dm = h->dm;
+  float* U = h->Ubuf[work];
+  if (ev) stage_event(ev[0], s, captured);
+  CandArgs c = own_cand_args(h, U);
+  if (gen == Gen::kFinish) {
+    c.local_mode = kLocalFinish;
+    e = launch_finish(c, local_blocks_for(h, (long long)dm.L + 1), s);
+  } else {
+    e = launch_generate(h, c, s);
+  }
+  if (e != cudaSuccess) return e;
   if (ev) stage_event(ev[1], s, captured);
-  RolloutArgs r = rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, dm.B, h->cost);
+  if (h->pipeline) {
+    if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+    if (ev) stage_event(ev[5], h->side, captured);
+    CandArgs nx = own_cand_args(h, h->Ubuf[work ^ 1]);
+    nx.iter_offset = 1;
+    nx.local_mode = kLocalNoise;
+    nx.U_mean = nullptr;
+    if ((e = launch_prepare(nx, h->prep_grid, h->prep_smem, h->side)) != cudaSuccess) return e;
+    if (ev) stage_event(ev[6], h->side, captured);
+    if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
+  }
+  RolloutArgs r = rollout_args(h, 0, h->iter_dev, h->x0, U, 0, dm.B, h->cost);
   if ((e = launch_rollout(h, r, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[2], s, captured);
-  SelectArgs sa{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
+  SelectArgs sa{h->cost, U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
                 h->elite, h->weight, h->ustar, nullptr, nullptr};
   if ((e = launch_select(sa, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[3], s, captured);
-  UpdateArgs ua{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
+  if (h->pipeline && (e = cudaStreamWaitEvent(s, h->ev_join, 0)) != cudaSuccess) return e;
+  UpdateArgs ua{U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
                 h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
   if ((e = launch_update(ua, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[4], s, captured);
+  return cudaSuccess;
+}
+
+// Host bookkeeping of one enqueued iteration: which buffer it used, whether
+// its successor's draws are prepared.
+void after_iteration(mtp_handle* h, int work) {
+  h->cur = work;
+  h->U = h->Ubuf[work];
+  if (h->pipeline) {
+    h->prep_valid = true;
+    h->prep_iter = h->iter_host + 1;
+  }
+  h->iter_host += 1;
+}
+
+// Sizes of a problem: P graph rows (floor(beta B), at most B - 1), L local
+// rows, and the mean row.
+Dims dims_of(const mtp_problem& p) {
+  Dims dm{};
+  dm.B = p.B;
+  dm.P = num_graph_samples(p.beta, p.B);
+  dm.L = p.B - dm.P - 1;
+  dm.E = p.E;
+  dm.H = p.horizon;
+  dm.n = p.ctrl_dim;
+  dm.d = p.state_dim;
+  dm.M = p.M;
+  dm.N = p.N;
+  return dm;
+}
+
+// A graph larger than 16 KB is written once per iteration rather than
+// regenerated in every graph block's shared memory.
+bool global_graph(const Dims& dm) { return (long long)dm.M * dm.N * dm.n > 4096; }
+
+// Graph paths per block: ~4K output elements per block, and at least 8
+// paths for Akima so its per-(path, dimension) coefficient pass is wide;
+// shrunk until the block's shared memory fits.
+int paths_per_block_for(const Dims& dm, int32_t interp, bool global_Z) {
+  const long long Hn = (long long)dm.H * dm.n;
+  int spb = (int)((4096 + Hn - 1) / Hn);
+  if (interp == MTP_INTERP_AKIMA && spb < 8) spb = 8;
+  if (spb < 1) spb = 1;
+  if (spb > 32) spb = 32;
+  for (;;) {
+    CandArgs probe{};
+    probe.dm = dm;
+    probe.interp = interp;
+    probe.graph_blocks = 1;
+    probe.paths_per_block = spb;
+    probe.Z_global = global_Z ? reinterpret_cast<float*>(16) : nullptr;  // only tested for null
+    if (candidates_smem_bytes(probe) <= kMaxSmem || spb == 1) break;
+    spb /= 2;
+  }
+  return spb;
+}
+
+// Fewest SMs the rollout must leave idle for the next iteration's
+// generation to run beside it.  Measured on the 7-link arm at B 4096 (128
+// rollout blocks): the 24 idle SMs prepare an iteration in 80 us, longer
+// than the rollout; giving the rollout 64-thread blocks to free 88 SMs
+// (28 us) still lost 1.5-4 us per plan step against no pipeline, because
+// the finishing pass reads the prepared draws back from DRAM when L2 was
+// flushed between steps.  The 2-D point mass at B 512 (136 idle SMs) gains
+// 4-7 us per step.
+constexpr int kMinPrepareSMs = 64;
+
+// Whether a single-instance plan step pipelines its generation (see
+// mtp_handle::pipeline), on how many SMs, with how much shared memory per
+// block.  The point-mass and chain rollouts take one block per 32-128
+// candidates; the legged rollout fills the GPU and is not pipelined.
+cudaError_t pipeline_plan(const mtp_problem& p, const Dims& dm, int paths_per_block, bool* on,
+                          int* grid, size_t* smem) {
+  *on = false;
+  *grid = 0;
+  *smem = 0;
+  int dev = 0, sms = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = init_prepare_attributes(smem)) != cudaSuccess) return e;
+  if ((p.flags & MTP_FLAG_NO_PIPELINE) || p.dyn == MTP_DYN_LEGGED) return cudaSuccess;
+  if (dm.L <= 0 && dm.P <= 0) return cudaSuccess;
+  const int free_sms = sms - rollout_blocks(dm.B);
+  if (free_sms < kMinPrepareSMs) return cudaSuccess;
+  CandArgs probe{};
+  probe.dm = dm;
+  probe.interp = p.interp;
+  probe.graph_blocks = dm.P > 0 ? 1 : 0;
+  probe.paths_per_block = paths_per_block;
+  if (prepare_smem_need(probe) > *smem) return cudaSuccess;
+  *on = true;
+  *grid = free_sms;
   return cudaSuccess;
 }
 
@@ -416,9 +567,12 @@ void free_handle(mtp_handle* h) {
   for (cudaEvent_t e : h->gevents) cudaEventDestroy(e);
   for (auto& kv : h->pgraphs) cudaGraphExecDestroy(kv.second);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   void* ptrs[] = {h->basis, h->bfirst, h->seg, h->delta, h->mu, h->sigma, h->mu_f, h->sigma_f,
                   h->iter_dev,
-                  h->U, h->cost, h->elite, h->weight, h->ustar, h->x0, h->Z};
+                  h->Ubuf[0], h->Ubuf[1], h->cost, h->elite, h->weight, h->ustar, h->x0, h->Z};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -440,39 +594,11 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   const mtp_problem& p = h->pr;
   cudaGetDevice(&h->device);
   Dims& dm = h->dm;
-  dm.B = p.B;
-  dm.P = num_graph_samples(p.beta, p.B);
-  dm.L = p.B - dm.P - 1;
-  dm.E = p.E;
-  dm.H = p.horizon;
-  dm.n = p.ctrl_dim;
-  dm.d = p.state_dim;
-  dm.M = p.M;
-  dm.N = p.N;
+  dm = dims_of(p);
   h->key.k0 = (uint32_t)(p.seed & 0xffffffffu);
   h->key.k1 = (uint32_t)(p.seed >> 32);
-  // graph paths per block: ~4K output elements per block, and at least 8
-  // paths for Akima so its per-(path, dimension) coefficient pass is wide;
-  // shrunk until the block's shared memory fits
-  const long long Hn = (long long)dm.H * dm.n;
-  // a graph larger than 16 KB is written once per iteration rather than
-  // regenerated in every graph block's shared memory
-  h->global_Z = (long long)dm.M * dm.N * dm.n > 4096;
-  int spb = (int)((4096 + Hn - 1) / Hn);
-  if (p.interp == MTP_INTERP_AKIMA && spb < 8) spb = 8;
-  if (spb < 1) spb = 1;
-  if (spb > 32) spb = 32;
-  for (;;) {
-    CandArgs probe{};
-    probe.dm = dm;
-    probe.interp = p.interp;
-    probe.graph_blocks = 1;
-    probe.paths_per_block = spb;
-    probe.Z_global = h->global_Z ? reinterpret_cast<float*>(16) : nullptr;  // only tested for null
-    if (candidates_smem_bytes(probe) <= kMaxSmem || spb == 1) break;
-    spb /= 2;
-  }
-  h->paths_per_block = spb;
+  h->global_Z = global_graph(dm);
+  h->paths_per_block = paths_per_block_for(dm, p.interp, h->global_Z);
   auto err = [&](mtp_status s) {
     g_create_error = h->err;
     free_handle(h);
@@ -481,11 +607,15 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   cudaError_t e;
   if ((e = init_candidate_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
   if ((e = init_select_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
+  if ((e = pipeline_plan(p, dm, h->paths_per_block, &h->pipeline, &h->prep_grid, &h->prep_smem)) !=
+      cudaSuccess)
+    return err(cuda_fail(h, e, "attributes"));
   if ((st = build_tables(h)) != MTP_OK) return err(st);
   const size_t rowsz = (size_t)dm.H * dm.n;
   if ((e = dalloc(&h->mu, rowsz)) || (e = dalloc(&h->sigma, rowsz)) ||
       (e = dalloc(&h->mu_f, rowsz)) || (e = dalloc(&h->sigma_f, rowsz)) ||
-      (e = dalloc(&h->iter_dev, 1)) || (e = dalloc(&h->U, rowsz * dm.B)) ||
+      (e = dalloc(&h->iter_dev, 1)) || (e = dalloc(&h->Ubuf[0], rowsz * dm.B)) ||
+      (h->pipeline && (e = dalloc(&h->Ubuf[1], rowsz * dm.B))) ||
       (e = dalloc(&h->cost, dm.B)) || (e = dalloc(&h->elite, dm.E)) ||
       (e = dalloc(&h->weight, dm.E)) || (e = dalloc(&h->ustar, dm.n)) ||
       (e = dalloc(&h->x0, dm.d)) || (e = dalloc(&h->Z, (size_t)dm.M * dm.N * dm.n)))
@@ -500,8 +630,14 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
       (e = cudaMemcpy(h->iter_dev, &zero, 4, cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(h->ustar, 0, dm.n * 4)))
     return err(cuda_fail(h, e, "cudaMemcpy"));
+  h->U = h->Ubuf[0];
   if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return err(cuda_fail(h, e, "cudaStreamCreate"));
+  if (h->pipeline &&
+      ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess))
+    return err(cuda_fail(h, e, "pipeline stream"));
   *out = h;
   return MTP_OK;
 }
@@ -519,6 +655,14 @@ mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes)
            + r((uint64_t)p.E * 4) + r((uint64_t)p.E * 8)                      // elites, weights
            + r((uint64_t)p.ctrl_dim * 4) + r((uint64_t)p.state_dim * 4)
            + r((uint64_t)p.M * p.N * p.ctrl_dim * 4);                         // graph Z
+  const Dims dm = dims_of(p);
+  bool on = false;
+  int grid = 0;
+  size_t smem = 0;
+  cudaError_t e = pipeline_plan(p, dm, paths_per_block_for(dm, p.interp, global_graph(dm)), &on, &grid,
+                                &smem);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
+  if (on) *bytes += r(rowsz * p.B * 4);  // the second candidate buffer of the pipelined plan step
   return MTP_OK;
 }
 
@@ -537,8 +681,10 @@ const char* mtp_last_error(const mtp_handle* h) {
 mtp_status mtp_get_sizes(const mtp_handle* h, mtp_sizes* out) {
   if (!h || !out) return MTP_ERR_INVALID_ARG;
   const Dims& d = h->dm;
-  // candidates (+ graph when written once), rollout, select, update
-  *out = mtp_sizes{d.B, d.P, d.L, d.E, d.H, d.n, d.d, d.M, d.N, h->global_Z && d.P > 0 ? 5 : 4};
+  // candidates (+ graph when written once), rollout, select, update; when
+  // pipelined: finish, prepare (graph in its shared memory), rollout, select, update
+  const int kpi = h->pipeline ? 5 : (h->global_Z && d.P > 0 ? 5 : 4);
+  *out = mtp_sizes{d.B, d.P, d.L, d.E, d.H, d.n, d.d, d.M, d.N, kpi, h->pipeline ? 1 : 0};
   return MTP_OK;
 }
 
@@ -644,6 +790,35 @@ mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U
   return MTP_OK;
 }
 
+// Candidate buffer and generation route of iteration j of a run of
+// iterations that starts from the handle's current state.
+static void iteration_plan(const mtp_handle* h, int c0, bool first_prepared, int j, int* work, Gen* gen) {
+  if (!h->pipeline) {
+    *work = 0;
+    *gen = Gen::kFull;
+    return;
+  }
+  *work = c0 ^ ((j + 1) & 1);
+  *gen = (j > 0 || first_prepared) ? Gen::kFinish : Gen::kFull;
+}
+
+static mtp_status read_stage_events(mtp_handle* h, const cudaEvent_t* ev, double* acc) {
+  cudaError_t e;
+  for (int st = 0; st < 4; ++st) {
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, ev[st], ev[st + 1])) != cudaSuccess)
+      return cuda_fail(h, e, "cudaEventElapsedTime");
+    acc[st] += ms;
+  }
+  if (h->pipeline) {
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, ev[5], ev[6])) != cudaSuccess)
+      return cuda_fail(h, e, "cudaEventElapsedTime");
+    acc[4] += ms;
+  }
+  return MTP_OK;
+}
+
 static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
   cudaError_t e;
   const bool use_graph = !(h->pr.flags & MTP_FLAG_NO_GRAPH);
@@ -651,24 +826,31 @@ static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
     for (int k = 0; k < iters; ++k) {
       cudaEvent_t* ev = nullptr;
       if (h->profiling) {
-        while (h->events.size() < h->ev_used + 5) {
+        while (h->events.size() < h->ev_used + kEvPerIter) {
           cudaEvent_t x;
           if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
           h->events.push_back(x);
         }
         ev = h->events.data() + h->ev_used;
-        h->ev_used += 5;
+        h->ev_used += kEvPerIter;
       }
-      if ((e = enqueue_iteration(h, s, ev)) != cudaSuccess) return cuda_fail(h, e, "plan_step");
+      const bool prepared = h->pipeline && h->prep_valid && h->prep_iter == h->iter_host;
+      int work;
+      Gen gen;
+      iteration_plan(h, h->cur, prepared, 0, &work, &gen);
+      if ((e = enqueue_iteration(h, s, work, gen, ev)) != cudaSuccess) return cuda_fail(h, e, "plan_step");
+      after_iteration(h, work);
     }
     return MTP_OK;
   }
-  // one captured graph per distinct iteration count (at most 64 iterations
-  // each); with profiling on, a second set of graphs also records the stage
-  // events, and each replay is waited for and its stage times accumulated
+  // one captured graph per distinct (iteration count, starting buffer,
+  // whether the first iteration's draws are prepared), at most 64
+  // iterations each; with profiling on, a second set of graphs also records
+  // the stage events, and each replay is waited for and its stage times
+  // accumulated
   constexpr int kChunk = 64;
   if (h->profiling) {
-    while (h->gevents.size() < 5 * kChunk) {
+    while (h->gevents.size() < (size_t)kEvPerIter * kChunk) {
       cudaEvent_t x;
       if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
       h->gevents.push_back(x);
@@ -678,15 +860,22 @@ static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
   int left = iters;
   while (left > 0) {
     const int chunk = left > kChunk ? kChunk : left;
-    auto it = cache.find(chunk);
+    const int c0 = h->cur;
+    const bool prepared = h->pipeline && h->prep_valid && h->prep_iter == h->iter_host;
+    const int key = chunk * 4 + c0 * 2 + (prepared ? 1 : 0);
+    auto it = cache.find(key);
     if (it == cache.end()) {
       cudaGraph_t graph;
       if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(h, e, "cudaStreamBeginCapture");
       for (int k = 0; k < chunk; ++k) {
-        cudaEvent_t* ev = h->profiling ? h->gevents.data() + 5 * k : nullptr;
-        if ((e = enqueue_iteration(h, h->cap_stream, ev, true)) != cudaSuccess) {
+        cudaEvent_t* ev = h->profiling ? h->gevents.data() + kEvPerIter * k : nullptr;
+        int work;
+        Gen gen;
+        iteration_plan(h, c0, prepared, k, &work, &gen);
+        if ((e = enqueue_iteration(h, h->cap_stream, work, gen, ev, true)) != cudaSuccess) {
           cudaStreamEndCapture(h->cap_stream, &graph);
+          if (graph) cudaGraphDestroy(graph);
           return cuda_fail(h, e, "capture");
         }
       }
@@ -696,18 +885,21 @@ static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
       e = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-      it = cache.emplace(chunk, exec).first;
+      it = cache.emplace(key, exec).first;
     }
     if ((e = cudaGraphLaunch(it->second, s)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    for (int k = 0; k < chunk; ++k) {
+      int work;
+      Gen gen;
+      iteration_plan(h, c0, prepared, k, &work, &gen);
+      after_iteration(h, work);
+    }
     if (h->profiling) {
       if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "profiled replay");
-      for (int k = 0; k < chunk; ++k)
-        for (int st = 0; st < 4; ++st) {
-          float ms = 0.f;
-          if ((e = cudaEventElapsedTime(&ms, h->gevents[5 * k + st], h->gevents[5 * k + st + 1])) != cudaSuccess)
-            return cuda_fail(h, e, "cudaEventElapsedTime");
-          h->stage_acc[st] += ms;
-        }
+      for (int k = 0; k < chunk; ++k) {
+        mtp_status st = read_stage_events(h, h->gevents.data() + kEvPerIter * k, h->stage_acc);
+        if (st != MTP_OK) return st;
+      }
       h->stage_iters += chunk;
     }
     left -= chunk;
@@ -723,7 +915,6 @@ mtp_status mtp_plan_step(mtp_handle* h, const float* d_x0, int32_t iters, float*
   mtp_status st = plan_device(h, iters, s);
   if (st != MTP_OK) return st;
   MTP_CUDA(h, cudaMemcpyAsync(d_ustar, h->ustar, h->dm.n * 4, cudaMemcpyDeviceToDevice, s));
-  h->iter_host += (uint32_t)iters;
   return MTP_OK;
 }
 
@@ -737,7 +928,6 @@ mtp_status mtp_plan_step_host(mtp_handle* h, const float* h_x0, int32_t iters, f
   if (st != MTP_OK) return st;
   MTP_CUDA(h, cudaMemcpyAsync(h_ustar, h->ustar, h->dm.n * 4, cudaMemcpyDeviceToHost, s));
   MTP_CUDA(h, cudaStreamSynchronize(s));
-  h->iter_host += (uint32_t)iters;
   return MTP_OK;
 }
 
@@ -786,30 +976,40 @@ mtp_status mtp_set_profiling(mtp_handle* h, int32_t enable) {
   if (!h) return MTP_ERR_INVALID_ARG;
   h->profiling = enable != 0;
   h->ev_used = 0;
-  for (int i = 0; i < 4; ++i) h->stage_acc[i] = 0.0;
+  for (int i = 0; i < 5; ++i) h->stage_acc[i] = 0.0;
   h->stage_iters = 0;
+  return MTP_OK;
+}
+
+static mtp_status stage_times(mtp_handle* h, double* ms5, int32_t* iterations) {
+  DeviceGuard g(h->device);
+  for (int i = 0; i < 5; ++i) ms5[i] = h->stage_acc[i];
+  const int64_t g_it = h->stage_iters;
+  for (int i = 0; i < 5; ++i) h->stage_acc[i] = 0.0;
+  h->stage_iters = 0;
+  const size_t n_it = h->ev_used / kEvPerIter;
+  // the update's end mark follows the side stream's work (the update waits for it)
+  if (n_it > 0) MTP_CUDA(h, cudaEventSynchronize(h->events[h->ev_used - kEvPerIter + 4]));
+  for (size_t k = 0; k < n_it; ++k) {
+    mtp_status st = read_stage_events(h, h->events.data() + kEvPerIter * k, ms5);
+    if (st != MTP_OK) return st;
+  }
+  if (iterations) *iterations = (int32_t)(n_it + g_it);
+  h->ev_used = 0;
   return MTP_OK;
 }
 
 mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations) {
   if (!h || !ms4) return MTP_ERR_INVALID_ARG;
-  DeviceGuard g(h->device);
-  for (int i = 0; i < 4; ++i) ms4[i] = h->stage_acc[i];
-  const int64_t g_it = h->stage_iters;
-  for (int i = 0; i < 4; ++i) h->stage_acc[i] = 0.0;
-  h->stage_iters = 0;
-  const size_t n_it = h->ev_used / 5;
-  if (n_it > 0) MTP_CUDA(h, cudaEventSynchronize(h->events[h->ev_used - 1]));
-  for (size_t k = 0; k < n_it; ++k) {
-    for (int st = 0; st < 4; ++st) {
-      float ms = 0.f;
-      MTP_CUDA(h, cudaEventElapsedTime(&ms, h->events[5 * k + st], h->events[5 * k + st + 1]));
-      ms4[st] += ms;
-    }
-  }
-  if (iterations) *iterations = (int32_t)(n_it + g_it);
-  h->ev_used = 0;
-  return MTP_OK;
+  double ms5[5];
+  mtp_status st = stage_times(h, ms5, iterations);
+  for (int i = 0; i < 4; ++i) ms4[i] = ms5[i];
+  return st;
+}
+
+mtp_status mtp_stage_times5(mtp_handle* h, double* ms5, int32_t* iterations) {
+  if (!h || !ms5) return MTP_ERR_INVALID_ARG;
+  return stage_times(h, ms5, iterations);
 }
 
 }  // extern "C"
@@ -911,7 +1111,7 @@ struct mtp_batch {
   cudaEvent_t fork_ev = nullptr;
   cudaStream_t group_stream[kMaxGroups] = {};
   cudaEvent_t group_done[kMaxGroups] = {};
-  std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, cudaGraphExec_t> graphs;  // key: graph_key(iterations, cur, first prepared)
   int runs_since_fill = 0;
   std::string err;
 };
@@ -1014,6 +1214,10 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
   hv.d_cand_start[0] = hv.d_z_start[0] = hv.d_local_start[0] = hv.d_warp_start[0] = 0;
   for (int pos = 0; pos < count; ++pos) {
     mtp_handle* h = handles[order[pos]];
+    // a batch makes every iteration's candidates in full, in the first buffer
+    h->cur = 0;
+    h->U = h->Ubuf[0];
+    h->prep_valid = false;
     const Dims& dm = h->dm;
     const size_t Hn = (size_t)dm.H * dm.n;
     CandArgs c = cand_args(h, 0, h->iter_dev);
@@ -1172,7 +1376,12 @@ cudaError_t run_batch(mtp_batch* b, const float* d_x0, int iters, float* d_ustar
   }
   e = launch_gather(b->t.d_ustar_src, b->t.d_us_off, d_ustar, b->count, s);
   if (e != cudaSuccess) return e;
-  for (mtp_handle* h : b->hs) h->iter_host += (uint32_t)iters;
+  for (mtp_handle* h : b->hs) {
+    h->iter_host += (uint32_t)iters;
+    h->cur = 0;  // the tables point at the first buffer (set when they were filled)
+    h->U = h->Ubuf[0];
+    h->prep_valid = false;
+  }
   return cudaSuccess;
 }
 

@@ -96,12 +96,23 @@ struct Dims {
   int32_t B, P, L, E, H, n, d, M, N;
 };
 
+// What the local-row pass writes into rows [0, local_rows): the finished
+// samples clamp(mu + sigma * eps) (kLocalFull), the standard normal draws eps
+// alone (kLocalNoise, which depend only on the key and the iteration and so
+// can be made ahead of the iteration's mean and spread), or the finished
+// samples from draws already stored there (kLocalFinish).  The arithmetic of
+// a finished sample is the same single fused multiply-add and clamp in every
+// mode, so the three routes give the same bits.
+enum LocalMode : int32_t { kLocalFull = 0, kLocalNoise = 1, kLocalFinish = 2 };
+
 // Candidate generation (Def. 1, Alg. 1, interpolation, local sampling).
 struct CandArgs {
   Dims dm;
   Key key;
   uint32_t iter;
   const uint32_t* d_iter;  // when set, the iteration is read from here
+  uint32_t iter_offset;    // added to that iteration (1: the next iteration's draws)
+  int32_t local_mode;      // LocalMode
   int32_t interp;          // mtp_interp
   int32_t degree;          // B-spline degree p
   int32_t bf16;            // B-spline contraction with BF16 operands (the basis table is
@@ -217,6 +228,17 @@ size_t select_smem_bytes(int B, int E);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 // batched forms: one launch over many planning problems
 cudaError_t launch_graph_Z(const CandArgs& a, float* Z, cudaStream_t s);
+// Pipelined generation of the next iteration (graph rows and local draws of
+// iteration d_iter + iter_offset) by `grid` persistent blocks that each take
+// a whole SM's shared memory, so that they only run on SMs no other kernel
+// occupies; and the finishing pass of the local rows and the mean row.
+cudaError_t init_prepare_attributes(size_t* dyn_smem);
+size_t prepare_smem_need(const CandArgs& a);
+cudaError_t launch_prepare(const CandArgs& a, int grid, size_t dyn_smem, cudaStream_t s);
+cudaError_t launch_finish(const CandArgs& a, int blocks, cudaStream_t s);
+// Blocks of the standalone rollout launch for `rows` candidates (point mass
+// and chain; the legged rollout is not counted here).
+int rollout_blocks(int rows);
 cudaError_t launch_local_batch(const CandArgs* d_args, const int* d_local_start, int count,
                                int total_blocks, cudaStream_t s);
 cudaError_t launch_graph_Z_batch(const CandArgs* d_args, float* const* d_Z, const int* d_block_start,

@@ -489,4 +489,10 @@ cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int 
   return chain_dispatch<1>(a, m, links, s);
 }
 
+int rollout_blocks(int rows) {
+  if (rows <= 0) return 0;
+  const int bd = rollout_block(rows);
+  return (rows + bd - 1) / bd;
+}
+
 }  // namespace mtp

@@ -32,6 +32,7 @@ DR = {"none": 0, "per_sample": 1, "shared": 2}
 FLAG_NO_KAHAN = 0x1
 FLAG_NO_GRAPH = 0x2
 FLAG_BF16_BASIS = 0x4
+FLAG_NO_PIPELINE = 0x8
 
 # every function include/mtp.h declares
 EXPORTS = [
@@ -39,7 +40,7 @@ EXPORTS = [
     "mtp_get_buffers", "mtp_sample_tensor", "mtp_interpolate", "mtp_sample_local",
     "mtp_generate_candidates", "mtp_rollout_cost", "mtp_rollout_states", "mtp_elite_update",
     "mtp_plan_step", "mtp_plan_step_host", "mtp_shift", "mtp_get_state", "mtp_set_state",
-    "mtp_set_profiling", "mtp_stage_times", "mtp_elite_update_noalloc",
+    "mtp_set_profiling", "mtp_stage_times", "mtp_stage_times5", "mtp_elite_update_noalloc",
     "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_layout", "mtp_batch_plan_step",
     "mtp_batch_autotune", "mtp_batch_reserve", "mtp_batch_fill", "mtp_batch_shift",
     "mtp_problem_device_bytes", "mtp_server_create", "mtp_server_destroy", "mtp_server_register",
@@ -82,7 +83,7 @@ class MtpProblem(C.Structure):
 
 class MtpSizes(C.Structure):
     _fields_ = [(k, C.c_int32) for k in ("B", "P", "L", "E", "H", "n", "d", "M", "N",
-                                         "kernels_per_iteration")]
+                                         "kernels_per_iteration", "pipelined")]
 
 
 class MtpBuffers(C.Structure):
@@ -138,6 +139,7 @@ def load_library(path: str = LIB_PATH):
         "mtp_set_state": (i32, [vp, vp, vp, u32]),
         "mtp_set_profiling": (i32, [vp, i32]),
         "mtp_stage_times": (i32, [vp, vp, vp]),
+        "mtp_stage_times5": (i32, [vp, vp, vp]),
         "mtp_elite_update_noalloc": (i32, [vp, vp, i32, i32, i32, i32, C.c_double, C.c_double,
                                            C.c_double, i32, vp, vp, vp, vp, vp]),
         "mtp_batch_create": (i32, [C.POINTER(vp), i32, C.POINTER(vp)]),
@@ -443,6 +445,16 @@ def mtp_stage_times(h: Handle):
     ms = (C.c_double * 4)()
     n = C.c_int32()
     _check(load_library().mtp_stage_times(h.ptr, C.addressof(ms), C.addressof(n)), h.ptr)
+    return [float(v) for v in ms], int(n.value)
+
+
+def mtp_stage_times5(h: Handle):
+    """(ms per stage [generate, rollout, select, update, prepare], iterations);
+    "prepare" is the next iteration's generation that a pipelined handle runs
+    on a second stream during the rollout."""
+    ms = (C.c_double * 5)()
+    n = C.c_int32()
+    _check(load_library().mtp_stage_times5(h.ptr, C.addressof(ms), C.addressof(n)), h.ptr)
     return [float(v) for v in ms], int(n.value)
 
 

@@ -395,13 +395,13 @@ def test_plan_step_teacher_forced(mtp, spec, iters, min_checked):
     x0 = np.array(spec["x0"], np.float64)
     x0_t = _t(x0)
     ustar = torch.empty(s["n"], device=DEV)
-    buf = mtp.mtp_get_buffers(h)
     checked = 0
     for k in range(iters):
         mu, sigma, it = mtp.mtp_get_state(h)
         assert it == k
         mtp.mtp_plan_step(h, x0_t, 1, ustar)
         torch.cuda.synchronize()
+        buf = mtp.mtp_get_buffers(h)  # a pipelined handle alternates candidate buffers
         Ug = _np(torch.as_tensor(buf["U"], device=DEV))
         cg = _np(torch.as_tensor(buf["cost"], device=DEV))
         eg = _np(torch.as_tensor(buf["elite"], device=DEV), np.int32)
@@ -591,11 +591,11 @@ def test_legged_plan_step_teacher_forced(mtp):
     h = mtp.mtp_create(spec)
     x0 = np.array(spec["x0"], np.float64)
     u = torch.empty(h.sizes["n"], device=DEV)
-    buf = mtp.mtp_get_buffers(h)
     for k in range(2):
         mu, sigma, it = mtp.mtp_get_state(h)
         mtp.mtp_plan_step(h, _t(x0), 1, u)
         torch.cuda.synchronize()
+        buf = mtp.mtp_get_buffers(h)
         Ug = _np(torch.as_tensor(buf["U"], device=DEV))
         cg = _np(torch.as_tensor(buf["cost"], device=DEV))
         eg = _np(torch.as_tensor(buf["elite"], device=DEV), np.int32)
