@@ -250,14 +250,21 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   }
   __syncthreads();
 
+  // u* = U[elite[0], 0, :], requested before the softmax so the load
+  // overlaps it
+  const int best_row = (int)(sel[0] & 0xffffffffu);
+  const float u_best = tid < a.n ? a.U[(size_t)best_row * a.H * a.n + tid] : 0.f;
   // softmax weights over the elites (FP64), shifted by the best cost
-  const double best = (double)a.cost[(int)(sel[0] & 0xffffffffu)];
+  const double best = (double)a.cost[best_row];
   const bool uniform = (a.update_rule == MTP_UPDATE_PLAIN_CEM) || !(best < INFINITY);
   double part = 0.0;
   // elites on consecutive threads: the FP64 pipe is occupied per warp
-  // instruction, so full warps do the exponentials at the least cost
+  // instruction, so full warps do the exponentials at the least cost.  A
+  // thread keeps its first weight for the normalisation (the launch gives at
+  // least min(E, 1024) threads, so with E <= 1024 that is its only one).
   const int nw = blockDim.x >> 5;
   const int k0 = tid;
+  double w_first = 0.0;
   for (int k = k0; k < E; k += blockDim.x) {
     const int idx = (int)(sel[k] & 0xffffffffu);
     a.elite[k] = idx;
@@ -265,7 +272,8 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
     double c = (double)a.cost[idx];
     if (isnan(c)) c = INFINITY;
     const double w = uniform ? 1.0 : exp(-(c - best) * a.inv_lambda);
-    a.weight[k] = w;
+    if (k == k0) w_first = w;
+    else a.weight[k] = w;
     part += w;
   }
 #pragma unroll
@@ -280,13 +288,10 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   }
   __syncthreads();
   const double inv_total = s_red[0];
-  for (int k = k0; k < E; k += blockDim.x) a.weight[k] = a.weight[k] * inv_total;
-  // u* = U[elite[0], 0, :]
-  const int best_row = (int)(sel[0] & 0xffffffffu);
-  for (int i = tid; i < a.n; i += blockDim.x) {
-    const float u = a.U[(size_t)best_row * a.H * a.n + i];
-    a.ustar[i] = u;
-    if (a.ustar_out) a.ustar_out[i] = u;
+  for (int k = k0; k < E; k += blockDim.x) a.weight[k] = (k == k0 ? w_first : a.weight[k]) * inv_total;
+  if (tid < a.n) {
+    a.ustar[tid] = u_best;
+    if (a.ustar_out) a.ustar_out[tid] = u_best;
   }
 }
 
@@ -327,6 +332,11 @@ __device__ __forceinline__ double canonical_sum(double (&part)[32 / G]) {
   return v;
 }
 
+// Rounds of 32 elites whose loads the update issues together (measured on
+// the C1 point mass, E 32: 1 or 2 rounds 46.1 us per plan step, 4 rounds
+// 47.7; the 7-link arm, E 64, the same within 1 us for 1, 2 and 4).
+constexpr int kUpdRounds = 2;
+
 // Groups of G lanes each own one (t, i) element.  Thread `gt` of `threads`
 // threads given to one planning problem.
 template <int G>
@@ -353,21 +363,62 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int thr
       p1[j] = 0.0;
       p2[j] = 0.0;
     }
-    // virtual lane v = sub + G j takes elites v, v + 32, ... in that order;
-    // the P gathers of one round are independent and issued together
-    if (valid)
-      for (int k0 = 0; k0 < a.E; k0 += 32) {
+    // virtual lane v = sub + G j takes elites v, v + 32, ... in that order.
+    // With few virtual lanes per thread, R rounds of 32 elites are gathered
+    // at once: first all their indices, then all their rows' values and
+    // weights, so a pass over the elites waits for two dependent loads
+    // rather than two per round.  With many, the P gathers of one round are
+    // already independent and issued together (R = 1).
+    constexpr int R = P == 1 ? kUpdRounds : (P == 2 ? kUpdRounds / 2 : 1);
+    if (valid) {
+      if constexpr (R > 1) {
+        for (int k0 = 0; k0 < a.E; k0 += 32 * R) {
+          int idx[R][P];
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          const int k = k0 + sub + G * j;
-          if (k < a.E) {
-            const double d = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - c;
-            const double wd = cem ? d : a.weight[k] * d;
-            p1[j] = p1[j] + wd;
-            p2[j] = fma(wd, d, p2[j]);
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              const int k = k0 + 32 * r + sub + G * j;
+              idx[r][j] = k < a.E ? __ldg(a.elite + k) : 0;
+            }
+          float uv[R][P];
+          double wv[R][P];
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              const int k = k0 + 32 * r + sub + G * j;
+              uv[r][j] = k < a.E ? __ldg(a.U + (size_t)idx[r][j] * Hn + e) : 0.f;
+              wv[r][j] = (k < a.E && !cem) ? a.weight[k] : 1.0;
+            }
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              const int k = k0 + 32 * r + sub + G * j;
+              if (k < a.E) {
+                const double d = (double)uv[r][j] - c;
+                const double wd = cem ? d : wv[r][j] * d;
+                p1[j] = p1[j] + wd;
+                p2[j] = fma(wd, d, p2[j]);
+              }
+            }
+        }
+      } else {
+        for (int k0 = 0; k0 < a.E; k0 += 32) {
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            const int k = k0 + sub + G * j;
+            if (k < a.E) {
+              const double d = (double)__ldg(a.U + (size_t)__ldg(a.elite + k) * Hn + e) - c;
+              const double wd = cem ? d : a.weight[k] * d;
+              p1[j] = p1[j] + wd;
+              p2[j] = fma(wd, d, p2[j]);
+            }
           }
         }
       }
+    }
     const double S1 = canonical_sum<G>(p1);
     const double S2 = canonical_sum<G>(p2);
     if (valid && sub == 0) {
@@ -484,8 +535,26 @@ cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_thread_st
 
 int update_threads(int H, int n) { return H * n; }
 
+// Threads of the single-instance selection block: about kSelKeys keys per
+// thread, at least 128 and at least E (up to 1024), so that with E <= 1024
+// every elite's weight has a thread of its own, as in the batched launch,
+// and both give the same sums.  Measured: on the C1 point mass (B 512) the
+// 128-thread block selects in 10.8-11.3 us against 12.2-12.6 with 1024
+// threads; on the 7-link arm (B 4096) 4 and 8 keys per thread tie and 16
+// are 3 us slower.
+constexpr int kSelKeys = 4;
+
+int select_threads(int B, int E) {
+  int t = (B + kSelKeys - 1) / kSelKeys;
+  if (t < E) t = E;
+  t = (t + 31) & ~31;
+  if (t < 128) t = 128;
+  if (t > kSelThreads) t = kSelThreads;
+  return t;
+}
+
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
-  k_select<<<1, kSelThreads, select_smem_bytes(a.B, a.E), s>>>(a);
+  k_select<<<1, select_threads(a.B, a.E), select_smem_bytes(a.B, a.E), s>>>(a);
   return cudaGetLastError();
 }
 
