@@ -38,11 +38,13 @@ __device__ __forceinline__ float akima_knot_slope(int a, int M, SlopeFn slope) {
 // Standard normal pair by Box-Muller from two 32-bit words.  The angle
 // 2 pi u2 is evaluated as pi + x with x = 2 pi (u2 - 1/2) in [-pi, pi), where
 // the SFU sine / cosine have absolute error about 4e-7; the radius keeps the
-// accurate logarithm because it is ill-conditioned for u1 near 1.
+// accurate logarithm because it is ill-conditioned for u1 near 1.  Its
+// square root is r2 * rsqrt(r2) (a few ulp; r2 = 0 when u1 = 1).
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& e0, float& e1) {
   const float u1 = (float)((w0 >> 8) + 1u) * 5.9604644775390625e-8f;  // (0, 1]
   const float u2 = (float)(w1 >> 8) * 5.9604644775390625e-8f;         // [0, 1)
-  const float radius = sqrtf(-2.f * logf(u1));
+  const float r2 = -2.f * logf(u1);
+  const float radius = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
   float sn, cs;
   __sincosf(6.28318530717958648f * (u2 - 0.5f), &sn, &cs);
   e0 = -radius * cs;
@@ -63,7 +65,10 @@ __device__ __forceinline__ void stage_box(const CandArgs& a, float* lo, float* h
 // Local rows (Alg. 2 local sampling) and the mean row: block `lb` of
 // `nlb` blocks given to them; mu + sigma * eps, four elements of a row per
 // generator call.  MODE (LocalMode) selects whether the draws, the finished
-// samples from stored draws, or both in one pass are made.
+// samples from stored draws, or both in one pass are made.  Each thread
+// keeps one group q of four consecutive (t, i) elements and walks rows
+// q-group by q-group with a fixed row stride, so the group's mean, spread
+// and box bounds are loaded once.
 template <int MODE>
 __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int nlb) {
   __shared__ float box_lo[MTP_MAX_CTRL], box_hi[MTP_MAX_CTRL];
@@ -73,86 +78,68 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
   const int n = dm.n;
   const int Hn = dm.H * n;
   const int G = (Hn + 3) >> 2;
-  const int items = a.local_rows * G + ((MODE != kLocalNoise && a.U_mean) ? G : 0);
-  const int stride = nlb * blockDim.x;
+  const int rows = a.local_rows + ((MODE != kLocalNoise && a.U_mean) ? 1 : 0);  // + the mean row
   // whole 16-byte groups: one vector load of mu and sigma and one vector
   // store per generator call (rows of a 16-byte aligned tensor stay aligned)
   const bool vec = (Hn & 3) == 0 &&
                    ((reinterpret_cast<uintptr_t>(a.U_local) | reinterpret_cast<uintptr_t>(a.mu) |
                      reinterpret_cast<uintptr_t>(a.sigma)) & 15) == 0;
-  // (row, group q, dimension of element 4q) of this thread's item, advanced
-  // by the grid stride without dividing (4G is a multiple of n when Hn is)
-  int e = lb * blockDim.x + threadIdx.x;
-  int row = e / G, q = e - row * G;
-  int i0 = (4 * q) % n;
-  const int srow = stride / G, sq = stride - srow * G, si = (4 * sq) % n;
-  for (; e < items; e += stride) {
-    int i = i0;  // advanced in place over the group's four elements
-    if (row < a.local_rows) {
-      float* dst = a.U_local + (size_t)row * Hn;
-      float eps[4];
-      if constexpr (MODE == kLocalFinish) {
-        if (vec) {
-          const float4 e4 = reinterpret_cast<const float4*>(dst)[q];
-          eps[0] = e4.x;
-          eps[1] = e4.y;
-          eps[2] = e4.z;
-          eps[3] = e4.w;
-        } else {
+  // threads [0, RS * QS): q-groups t % QS, t % QS + QS, ...; rows t / QS,
+  // t / QS + RS, ... (QS = G when there are at least G threads)
+  const int T = nlb * blockDim.x;
+  const int t = lb * blockDim.x + threadIdx.x;
+  const int QS = T >= G ? G : T;
+  const int RS = T / QS;
+  if (t >= RS * QS) return;
+  for (int q = t % QS; q < G; q += QS) {
+    float mv[4], sv[4], lo[4], hi[4];
 #pragma unroll
-          for (int w = 0; w < 4; ++w) eps[w] = (4 * q + w < Hn) ? dst[4 * q + w] : 0.f;
+    for (int w = 0; w < 4; ++w) {
+      const int el = 4 * q + w;
+      const int i = el % n;
+      lo[w] = box_lo[i];
+      hi[w] = box_hi[i];
+      mv[w] = el < Hn ? a.mu[el] : 0.f;
+      sv[w] = el < Hn ? a.sigma[el] : 0.f;
+    }
+    for (int row = t / QS; row < rows; row += RS) {
+      if (row < a.local_rows) {
+        float* dst = a.U_local + (size_t)row * Hn;
+        float eps[4];
+        if constexpr (MODE == kLocalFinish) {
+          if (vec) {
+            const float4 e4 = reinterpret_cast<const float4*>(dst)[q];
+            eps[0] = e4.x;
+            eps[1] = e4.y;
+            eps[2] = e4.z;
+            eps[3] = e4.w;
+          } else {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) eps[w] = (4 * q + w < Hn) ? dst[4 * q + w] : 0.f;
+          }
+        } else {
+          const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
+          box_muller(r.x, r.y, eps[0], eps[1]);
+          box_muller(r.z, r.w, eps[2], eps[3]);
         }
-      } else {
-        const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
-        box_muller(r.x, r.y, eps[0], eps[1]);
-        box_muller(r.z, r.w, eps[2], eps[3]);
-      }
-      if constexpr (MODE == kLocalNoise) {
+        float o[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+          o[w] = MODE == kLocalNoise ? eps[w] : clamp_box(fmaf(sv[w], eps[w], mv[w]), lo[w], hi[w]);
         if (vec) {
-          reinterpret_cast<float4*>(dst)[q] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+          reinterpret_cast<float4*>(dst)[q] = make_float4(o[0], o[1], o[2], o[3]);
         } else {
 #pragma unroll
           for (int w = 0; w < 4; ++w)
-            if (4 * q + w < Hn) dst[4 * q + w] = eps[w];
+            if (4 * q + w < Hn) dst[4 * q + w] = o[w];
         }
-      } else if (vec) {
-        const float4 s4 = __ldg(reinterpret_cast<const float4*>(a.sigma) + q);
-        const float4 m4 = __ldg(reinterpret_cast<const float4*>(a.mu) + q);
-        const float sv[4] = {s4.x, s4.y, s4.z, s4.w}, mv[4] = {m4.x, m4.y, m4.z, m4.w};
-        float o[4];
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          o[w] = clamp_box(fmaf(sv[w], eps[w], mv[w]), box_lo[i], box_hi[i]);
-          if (++i == n) i = 0;
-        }
-        reinterpret_cast<float4*>(dst)[q] = make_float4(o[0], o[1], o[2], o[3]);
       } else {
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           const int el = 4 * q + w;
-          if (el < Hn) {
-            const float u = fmaf(a.sigma[el], eps[w], a.mu[el]);
-            dst[el] = clamp_box(u, box_lo[i], box_hi[i]);
-          }
-          if (++i == n) i = 0;
+          if (el < Hn) a.U_mean[el] = clamp_box(mv[w], lo[w], hi[w]);
         }
       }
-    } else {
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int el = 4 * q + w;
-        if (el < Hn) a.U_mean[el] = clamp_box(a.mu[el], box_lo[i], box_hi[i]);
-        if (++i == n) i = 0;
-      }
-    }
-    row += srow;
-    q += sq;
-    i0 += si;
-    if (i0 >= n) i0 -= n;
-    if (q >= G) {
-      q -= G;
-      ++row;
-      if ((Hn & 3) != 0) i0 = (4 * q) % n;  // 4G = Hn + padding: recompute
     }
   }
 }
