@@ -290,17 +290,20 @@ CandArgs cand_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter) {
   return a;
 }
 
-// Blocks of 256 threads for the local rows: about kLocalRowsPerThread rows
+// Blocks of 256 threads for the local rows: about `rows_per_thread` rows
 // per thread, each thread on one group of four elements, at most 8 blocks
-// per SM (measured on the 7-link arm: 1, 4 and 16 rows per thread generate
-// in 17.7-18.1, 16.7 and 17.0 us; the legged workload, capped at 8 blocks
-// per SM, does not change).
+// per SM.  Generating them, 4 rows per thread (measured on the 7-link arm:
+// 1, 4 and 16 rows per thread generate in 17.7-18.1, 16.7 and 17.0 us; the
+// legged workload, capped at 8 blocks per SM, does not change).  Finishing
+// stored draws, one row per thread: that pass only waits for its loads.
 constexpr int kLocalRowsPerThread = 4;
+constexpr int kFinishRowsPerThread = 1;
 
-int local_blocks_for(const mtp_handle* h, long long rows_plus_mean) {
+int local_blocks_for(const mtp_handle* h, long long rows_plus_mean,
+                     int rows_per_thread = kLocalRowsPerThread) {
   const long long G = ((long long)h->dm.H * h->dm.n + 3) / 4;
   long long items = rows_plus_mean * G;
-  long long blocks = (items + 256LL * kLocalRowsPerThread - 1) / (256LL * kLocalRowsPerThread);
+  long long blocks = (items + 256LL * rows_per_thread - 1) / (256LL * rows_per_thread);
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
   return (int)blocks;
@@ -443,7 +446,7 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, int work, Gen gen, 
   CandArgs c = own_cand_args(h, U);
   if (gen == Gen::kFinish) {
     c.local_mode = kLocalFinish;
-    e = launch_finish(c, local_blocks_for(h, (long long)dm.L + 1), s);
+    e = launch_finish(c, local_blocks_for(h, (long long)dm.L + 1, kFinishRowsPerThread), s);
   } else {
     e = launch_generate(h, c, s);
   }
