@@ -78,9 +78,9 @@ typedef enum { MTP_DR_NONE = 0, MTP_DR_PER_SAMPLE = 1, MTP_DR_SHARED = 2 } mtp_d
                                      FP32 pipe: the contraction stores 4 bytes per p+1
                                      products, so tensor cores would not shorten it */
 #define MTP_FLAG_NO_PIPELINE 0x8u /* mtp_plan_step makes each iteration's candidates in
-                                     full on the critical path instead of preparing the
-                                     next iteration's graph rows and draws during the
-                                     rollout (results are the same bits either way) */
+                                     full on the critical path instead of preparing parts
+                                     of the next iteration's during the rollout (results
+                                     are the same bits either way) */
 
 /* One planning problem (Sec. 2.1 problem statement, Alg. 2 inputs, Table 3
  * hyper-parameters).  Plain data; mtp_create copies it. */
@@ -127,8 +127,9 @@ typedef struct mtp_sizes {
   int32_t B, P, L, E, H, n, d, M, N;
   int32_t kernels_per_iteration; /* kernel launches of one mtp_plan_step iteration (after
                                     the first, when pipelined) */
-  int32_t pipelined;             /* 1: mtp_plan_step prepares each next iteration's graph
-                                    rows and draws on the SMs its rollout leaves idle */
+  int32_t pipelined;             /* mtp_plan_step prepares each next iteration's graph rows
+                                    (1) or graph rows and local draws (2) on the SMs its
+                                    rollout leaves idle; 0: not pipelined */
 } mtp_sizes;
 
 /* Device buffers owned by a handle (valid until mtp_destroy).  After
@@ -217,11 +218,12 @@ mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U
  * (d) using and advancing the handle's iteration counter; writes the last
  * iteration's u* to d_ustar (n).  Replays a captured CUDA graph unless
  * MTP_FLAG_NO_GRAPH is set.  On a pipelined handle (mtp_sizes.pipelined)
- * each iteration also prepares the next iteration's graph rows and local
- * draws on a second stream, on the SMs the rollout leaves idle, and the next
- * iteration (in this call or the next, unless mtp_set_state or a batch run
- * changed the iteration counter in between) only finishes its local rows and
- * mean row.  The results are the same bits as without the pipeline. */
+ * each iteration also prepares the next iteration's graph rows (and, with
+ * enough idle SMs, its local draws) on a second stream, on the SMs the
+ * rollout leaves idle, and the next iteration (in this call or the next,
+ * unless mtp_set_state or a batch run changed the iteration counter in
+ * between) only makes or finishes its local rows and mean row.  The results
+ * are the same bits as without the pipeline. */
 mtp_status mtp_plan_step(mtp_handle* h, const float* d_x0, int32_t iters, float* d_ustar,
                          void* stream);
 

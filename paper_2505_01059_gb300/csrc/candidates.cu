@@ -402,9 +402,9 @@ __global__ void __launch_bounds__(kThreads) k_graph_Z_batch(const CandArgs* __re
 // kernel can share the SM and slow that kernel's warps).  Each block makes
 // the graph Z of iteration d_iter + iter_offset once in shared memory, then
 // the graph rows of graph blocks blockIdx.x, blockIdx.x + gridDim.x, ...,
-// then its grid-stride share of the local rows' standard normal draws.  The
-// mean and spread are not read: the finishing pass applies them once they
-// are known.
+// then (when U_local is set) its grid-stride share of the local rows'
+// standard normal draws.  The mean and spread are not read: the finishing
+// pass applies them once they are known.
 __global__ void __launch_bounds__(kPrepThreads, 1) k_prepare(const CandArgs a) {
   extern __shared__ float smem[];
   if (a.graph_blocks > 0) {
@@ -428,10 +428,12 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Local rows from their stored draws, clamp(mu + sigma * eps), and the mean
-// row.  The graph rows, made during the previous iteration and possibly
-// evicted from L2 since, are prefetched back into L2 for the rollout that
-// follows (16 KB per request, the 16-byte aligned interior of the rows).
+// The local rows and the mean row of an iteration whose graph rows were
+// made during the previous one: from their stored draws, clamp(mu + sigma *
+// eps) (local_mode kLocalFinish), or drawn here (kLocalFull).  The graph
+// rows, possibly evicted from L2 since they were made, are prefetched back
+// into L2 for the rollout that follows (16 KB per request, the 16-byte
+// aligned interior of the rows).
 __global__ void __launch_bounds__(kThreads) k_finish(const CandArgs a) {
   if (threadIdx.x == 0 && a.U_graph && a.graph_rows > 0) {
     const uintptr_t b = reinterpret_cast<uintptr_t>(a.U_graph);
@@ -441,7 +443,8 @@ __global__ void __launch_bounds__(kThreads) k_finish(const CandArgs a) {
     for (uintptr_t p = lo + (uintptr_t)blockIdx.x * kChunk; p < hi; p += (uintptr_t)gridDim.x * kChunk)
       prefetch_l2_bulk(reinterpret_cast<const void*>(p), (uint32_t)(hi - p < kChunk ? hi - p : kChunk));
   }
-  local_rows_body<kLocalFinish>(a, blockIdx.x, gridDim.x);
+  if (a.local_mode == kLocalFinish) local_rows_body<kLocalFinish>(a, blockIdx.x, gridDim.x);
+  else local_rows_body<kLocalFull>(a, blockIdx.x, gridDim.x);
 }
 
 // Def. 1 / Alg. 1 outputs for inspection: Z, I and C written to global memory.

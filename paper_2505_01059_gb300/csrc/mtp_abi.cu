@@ -63,10 +63,12 @@ struct mtp_handle {
   // (the graph rows and the local rows' standard normal draws) depends only
   // on the key and the iteration number, not on the mean and spread.  When
   // the rollout leaves SMs idle, a single-instance iteration therefore
-  // makes the next iteration's graph rows and draws on those SMs while its
-  // rollout runs (on `side`), into the other candidate buffer; the next
-  // iteration then only finishes its local rows and mean row.
+  // makes the next iteration's graph rows (and, with many idle SMs, its
+  // draws) on those SMs while its rollout runs (on `side`), into the other
+  // candidate buffer; the next iteration then only makes (or finishes) its
+  // local rows and mean row.
   bool pipeline = false;
+  bool prep_local = false;    // the local draws are prepared too (else only the graph rows)
   float* Ubuf[2] = {nullptr, nullptr};
   int cur = 0;                // Ubuf[cur] holds the latest iteration's candidates
   bool prep_valid = false;    // Ubuf[cur ^ 1] holds the draws and graph rows of prep_iter
@@ -445,8 +447,10 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, int work, Gen gen, 
   if (ev) stage_event(ev[0], s, captured);
   CandArgs c = own_cand_args(h, U);
   if (gen == Gen::kFinish) {
-    c.local_mode = kLocalFinish;
-    e = launch_finish(c, local_blocks_for(h, (long long)dm.L + 1, kFinishRowsPerThread), s);
+    c.local_mode = h->prep_local ? kLocalFinish : kLocalFull;
+    e = launch_finish(c, local_blocks_for(h, (long long)dm.L + 1,
+                                          h->prep_local ? kFinishRowsPerThread : kLocalRowsPerThread),
+                      s);
   } else {
     e = launch_generate(h, c, s);
   }
@@ -460,6 +464,7 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, int work, Gen gen, 
     nx.iter_offset = 1;
     nx.local_mode = kLocalNoise;
     nx.U_mean = nullptr;
+    if (!h->prep_local) nx.U_local = nullptr;
     if ((e = launch_prepare(nx, h->prep_grid, h->prep_smem, h->side)) != cudaSuccess) return e;
     if (ev) stage_event(ev[6], h->side, captured);
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
@@ -533,23 +538,28 @@ int paths_per_block_for(const Dims& dm, int32_t interp, bool global_Z) {
   return spb;
 }
 
-// Fewest SMs the rollout must leave idle for the next iteration's
-// generation to run beside it.  Measured on the 7-link arm at B 4096 (128
-// rollout blocks): the 24 idle SMs prepare an iteration in 80 us, longer
-// than the rollout; giving the rollout 64-thread blocks to free 88 SMs
-// (28 us) still lost 1.5-4 us per plan step against no pipeline, because
-// the finishing pass reads the prepared draws back from DRAM when L2 was
-// flushed between steps.  The 2-D point mass at B 512 (136 idle SMs) gains
-// 4-7 us per step.
-constexpr int kMinPrepareSMs = 64;
+// Idle SMs for the pipeline.  From kMinPrepareSMs the next iteration's
+// graph rows are prepared beside the rollout and the local rows are drawn
+// on the critical path; from kFullPrepareSMs the local rows' draws are
+// prepared too and only finished on the critical path.  Measured with L2
+// flushed between plan steps, as the bench does:
+//  - 7-link arm, B 4096 (24 idle SMs): preparing the draws too lost
+//    1.5-13 us per step (their finishing pass reads them back from DRAM,
+//    and 24 SMs prepare both in 80 us, longer than the rollout);
+//  - 2-D point mass, B 512 (136 idle SMs): preparing the draws too gains
+//    4-7 us per step.
+constexpr int kMinPrepareSMs = 16;
+constexpr int kFullPrepareSMs = 64;
 
 // Whether a single-instance plan step pipelines its generation (see
-// mtp_handle::pipeline), on how many SMs, with how much shared memory per
-// block.  The point-mass and chain rollouts take one block per 32-128
-// candidates; the legged rollout fills the GPU and is not pipelined.
+// mtp_handle::pipeline), whether the local draws are prepared too, on how
+// many SMs, with how much shared memory per block.  The point-mass and
+// chain rollouts take one block per 32-128 candidates; the legged rollout
+// fills the GPU and is not pipelined.
 cudaError_t pipeline_plan(const mtp_problem& p, const Dims& dm, int paths_per_block, bool* on,
-                          int* grid, size_t* smem) {
+                          bool* local, int* grid, size_t* smem) {
   *on = false;
+  *local = false;
   *grid = 0;
   *smem = 0;
   int dev = 0, sms = 0;
@@ -558,9 +568,10 @@ cudaError_t pipeline_plan(const mtp_problem& p, const Dims& dm, int paths_per_bl
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = init_prepare_attributes(smem)) != cudaSuccess) return e;
   if ((p.flags & MTP_FLAG_NO_PIPELINE) || p.dyn == MTP_DYN_LEGGED) return cudaSuccess;
-  if (dm.L <= 0 && dm.P <= 0) return cudaSuccess;
   const int free_sms = sms - rollout_blocks(dm.B);
   if (free_sms < kMinPrepareSMs) return cudaSuccess;
+  const bool draws = free_sms >= kFullPrepareSMs && dm.L > 0;
+  if (!draws && dm.P <= 0) return cudaSuccess;  // nothing to prepare
   CandArgs probe{};
   probe.dm = dm;
   probe.interp = p.interp;
@@ -568,6 +579,7 @@ cudaError_t pipeline_plan(const mtp_problem& p, const Dims& dm, int paths_per_bl
   probe.paths_per_block = paths_per_block;
   if (prepare_smem_need(probe) > *smem) return cudaSuccess;
   *on = true;
+  *local = draws;
   *grid = free_sms;
   return cudaSuccess;
 }
@@ -618,7 +630,8 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   cudaError_t e;
   if ((e = init_candidate_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
   if ((e = init_select_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
-  if ((e = pipeline_plan(p, dm, h->paths_per_block, &h->pipeline, &h->prep_grid, &h->prep_smem)) !=
+  if ((e = pipeline_plan(p, dm, h->paths_per_block, &h->pipeline, &h->prep_local, &h->prep_grid,
+                         &h->prep_smem)) !=
       cudaSuccess)
     return err(cuda_fail(h, e, "attributes"));
   if ((st = build_tables(h)) != MTP_OK) return err(st);
@@ -667,11 +680,11 @@ mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes)
            + r((uint64_t)p.ctrl_dim * 4) + r((uint64_t)p.state_dim * 4)
            + r((uint64_t)p.M * p.N * p.ctrl_dim * 4);                         // graph Z
   const Dims dm = dims_of(p);
-  bool on = false;
+  bool on = false, local = false;
   int grid = 0;
   size_t smem = 0;
-  cudaError_t e = pipeline_plan(p, dm, paths_per_block_for(dm, p.interp, global_graph(dm)), &on, &grid,
-                                &smem);
+  cudaError_t e = pipeline_plan(p, dm, paths_per_block_for(dm, p.interp, global_graph(dm)), &on, &local,
+                                &grid, &smem);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
   if (on) *bytes += r(rowsz * p.B * 4);  // the second candidate buffer of the pipelined plan step
   return MTP_OK;
@@ -695,7 +708,8 @@ mtp_status mtp_get_sizes(const mtp_handle* h, mtp_sizes* out) {
   // candidates (+ graph when written once), rollout, select, update; when
   // pipelined: finish, prepare (graph in its shared memory), rollout, select, update
   const int kpi = h->pipeline ? 5 : (h->global_Z && d.P > 0 ? 5 : 4);
-  *out = mtp_sizes{d.B, d.P, d.L, d.E, d.H, d.n, d.d, d.M, d.N, kpi, h->pipeline ? 1 : 0};
+  *out = mtp_sizes{d.B, d.P, d.L, d.E, d.H, d.n, d.d, d.M, d.N, kpi,
+                   h->pipeline ? (h->prep_local ? 2 : 1) : 0};
   return MTP_OK;
 }
 

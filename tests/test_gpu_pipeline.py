@@ -26,6 +26,7 @@ def mtp():
 
 
 SPECS = [
+    W.chain(),                                             # 7-link arm, B 4096: graph rows only
     W.chain(B=2048),                                       # 7-link arm, Akima
     W.chain(links=5, B=2048, H=64, interp="linear"),       # straight lines
     W.pointmass(),                                         # C1: B 512, cubic B-spline
@@ -79,7 +80,9 @@ def _run(mtp, spec, flags):
 def test_pipelined_matches_unpipelined(mtp, spec, graph_flags):
     s_p, a = _run(mtp, spec, graph_flags)
     s_n, b = _run(mtp, spec, graph_flags | mtp.FLAG_NO_PIPELINE)
-    assert s_p["pipelined"] == 1 and s_n["pipelined"] == 0
+    # graph rows only: the 4096-candidate arm (24 idle SMs) and a problem without local rows
+    only_graph = spec["B"] == 4096 or s_p["L"] == 0
+    assert s_p["pipelined"] == (1 if only_graph else 2) and s_n["pipelined"] == 0
     assert s_p["kernels_per_iteration"] == 5
     for k, (x, y) in enumerate(zip(a, b)):
         for name, vx, vy in zip(("mu", "sigma", "iter", "ustar", "U", "cost"), x, y):
@@ -88,24 +91,25 @@ def test_pipelined_matches_unpipelined(mtp, spec, graph_flags):
 
 def test_legged_and_tiny_problems_are_not_pipelined(mtp):
     # the legged rollout fills the GPU; B 1 has no draws or graph rows; the
-    # others' rollouts leave fewer than 64 SMs idle
+    # last one's rollout leaves no SM idle
     for spec in (W.legged(links=4, B=256, H=32, M=6, N=16, E=16), W.pointmass(B=1, E=1),
-                 W.chain(), W.pointmass(B=8192, H=16, E=8)):
+                 W.pointmass(B=8192, H=16, E=8)):
         h = mtp.mtp_create(spec)
         assert h.sizes["pipelined"] == 0, spec["B"]
         mtp.mtp_destroy(h)
 
 
 def test_device_bytes_count_the_second_buffer(mtp):
-    spec = W.chain(B=2048)
-    b_p = mtp.mtp_problem_device_bytes(spec)
-    b_n = mtp.mtp_problem_device_bytes(dict(spec, flags=mtp.FLAG_NO_PIPELINE))
-    assert b_p - b_n == spec["B"] * spec["H"] * spec["n"] * 4
+    for spec in (W.chain(), W.chain(B=2048)):
+        b_p = mtp.mtp_problem_device_bytes(spec)
+        b_n = mtp.mtp_problem_device_bytes(dict(spec, flags=mtp.FLAG_NO_PIPELINE))
+        assert b_p - b_n == spec["B"] * spec["H"] * spec["n"] * 4
 
 
 @pytest.mark.parametrize("graph_flags", [0, 0x2])
-def test_profiled_pipeline_reports_the_overlapped_preparation(mtp, graph_flags):
-    spec = dict(W.chain(B=2048), flags=graph_flags)
+@pytest.mark.parametrize("B", [4096, 2048])
+def test_profiled_pipeline_reports_the_overlapped_preparation(mtp, graph_flags, B):
+    spec = dict(W.chain(B=B), flags=graph_flags)
     h = mtp.mtp_create(spec)
     x0 = torch.tensor(spec["x0"], dtype=torch.float32, device=DEV)
     u = torch.empty(h.sizes["n"], device=DEV)
