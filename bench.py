@@ -489,7 +489,7 @@ def run_ours(args, spec, name):
             "stage_ms_per_step": dict(zip(("generate", "rollout", "select", "update"),
                                           [v / max(n_it, 1) for v in stage_ms])),
             "stage_share": share,
-            "pipelined": bool(s["pipelined"]),
+            "pipelined": {0: "no", 1: "graph rows", 2: "graph rows and draws"}[s["pipelined"]],
             "prepare_overlapped_ms_per_step": prep_ms / max(n_it, 1),
             "roofline": {"bound": "alu", "kernel": ROLLOUT_KERNEL[spec["dyn"]],
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
