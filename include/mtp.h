@@ -306,10 +306,13 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_grou
 /* mtp_shift(h, k) of every instance of the batch in one launch. */
 mtp_status mtp_batch_shift(mtp_batch* b, int32_t k, void* stream);
 
-/* Device bytes mtp_create requests for `problem`, each allocation rounded up
- * to 512 bytes (the candidate tensor U dominates: B * H * n floats).  The serving layer admits
- * robots against a memory budget with it.  MTP_ERR_INVALID_ARG when the
- * problem does not validate. */
+/* Device bytes a handle for `problem` uses, each allocation rounded up to
+ * 512 bytes (the candidate tensor U dominates: B * H * n floats).  A
+ * pipelined problem counts the second candidate buffer, which the first
+ * single-instance mtp_plan_step allocates (a handle planned only in batches
+ * never does; MTP_FLAG_NO_PIPELINE leaves it out).  The serving layer admits
+ * robots against a memory budget with it, with the pipeline off.
+ * MTP_ERR_INVALID_ARG when the problem does not validate. */
 mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes);
 
 /* Re-planning server (continuous batching).  Robots are registered with

@@ -639,7 +639,6 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   if ((e = dalloc(&h->mu, rowsz)) || (e = dalloc(&h->sigma, rowsz)) ||
       (e = dalloc(&h->mu_f, rowsz)) || (e = dalloc(&h->sigma_f, rowsz)) ||
       (e = dalloc(&h->iter_dev, 1)) || (e = dalloc(&h->Ubuf[0], rowsz * dm.B)) ||
-      (h->pipeline && (e = dalloc(&h->Ubuf[1], rowsz * dm.B))) ||
       (e = dalloc(&h->cost, dm.B)) || (e = dalloc(&h->elite, dm.E)) ||
       (e = dalloc(&h->weight, dm.E)) || (e = dalloc(&h->ustar, dm.n)) ||
       (e = dalloc(&h->x0, dm.d)) || (e = dalloc(&h->Z, (size_t)dm.M * dm.N * dm.n)))
@@ -657,11 +656,6 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   h->U = h->Ubuf[0];
   if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return err(cuda_fail(h, e, "cudaStreamCreate"));
-  if (h->pipeline &&
-      ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess ||
-       (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-       (e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess))
-    return err(cuda_fail(h, e, "pipeline stream"));
   *out = h;
   return MTP_OK;
 }
@@ -844,8 +838,36 @@ static mtp_status read_stage_events(mtp_handle* h, const cudaEvent_t* ev, double
   return MTP_OK;
 }
 
+// The pipeline's second candidate buffer, stream and events, made by the
+// first single-instance plan step that uses them (a handle planned only in
+// batches never needs them).  If they cannot be made the handle plans
+// without the pipeline, which gives the same results.
+static void ensure_pipeline(mtp_handle* h) {
+  if (!h->pipeline || h->side) return;
+  const size_t n = (size_t)h->dm.H * h->dm.n * h->dm.B;
+  if (dalloc(&h->Ubuf[1], n) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();  // clear the failure: the plain path needs none of these
+    if (h->Ubuf[1]) cudaFree(h->Ubuf[1]);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    h->Ubuf[1] = nullptr;
+    h->side = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
+    h->pipeline = false;
+    h->prep_local = false;
+    h->prep_valid = false;
+    h->cur = 0;
+    h->U = h->Ubuf[0];
+  }
+}
+
 static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
   cudaError_t e;
+  ensure_pipeline(h);
   const bool use_graph = !(h->pr.flags & MTP_FLAG_NO_GRAPH);
   if (!use_graph) {
     for (int k = 0; k < iters; ++k) {

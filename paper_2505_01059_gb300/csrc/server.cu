@@ -281,8 +281,12 @@ mtp_status mtp_server_destroy(mtp_server* S) {
 
 mtp_status mtp_server_register(mtp_server* S, const mtp_problem* problem, int32_t* robot) {
   if (!S || !problem || !robot) return server_fail(S, MTP_ERR_INVALID_ARG, "register: null argument");
+  // served robots are planned in batches only: no single-instance pipeline
+  // (and so no second candidate buffer in the footprint)
+  mtp_problem pr = *problem;
+  pr.flags |= MTP_FLAG_NO_PIPELINE;
   uint64_t bytes = 0;
-  mtp_status st = mtp_problem_device_bytes(problem, &bytes);
+  mtp_status st = mtp_problem_device_bytes(&pr, &bytes);
   if (st != MTP_OK) return server_fail(S, st, std::string("register: ") + mtp_last_error(nullptr));
   // admission is decided and reserved under the lock; the handle (device
   // allocations, synchronous copies) is created outside it, so cycles that
@@ -301,7 +305,7 @@ mtp_status mtp_server_register(mtp_server* S, const mtp_problem* problem, int32_
   mtp_handle* h = nullptr;
   {
     DeviceScope g(S->device);
-    st = mtp_create(problem, &h);
+    st = mtp_create(&pr, &h);
   }
   std::lock_guard<std::mutex> lock(S->reg_mu);
   --S->registering;

@@ -128,8 +128,11 @@ def test_queue_limit_refuses_submits(mtp):
 def test_memory_budget_admission(mtp):
     small = W.pointmass(B=256, E=16)
     big = W.chain(links=7, B=8192, H=256)
-    b_small = mtp.mtp_problem_device_bytes(small)
-    b_big = mtp.mtp_problem_device_bytes(big)
+    # the server plans its robots in batches, without the single-instance
+    # pipeline's second candidate buffer
+    b_small = mtp.mtp_problem_device_bytes(dict(small, flags=mtp.FLAG_NO_PIPELINE))
+    b_big = mtp.mtp_problem_device_bytes(dict(big, flags=mtp.FLAG_NO_PIPELINE))
+    assert mtp.mtp_problem_device_bytes(small) - b_small == 256 * 64 * 2 * 4
     assert b_big > 8192 * 256 * 7 * 4  # the candidate tensor alone
     srv = mtp.mtp_server_create(max_batch=4, memory_budget=2 * b_small + b_big // 2)
     assert mtp.mtp_server_register(srv, small) == 0
