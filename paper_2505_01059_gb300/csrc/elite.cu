@@ -21,6 +21,12 @@ __device__ __forceinline__ uint32_t order_key(float f) {
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
+// The cost an order key stands for (NaN costs come back as +inf, -0 as +0,
+// as the selection and the softmax treat them).
+__device__ __forceinline__ float key_cost(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 __device__ __forceinline__ int next_pow2(int v) {
   int p = 1;
   while (p < v) p <<= 1;
@@ -253,6 +259,44 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   // u* = U[elite[0], 0, :], requested before the softmax so the load
   // overlaps it
   const int best_row = (int)(sel[0] & 0xffffffffu);
+  if (E <= 64) {
+    // One warp, elites lane and lane + 32, their costs decoded from the
+    // sorted order keys (no global reload), no block barrier.  The two
+    // halves are reduced separately and then added, which is the order of
+    // the block-wide reduction below for the same E, so the weights are the
+    // same bits either way.
+    if (wid != 0) return;
+    const float u_best = lane < a.n ? a.U[(size_t)best_row * a.H * a.n + lane] : 0.f;
+    const double best = (double)key_cost((uint32_t)(sel[0] >> 32));
+    const bool uniform = (a.update_rule == MTP_UPDATE_PLAIN_CEM) || !(best < INFINITY);
+    double w[2] = {0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      if (k < E) {
+        const unsigned long long e = sel[k];
+        const int idx = (int)(e & 0xffffffffu);
+        a.elite[k] = idx;
+        if (a.elite_out) a.elite_out[k] = idx;
+        const double c = (double)key_cost((uint32_t)(e >> 32));
+        w[h] = uniform ? 1.0 : exp(-(c - best) * a.inv_lambda);
+      }
+    }
+    double s0 = w[0], s1 = w[1];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    const double inv_total = 1.0 / (s0 + s1);
+    if (lane < E) a.weight[lane] = w[0] * inv_total;
+    if (lane + 32 < E) a.weight[lane + 32] = w[1] * inv_total;
+    if (lane < a.n) {
+      a.ustar[lane] = u_best;
+      if (a.ustar_out) a.ustar_out[lane] = u_best;
+    }
+    return;
+  }
   const float u_best = tid < a.n ? a.U[(size_t)best_row * a.H * a.n + tid] : 0.f;
   // softmax weights over the elites (FP64), shifted by the best cost
   const double best = (double)a.cost[best_row];
@@ -337,6 +381,39 @@ __device__ __forceinline__ double canonical_sum(double (&part)[32 / G]) {
 // 47.7; the 7-link arm, E 64, the same within 1 us for 1, 2 and 4).
 constexpr int kUpdRounds = 2;
 
+// Threads per block of the update launches.
+constexpr int kUpdThreads = 128;
+
+// The new mean and spread of element e from the sums over the elites of
+// d = u - c and w d^2 (shift c), then the floor and the smoothing.
+__device__ __forceinline__ void finish_element(const UpdateArgs& a, int e, double c, double S1,
+                                               double S2, bool cem) {
+  if (cem) {
+    // Sec. 2.1 CEM update: mean and unbiased variance of the elites
+    const double E = (double)a.E;
+    const double m1 = c + S1 / E;
+    const double ss = fmax(S2 - S1 * (S1 / E), 0.0);
+    const double s1 = a.E > 1 ? sqrt(ss / (E - 1.0)) : 0.0;
+    const double mn = a.alpha * a.mu[e] + (1.0 - a.alpha) * m1;
+    const double sn = a.alpha * a.sigma[e] + (1.0 - a.alpha) * s1;
+    a.mu[e] = mn;
+    a.sigma[e] = sn;
+    a.mu_f[e] = (float)mn;
+    a.sigma_f[e] = (float)sn;
+  } else {
+    // Alg. 2: weighted mean and standard deviation (weights sum to one)
+    const double m1 = c + S1;
+    double s1 = sqrt(fmax(S2 - S1 * S1, 0.0));
+    if (s1 < a.sigma_min) s1 = a.sigma_min;
+    const double mn = m1 + a.alpha * (a.mu[e] - m1);
+    const double sn = s1 + a.alpha * (a.sigma[e] - s1);
+    a.mu[e] = mn;
+    a.sigma[e] = sn;
+    a.mu_f[e] = (float)mn;
+    a.sigma_f[e] = (float)sn;
+  }
+}
+
 // Groups of G lanes each own one (t, i) element.  Thread `gt` of `threads`
 // threads given to one planning problem.
 template <int G>
@@ -346,11 +423,19 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int thr
   const int Hn = a.H * a.n;
   const bool cem = a.update_rule == MTP_UPDATE_PLAIN_CEM;
   // G == 1: thread gt owns elements gt, gt + threads, ... (no shuffles).
-  // G > 1: the loop runs warp-uniformly (threads is a multiple of 32) and
-  // groups past the end idle through the shuffles.
+  // G > 1: the loop runs block-uniformly (as many sweeps as the block's first
+  // group needs; groups past the end idle through the shuffles), so that
+  // each sweep ends with the block's elements finished together: lane 0 of
+  // each group leaves its sums in shared memory and thread s finishes group
+  // s's element.  That is one stream of FP64 instructions for all of the
+  // block's elements instead of one per element, with the same arithmetic.
   const int per_sweep = (G == 1) ? threads : (threads / 32) * (32 / G);
   const int first = (G == 1) ? gt : (gt / 32) * (32 / G) + (threadIdx.x & 31) / G;
-  const int sweeps = (G == 1) ? 0 : (Hn - (gt / 32) * (32 / G) + per_sweep - 1) / per_sweep;
+  const int block_first = ((gt - (int)threadIdx.x) / 32) * (32 / G);
+  const int sweeps = (G == 1) ? 0 : (Hn - block_first + per_sweep - 1) / per_sweep;
+  constexpr int kGroups = G > 1 ? kUpdThreads / G : 1;
+  __shared__ double sh_S1[kGroups], sh_S2[kGroups], sh_c[kGroups];
+  __shared__ int sh_e[kGroups];
   for (int it = 0, e = first; (G == 1) ? (e < Hn) : (it < sweeps); ++it, e += per_sweep) {
     const bool valid = e < Hn;
     // one pass over the elites: sums of d = u - c and d^2 with the shift c =
@@ -421,45 +506,34 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int gt, int thr
     }
     const double S1 = canonical_sum<G>(p1);
     const double S2 = canonical_sum<G>(p2);
-    if (valid && sub == 0) {
-      if (cem) {
-        // Sec. 2.1 CEM update: mean and unbiased variance of the elites
-        const double E = (double)a.E;
-        const double m1 = c + S1 / E;
-        const double ss = fmax(S2 - S1 * (S1 / E), 0.0);
-        const double s1 = a.E > 1 ? sqrt(ss / (E - 1.0)) : 0.0;
-        const double mn = a.alpha * a.mu[e] + (1.0 - a.alpha) * m1;
-        const double sn = a.alpha * a.sigma[e] + (1.0 - a.alpha) * s1;
-        a.mu[e] = mn;
-        a.sigma[e] = sn;
-        a.mu_f[e] = (float)mn;
-        a.sigma_f[e] = (float)sn;
-      } else {
-        // Alg. 2: weighted mean and standard deviation (weights sum to one)
-        const double m1 = c + S1;
-        double s1 = sqrt(fmax(S2 - S1 * S1, 0.0));
-        if (s1 < a.sigma_min) s1 = a.sigma_min;
-        const double mn = m1 + a.alpha * (a.mu[e] - m1);
-        const double sn = s1 + a.alpha * (a.sigma[e] - s1);
-        a.mu[e] = mn;
-        a.sigma[e] = sn;
-        a.mu_f[e] = (float)mn;
-        a.sigma_f[e] = (float)sn;
+    if constexpr (G == 1) {
+      if (valid) finish_element(a, e, c, S1, S2, cem);
+    } else {
+      const int slot = threadIdx.x / G;
+      if (sub == 0) {
+        sh_S1[slot] = S1;
+        sh_S2[slot] = S2;
+        sh_c[slot] = c;
+        sh_e[slot] = valid ? e : -1;
       }
+      __syncthreads();
+      if (threadIdx.x < kGroups && sh_e[threadIdx.x] >= 0)
+        finish_element(a, sh_e[threadIdx.x], sh_c[threadIdx.x], sh_S1[threadIdx.x], sh_S2[threadIdx.x], cem);
+      __syncthreads();  // the next sweep rewrites the slots
     }
   }
   if (a.d_iter && gt == 0) *a.d_iter += 1u;
 }
 
 template <int G>
-__global__ void __launch_bounds__(128) k_update(const UpdateArgs a) {
+__global__ void __launch_bounds__(kUpdThreads) k_update(const UpdateArgs a) {
   update_body<G>(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // Many planning problems: thread_start (count + 1 entries) holds each
 // instance's first thread.
 template <int G>
-__global__ void __launch_bounds__(128) k_update_batch(const UpdateArgs* __restrict__ args,
+__global__ void __launch_bounds__(kUpdThreads) k_update_batch(const UpdateArgs* __restrict__ args,
                                                       const int* __restrict__ thread_start,
                                                       int count) {
   // thread_start holds absolute thread numbers; this launch starts at thread_start[0]
@@ -529,7 +603,7 @@ cudaError_t launch_select_batch(const SelectArgs* d_args, int count, size_t smem
 cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_thread_start, int count,
                                 int total_threads, cudaStream_t s) {
   if (total_threads <= 0) return cudaSuccess;
-  k_update_batch<1><<<(total_threads + 127) / 128, 128, 0, s>>>(d_args, d_thread_start, count);
+  k_update_batch<1><<<(total_threads + kUpdThreads - 1) / kUpdThreads, kUpdThreads, 0, s>>>(d_args, d_thread_start, count);
   return cudaGetLastError();
 }
 
@@ -568,14 +642,14 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   int G = 1;
   while (G < 32 && (long long)Hn * G < 152 * 256) G <<= 1;
   const long long threads = (long long)Hn * G;
-  const int blocks = (int)((threads + 127) / 128);
+  const int blocks = (int)((threads + kUpdThreads - 1) / kUpdThreads);
   switch (G) {
-    case 1: k_update<1><<<blocks, 128, 0, s>>>(a); break;
-    case 2: k_update<2><<<blocks, 128, 0, s>>>(a); break;
-    case 4: k_update<4><<<blocks, 128, 0, s>>>(a); break;
-    case 8: k_update<8><<<blocks, 128, 0, s>>>(a); break;
-    case 16: k_update<16><<<blocks, 128, 0, s>>>(a); break;
-    default: k_update<32><<<blocks, 128, 0, s>>>(a); break;
+    case 1: k_update<1><<<blocks, kUpdThreads, 0, s>>>(a); break;
+    case 2: k_update<2><<<blocks, kUpdThreads, 0, s>>>(a); break;
+    case 4: k_update<4><<<blocks, kUpdThreads, 0, s>>>(a); break;
+    case 8: k_update<8><<<blocks, kUpdThreads, 0, s>>>(a); break;
+    case 16: k_update<16><<<blocks, kUpdThreads, 0, s>>>(a); break;
+    default: k_update<32><<<blocks, kUpdThreads, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }
