@@ -85,7 +85,10 @@ struct mtp_handle {
   float* Z = nullptr;  // (M, N, n) graph of the current iteration (batched planning)
   // replay
   cudaStream_t cap_stream = nullptr;
-  std::map<int, cudaGraphExec_t> graphs;  // key: graph_key(iterations, cur, first prepared)
+  std::map<int, cudaGraphExec_t> graphs;   // key: (iterations, cur, first prepared)
+  std::map<int, cudaGraphExec_t> hgraphs;  // the same with the host-pointer step's copies
+  float* x0_pin = nullptr;                 // pinned staging of mtp_plan_step_host: start state
+  float* ustar_pin = nullptr;              // and u*, written by the selection kernel
   // profiling
   bool profiling = false;
   std::vector<cudaEvent_t> events;  // eager launches: kEvPerIter per iteration, read by mtp_stage_times
@@ -440,7 +443,7 @@ enum class Gen { kFull, kFinish };
 // stream while this iteration's rollout runs; the update, which advances
 // iter_dev, waits for them.
 cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, int work, Gen gen, cudaEvent_t* ev,
-                              bool captured = false) {
+                              bool captured = false, float* ustar_out = nullptr) {
   cudaError_t e;
   const Dims& dm = h->dm;
   float* U = h->Ubuf[work];
@@ -473,7 +476,7 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, int work, Gen gen, 
   if ((e = launch_rollout(h, r, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[2], s, captured);
   SelectArgs sa{h->cost, U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
-                h->elite, h->weight, h->ustar, nullptr, nullptr};
+                h->elite, h->weight, h->ustar, nullptr, ustar_out};
   if ((e = launch_select(sa, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[3], s, captured);
   if (h->pipeline && (e = cudaStreamWaitEvent(s, h->ev_join, 0)) != cudaSuccess) return e;
@@ -589,6 +592,9 @@ void free_handle(mtp_handle* h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   for (cudaEvent_t e : h->gevents) cudaEventDestroy(e);
   for (auto& kv : h->pgraphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : h->hgraphs) cudaGraphExecDestroy(kv.second);
+  if (h->x0_pin) cudaFreeHost(h->x0_pin);
+  if (h->ustar_pin) cudaFreeHost(h->ustar_pin);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -965,11 +971,91 @@ mtp_status mtp_plan_step(mtp_handle* h, const float* d_x0, int32_t iters, float*
   return MTP_OK;
 }
 
+// mtp_plan_step_host in one graph launch: the start state is staged in
+// pinned memory and its upload is the graph's first node, and the last
+// iteration's selection kernel writes u* straight into pinned memory, so a
+// call is one graph launch and one synchronisation.  Up to 64 iterations,
+// graph mode, profiling off; otherwise the caller takes the general path.
+static bool plan_host_graph(mtp_handle* h, const float* h_x0, int32_t iters, float* h_ustar,
+                            cudaStream_t s, mtp_status* st) {
+  constexpr int kChunk = 64;
+  if ((h->pr.flags & MTP_FLAG_NO_GRAPH) || h->profiling || iters > kChunk) return false;
+  cudaError_t e;
+  if (!h->x0_pin) {
+    if (cudaMallocHost(&h->x0_pin, (size_t)h->dm.d * 4) != cudaSuccess ||
+        cudaMallocHost(&h->ustar_pin, (size_t)h->dm.n * 4) != cudaSuccess) {
+      cudaGetLastError();
+      if (h->x0_pin) cudaFreeHost(h->x0_pin);
+      h->x0_pin = nullptr;
+      h->ustar_pin = nullptr;
+      return false;
+    }
+  }
+  ensure_pipeline(h);
+  std::memcpy(h->x0_pin, h_x0, (size_t)h->dm.d * 4);
+  const int c0 = h->cur;
+  const bool prepared = h->pipeline && h->prep_valid && h->prep_iter == h->iter_host;
+  const int key = iters * 4 + c0 * 2 + (prepared ? 1 : 0);
+  auto it = h->hgraphs.find(key);
+  if (it == h->hgraphs.end()) {
+    cudaGraph_t graph;
+    if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      *st = cuda_fail(h, e, "cudaStreamBeginCapture");
+      return true;
+    }
+    e = cudaMemcpyAsync(h->x0, h->x0_pin, (size_t)h->dm.d * 4, cudaMemcpyHostToDevice, h->cap_stream);
+    for (int k = 0; k < iters && e == cudaSuccess; ++k) {
+      int work;
+      Gen gen;
+      iteration_plan(h, c0, prepared, k, &work, &gen);
+      e = enqueue_iteration(h, h->cap_stream, work, gen, nullptr, true,
+                            k == iters - 1 ? h->ustar_pin : nullptr);
+    }
+    if (e != cudaSuccess) {
+      cudaStreamEndCapture(h->cap_stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      *st = cuda_fail(h, e, "capture");
+      return true;
+    }
+    if ((e = cudaStreamEndCapture(h->cap_stream, &graph)) != cudaSuccess) {
+      *st = cuda_fail(h, e, "cudaStreamEndCapture");
+      return true;
+    }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      *st = cuda_fail(h, e, "cudaGraphInstantiate");
+      return true;
+    }
+    it = h->hgraphs.emplace(key, exec).first;
+  }
+  if ((e = cudaGraphLaunch(it->second, s)) != cudaSuccess) {
+    *st = cuda_fail(h, e, "cudaGraphLaunch");
+    return true;
+  }
+  for (int k = 0; k < iters; ++k) {
+    int work;
+    Gen gen;
+    iteration_plan(h, c0, prepared, k, &work, &gen);
+    after_iteration(h, work);
+  }
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    *st = cuda_fail(h, e, "cudaStreamSynchronize");
+    return true;
+  }
+  std::memcpy(h_ustar, h->ustar_pin, (size_t)h->dm.n * 4);
+  *st = MTP_OK;
+  return true;
+}
+
 mtp_status mtp_plan_step_host(mtp_handle* h, const float* h_x0, int32_t iters, float* h_ustar,
                               void* stream) {
   if (!h || !h_x0 || !h_ustar || iters < 1) return fail(h, MTP_ERR_INVALID_ARG, "plan_step_host: bad argument");
   DeviceGuard g(h->device);
   cudaStream_t s = (cudaStream_t)stream;
+  mtp_status hs = MTP_OK;
+  if (plan_host_graph(h, h_x0, iters, h_ustar, s, &hs)) return hs;
   MTP_CUDA(h, cudaMemcpyAsync(h->x0, h_x0, h->dm.d * 4, cudaMemcpyHostToDevice, s));
   mtp_status st = plan_device(h, iters, s);
   if (st != MTP_OK) return st;
