@@ -161,6 +161,40 @@ __device__ __forceinline__ void regenerate_Z(const CandArgs& a, float* Z, uint32
   }
 }
 
+template <int V>
+struct Int {
+  static constexpr int value = V;
+};
+
+// Clamped stores of `total` interpolated elements of consecutive rows,
+// u = f(path, t, i), coalesced over (t, i); each thread's (path, t, i)
+// position advances by a fixed stride, so it is carried along instead of
+// divided out.
+template <class F>
+__device__ __forceinline__ void store_rows(const CandArgs& a, float* out, int total, const float* box_lo,
+                                           const float* box_hi, F f) {
+  const int H = a.dm.H, n = a.dm.n, Hn = H * n;
+  int e = threadIdx.x;
+  int sp = e / Hn, rem = e - sp * Hn;
+  int t = rem / n, i = rem - t * n;
+  const int ds = blockDim.x / Hn, drem = blockDim.x - ds * Hn;
+  const int dt = drem / n, di = drem - dt * n;
+  for (; e < total; e += blockDim.x) {
+    out[e] = clamp_box(f(sp, t, i), box_lo[i], box_hi[i]);
+    sp += ds;
+    t += dt;
+    i += di;
+    if (i >= n) {
+      i -= n;
+      ++t;
+    }
+    if (t >= H) {
+      t -= H;
+      ++sp;
+    }
+  }
+}
+
 // Graph rows of graph block `bid` (Alg. 1 and the interpolation): its paths'
 // layer indices, their waypoints gathered from the graph Zs (shared or
 // global memory) into C (shared memory, followed by the Akima scratch), and
@@ -240,52 +274,52 @@ __device__ __forceinline__ void graph_paths_body(const CandArgs& a, const float*
     __syncthreads();
   }
 
-  // Interpolate and store rows b0 .. b0+nb-1 (coalesced over (t, i)); the
-  // (path, t, i) position of each thread advances by a fixed stride, so it
-  // is carried along instead of divided out.
+  // Interpolate and store rows b0 .. b0+nb-1 (coalesced over (t, i)),
+  // with the interpolation kind (and the B-spline degree) fixed at compile
+  // time so the per-element sum is unrolled.
   float* out = a.U_graph + (size_t)b0 * Hn;
   const int total = nb * Hn;
-  int e = threadIdx.x;
-  int sp = e / Hn, rem = e - sp * Hn;
-  int t = rem / n, i = rem - t * n;
-  const int ds = blockDim.x / Hn, drem = blockDim.x - ds * Hn;
-  const int dt = drem / n, di = drem - dt * n;
-  for (; e < total; e += blockDim.x) {
-    float u;
-    if (a.interp == MTP_INTERP_BSPLINE) {
-      // Def. 2: sum over the (p+1)-wide non-zero window of basis row t.
-      const int f = a.bfirst[t];
-      const float* brow = a.basis + (size_t)t * M;
-      const float* zc = C + sp * M * n + i;
-      u = 0.f;
-      for (int q = 0; q <= a.degree; ++q) {
-        const int m = f + q;
-        if (m < M) u = fmaf(brow[m], zc[m * n], u);
-      }
-    } else if (a.interp == MTP_INTERP_AKIMA) {
+  if (a.interp == MTP_INTERP_BSPLINE) {
+    // Def. 2: sum over the (p+1)-wide non-zero window of basis row t.
+    auto bspline = [&](auto D) {
+      store_rows(a, out, total, box_lo, box_hi, [&](int sp, int t, int i) {
+        constexpr int deg = decltype(D)::value;
+        const int f = a.bfirst[t];
+        const float* brow = a.basis + (size_t)t * M;
+        const float* zc = C + sp * M * n + i;
+        float u = 0.f;
+#pragma unroll
+        for (int q = 0; q <= deg; ++q) {
+          const int m = f + q;
+          if (m < M) u = fmaf(brow[m], zc[m * n], u);
+        }
+        return u;
+      });
+    };
+    switch (a.degree) {
+      case 0: bspline(Int<0>{}); break;
+      case 1: bspline(Int<1>{}); break;
+      case 2: bspline(Int<2>{}); break;
+      case 3: bspline(Int<3>{}); break;
+      case 4: bspline(Int<4>{}); break;
+      case 5: bspline(Int<5>{}); break;
+      case 6: bspline(Int<6>{}); break;
+      default: bspline(Int<7>{}); break;
+    }
+  } else if (a.interp == MTP_INTERP_AKIMA) {
+    store_rows(a, out, total, box_lo, box_hi, [&](int sp, int t, int i) {
       const int k = a.seg[t];
       const float dl = a.delta[t];
       const float* cf = coef + ((size_t)(sp * n + i) * (M - 1) + k) * 4;
-      u = fmaf(fmaf(fmaf(cf[3], dl, cf[2]), dl, cf[1]), dl, cf[0]);
-    } else {
+      return fmaf(fmaf(fmaf(cf[3], dl, cf[2]), dl, cf[1]), dl, cf[0]);
+    });
+  } else {
+    store_rows(a, out, total, box_lo, box_hi, [&](int sp, int t, int i) {
       const int k = a.seg[t];
       const float w = fminf(a.delta[t] * a.inv_h, 1.f);
       const float z0 = C[(sp * M + k) * n + i], z1 = C[(sp * M + k + 1) * n + i];
-      u = fmaf(w, z1 - z0, z0);
-    }
-    out[e] = clamp_box(u, box_lo[i], box_hi[i]);
-    // advance (sp, t, i) by blockDim.x elements
-    sp += ds;
-    t += dt;
-    i += di;
-    if (i >= n) {
-      i -= n;
-      ++t;
-    }
-    if (t >= H) {
-      t -= H;
-      ++sp;
-    }
+      return fmaf(w, z1 - z0, z0);
+    });
   }
 }
 
@@ -311,7 +345,7 @@ __device__ __forceinline__ void candidates_body(const CandArgs& a, float* smem, 
   local_rows_body<kLocalFull>(a, bid - a.graph_blocks, nblocks - a.graph_blocks);
 }
 
-__global__ void __launch_bounds__(kThreads) k_candidates(const CandArgs a) {
+__global__ void __launch_bounds__(kThreads, 5) k_candidates(const CandArgs a) {
   extern __shared__ float smem[];
   candidates_body(a, smem, blockIdx.x, gridDim.x);
 }
