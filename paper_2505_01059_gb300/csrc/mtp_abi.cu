@@ -519,12 +519,18 @@ Dims dims_of(const mtp_problem& p) {
 // regenerated in every graph block's shared memory.
 bool global_graph(const Dims& dm) { return (long long)dm.M * dm.N * dm.n > 4096; }
 
-// Graph paths per block: ~4K output elements per block, and at least 8
-// paths for Akima so its per-(path, dimension) coefficient pass is wide;
-// shrunk until the block's shared memory fits.
+// Graph paths per block, at most 32: about 64K output elements per block for
+// B-spline rows, whose blocks otherwise repeat their fixed costs (two
+// barriers, the gather of the waypoints) for little work (measured on the
+// legged workload, 3,840 elements per row: 4K / 8K / 16K / 32K / 64K / 128K
+// elements per block generate in 140.9 / 136.0 / 131.7 / 123.5 / 120.4 /
+// 128.2 us); about 4K for Akima and straight lines, and at least 8 paths
+// for Akima so its per-(path, dimension) coefficient pass is wide; shrunk
+// until the block's shared memory fits.
 int paths_per_block_for(const Dims& dm, int32_t interp, bool global_Z) {
   const long long Hn = (long long)dm.H * dm.n;
-  int spb = (int)((4096 + Hn - 1) / Hn);
+  const long long target = interp == MTP_INTERP_BSPLINE ? 65536 : 4096;
+  int spb = (int)std::min<long long>((target + Hn - 1) / Hn, 32);
   if (interp == MTP_INTERP_AKIMA && spb < 8) spb = 8;
   if (spb < 1) spb = 1;
   if (spb > 32) spb = 32;
