@@ -74,6 +74,7 @@ struct mtp_handle {
   bool prep_valid = false;    // Ubuf[cur ^ 1] holds the draws and graph rows of prep_iter
   uint32_t prep_iter = 0;
   int prep_grid = 0;          // SMs the rollout leaves free
+  int prep_spb = 1;           // graph paths per pass of a k_prepare block
   size_t prep_smem = 0;       // dynamic shared memory of a k_prepare block (a whole SM)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -468,6 +469,8 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, int work, Gen gen, 
     nx.local_mode = kLocalNoise;
     nx.U_mean = nullptr;
     if (!h->prep_local) nx.U_local = nullptr;
+    nx.paths_per_block = h->prep_spb;
+    nx.graph_blocks = (dm.P + h->prep_spb - 1) / h->prep_spb;
     if ((e = launch_prepare(nx, h->prep_grid, h->prep_smem, h->side)) != cudaSuccess) return e;
     if (ev) stage_event(ev[6], h->side, captured);
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
@@ -519,6 +522,13 @@ Dims dims_of(const mtp_problem& p) {
 // regenerated in every graph block's shared memory.
 bool global_graph(const Dims& dm) { return (long long)dm.M * dm.N * dm.n > 4096; }
 
+// Akima paths per block where blocks do not end the critical path: the
+// persistent preparation and the batched launch (measured on the 7-link arm:
+// 8 / 16 / 32 paths prepare an iteration's graph rows in 57 / 45 / 37 us; the
+// batch of 256 instances takes 3.78 / 3.72 / 3.70 ms; a lone unpipelined arm
+// generates in 16.4 / 18.4 / 25 us, where the last blocks set the time).
+constexpr int kWideAkimaPaths = 32;
+
 // Graph paths per block, at most 32: about 64K output elements per block for
 // B-spline rows, whose blocks otherwise repeat their fixed costs (two
 // barriers, the gather of the waypoints) for little work (measured on the
@@ -566,11 +576,12 @@ constexpr int kFullPrepareSMs = 64;
 // chain rollouts take one block per 32-128 candidates; the legged rollout
 // fills the GPU and is not pipelined.
 cudaError_t pipeline_plan(const mtp_problem& p, const Dims& dm, int paths_per_block, bool* on,
-                          bool* local, int* grid, size_t* smem) {
+                          bool* local, int* grid, size_t* smem, int* prep_spb) {
   *on = false;
   *local = false;
   *grid = 0;
   *smem = 0;
+  *prep_spb = paths_per_block;
   int dev = 0, sms = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -587,6 +598,10 @@ cudaError_t pipeline_plan(const mtp_problem& p, const Dims& dm, int paths_per_bl
   probe.graph_blocks = dm.P > 0 ? 1 : 0;
   probe.paths_per_block = paths_per_block;
   if (prepare_smem_need(probe) > *smem) return cudaSuccess;
+  // a persistent block passes over many paths: wider Akima passes there
+  probe.paths_per_block = std::max(paths_per_block, kWideAkimaPaths * (p.interp == MTP_INTERP_AKIMA));
+  while (probe.paths_per_block > paths_per_block && prepare_smem_need(probe) > *smem) probe.paths_per_block /= 2;
+  *prep_spb = std::max(probe.paths_per_block, paths_per_block);
   *on = true;
   *local = draws;
   *grid = free_sms;
@@ -643,7 +658,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   if ((e = init_candidate_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
   if ((e = init_select_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
   if ((e = pipeline_plan(p, dm, h->paths_per_block, &h->pipeline, &h->prep_local, &h->prep_grid,
-                         &h->prep_smem)) !=
+                         &h->prep_smem, &h->prep_spb)) !=
       cudaSuccess)
     return err(cuda_fail(h, e, "attributes"));
   if ((st = build_tables(h)) != MTP_OK) return err(st);
@@ -689,8 +704,9 @@ mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes)
   bool on = false, local = false;
   int grid = 0;
   size_t smem = 0;
+  int spb = 1;
   cudaError_t e = pipeline_plan(p, dm, paths_per_block_for(dm, p.interp, global_graph(dm)), &on, &local,
-                                &grid, &smem);
+                                &grid, &smem, &spb);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
   if (on) *bytes += r(rowsz * p.B * 4);  // the second candidate buffer of the pipelined plan step
   return MTP_OK;
@@ -1369,7 +1385,7 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
     // one launch gives every block the largest instance's shared memory, so
     // paths per block shrink until the instance fits kBatchGraphSmem (a
     // path's values do not depend on how paths are grouped into blocks)
-    c.paths_per_block = h->paths_per_block;
+    c.paths_per_block = std::max(h->paths_per_block, kWideAkimaPaths * (h->pr.interp == MTP_INTERP_AKIMA));
     c.graph_blocks = 1;  // counts the graph part in candidates_smem_bytes
     while (c.paths_per_block > 1 && candidates_smem_bytes(c) > kBatchGraphSmem) c.paths_per_block /= 2;
     c.graph_blocks = (dm.P + c.paths_per_block - 1) / c.paths_per_block;
