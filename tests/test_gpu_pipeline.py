@@ -146,3 +146,32 @@ def test_batch_run_between_pipelined_steps(mtp):
         mtp.mtp_destroy(g)
     for x, y in zip(res[0], res[1]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("flags,iters,profile", [
+    (0, 1, False),       # one graph launch: staged start state, u* written to pinned memory
+    (0, 3, False),
+    (0, 70, False),      # more than 64 iterations: the copies around chunked graphs
+    (0x2, 2, False),     # eager launches
+    (0, 2, True),        # profiling: the copies around the profiled graphs
+])
+def test_host_step_paths_match_device_step(mtp, flags, iters, profile):
+    """mtp_plan_step_host gives what mtp_plan_step gives a twin handle, call
+    after call, whichever route it takes."""
+    spec = dict(W.chain(links=3, B=1024, H=32, E=16), flags=flags)
+    h, t = mtp.mtp_create(spec), mtp.mtp_create(spec)
+    if profile:
+        mtp.mtp_set_profiling(h, True)
+    rng = np.random.default_rng(iters)
+    u_dev = torch.empty(spec["n"], device=DEV)
+    for call in range(3):
+        x0 = (np.asarray(spec["x0"]) + rng.uniform(-0.1, 0.1, size=spec["d"])).astype(np.float32)
+        u_host = np.full(spec["n"], np.nan, np.float32)
+        mtp.mtp_plan_step_host(h, x0, iters, u_host)
+        mtp.mtp_plan_step(t, torch.tensor(x0, device=DEV), iters, u_dev)
+        torch.cuda.synchronize()
+        assert np.array_equal(u_host, u_dev.cpu().numpy()), call
+        for a, b in zip(mtp.mtp_get_state(h), mtp.mtp_get_state(t)):
+            assert np.array_equal(a, b), call
+    mtp.mtp_destroy(h)
+    mtp.mtp_destroy(t)
