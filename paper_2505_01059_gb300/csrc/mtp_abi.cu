@@ -893,6 +893,59 @@ static void ensure_pipeline(mtp_handle* h) {
   }
 }
 
+// The CUDA graph of `chunk` iterations starting from buffer c0 (the first
+// iteration's draws prepared or not), captured on first use into `cache`.
+// With `events` (profiling) each iteration records its stage events; with
+// `x0_src` (pinned) the graph first uploads the start state from it, and the
+// last iteration's selection also writes u* to `ustar_dst` (pinned).
+static mtp_status chunk_graph(mtp_handle* h, std::map<int, cudaGraphExec_t>& cache, int chunk, int c0,
+                              bool prepared, bool events, const float* x0_src, float* ustar_dst,
+                              cudaGraphExec_t* out) {
+  const int key = chunk * 4 + c0 * 2 + (prepared ? 1 : 0);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return MTP_OK;
+  }
+  cudaError_t e;
+  cudaGraph_t graph;
+  if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return cuda_fail(h, e, "cudaStreamBeginCapture");
+  if (x0_src)
+    e = cudaMemcpyAsync(h->x0, x0_src, (size_t)h->dm.d * 4, cudaMemcpyHostToDevice, h->cap_stream);
+  for (int k = 0; k < chunk && e == cudaSuccess; ++k) {
+    cudaEvent_t* ev = events ? h->gevents.data() + kEvPerIter * k : nullptr;
+    int work;
+    Gen gen;
+    iteration_plan(h, c0, prepared, k, &work, &gen);
+    e = enqueue_iteration(h, h->cap_stream, work, gen, ev, true, k == chunk - 1 ? ustar_dst : nullptr);
+  }
+  if (e != cudaSuccess) {
+    cudaStreamEndCapture(h->cap_stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(h, e, "capture");
+  }
+  if ((e = cudaStreamEndCapture(h->cap_stream, &graph)) != cudaSuccess)
+    return cuda_fail(h, e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  cache.emplace(key, exec);
+  *out = exec;
+  return MTP_OK;
+}
+
+// Host bookkeeping of a launched chunk (see after_iteration).
+static void after_chunk(mtp_handle* h, int chunk, int c0, bool prepared) {
+  for (int k = 0; k < chunk; ++k) {
+    int work;
+    Gen gen;
+    iteration_plan(h, c0, prepared, k, &work, &gen);
+    after_iteration(h, work);
+  }
+}
+
 static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
   cudaError_t e;
   ensure_pipeline(h);
@@ -937,43 +990,16 @@ static mtp_status plan_device(mtp_handle* h, int32_t iters, cudaStream_t s) {
     const int chunk = left > kChunk ? kChunk : left;
     const int c0 = h->cur;
     const bool prepared = h->pipeline && h->prep_valid && h->prep_iter == h->iter_host;
-    const int key = chunk * 4 + c0 * 2 + (prepared ? 1 : 0);
-    auto it = cache.find(key);
-    if (it == cache.end()) {
-      cudaGraph_t graph;
-      if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return cuda_fail(h, e, "cudaStreamBeginCapture");
-      for (int k = 0; k < chunk; ++k) {
-        cudaEvent_t* ev = h->profiling ? h->gevents.data() + kEvPerIter * k : nullptr;
-        int work;
-        Gen gen;
-        iteration_plan(h, c0, prepared, k, &work, &gen);
-        if ((e = enqueue_iteration(h, h->cap_stream, work, gen, ev, true)) != cudaSuccess) {
-          cudaStreamEndCapture(h->cap_stream, &graph);
-          if (graph) cudaGraphDestroy(graph);
-          return cuda_fail(h, e, "capture");
-        }
-      }
-      if ((e = cudaStreamEndCapture(h->cap_stream, &graph)) != cudaSuccess)
-        return cuda_fail(h, e, "cudaStreamEndCapture");
-      cudaGraphExec_t exec;
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-      it = cache.emplace(key, exec).first;
-    }
-    if ((e = cudaGraphLaunch(it->second, s)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
-    for (int k = 0; k < chunk; ++k) {
-      int work;
-      Gen gen;
-      iteration_plan(h, c0, prepared, k, &work, &gen);
-      after_iteration(h, work);
-    }
+    cudaGraphExec_t exec;
+    mtp_status st = chunk_graph(h, cache, chunk, c0, prepared, h->profiling, nullptr, nullptr, &exec);
+    if (st != MTP_OK) return st;
+    if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    after_chunk(h, chunk, c0, prepared);
     if (h->profiling) {
       if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "profiled replay");
       for (int k = 0; k < chunk; ++k) {
-        mtp_status st = read_stage_events(h, h->gevents.data() + kEvPerIter * k, h->stage_acc);
-        if (st != MTP_OK) return st;
+        const mtp_status rs = read_stage_events(h, h->gevents.data() + kEvPerIter * k, h->stage_acc);
+        if (rs != MTP_OK) return rs;
       }
       h->stage_iters += chunk;
     }
@@ -1017,51 +1043,14 @@ static bool plan_host_graph(mtp_handle* h, const float* h_x0, int32_t iters, flo
   std::memcpy(h->x0_pin, h_x0, (size_t)h->dm.d * 4);
   const int c0 = h->cur;
   const bool prepared = h->pipeline && h->prep_valid && h->prep_iter == h->iter_host;
-  const int key = iters * 4 + c0 * 2 + (prepared ? 1 : 0);
-  auto it = h->hgraphs.find(key);
-  if (it == h->hgraphs.end()) {
-    cudaGraph_t graph;
-    if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
-      *st = cuda_fail(h, e, "cudaStreamBeginCapture");
-      return true;
-    }
-    e = cudaMemcpyAsync(h->x0, h->x0_pin, (size_t)h->dm.d * 4, cudaMemcpyHostToDevice, h->cap_stream);
-    for (int k = 0; k < iters && e == cudaSuccess; ++k) {
-      int work;
-      Gen gen;
-      iteration_plan(h, c0, prepared, k, &work, &gen);
-      e = enqueue_iteration(h, h->cap_stream, work, gen, nullptr, true,
-                            k == iters - 1 ? h->ustar_pin : nullptr);
-    }
-    if (e != cudaSuccess) {
-      cudaStreamEndCapture(h->cap_stream, &graph);
-      if (graph) cudaGraphDestroy(graph);
-      *st = cuda_fail(h, e, "capture");
-      return true;
-    }
-    if ((e = cudaStreamEndCapture(h->cap_stream, &graph)) != cudaSuccess) {
-      *st = cuda_fail(h, e, "cudaStreamEndCapture");
-      return true;
-    }
-    cudaGraphExec_t exec;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      *st = cuda_fail(h, e, "cudaGraphInstantiate");
-      return true;
-    }
-    it = h->hgraphs.emplace(key, exec).first;
-  }
-  if ((e = cudaGraphLaunch(it->second, s)) != cudaSuccess) {
+  cudaGraphExec_t exec;
+  *st = chunk_graph(h, h->hgraphs, iters, c0, prepared, false, h->x0_pin, h->ustar_pin, &exec);
+  if (*st != MTP_OK) return true;
+  if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) {
     *st = cuda_fail(h, e, "cudaGraphLaunch");
     return true;
   }
-  for (int k = 0; k < iters; ++k) {
-    int work;
-    Gen gen;
-    iteration_plan(h, c0, prepared, k, &work, &gen);
-    after_iteration(h, work);
-  }
+  after_chunk(h, iters, c0, prepared);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
     *st = cuda_fail(h, e, "cudaStreamSynchronize");
     return true;
