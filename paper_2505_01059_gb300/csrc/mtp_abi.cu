@@ -1,8 +1,10 @@
-// mtp_abi.cu -- the C ABI of include/mtp.h: problem validation, the handle's
-// device state, host precompute of the interpolation tables (Sec. 8 step
-// "host precompute": B-spline basis of Def. 2 by the closed-form cardinal
-// B-spline, Akima / straight-line piece table of Def. 3), and the launch
-// sequence of one planner iteration (Alg. 2), replayed as a CUDA graph.
+// mtp_abi.cu -- the single-instance part of the C ABI of include/mtp.h:
+// problem validation, the handle's device state, host precompute of the
+// interpolation tables (the B-spline basis of Def. 2 by the closed-form
+// cardinal B-spline, the Akima / straight-line piece table of Def. 3), and
+// the launch sequence of one planner iteration (Alg. 2), pipelined when the
+// rollout leaves SMs idle and replayed as a CUDA graph.  Batched planning is
+// in batch_abi.cu, serving in server.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -12,7 +14,7 @@
 #include <type_traits>
 #include <vector>
 
-#include "mtp_device.cuh"
+#include "handle.cuh"
 
 using namespace mtp;
 
@@ -22,84 +24,10 @@ thread_local std::string g_create_error;
 
 constexpr size_t kMaxSmem = 200 * 1024;
 
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-    else prev = -1;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
 }  // namespace
 
 void mtp::set_thread_error(const std::string& msg) { g_create_error = msg; }
 
-struct mtp_handle {
-  mtp_problem pr{};
-  Dims dm{};
-  int device = 0;
-  Key key{};
-  // interpolation tables
-  float* basis = nullptr;
-  int32_t* bfirst = nullptr;
-  int32_t* seg = nullptr;
-  float* delta = nullptr;
-  float inv_h = 1.f;
-  int paths_per_block = 1;
-  bool global_Z = false;  // Z written once per iteration instead of per graph block
-  // planner state
-  double* mu = nullptr;
-  double* sigma = nullptr;
-  float* mu_f = nullptr;     // FP32 copies read by the samplers
-  float* sigma_f = nullptr;
-  uint32_t* iter_dev = nullptr;
-  uint32_t iter_host = 0;
-  // scratch of one iteration
-  float* U = nullptr;  // candidates of the latest iteration: Ubuf[cur]
-  // Pipelined generation.  Everything costly in an iteration's candidates
-  // (the graph rows and the local rows' standard normal draws) depends only
-  // on the key and the iteration number, not on the mean and spread.  When
-  // the rollout leaves SMs idle, a single-instance iteration therefore
-  // makes the next iteration's graph rows (and, with many idle SMs, its
-  // draws) on those SMs while its rollout runs (on `side`), into the other
-  // candidate buffer; the next iteration then only makes (or finishes) its
-  // local rows and mean row.
-  bool pipeline = false;
-  bool prep_local = false;    // the local draws are prepared too (else only the graph rows)
-  float* Ubuf[2] = {nullptr, nullptr};
-  int cur = 0;                // Ubuf[cur] holds the latest iteration's candidates
-  bool prep_valid = false;    // Ubuf[cur ^ 1] holds the draws and graph rows of prep_iter
-  uint32_t prep_iter = 0;
-  int prep_grid = 0;          // SMs the rollout leaves free
-  int prep_spb = 1;           // graph paths per pass of a k_prepare block
-  size_t prep_smem = 0;       // dynamic shared memory of a k_prepare block (a whole SM)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  float* cost = nullptr;
-  int32_t* elite = nullptr;
-  double* weight = nullptr;
-  float* ustar = nullptr;
-  float* x0 = nullptr;
-  float* Z = nullptr;  // (M, N, n) graph of the current iteration (batched planning)
-  // replay
-  cudaStream_t cap_stream = nullptr;
-  std::map<int, cudaGraphExec_t> graphs;   // key: (iterations, cur, first prepared)
-  std::map<int, cudaGraphExec_t> hgraphs;  // the same with the host-pointer step's copies
-  float* x0_pin = nullptr;                 // pinned staging of mtp_plan_step_host: start state
-  float* ustar_pin = nullptr;              // and u*, written by the selection kernel
-  // profiling
-  bool profiling = false;
-  std::vector<cudaEvent_t> events;  // eager launches: kEvPerIter per iteration, read by mtp_stage_times
-  size_t ev_used = 0;
-  std::vector<cudaEvent_t> gevents;            // inside profiled graphs: kEvPerIter per iteration
-  std::map<int, cudaGraphExec_t> pgraphs;      // graphs with the stage events captured
-  double stage_acc[5] = {0, 0, 0, 0, 0};       // read from gevents after each profiled replay
-  int64_t stage_iters = 0;
-  std::string err;
-};
 
 namespace {
 
@@ -272,6 +200,9 @@ mtp_status build_tables(mtp_handle* h) {
   return MTP_OK;
 }
 
+}  // namespace
+
+namespace mtp {
 CandArgs cand_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter) {
   CandArgs a{};
   a.dm = h->dm;
@@ -295,6 +226,9 @@ CandArgs cand_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter) {
   }
   return a;
 }
+}  // namespace mtp
+
+namespace {
 
 // Blocks of 256 threads for the local rows: about `rows_per_thread` rows
 // per thread, each thread on one group of four elements, at most 8 blocks
@@ -315,6 +249,9 @@ int local_blocks_for(const mtp_handle* h, long long rows_plus_mean,
   return (int)blocks;
 }
 
+}  // namespace
+
+namespace mtp {
 RolloutArgs rollout_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter,
                          const float* x0, const float* U, int row0, int rows, float* cost) {
   RolloutArgs a{};
@@ -387,6 +324,9 @@ LeggedModel legged_model(const mtp_problem& p) {
   m.w_term = p.w_term;
   return m;
 }
+}  // namespace mtp
+
+namespace {
 
 // Candidate generation of one handle (graph rows, local rows, mean row as
 // `c` asks), with the graph written first when it is not regenerated per block.
@@ -521,13 +461,6 @@ Dims dims_of(const mtp_problem& p) {
 // A graph larger than 16 KB is written once per iteration rather than
 // regenerated in every graph block's shared memory.
 bool global_graph(const Dims& dm) { return (long long)dm.M * dm.N * dm.n > 4096; }
-
-// Akima paths per block where blocks do not end the critical path: the
-// persistent preparation and the batched launch (measured on the 7-link arm:
-// 8 / 16 / 32 paths prepare an iteration's graph rows in 57 / 45 / 37 us; the
-// batch of 256 instances takes 3.78 / 3.72 / 3.70 ms; a lone unpipelined arm
-// generates in 16.4 / 18.4 / 25 us, where the last blocks set the time).
-constexpr int kWideAkimaPaths = 32;
 
 // Graph paths per block, at most 32: about 64K output elements per block for
 // B-spline rows, whose blocks otherwise repeat their fixed costs (two
@@ -1154,531 +1087,6 @@ mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations) {
 mtp_status mtp_stage_times5(mtp_handle* h, double* ms5, int32_t* iterations) {
   if (!h || !ms5) return MTP_ERR_INVALID_ARG;
   return stage_times(h, ms5, iterations);
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------------------
-// Batched planning over many handles
-// ---------------------------------------------------------------------------
-
-namespace {
-
-struct BatchGroup {
-  int dyn = 0, n = 0;
-  int first = 0, count = 0;   // instances [first, first + count) of the sorted order
-  int model_first = 0;        // first model of this group in its dynamics' table
-  int rows_first = 0;         // offset of this group's row_start segment
-  int total_rows = 0;
-  int block = 128;
-  // this group's share of the generation, selection and update launches
-  int z_blocks = 0, cand_blocks = 0, local_blocks = 0, upd_threads = 0;
-  size_t cand_smem = 0, sel_smem = 0;
-};
-
-constexpr int kMaxGroups = 64;
-constexpr size_t kBatchGraphSmem = 40 * 1024;  // four graph blocks per SM
-
-// Device tables of a batch, packed into one device block that is refilled in
-// place from a pinned host mirror with one copy.  The layout depends on the
-// instance count, so the pointers are set on every fill.
-struct BatchTables {
-  int cap = 0;
-  size_t block_bytes = 0;
-  unsigned char* d_block = nullptr;
-  unsigned char* h_block = nullptr;  // pinned mirror
-  cudaEvent_t copied = nullptr;      // the mirror's last copy has been read
-  CandArgs* d_cand = nullptr;
-  int* d_cand_start = nullptr;
-  int* d_local_start = nullptr;
-  float** d_Z = nullptr;
-  int* d_z_start = nullptr;
-  RolloutArgs* d_ra = nullptr;  // in group order
-  PointMassModel* d_pm = nullptr;
-  ChainModel* d_cm = nullptr;
-  LeggedModel* d_lm = nullptr;
-  int* d_row_start = nullptr;  // one segment of (members + 1) entries per group
-  SelectArgs* d_sel = nullptr;
-  UpdateArgs* d_upd = nullptr;
-  int* d_warp_start = nullptr;
-  float** d_x0_dst = nullptr;
-  float** d_ustar_src = nullptr;
-  int* d_x0_off = nullptr;
-  int* d_us_off = nullptr;
-};
-
-// Packs the tables of `count` instances (n_pm point masses, n_cm chains,
-// n_lm legged robots, `groups` rollout groups) at 64-byte boundaries; with
-// `base` null it only returns the size.
-size_t layout_tables(BatchTables* t, unsigned char* base, int count, int n_pm, int n_cm, int n_lm,
-                     int groups) {
-  size_t off = 0;
-  auto take = [&](auto** field, size_t n) {
-    using T = std::remove_pointer_t<std::remove_reference_t<decltype(*field)>>;
-    off = (off + 63) & ~size_t(63);
-    if (base) *field = reinterpret_cast<T*>(base + off);
-    off += sizeof(T) * n;
-  };
-  BatchTables dummy;
-  BatchTables* d = t ? t : &dummy;
-  take(&d->d_cand, count);
-  take(&d->d_cand_start, count + 1);
-  take(&d->d_local_start, count + 1);
-  take(&d->d_Z, count);
-  take(&d->d_z_start, count + 1);
-  take(&d->d_ra, count);
-  take(&d->d_pm, n_pm);
-  take(&d->d_cm, n_cm);
-  take(&d->d_lm, n_lm);
-  take(&d->d_row_start, count + groups);
-  take(&d->d_sel, count);
-  take(&d->d_upd, count);
-  take(&d->d_warp_start, count + 1);
-  take(&d->d_x0_dst, count);
-  take(&d->d_ustar_src, count);
-  take(&d->d_x0_off, count + 1);
-  take(&d->d_us_off, count + 1);
-  return off;
-}
-
-}  // namespace
-
-struct mtp_batch {
-  std::vector<mtp_handle*> hs;  // in the caller's order
-  int device = 0;
-  BatchTables t;
-  int count = 0;
-  std::vector<BatchGroup> groups;
-  std::map<std::pair<int, int>, int> tuned;  // (dyn, n) -> block chosen by the autotuner
-  std::vector<int> x0_off, us_off;
-  cudaStream_t cap_stream = nullptr;
-  cudaEvent_t fork_ev = nullptr;
-  cudaStream_t group_stream[kMaxGroups] = {};
-  cudaEvent_t group_done[kMaxGroups] = {};
-  std::map<int, cudaGraphExec_t> graphs;  // key: graph_key(iterations, cur, first prepared)
-  int runs_since_fill = 0;
-  std::string err;
-};
-
-namespace {
-
-mtp_status batch_fail(mtp_batch* b, mtp_status st, const std::string& msg) {
-  if (b) b->err = msg;
-  g_create_error = msg;
-  return st;
-}
-
-void drop_graphs(mtp_batch* b) {
-  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
-  b->graphs.clear();
-}
-
-void free_batch(mtp_batch* b) {
-  drop_graphs(b);
-  if (b->t.d_block) cudaFree(b->t.d_block);
-  if (b->t.h_block) cudaFreeHost(b->t.h_block);
-  if (b->t.copied) cudaEventDestroy(b->t.copied);
-  for (int g = 0; g < kMaxGroups; ++g) {
-    if (b->group_stream[g]) cudaStreamDestroy(b->group_stream[g]);
-    if (b->group_done[g]) cudaEventDestroy(b->group_done[g]);
-  }
-  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
-  delete b;
-}
-
-cudaError_t alloc_batch(mtp_batch* b, int cap) {
-  BatchTables& t = b->t;
-  t.cap = cap;
-  // every instance could be of any dynamics and every one its own group
-  t.block_bytes = layout_tables(nullptr, nullptr, cap, cap, cap, cap, std::min(cap, kMaxGroups));
-  cudaError_t e;
-  if ((e = cudaMalloc((void**)&t.d_block, t.block_bytes)) ||
-      (e = cudaMallocHost((void**)&t.h_block, t.block_bytes)) ||
-      (e = cudaEventCreateWithFlags(&t.copied, cudaEventDisableTiming)) ||
-      (e = cudaEventRecord(t.copied, 0)) ||
-      (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) ||
-      (e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)))
-    return e;
-  return cudaSuccess;
-}
-
-int group_key_n(const mtp_handle* h) {
-  return h->pr.dyn == MTP_DYN_POINTMASS ? h->dm.n : h->pr.n_links;
-}
-
-// Fills the batch's tables for `handles` (at most the capacity, distinct,
-// on the batch's device) with one host-to-device copy on `s`.  Instances are
-// grouped by (dynamics, dimension) for the rollouts; everything else keeps
-// the caller's order.  Captured graphs are dropped: their launches baked in
-// the previous layout.
-cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cudaStream_t s) {
-  BatchTables& t = b->t;
-  cudaError_t e;
-  if ((e = cudaEventSynchronize(t.copied))) return e;  // the mirror is free again
-  drop_graphs(b);
-  b->runs_since_fill = 0;
-  b->count = 0;  // unusable until this fill has succeeded
-  b->hs.clear();
-  // rollout groups: sorted by (dynamics, dimension), stable in the caller's order
-  std::vector<int> order(count);
-  for (int i = 0; i < count; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    const int dx = handles[x]->pr.dyn, dy = handles[y]->pr.dyn;
-    if (dx != dy) return dx < dy;
-    return group_key_n(handles[x]) < group_key_n(handles[y]);
-  });
-  b->groups.clear();
-  int n_dyn[3] = {0, 0, 0};
-  for (int pos = 0; pos < count; ++pos) {
-    const mtp_handle* h = handles[order[pos]];
-    const int dyn = h->pr.dyn, n = group_key_n(h);
-    if (b->groups.empty() || b->groups.back().dyn != dyn || b->groups.back().n != n) {
-      if ((int)b->groups.size() == kMaxGroups) return cudaErrorInvalidValue;
-      BatchGroup g;
-      g.dyn = dyn;
-      g.n = n;
-      g.first = pos;
-      g.model_first = n_dyn[dyn];
-      auto it = b->tuned.find({dyn, n});
-      g.block = it != b->tuned.end() ? it->second : 128;
-      b->groups.push_back(g);
-    }
-    ++b->groups.back().count;
-    ++n_dyn[dyn];
-  }
-  layout_tables(&t, t.h_block, count, n_dyn[MTP_DYN_POINTMASS], n_dyn[MTP_DYN_CHAIN],
-                n_dyn[MTP_DYN_LEGGED], (int)b->groups.size());
-  // host views of the mirror (same offsets as the device block)
-  BatchTables hv = t;
-  const size_t used = layout_tables(&t, t.d_block, count, n_dyn[MTP_DYN_POINTMASS],
-                                    n_dyn[MTP_DYN_CHAIN], n_dyn[MTP_DYN_LEGGED], (int)b->groups.size());
-  // candidate generation, selection and update tables in group order, so
-  // that each group's stream launches them over a contiguous range
-  hv.d_cand_start[0] = hv.d_z_start[0] = hv.d_local_start[0] = hv.d_warp_start[0] = 0;
-  for (int pos = 0; pos < count; ++pos) {
-    mtp_handle* h = handles[order[pos]];
-    // a batch makes every iteration's candidates in full, in the first buffer
-    h->cur = 0;
-    h->U = h->Ubuf[0];
-    h->prep_valid = false;
-    const Dims& dm = h->dm;
-    const size_t Hn = (size_t)dm.H * dm.n;
-    CandArgs c = cand_args(h, 0, h->iter_dev);
-    c.U_graph = h->U + Hn * dm.L;
-    c.graph_rows = dm.P;
-    c.U_local = h->U;
-    c.local_rows = dm.L;
-    c.U_mean = h->U + Hn * (dm.B - 1);
-    c.Z_global = h->Z;
-    // one launch gives every block the largest instance's shared memory, so
-    // paths per block shrink until the instance fits kBatchGraphSmem (a
-    // path's values do not depend on how paths are grouped into blocks)
-    c.paths_per_block = std::max(h->paths_per_block, kWideAkimaPaths * (h->pr.interp == MTP_INTERP_AKIMA));
-    c.graph_blocks = 1;  // counts the graph part in candidates_smem_bytes
-    while (c.paths_per_block > 1 && candidates_smem_bytes(c) > kBatchGraphSmem) c.paths_per_block /= 2;
-    c.graph_blocks = (dm.P + c.paths_per_block - 1) / c.paths_per_block;
-    hv.d_Z[pos] = h->Z;
-    hv.d_z_start[pos + 1] = hv.d_z_start[pos] + (dm.M * dm.N * ((dm.n + 3) / 4) + 255) / 256;
-    const long long items = ((long long)dm.L + 1) * (((long long)Hn + 3) / 4);
-    hv.d_cand[pos] = c;
-    hv.d_cand_start[pos + 1] = hv.d_cand_start[pos] + c.graph_blocks;  // local rows run apart
-    hv.d_local_start[pos + 1] = hv.d_local_start[pos] + (int)std::max<long long>(1, (items + 1023) / 1024);
-    hv.d_sel[pos] = SelectArgs{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
-                               h->elite, h->weight, h->ustar, nullptr, nullptr};
-    hv.d_upd[pos] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
-                               h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
-    hv.d_warp_start[pos + 1] = hv.d_warp_start[pos] + update_threads(dm.H, dm.n);
-  }
-  for (auto& g : b->groups) {
-    const int a0 = g.first, a1 = g.first + g.count;
-    g.z_blocks = hv.d_z_start[a1] - hv.d_z_start[a0];
-    g.cand_blocks = hv.d_cand_start[a1] - hv.d_cand_start[a0];
-    g.local_blocks = hv.d_local_start[a1] - hv.d_local_start[a0];
-    g.upd_threads = hv.d_warp_start[a1] - hv.d_warp_start[a0];
-    g.cand_smem = g.sel_smem = 0;
-    for (int pos = a0; pos < a1; ++pos) {
-      g.cand_smem = std::max(g.cand_smem, candidates_smem_bytes(hv.d_cand[pos]));
-      g.sel_smem = std::max(g.sel_smem, select_smem_bytes(hv.d_sel[pos].B, hv.d_sel[pos].E));
-    }
-  }
-  // rollouts, in group order; whole warps per instance
-  int rs = 0;
-  for (auto& g : b->groups) {
-    g.rows_first = rs;
-    int* row = hv.d_row_start + rs;
-    row[0] = 0;
-    for (int j = 0; j < g.count; ++j) {
-      mtp_handle* h = handles[order[g.first + j]];
-      hv.d_ra[g.first + j] = rollout_args(h, 0, h->iter_dev, h->x0, h->U, 0, h->dm.B, h->cost);
-      const int m = g.model_first + j;
-      if (g.dyn == MTP_DYN_POINTMASS) hv.d_pm[m] = pointmass_model(h->pr);
-      else if (g.dyn == MTP_DYN_LEGGED) hv.d_lm[m] = legged_model(h->pr);
-      else hv.d_cm[m] = chain_model(h->pr);
-      row[j + 1] = row[j] + ((h->dm.B + 31) / 32) * 32;
-    }
-    g.total_rows = row[g.count];
-    rs += g.count + 1;
-  }
-  // packing of x0 and u*, in the caller's order
-  b->x0_off.assign(count + 1, 0);
-  b->us_off.assign(count + 1, 0);
-  hv.d_x0_off[0] = hv.d_us_off[0] = 0;
-  for (int i = 0; i < count; ++i) {
-    mtp_handle* h = handles[i];
-    hv.d_x0_dst[i] = h->x0;
-    hv.d_ustar_src[i] = h->ustar;
-    b->x0_off[i + 1] = b->x0_off[i] + h->dm.d;
-    b->us_off[i + 1] = b->us_off[i] + h->dm.n;
-    hv.d_x0_off[i + 1] = b->x0_off[i + 1];
-    hv.d_us_off[i + 1] = b->us_off[i + 1];
-  }
-  if ((e = cudaMemcpyAsync(t.d_block, t.h_block, used, cudaMemcpyHostToDevice, s)) ||
-      (e = cudaEventRecord(t.copied, s)))
-    return e;
-  b->hs.assign(handles, handles + count);
-  b->count = count;
-  for (size_t g = 0; g < b->groups.size(); ++g) {
-    if (!b->group_stream[g]) {
-      if ((e = cudaStreamCreateWithFlags(&b->group_stream[g], cudaStreamNonBlocking)) ||
-          (e = cudaEventCreateWithFlags(&b->group_done[g], cudaEventDisableTiming)))
-        return e;
-    }
-  }
-  return cudaSuccess;
-}
-
-cudaError_t launch_group(const mtp_batch* b, const BatchGroup& g, int block, cudaStream_t s) {
-  const BatchTables& t = b->t;
-  const RolloutArgs* ra = t.d_ra + g.first;
-  const int* rs = t.d_row_start + g.rows_first;
-  if (g.dyn == MTP_DYN_POINTMASS)
-    return launch_rollout_pointmass_batch(ra, t.d_pm + g.model_first, rs, g.count, g.total_rows, g.n, block, s);
-  if (g.dyn == MTP_DYN_LEGGED)  // fixed 64-thread blocks (shared-memory staging)
-    return launch_rollout_legged_batch(ra, t.d_lm + g.model_first, rs, g.count, g.total_rows, g.n, s);
-  return launch_rollout_chain_batch(ra, t.d_cm + g.model_first, rs, g.count, g.total_rows, g.n, block, s);
-}
-
-// One batched Alg. 2 iteration.  Each (dynamics, dimension) group runs its
-// whole iteration on its own stream: graphs, graph paths and local rows of
-// its instances, its rollouts, one selection block per instance, the update.
-// Groups overlap one another (one group's generation fills the issue slots
-// that the others' latency-bound rollouts leave idle).
-cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
-  cudaError_t e;
-  const BatchTables& t = b->t;
-  if ((e = cudaEventRecord(b->fork_ev, s))) return e;
-  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
-    const BatchGroup& g = b->groups[gi];
-    cudaStream_t gs = b->group_stream[gi];
-    const int f = g.first;
-    if ((e = cudaStreamWaitEvent(gs, b->fork_ev, 0))) return e;
-    if ((e = launch_graph_Z_batch(t.d_cand + f, t.d_Z + f, t.d_z_start + f, g.count, g.z_blocks, gs))) return e;
-    if ((e = launch_candidates_batch(t.d_cand + f, t.d_cand_start + f, g.count, g.cand_blocks, g.cand_smem, gs)))
-      return e;
-    if ((e = launch_local_batch(t.d_cand + f, t.d_local_start + f, g.count, g.local_blocks, gs))) return e;
-    if ((e = launch_group(b, g, g.block, gs))) return e;
-    if ((e = launch_select_batch(t.d_sel + f, g.count, g.sel_smem, gs))) return e;
-    if ((e = launch_update_batch(t.d_upd + f, t.d_warp_start + f, g.count, g.upd_threads, gs))) return e;
-    if ((e = cudaEventRecord(b->group_done[gi], gs))) return e;
-  }
-  for (size_t gi = 0; gi < b->groups.size(); ++gi)
-    if ((e = cudaStreamWaitEvent(s, b->group_done[gi], 0))) return e;
-  return cudaSuccess;
-}
-
-// scatter x0 -> iterations -> gather u*.  The first run after a fill
-// launches eagerly; later runs over the same layout replay captured graphs.
-cudaError_t run_batch(mtp_batch* b, const float* d_x0, int iters, float* d_ustar, cudaStream_t s) {
-  const bool graphs = b->runs_since_fill++ > 0;
-  cudaError_t e = launch_scatter(d_x0, b->t.d_x0_dst, b->t.d_x0_off, b->count, s);
-  if (e != cudaSuccess) return e;
-  if (!graphs) {
-    for (int k = 0; k < iters; ++k)
-      if ((e = enqueue_batch_iteration(b, s))) return e;
-  } else {
-    int left = iters;
-    while (left > 0) {
-      const int chunk = left > 64 ? 64 : left;
-      auto it = b->graphs.find(chunk);
-      if (it == b->graphs.end()) {
-        cudaGraph_t graph;
-        if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal))) return e;
-        for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = enqueue_batch_iteration(b, b->cap_stream);
-        cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
-        if (e != cudaSuccess) return e;
-        if (e2 != cudaSuccess) return e2;
-        cudaGraphExec_t exec;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return e;
-        it = b->graphs.emplace(chunk, exec).first;
-      }
-      if ((e = cudaGraphLaunch(it->second, s))) return e;
-      left -= chunk;
-    }
-  }
-  e = launch_gather(b->t.d_ustar_src, b->t.d_us_off, d_ustar, b->count, s);
-  if (e != cudaSuccess) return e;
-  for (mtp_handle* h : b->hs) {
-    h->iter_host += (uint32_t)iters;
-    h->cur = 0;  // the tables point at the first buffer (set when they were filled)
-    h->U = h->Ubuf[0];
-    h->prep_valid = false;
-  }
-  return cudaSuccess;
-}
-
-}  // namespace
-
-extern "C" {
-
-static mtp_status check_batch_handles(mtp_handle* const* handles, int32_t count, int dev) {
-  for (int i = 0; i < count; ++i) {
-    if (!handles[i]) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch: null handle");
-    if (handles[i]->device != dev)
-      return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch: handles must live on the batch's device");
-    for (int j = 0; j < i; ++j)
-      if (handles[j] == handles[i]) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch: repeated handle");
-  }
-  return MTP_OK;
-}
-
-mtp_status mtp_batch_reserve(int32_t capacity, mtp_batch** out) {
-  if (!out || capacity < 1) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_reserve: bad argument");
-  *out = nullptr;
-  mtp_batch* b = new mtp_batch();
-  cudaGetDevice(&b->device);
-  cudaError_t e = init_candidate_attributes();
-  if (e == cudaSuccess) e = init_select_attributes();
-  if (e == cudaSuccess) e = alloc_batch(b, capacity);
-  if (e != cudaSuccess) {
-    mtp_status st = batch_fail(nullptr, e == cudaErrorMemoryAllocation ? MTP_ERR_OUT_OF_MEMORY : MTP_ERR_CUDA,
-                               std::string("batch_reserve: ") + cudaGetErrorString(e));
-    free_batch(b);
-    return st;
-  }
-  *out = b;
-  return MTP_OK;
-}
-
-mtp_status mtp_batch_fill(mtp_batch* b, mtp_handle* const* handles, int32_t count, void* stream) {
-  if (!b || !handles || count < 1 || count > b->t.cap)
-    return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_fill: bad argument (count must be 1 .. capacity)");
-  mtp_status st = check_batch_handles(handles, count, b->device);
-  if (st != MTP_OK) return batch_fail(b, st, g_create_error);
-  DeviceGuard guard(b->device);
-  cudaError_t e = fill_batch(b, handles, count, (cudaStream_t)stream);
-  if (e == cudaErrorInvalidValue)
-    return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_fill: more than 64 (dynamics, dimension) groups");
-  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch_fill: ") + cudaGetErrorString(e));
-  return MTP_OK;
-}
-
-mtp_status mtp_batch_create(mtp_handle* const* handles, int32_t count, mtp_batch** out) {
-  if (!handles || !out || count < 1) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch_create: bad argument");
-  *out = nullptr;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  mtp_status st = check_batch_handles(handles, count, dev);
-  if (st != MTP_OK) return st;
-  mtp_batch* b = nullptr;
-  if ((st = mtp_batch_reserve(count, &b)) != MTP_OK) return st;
-  if ((st = mtp_batch_fill(b, handles, count, b->cap_stream)) != MTP_OK) {
-    g_create_error = b->err;
-    free_batch(b);
-    return st;
-  }
-  cudaError_t e = cudaStreamSynchronize(b->cap_stream);
-  if (e != cudaSuccess) {
-    free_batch(b);
-    return batch_fail(nullptr, MTP_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
-  }
-  *out = b;
-  return MTP_OK;
-}
-
-mtp_status mtp_batch_destroy(mtp_batch* b) {
-  if (!b) return MTP_ERR_INVALID_ARG;
-  DeviceGuard g(b->device);
-  cudaDeviceSynchronize();
-  free_batch(b);
-  return MTP_OK;
-}
-
-mtp_status mtp_batch_layout(const mtp_batch* b, int32_t* x0_offset, int32_t* ustar_offset) {
-  if (!b || b->count < 1) return MTP_ERR_INVALID_ARG;
-  const size_t c = b->hs.size() + 1;
-  if (x0_offset) std::copy(b->x0_off.begin(), b->x0_off.begin() + c, x0_offset);
-  if (ustar_offset) std::copy(b->us_off.begin(), b->us_off.begin() + c, ustar_offset);
-  return MTP_OK;
-}
-
-mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, float* d_ustar,
-                               void* stream) {
-  if (!b || !d_x0 || !d_ustar || iters < 1 || b->count < 1)
-    return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_plan_step: bad argument (or batch never filled)");
-  DeviceGuard guard(b->device);
-  cudaError_t e = run_batch(b, d_x0, iters, d_ustar, (cudaStream_t)stream);
-  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch_plan_step: ") + cudaGetErrorString(e));
-  return MTP_OK;
-}
-
-mtp_status mtp_batch_shift(mtp_batch* b, int32_t k, void* stream) {
-  if (!b || k < 0 || b->count < 1) return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_shift: bad argument");
-  DeviceGuard guard(b->device);
-  cudaError_t e = launch_shift_batch(b->t.d_upd, b->count, k, (cudaStream_t)stream);
-  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("batch_shift: ") + cudaGetErrorString(e));
-  return MTP_OK;
-}
-
-mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_groups, void* stream) {
-  if (!b) return MTP_ERR_INVALID_ARG;
-  if (b->count < 1) return batch_fail(b, MTP_ERR_INVALID_ARG, "autotune: batch never filled");
-  DeviceGuard guard(b->device);
-  (void)stream;
-  cudaEventSynchronize(b->t.copied);  // the tables may have been filled on another stream
-  const int cand[3] = {32, 64, 128};  // the rollout kernels are bounded at 128 threads
-  cudaEvent_t t0, t1;
-  cudaEventCreate(&t0);
-  cudaEventCreate(&t1);
-  cudaError_t e = cudaSuccess;
-  for (auto& g : b->groups) {
-    if (g.dyn == MTP_DYN_LEGGED) continue;  // fixed block size
-    float best = 1e30f;
-    int best_block = g.block;
-    for (int block : cand) {
-      float ms_min = 1e30f;
-      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-        cudaEventRecord(t0, b->cap_stream);
-        e = launch_group(b, g, block, b->cap_stream);
-        cudaEventRecord(t1, b->cap_stream);
-        cudaEventSynchronize(t1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, t0, t1);
-        ms_min = std::min(ms_min, ms);
-      }
-      if (ms_min < best) {
-        best = ms_min;
-        best_block = block;
-      }
-    }
-    g.block = best_block;
-    b->tuned[{g.dyn, g.n}] = best_block;
-  }
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
-  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);  // tiles changed: recapture
-  b->graphs.clear();
-  if (n_groups) *n_groups = (int32_t)b->groups.size();
-  if (blocks_out)
-    for (size_t i = 0; i < b->groups.size(); ++i) {
-      blocks_out[3 * i + 0] = b->groups[i].dyn;
-      blocks_out[3 * i + 1] = b->groups[i].n;
-      blocks_out[3 * i + 2] = b->groups[i].block;
-    }
-  return MTP_OK;
 }
 
 }  // extern "C"
