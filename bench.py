@@ -104,13 +104,24 @@ KERNEL_HEADERS = ("paper_2505_01059_gb300/csrc/rollout_common.cuh",
                   "paper_2505_01059_gb300/csrc/mtp_device.cuh", "include/mtp.h")
 
 
+def _code_text(path: str) -> str:
+    """A C / CUDA source with its comments removed and its whitespace
+    collapsed: what the compiler sees, less the prose."""
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_digest(kernel_file: str) -> str:
-    """sha256 over a rollout kernel's source file and the headers it is
-    compiled with, so that a change to either retires its profile."""
+    """sha256 over the code of a rollout kernel's source file and of the
+    headers it is compiled with (comments and whitespace left out), so that
+    a change to the code of either retires its profile."""
     h = hashlib.sha256()
     for rel in ("paper_2505_01059_gb300/csrc/" + kernel_file,) + KERNEL_HEADERS:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        h.update(_code_text(os.path.join(ROOT, rel)).encode())
+        h.update(b"\0")
     return h.hexdigest()
 
 

@@ -148,6 +148,11 @@ typedef struct mtp_buffers {
   uint32_t* iter;  /* device iteration counter */
 } mtp_buffers;
 
+/* One planning problem's resident state.  A handle is used by one host
+ * thread at a time (calls on it are not synchronised with one another), and
+ * its work on the GPU is ordered by the streams the caller passes: calls on
+ * different streams must be ordered by the caller.  Different handles are
+ * independent. */
 typedef struct mtp_handle mtp_handle;
 
 /* sizeof(mtp_problem) as compiled into the library, so a binding can check
