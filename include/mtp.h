@@ -48,7 +48,7 @@ typedef enum {
   MTP_ERR_ADMISSION = 4,     /* serving: over the memory budget, robot count or queue depth */
   MTP_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
   MTP_ERR_NOT_READY = 6,     /* serving: the result is not there yet */
-  MTP_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+  MTP_ERR_UNSUPPORTED = 7    /* valid request the library does not implement */
 } mtp_status;
 
 typedef enum { MTP_DYN_POINTMASS = 0, MTP_DYN_CHAIN = 1, MTP_DYN_LEGGED = 2 } mtp_dyn;
