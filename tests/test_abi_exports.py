@@ -82,3 +82,20 @@ def test_workloads_hold_no_planner_arithmetic():
         elif isinstance(node, ast.ImportFrom):
             mods.add(node.module)
     assert mods <= {"numpy", "__future__"}, mods
+
+
+@pytest.mark.parametrize("bad,word", [
+    (dict(E=0), "E"), (dict(E=10_000), "E"), (dict(beta=1.5), "beta"), (dict(alpha=1.0), "alpha"),
+    (dict(M=1), "M"), (dict(sigma_min=0.0), "sigma"), (dict(interp="bspline", degree=9), "degree"),
+    (dict(dt=0.0), "dt"), (dict(B=0), "B"),
+])
+def test_invalid_problems_rejected_before_any_device_work(lib, bad, word):
+    """mtp_create validates the problem on the host first: an invalid one is
+    refused with MTP_ERR_INVALID_ARG and a message naming the field, with or
+    without a GPU."""
+    from paper_2505_01059_gb300 import mtp, workloads as W
+    spec = dict(W.pointmass(B=512), **bad)
+    with pytest.raises(mtp.MtpError) as ei:
+        mtp.mtp_create(spec)
+    assert ei.value.status == 1
+    assert word.lower() in str(ei.value).lower()
