@@ -549,7 +549,7 @@ cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t 
 cudaError_t launch_graph_Z(const CandArgs& a, float* Z, cudaStream_t s) {
   const int items = a.dm.M * a.dm.N * ((a.dm.n + 3) / 4);
   int blocks = (items + kThreads - 1) / kThreads;
-  if (blocks > 152) blocks = 152;
+  if (blocks > device_sms()) blocks = device_sms();
   if (blocks <= 0) return cudaSuccess;
   k_graph_Z<<<blocks, kThreads, 0, s>>>(a, Z);
   return cudaGetLastError();

@@ -662,7 +662,7 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Lanes per element: as many as keep roughly 38K threads busy, up to a warp.
+// Lanes per element: as many as keep about 256 threads per SM busy, up to a warp.
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   const int Hn = a.H * a.n;
   // lanes per element: enough threads to spread the gathers over the GPU.
@@ -670,7 +670,8 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   // lanes win even though each lane repeats the FP64 butterfly (8 lanes per
   // element measured slower than 32 on the 7-link arm workload)
   int G = 1;
-  while (G < 32 && (long long)Hn * G < 152 * 256) G <<= 1;
+  const long long want = (long long)device_sms() * 256;
+  while (G < 32 && (long long)Hn * G < want) G <<= 1;
   const long long threads = (long long)Hn * G;
   const int blocks = (int)((threads + kUpdThreads - 1) / kUpdThreads);
   switch (G) {

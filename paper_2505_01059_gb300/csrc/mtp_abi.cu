@@ -6,6 +6,7 @@
 // rollout leaves SMs idle and replayed as a CUDA graph.  Batched planning is
 // in batch_abi.cu, serving in server.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -104,7 +105,7 @@ mtp_status validate(const mtp_problem& p) {
   for (int i = 0; i < p.ctrl_dim; ++i)
     if (!(p.u_min[i] < p.u_max[i]) || !std::isfinite(p.u_min[i]) || !std::isfinite(p.u_max[i]))
       return bad("control box: need finite u_min < u_max");
-  if (p.M < 2 || p.M > 64) return bad("M must be in 2..64");
+  if (p.M < 1 || p.M > 64) return bad("M must be in 1..64");
   if (p.N < 1) return bad("N must be >= 1");
   if (p.B < 1 || p.B > (1 << 24)) return bad("B must be in 1..2^24");
   if (p.E < 1 || p.E > p.B) return bad("E must be in 1..B");
@@ -126,6 +127,20 @@ mtp_status validate(const mtp_problem& p) {
   if ((p.flags & MTP_FLAG_BF16_BASIS) && p.interp != MTP_INTERP_BSPLINE)
     return fail(nullptr, MTP_ERR_UNSUPPORTED, "the BF16 basis applies to B-spline interpolation only");
   return MTP_OK;
+}
+
+// A one-layer graph (M = 1) makes constant paths whatever the interpolation
+// (each path is its single waypoint held over the horizon).  The handle runs
+// that as the degree-0 B-spline over one basis function, which is 1 at every
+// step; no contraction rounds the waypoint, so BF16 operands do not apply.
+mtp_problem normalized(const mtp_problem& in) {
+  mtp_problem p = in;
+  if (p.M == 1) {
+    p.interp = MTP_INTERP_BSPLINE;
+    p.bspline_degree = 0;
+    p.flags &= ~MTP_FLAG_BF16_BASIS;
+  }
+  return p;
 }
 
 template <class T>
@@ -203,6 +218,22 @@ mtp_status build_tables(mtp_handle* h) {
 }  // namespace
 
 namespace mtp {
+int device_sms() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < kMaxDevices) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    sms = 1;
+  if (dev < kMaxDevices) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
 CandArgs cand_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter) {
   CandArgs a{};
   a.dm = h->dm;
@@ -244,7 +275,8 @@ int local_blocks_for(const mtp_handle* h, long long rows_plus_mean,
   const long long G = ((long long)h->dm.H * h->dm.n + 3) / 4;
   long long items = rows_plus_mean * G;
   long long blocks = (items + 256LL * rows_per_thread - 1) / (256LL * rows_per_thread);
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  const long long cap = (long long)mtp::device_sms() * 8;
+  if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   return (int)blocks;
 }
@@ -573,7 +605,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   mtp_status st = validate(*problem);
   if (st != MTP_OK) return st;
   mtp_handle* h = new mtp_handle();
-  h->pr = *problem;
+  h->pr = normalized(*problem);
   const mtp_problem& p = h->pr;
   cudaGetDevice(&h->device);
   Dims& dm = h->dm;
@@ -624,7 +656,7 @@ mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes)
   if (!problem || !bytes) return fail(nullptr, MTP_ERR_INVALID_ARG, "null argument");
   mtp_status st = validate(*problem);
   if (st != MTP_OK) return st;
-  const mtp_problem& p = *problem;
+  const mtp_problem p = normalized(*problem);
   const uint64_t rowsz = (uint64_t)p.horizon * p.ctrl_dim;
   auto r = [](uint64_t b) { return (b + 511) & ~uint64_t(511); };  // allocation granularity
   *bytes = r((uint64_t)p.horizon * p.M * 4) + 3 * r((uint64_t)p.horizon * 4)  // tables

@@ -207,6 +207,9 @@ struct UpdateArgs {
 
 // host-side launchers (defined in the .cu files)
 void set_thread_error(const std::string& msg);  // text for mtp_last_error(NULL)
+// Streaming multiprocessors of the current device, queried once per device
+// and cached (launch shapes are sized from it, never from a fixed count).
+int device_sms();
 size_t candidates_smem_bytes(const CandArgs& a);
 cudaError_t init_candidate_attributes();
 cudaError_t init_select_attributes();

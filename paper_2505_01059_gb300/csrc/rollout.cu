@@ -24,8 +24,9 @@ constexpr int kThreads = 128;
 // Threads per block: fill as many SMs as the batch allows (one thread per
 // candidate; small batches get one warp per block).
 inline int rollout_block(int rows) {
+  const int sms = device_sms();
   int bd = 128;
-  while (bd > 32 && (rows + bd - 1) / bd < 152) bd >>= 1;
+  while (bd > 32 && (rows + bd - 1) / bd < sms) bd >>= 1;
   return bd;
 }
 

@@ -462,9 +462,16 @@ def mtp_elite_update_noalloc(cost, U, E: int, lam: float, alpha: float, sigma_mi
                              update_rule: str, mu, sigma, elite=None, ustar=None, stream=None):
     """The handle-free elite update: cost (B), U (B, H, n) float32; mu, sigma
     (H, n) float64 CUDA tensors updated in place; elite (E) int32 and ustar
-    (n) float32 optional outputs.  Allocates nothing."""
+    (n) float32 optional outputs.  Allocates nothing.  The library runs the
+    call on the current CUDA device, so every tensor must live there."""
     import torch
     B, H, n = U.shape
+    dev = torch.cuda.current_device()
+    for name, t in (("cost", cost), ("U", U), ("mu", mu), ("sigma", sigma), ("elite", elite),
+                    ("ustar", ustar)):
+        if t is not None and getattr(t, "is_cuda", False) and t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, but the current device is "
+                             f"cuda:{dev}")
     _check(load_library().mtp_elite_update_noalloc(
         _dptr(cost, _f32(), B, "cost"), _dptr(U, _f32(), B * H * n, "U"), B, E, H, n,
         float(lam), float(alpha), float(sigma_min), UPDATE[update_rule],

@@ -86,7 +86,7 @@ def test_workloads_hold_no_planner_arithmetic():
 
 @pytest.mark.parametrize("bad,word", [
     (dict(E=0), "E"), (dict(E=10_000), "E"), (dict(beta=1.5), "beta"), (dict(alpha=1.0), "alpha"),
-    (dict(M=1), "M"), (dict(sigma_min=0.0), "sigma"), (dict(interp="bspline", degree=9), "degree"),
+    (dict(M=0), "M"), (dict(sigma_min=0.0), "sigma"), (dict(interp="bspline", degree=9), "degree"),
     (dict(dt=0.0), "dt"), (dict(B=0), "B"),
 ])
 def test_invalid_problems_rejected_before_any_device_work(lib, bad, word):

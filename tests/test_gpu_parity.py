@@ -64,6 +64,7 @@ def _cost_close(gpu, ref, rtol=COST_RTOL):
     W.chain(),                                       # 7-link arm, 8 x 32 graph, 4096 candidates
     W.pointmass(k=5, M=7, N=13, B=333, beta=0.37),   # ragged sizes
     W.chain(links=3, M=16, N=64, B=8192, beta=0.9),
+    W.pointmass(k=3, M=1, N=5, B=100, interp="akima"),  # one layer
 ])
 def test_sample_tensor(mtp, spec):
     h = mtp.mtp_create(spec)
@@ -103,6 +104,10 @@ INTERP_CASES = [
     ("akima", 0, "valid_span", 16, 256, 12, 31),
     ("linear", 0, "valid_span", 5, 41, 3, 29),
     ("linear", 0, "paper_literal", 4, 16, 2, 9),
+    # one layer: a constant path whatever the interpolation
+    ("bspline", 0, "valid_span", 1, 64, 3, 20),
+    ("akima", 0, "valid_span", 1, 33, 2, 9),
+    ("linear", 0, "paper_literal", 1, 16, 4, 5),
 ]
 
 
@@ -504,7 +509,7 @@ def test_shift(mtp):
 
 
 @pytest.mark.parametrize("bad", [dict(E=0), dict(E=10_000), dict(beta=1.5), dict(alpha=1.0),
-                                 dict(M=1), dict(sigma_min=0.0), dict(interp="bspline", degree=9),
+                                 dict(M=0), dict(sigma_min=0.0), dict(interp="bspline", degree=9),
                                  dict(u_min=[1.0, 1.0], u_max=[0.0, 2.0]), dict(dt=0.0)])
 def test_invalid_problems_rejected(mtp, bad):
     spec = dict(W.pointmass(B=512), **bad)

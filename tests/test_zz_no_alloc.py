@@ -5,8 +5,11 @@ mtp_elite_update_noalloc is for callers that cannot allocate device memory
 (they cannot create a handle, whose buffers come from cudaMalloc).  Through
 the C ABI it is called twice in a row with different costs, and each time
 its elite indices, u*, new mean and new spread are compared with what
-mtp_elite_update produces from the same inputs on a handle.  This file is
-collected last and also runs on its own in a fresh process.
+mtp_elite_update produces from the same inputs on a handle: both run the
+same selection and update kernels, so the results must be the same bits.
+The device's free memory and PyTorch's allocated bytes are read around the
+calls and must not change.  The file is collected last, so a run that stops
+at its first failure has run every other test before this one.
 """
 import numpy as np
 import pytest
@@ -30,10 +33,19 @@ def mtp():
     return m
 
 
-@pytest.mark.parametrize("rule,alpha,E", [("softmax", 0.0, 64), ("softmax", 0.25, 512),
-                                          ("plain_cem", 0.1, 16)])
-def test_noalloc_matches_handle_update_twice(mtp, rule, alpha, E):
-    spec = W.chain(links=7, B=4096, E=E, H=128, alpha=alpha, update_rule=rule)
+def _memory():
+    """(free device bytes as the driver reports them, PyTorch's allocated bytes)."""
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+
+
+@pytest.mark.parametrize("rule,alpha,E,B", [("softmax", 0.0, 64, 4096), ("softmax", 0.25, 512, 4096),
+                                            ("plain_cem", 0.1, 16, 4096),
+                                            # more elites than selection threads: each
+                                            # thread keeps several elites' weights
+                                            ("softmax", 0.0, 2048, 4096)])
+def test_noalloc_matches_handle_update_twice(mtp, rule, alpha, E, B):
+    spec = W.chain(links=7, B=B, E=E, H=128, alpha=alpha, update_rule=rule)
     h = mtp.mtp_create(spec)
     s = h.sizes
     rng = np.random.default_rng(E)
@@ -43,25 +55,58 @@ def test_noalloc_matches_handle_update_twice(mtp, rule, alpha, E):
     mtp.mtp_set_state(h, mu, sigma, 0)
     mu_d = torch.tensor(mu, dtype=torch.float64, device=DEV)
     sg_d = torch.tensor(sigma, dtype=torch.float64, device=DEV)
+    el = torch.full((E,), -1, dtype=torch.int32, device=DEV)
+    us = torch.zeros(s["n"], dtype=torch.float32, device=DEV)
+    el_ref = torch.empty(E, dtype=torch.int32, device=DEV)
+    us_ref = torch.empty(s["n"], dtype=torch.float32, device=DEV)
+    mem = []
     for call in range(2):
         U = torch.tensor(rng.uniform(lo, hi, size=(s["B"], s["H"], s["n"])), dtype=torch.float32,
                          device=DEV)
         cost = torch.tensor(rng.uniform(100.0, 200.0, size=s["B"]), dtype=torch.float32, device=DEV)
         # existing entry point on a handle
-        el_ref = torch.empty(E, dtype=torch.int32, device=DEV)
-        us_ref = torch.empty(s["n"], dtype=torch.float32, device=DEV)
         mtp.mtp_elite_update(h, cost, U, el_ref, us_ref)
         mu_ref, sg_ref, _ = mtp.mtp_get_state(h)
         # the allocation-free entry point on caller-owned state
-        el = torch.full((E,), -1, dtype=torch.int32, device=DEV)
-        us = torch.zeros(s["n"], dtype=torch.float32, device=DEV)
+        el.fill_(-1)
+        us.zero_()
+        before = _memory()
         mtp.mtp_elite_update_noalloc(cost, U, E, spec["lambda"], alpha, spec["sigma_min"], rule,
                                      mu_d, sg_d, el, us)
-        torch.cuda.synchronize()
+        after = _memory()
+        mem.append((before, after))
         assert torch.equal(el, el_ref), f"call {call}: elite indices differ"
         assert torch.equal(us, us_ref), f"call {call}: u* differs"
-        np.testing.assert_allclose(mu_d.cpu().numpy(), mu_ref, rtol=1e-12, atol=1e-14)
-        np.testing.assert_allclose(sg_d.cpu().numpy(), sg_ref, rtol=1e-12, atol=1e-14)
+        assert np.array_equal(mu_d.cpu().numpy(), mu_ref), f"call {call}: mean differs"
+        assert np.array_equal(sg_d.cpu().numpy(), sg_ref), f"call {call}: spread differs"
+    # the second call allocates nothing at all; the first may only have
+    # loaded code (the driver's free count moves in whole pages, if at all)
+    assert mem[1][0] == mem[1][1], f"device memory changed over the second call: {mem[1]}"
+    assert mem[0][0][1] == mem[0][1][1], "PyTorch allocated memory during the first call"
+    mtp.mtp_destroy(h)
+
+
+def test_noalloc_without_optional_outputs(mtp):
+    """elite and u* may be left out: the mean and spread are still updated."""
+    spec = W.pointmass(B=2048, E=32, H=64)
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    rng = np.random.default_rng(3)
+    mu = rng.uniform(-0.5, 0.5, size=(s["H"], s["n"]))
+    sigma = rng.uniform(0.1, 1.0, size=(s["H"], s["n"]))
+    mtp.mtp_set_state(h, mu, sigma, 0)
+    U = torch.tensor(rng.uniform(-1, 1, size=(s["B"], s["H"], s["n"])), dtype=torch.float32,
+                     device=DEV)
+    cost = torch.tensor(rng.uniform(0.0, 5.0, size=s["B"]), dtype=torch.float32, device=DEV)
+    mtp.mtp_elite_update(h, cost, U, None, None)
+    mu_ref, sg_ref, _ = mtp.mtp_get_state(h)
+    mu_d = torch.tensor(mu, dtype=torch.float64, device=DEV)
+    sg_d = torch.tensor(sigma, dtype=torch.float64, device=DEV)
+    mtp.mtp_elite_update_noalloc(cost, U, 32, spec["lambda"], 0.0, spec["sigma_min"], "softmax",
+                                 mu_d, sg_d)
+    torch.cuda.synchronize()
+    assert np.array_equal(mu_d.cpu().numpy(), mu_ref)
+    assert np.array_equal(sg_d.cpu().numpy(), sg_ref)
     mtp.mtp_destroy(h)
 
 
