@@ -39,6 +39,7 @@
  * (index, sub-index/4, iteration, stream tag); each call yields four words.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -765,6 +766,54 @@ void or_rollout_costs(const or_problem* pr, uint32_t iter, const double* x0, con
   }
 }
 
+/* The same costs with the candidates split into `threads` contiguous chunks,
+ * one POSIX thread per chunk.  Each candidate's cost is computed exactly as
+ * above (candidates are independent until the selection), so the result does
+ * not depend on the thread count; this only spreads the slow FP64 rollouts
+ * over the host's cores. */
+typedef struct {
+  const or_problem* pr;
+  uint32_t iter;
+  const double* x0;
+  const double* U;
+  int32_t row0, nrows;
+  double* cost;
+} or_chunk;
+
+static void* rollout_chunk(void* arg) {
+  or_chunk* c = (or_chunk*)arg;
+  or_rollout_costs(c->pr, c->iter, c->x0, c->U, c->row0, c->nrows, c->cost);
+  return NULL;
+}
+
+void or_rollout_costs_threads(const or_problem* pr, uint32_t iter, const double* x0,
+                              const double* U, int32_t row0, int32_t nrows, double* cost,
+                              int32_t threads) {
+  if (threads > nrows) threads = nrows;
+  if (threads <= 1) {
+    or_rollout_costs(pr, iter, x0, U, row0, nrows, cost);
+    return;
+  }
+  size_t row = (size_t)pr->H * pr->n;
+  pthread_t* tid = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
+  or_chunk* ch = (or_chunk*)malloc(sizeof(or_chunk) * (size_t)threads);
+  int* started = (int*)calloc((size_t)threads, sizeof(int));
+  int32_t at = 0;
+  for (int k = 0; k < threads; ++k) {
+    int32_t cnt = nrows / threads + (k < nrows % threads ? 1 : 0);
+    ch[k].pr = pr; ch[k].iter = iter; ch[k].x0 = x0;
+    ch[k].U = U + row * (size_t)at;
+    ch[k].row0 = row0 + at; ch[k].nrows = cnt;
+    ch[k].cost = cost + at;
+    at += cnt;
+    started[k] = pthread_create(&tid[k], NULL, rollout_chunk, &ch[k]) == 0;
+    if (!started[k]) rollout_chunk(&ch[k]); /* no thread to be had: run it here */
+  }
+  for (int k = 0; k < threads; ++k)
+    if (started[k]) pthread_join(tid[k], NULL);
+  free(started); free(ch); free(tid);
+}
+
 /* State trajectory (H+1) x d of candidate b under its own randomised model. */
 double or_rollout_states(const or_problem* pr, uint32_t iter, const double* x0, const double* Ub,
                          int32_t b, double* states) {
@@ -878,9 +927,9 @@ void or_shift(int H, int n, int k, double* mu, double* sigma) {
 /* One full planner iteration (Alg. 2 loop body).                             */
 /* ------------------------------------------------------------------------- */
 
-int or_plan_iteration(const or_problem* pr, uint32_t iter, const double* x0, double* mu,
-                      double* sigma, double* U_out, double* cost_out, int32_t* elite_out,
-                      double* ustar) {
+int or_plan_iteration_threads(const or_problem* pr, uint32_t iter, const double* x0, double* mu,
+                              double* sigma, double* U_out, double* cost_out, int32_t* elite_out,
+                              double* ustar, int32_t threads) {
   int32_t P = pr->P, L = pr->B - P - 1;
   size_t row = (size_t)pr->H * pr->n;
   double* Z = (double*)malloc(sizeof(double) * (size_t)pr->M * pr->N * pr->n);
@@ -900,7 +949,7 @@ int or_plan_iteration(const or_problem* pr, uint32_t iter, const double* x0, dou
   or_local_samples(pr, iter, mu, sigma, L, UL);
   or_stack_clamp(pr, UL, UG, mu, U);
   /* rollout, cost, elites, update */
-  or_rollout_costs(pr, iter, x0, U, 0, pr->B, cost);
+  or_rollout_costs_threads(pr, iter, x0, U, 0, pr->B, cost, threads);
   or_top_e(cost, pr->B, pr->E, elite);
   or_elite_update(pr, U, cost, elite, mu, sigma, ustar);
   free(Z); free(I); free(C); free(UG); free(UL);
@@ -908,6 +957,12 @@ int or_plan_iteration(const or_problem* pr, uint32_t iter, const double* x0, dou
   if (!cost_out) free(cost);
   if (!elite_out) free(elite);
   return 0;
+}
+
+int or_plan_iteration(const or_problem* pr, uint32_t iter, const double* x0, double* mu,
+                      double* sigma, double* U_out, double* cost_out, int32_t* elite_out,
+                      double* ustar) {
+  return or_plan_iteration_threads(pr, iter, x0, mu, sigma, U_out, cost_out, elite_out, ustar, 1);
 }
 
 /* Cost-entropy diagnostic of Sec. 4.1 with the sign read as exp(-J/lambda). */

@@ -68,7 +68,7 @@ def build_oracle(force: bool = False) -> str:
                 and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
             return _LIB_PATH
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-pthread",
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
@@ -108,12 +108,16 @@ def _load():
             "or_chain_energy": (C.c_double, [C.c_int, dp, dp, C.c_double, dp, dp]),
             "or_legged_forward_dynamics": (C.c_int, [pp, dp, C.c_double, dp, dp, dp, dp]),
             "or_rollout_costs": (None, [pp, C.c_uint32, dp, dp, C.c_int32, C.c_int32, dp]),
+            "or_rollout_costs_threads": (None, [pp, C.c_uint32, dp, dp, C.c_int32, C.c_int32, dp,
+                                                C.c_int32]),
             "or_rollout_states": (C.c_double, [pp, C.c_uint32, dp, dp, C.c_int32, dp]),
             "or_top_e": (None, [dp, C.c_int32, C.c_int32, ip]),
             "or_softmax_weights": (None, [dp, ip, C.c_int32, C.c_double, dp]),
             "or_elite_update": (None, [pp, dp, dp, ip, dp, dp, dp]),
             "or_shift": (None, [C.c_int, C.c_int, C.c_int, dp, dp]),
             "or_plan_iteration": (C.c_int, [pp, C.c_uint32, dp, dp, dp, dp, dp, ip, dp]),
+            "or_plan_iteration_threads": (C.c_int, [pp, C.c_uint32, dp, dp, dp, dp, dp, ip, dp,
+                                                    C.c_int32]),
             "or_cost_entropy": (C.c_double, [dp, C.c_int32, C.c_double]),
         }
         for name, (res, args) in sig.items():
@@ -363,13 +367,27 @@ def legged_forward_dynamics(spec, mass, mu_scale, q, qd, tau) -> np.ndarray:
     return qdd
 
 
-def rollout_costs(spec, it: int, x0, U, row0: int = 0) -> np.ndarray:
-    """Costs of candidates row0 .. row0+len(U)-1 (U holds only those rows)."""
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def rollout_costs(spec, it: int, x0, U, row0: int = 0, threads: int = 1) -> np.ndarray:
+    """Costs of candidates row0 .. row0+len(U)-1 (U holds only those rows);
+    threads > 1 splits the candidates over that many host threads (same
+    per-candidate arithmetic, so the same values)."""
     pr = _pr(spec)
     x0 = _f64(x0)
     U = _f64(U, (-1, pr.H, pr.n))
     cost = np.empty(U.shape[0], np.float64)
-    _load().or_rollout_costs(C.byref(pr), it, _dp(x0), _dp(U), row0, U.shape[0], _dp(cost))
+    if threads > 1:
+        _load().or_rollout_costs_threads(C.byref(pr), it, _dp(x0), _dp(U), row0, U.shape[0],
+                                         _dp(cost), int(threads))
+    else:
+        _load().or_rollout_costs(C.byref(pr), it, _dp(x0), _dp(U), row0, U.shape[0], _dp(cost))
     return cost
 
 
@@ -421,8 +439,9 @@ def shift(mu, sigma, k: int):
     return mu, sigma
 
 
-def plan_iteration(spec, it: int, x0, mu, sigma):
-    """One Alg. 2 iteration.  Returns dict(U, cost, elite, mu, sigma, ustar)."""
+def plan_iteration(spec, it: int, x0, mu, sigma, threads: int = 1):
+    """One Alg. 2 iteration.  Returns dict(U, cost, elite, mu, sigma, ustar).
+    threads > 1 rolls the candidates out on that many host threads."""
     pr = _pr(spec)
     x0 = _f64(x0)
     mu = _f64(mu, (pr.H, pr.n)).copy()
@@ -431,8 +450,8 @@ def plan_iteration(spec, it: int, x0, mu, sigma):
     cost = np.empty(pr.B, np.float64)
     elite = np.empty(pr.E, np.int32)
     ustar = np.empty(pr.n, np.float64)
-    _load().or_plan_iteration(C.byref(pr), it, _dp(x0), _dp(mu), _dp(sigma), _dp(U), _dp(cost),
-                              _ip(elite), _dp(ustar))
+    _load().or_plan_iteration_threads(C.byref(pr), it, _dp(x0), _dp(mu), _dp(sigma), _dp(U),
+                                      _dp(cost), _ip(elite), _dp(ustar), int(threads))
     return {"U": U, "cost": cost, "elite": elite, "mu": mu, "sigma": sigma, "ustar": ustar}
 
 

@@ -132,12 +132,15 @@ mtp_status validate(const mtp_problem& p) {
 // A one-layer graph (M = 1) makes constant paths whatever the interpolation
 // (each path is its single waypoint held over the horizon).  The handle runs
 // that as the degree-0 B-spline over one basis function, which is 1 at every
-// step; no contraction rounds the waypoint, so BF16 operands do not apply.
+// step of its valid span (the span then covers the whole horizon, so the
+// time reading does not matter); no contraction rounds the waypoint, so BF16
+// operands do not apply.
 mtp_problem normalized(const mtp_problem& in) {
   mtp_problem p = in;
   if (p.M == 1) {
     p.interp = MTP_INTERP_BSPLINE;
     p.bspline_degree = 0;
+    p.time_mapping = MTP_TIME_VALID_SPAN;
     p.flags &= ~MTP_FLAG_BF16_BASIS;
   }
   return p;

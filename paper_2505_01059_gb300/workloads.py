@@ -95,8 +95,9 @@ def legged(seed: int = 5, links: int = 16, H: int = 256, M: int = 16, N: int = 6
     """Floating-base planar chain with ground contact; with the defaults this
     is the 16-link workload: k 1e4, c 100, friction 0.8 (per-sample scale
     U[0.8, 1.2], also on every link mass), dt 0.002, H 256, graph 16 x 64,
-    16384 candidates, beta 0.3.  Links are U[2, 4] kg and U[0.15, 0.3] m and
-    the chain starts flat, 2 cm above the ground: with lighter links the
+    16384 candidates, beta 0.3, quadratic B-spline with BF16 operands in the
+    basis contraction (flags 0x4, FP32 sums).  Links are U[2, 4] kg and
+    U[0.15, 0.3] m and the chain starts flat, 2 cm above the ground: with lighter links the
     explicit spring-damper contact at dt 0.002 is unstable (the damper needs
     an effective mass above c dt / 2 = 0.1 kg at each contact point)."""
     rng = np.random.default_rng(seed)
@@ -116,6 +117,7 @@ def legged(seed: int = 5, links: int = 16, H: int = 256, M: int = 16, N: int = 6
         k_contact=1e4, c_contact=100.0, mu_friction=0.8, v_slip=0.01,
         dr_mode="per_sample", dr_lo=0.8, dr_hi=1.2,
         x0=q0.tolist() + [0.0] * nq, iters=iters,
+        flags=0x4 if interp == "bspline" else 0,
     )
     spec["lambda"] = 1.0
     spec.update(over)
@@ -131,10 +133,12 @@ def initial_distribution(spec: dict):
     return mu, sigma
 
 
-def batch(seed: int = 3, count: int = 256) -> list[dict]:
+def batch(seed: int = 3, count: int = 256, bf16: bool = False) -> list[dict]:
     """Uneven instances: half k-D point masses (k in 2..12), half chains of
     3..9 links; H in {32, 64, 128, 256}, B in 512..8192 (powers of two),
-    M in 4..16, N in {8, 16, 32, 64}, B-spline or Akima at random."""
+    M in 4..16, N in {8, 16, 32, 64}, B-spline or Akima at random.  With
+    bf16, the B-spline instances contract their basis with BF16 operands
+    (flags 0x4); the drawn sizes are the same either way."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
@@ -152,6 +156,8 @@ def batch(seed: int = 3, count: int = 256) -> list[dict]:
             links = int(rng.integers(3, 10))
             spec = chain(seed=2000 + i, links=links, H=H, M=M, N=N, B=B, interp=interp, E=E,
                          iters=1)
+        if bf16 and interp == "bspline":
+            spec["flags"] = spec.get("flags", 0) | 0x4
         out.append(spec)
     return out
 

@@ -116,3 +116,66 @@ def test_batch_refill_in_place_and_shift(mtp):
     mtp.mtp_batch_destroy(b)
     for h in handles + twins:
         mtp.mtp_destroy(h)
+
+
+def _boundary_clear(cost, E, rtol=1e-4):
+    srt = np.sort(np.where(np.isnan(cost), np.inf, cost))
+    if E >= len(srt):
+        return True
+    a, b = srt[E - 1], srt[E]
+    return (b - a) > 2 * rtol * max(abs(a), 1.0)
+
+
+def test_batched_kernels_against_oracle(mtp):
+    """The batched kernels (graph, candidate, local-row, rollout, selection
+    and update launches over many instances) are separate code from the
+    single-instance kernels, so each instance of a mixed batch is also held
+    to the FP64 oracle, teacher-forced over two iterations (the first
+    launched directly, the second a graph replay): candidates, costs of the
+    GPU's candidates, elites exact on the GPU's costs, the FP64 update of
+    the GPU's candidates, and u*."""
+    import oracle as orc
+    specs = [W.pointmass(k=5, H=64, M=7, N=16, B=1024, interp="bspline", degree=2, iters=1),
+             W.chain(links=5, H=128, M=9, N=32, B=2048, interp="akima", iters=1),
+             W.pointmass(k=3, B=600, flags=0x4),                       # BF16 basis operands
+             W.chain(links=3, H=32, M=4, N=8, B=512, interp="bspline", E=16, iters=1),
+             W.legged(links=4, B=256, H=32, M=6, N=16, E=16)]
+    handles = [mtp.mtp_create(s) for s in specs]
+    b = mtp.mtp_batch_create(handles)
+    rng = np.random.default_rng(21)
+    x0s = [(np.asarray(s["x0"]) + (0.0 if s["dyn"] == "legged" else
+            rng.uniform(-0.2, 0.2, size=s["d"]))).astype(np.float32) for s in specs]
+    x0 = torch.tensor(np.concatenate(x0s), device=DEV)
+    us = torch.empty(b.ustar_offset[-1], device=DEV)
+    threads = orc.host_threads()
+    for it in range(2):
+        before = [mtp.mtp_get_state(h) for h in handles]
+        mtp.mtp_batch_plan_step(b, x0, 1, us)
+        torch.cuda.synchronize()
+        for i, (spec, h) in enumerate(zip(specs, handles)):
+            mu, sigma, k = before[i]
+            assert k == it
+            buf = mtp.mtp_get_buffers(h)
+            Ug = torch.as_tensor(buf["U"], device=DEV).cpu().numpy().astype(np.float64)
+            cg = torch.as_tensor(buf["cost"], device=DEV).cpu().numpy().astype(np.float64)
+            eg = torch.as_tensor(buf["elite"], device=DEV).cpu().numpy()
+            xx = x0s[i].astype(np.float64)
+            ref = orc.plan_iteration(spec, it, xx, mu, sigma, threads=threads)
+            rng_span = (np.array(spec["u_max"]) - np.array(spec["u_min"])).max()
+            assert np.abs(Ug - ref["U"]).max() <= 2e-5 * rng_span, (i, it)
+            c_ref = orc.rollout_costs(spec, it, xx, Ug, threads=threads)
+            err = np.abs(cg - c_ref) / np.maximum(np.abs(c_ref), 1.0)
+            err[np.isinf(cg) & np.isinf(c_ref)] = 0.0
+            assert err.max() <= 1e-4, (i, it, err.max())
+            assert np.array_equal(eg, orc.top_e(cg, spec["E"])), (i, it)
+            if _boundary_clear(c_ref, spec["E"]):
+                assert set(eg.tolist()) == set(orc.top_e(c_ref, spec["E"]).tolist()), (i, it)
+            mu_r, sg_r, us_r = orc.elite_update(spec, Ug, cg, eg, mu, sigma)
+            mu_g, sg_g, _ = mtp.mtp_get_state(h)
+            np.testing.assert_allclose(mu_g, mu_r, rtol=1e-9, atol=1e-12)
+            np.testing.assert_allclose(sg_g, sg_r, rtol=1e-9, atol=1e-12)
+            lo, hi = b.ustar_offset[i], b.ustar_offset[i + 1]
+            assert np.array_equal(us[lo:hi].cpu().numpy().astype(np.float64), us_r), (i, it)
+    mtp.mtp_batch_destroy(b)
+    for h in handles:
+        mtp.mtp_destroy(h)
