@@ -311,6 +311,23 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_grou
 /* mtp_shift(h, k) of every instance of the batch in one launch. */
 mtp_status mtp_batch_shift(mtp_batch* b, int32_t k, void* stream);
 
+/* Kernel launches one mtp_batch_plan_step(b, ..., iters, ...) issues: per
+ * iteration, each (dynamics, dimension) group's graph, graph-path, local-row,
+ * rollout, selection and update launches that have work, plus the scatter of
+ * the start states and the gather of u* once per call. */
+mtp_status mtp_batch_launches(const mtp_batch* b, int32_t iters, int32_t* launches);
+
+/* Device time of each group's rollout launch (Alg. 2 rollout fused with the
+ * cost, Eq. 2) run alone on `stream` with its current tile, averaged over
+ * `reps` launches timed with CUDA events: ms_out[g] (may be NULL).
+ * info_out (6 per group, may be NULL): dynamics, dimension (point-mass axes
+ * or links), candidates per block, instances, candidates (sum of B) and
+ * rollout steps (sum of B * H).  *n_groups is the group count; max_groups
+ * must be at least that when an output array is given.  Synchronous;
+ * overwrites the handles' cost buffers. */
+mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, int32_t* info_out,
+                                   int32_t max_groups, int32_t* n_groups, void* stream);
+
 /* Device bytes a handle for `problem` uses, each allocation rounded up to
  * 512 bytes (the candidate tensor U dominates: B * H * n floats).  A
  * pipelined problem counts the second candidate buffer, which the first

@@ -99,7 +99,8 @@ size_t layout_tables(BatchTables* t, unsigned char* base, int count, int n_pm, i
 }  // namespace
 
 struct mtp_batch {
-  std::vector<mtp_handle*> hs;  // in the caller's order
+  std::vector<mtp_handle*> hs;         // in the caller's order
+  std::vector<mtp_handle*> hs_sorted;  // in group order (groups[g].first indexes it)
   int device = 0;
   BatchTables t;
   int count = 0;
@@ -292,6 +293,8 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
       (e = cudaEventRecord(t.copied, s)))
     return e;
   b->hs.assign(handles, handles + count);
+  b->hs_sorted.resize(count);
+  for (int pos = 0; pos < count; ++pos) b->hs_sorted[pos] = handles[order[pos]];
   b->count = count;
   for (size_t g = 0; g < b->groups.size(); ++g) {
     if (!b->group_stream[g]) {
@@ -533,6 +536,66 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_grou
       blocks_out[3 * i + 1] = b->groups[i].n;
       blocks_out[3 * i + 2] = b->groups[i].block;
     }
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_launches(const mtp_batch* b, int32_t iters, int32_t* launches) {
+  if (!b || !launches || iters < 1 || b->count < 1) return MTP_ERR_INVALID_ARG;
+  long long per_iter = 0;
+  for (const auto& g : b->groups) {
+    per_iter += (g.z_blocks > 0) + (g.cand_blocks > 0) + (g.local_blocks > 0);
+    per_iter += (g.total_rows > 0) + (g.count > 0) + (g.upd_threads > 0);
+  }
+  *launches = (int32_t)(2 + per_iter * iters);  // scatter of x0 and gather of u* once per call
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, int32_t* info_out,
+                                   int32_t max_groups, int32_t* n_groups, void* stream) {
+  if (!b || reps < 1 || !n_groups) return MTP_ERR_INVALID_ARG;
+  if (b->count < 1) return batch_fail(b, MTP_ERR_INVALID_ARG, "rollout_times: batch never filled");
+  DeviceGuard guard(b->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  *n_groups = (int32_t)b->groups.size();
+  if ((ms_out || info_out) && max_groups < (int32_t)b->groups.size())
+    return batch_fail(b, MTP_ERR_INVALID_ARG, "rollout_times: max_groups below the group count");
+  cudaEvent_t t0, t1;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("rollout_times: ") + cudaGetErrorString(e));
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->t.copied, 0);  // tables filled on another stream
+  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+    const BatchGroup& g = b->groups[gi];
+    double sum = 0.0;
+    for (int rep = 0; rep < reps && e == cudaSuccess; ++rep) {
+      if ((e = cudaEventRecord(t0, s))) break;
+      if ((e = launch_group(b, g, g.block, s))) break;
+      if ((e = cudaEventRecord(t1, s))) break;
+      if ((e = cudaEventSynchronize(t1))) break;
+      float ms = 0.f;
+      if ((e = cudaEventElapsedTime(&ms, t0, t1))) break;
+      sum += ms;
+    }
+    if (ms_out) ms_out[gi] = sum / reps;
+    if (info_out) {
+      long long rows = 0, steps = 0;
+      for (int j = 0; j < g.count; ++j) {
+        const mtp_handle* h = b->hs_sorted[g.first + j];
+        rows += h->dm.B;
+        steps += (long long)h->dm.B * h->dm.H;
+      }
+      int32_t* o = info_out + 6 * gi;
+      o[0] = g.dyn;
+      o[1] = g.n;
+      o[2] = g.block;
+      o[3] = g.count;
+      o[4] = (int32_t)rows;
+      o[5] = (int32_t)std::min<long long>(steps, 0x7fffffff);
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("rollout_times: ") + cudaGetErrorString(e));
   return MTP_OK;
 }
 

@@ -43,6 +43,7 @@ EXPORTS = [
     "mtp_set_profiling", "mtp_stage_times", "mtp_stage_times5", "mtp_elite_update_noalloc",
     "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_layout", "mtp_batch_plan_step",
     "mtp_batch_autotune", "mtp_batch_reserve", "mtp_batch_fill", "mtp_batch_shift",
+    "mtp_batch_launches", "mtp_batch_rollout_times",
     "mtp_problem_device_bytes", "mtp_server_create", "mtp_server_destroy", "mtp_server_register",
     "mtp_submit", "mtp_poll", "mtp_server_get_stats", "mtp_server_last_error",
     "mtp_submit_many", "mtp_poll_many",
@@ -147,6 +148,8 @@ def load_library(path: str = LIB_PATH):
         "mtp_batch_layout": (i32, [vp, vp, vp]),
         "mtp_batch_plan_step": (i32, [vp, vp, i32, vp, vp]),
         "mtp_batch_autotune": (i32, [vp, vp, vp, vp]),
+        "mtp_batch_launches": (i32, [vp, i32, vp]),
+        "mtp_batch_rollout_times": (i32, [vp, i32, vp, vp, i32, vp, vp]),
         "mtp_batch_reserve": (i32, [i32, C.POINTER(vp)]),
         "mtp_batch_fill": (i32, [vp, C.POINTER(vp), i32, vp]),
         "mtp_batch_shift": (i32, [vp, i32, vp]),
@@ -574,6 +577,28 @@ def mtp_batch_autotune(b: Batch, stream=None):
     _check(load_library().mtp_batch_autotune(b.ptr, C.addressof(out), C.addressof(ng),
                                              _stream(stream)))
     return [(out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i in range(ng.value)]
+
+
+def mtp_batch_launches(b: Batch, iters: int = 1) -> int:
+    """Kernel launches of one mtp_batch_plan_step(b, ..., iters, ...)."""
+    n = C.c_int32()
+    _check(load_library().mtp_batch_launches(b.ptr, int(iters), C.addressof(n)))
+    return int(n.value)
+
+
+def mtp_batch_rollout_times(b: Batch, reps: int = 3, stream=None):
+    """Each group's rollout launch timed alone: a list of dicts with dyn,
+    dim, block, instances, candidates, steps and ms (average device time)."""
+    groups = max(1, len(b.handles))
+    ms = (C.c_double * groups)()
+    info = (C.c_int32 * (6 * groups))()
+    ng = C.c_int32()
+    _check(load_library().mtp_batch_rollout_times(b.ptr, int(reps), C.addressof(ms),
+                                                  C.addressof(info), groups, C.addressof(ng),
+                                                  _stream(stream)))
+    keys = ("dyn", "dim", "block", "instances", "candidates", "steps")
+    return [dict(zip(keys, (int(info[6 * g + k]) for k in range(6))), ms=float(ms[g]))
+            for g in range(ng.value)]
 
 
 # ----------------------------------------------------------------------------
