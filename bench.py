@@ -126,7 +126,11 @@ def fp32_peak(sm_mhz: float, sms: int) -> tuple[float, str]:
 
 
 KERNEL_HEADERS = ("paper_2505_01059_gb300/csrc/rollout_common.cuh",
+                  "paper_2505_01059_gb300/csrc/rollout_kernels.cuh",
                   "paper_2505_01059_gb300/csrc/mtp_device.cuh", "include/mtp.h")
+KERNEL_FILE = {"pointmass": "rollout_pm.cu", "chain": "rollout_chain.cu", "legged": "legged.cu"}
+BATCH_KERNEL_FILE = {"pointmass": "rollout_pm_batch.cu", "chain": "rollout_chain_batch.cu",
+                     "legged": "legged.cu"}
 
 
 def _code_text(path: str) -> str:
@@ -154,7 +158,8 @@ def profiled_traffic(kernel_file: str, summary: str, key: str = "dram_bytes_per_
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current sources of the kernel (else None)."""
     prof = os.path.join(ROOT, "profiles", summary)
-    if not os.path.exists(prof):
+    if not os.path.exists(prof) or not os.path.exists(
+            os.path.join(ROOT, "paper_2505_01059_gb300/csrc", kernel_file)):
         return None
     text = open(prof).read()
     m_hash = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
@@ -445,14 +450,15 @@ def batch_rollout_roofline(mtp, b, specs, sms: int) -> tuple[dict, list]:
         fl = sum(flops_per_step(s) * s["B"] * s["H"] for s in members)
         achieved = fl / (g["ms"] / 1e3) / 1e12
         out.append({"kernel": f"{ROLLOUT_KERNEL[dyn]}_batch<{g['dim']}>", "dyn": dyn,
-                    "dim": g["dim"], "block": g["block"], "instances": g["instances"],
+                    "dim": g["dim"], "block": g["block"], "chunk": g["chunk"],
+                    "instances": g["instances"],
                     "rollout_steps": g["steps"], "flops_per_launch": fl,
                     "duration_us": g["ms"] * 1e3, "achieved_tflops": achieved,
                     "frac": achieved / peak})
     dom = max(out, key=lambda r: r["duration_us"])
     roof = {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved_tflops"],
             "peak": peak, "unit": "TFLOP/s", "frac": dom["frac"],
-            "traffic": profiled_traffic("rollout.cu", "rollout_batch_groups.txt",
+            "traffic": profiled_traffic(BATCH_KERNEL_FILE[dom["dyn"]], "rollout_batch_groups.txt",
                                         key=f"dram_bytes_per_launch_{dom['dyn']}{dom['dim']}"),
             "flops_per_launch": dom["flops_per_launch"], "duration_us": dom["duration_us"],
             "timing": "CUDA events around the group's rollout launch, run alone on its stream "
@@ -929,7 +935,7 @@ def run_single(args, mtp, dev, spec, name, steps, pg=None, world=1, rank=0, flus
     peak, note = fp32_peak(peaks().get("sm_max_mhz", 2070.0), device_sms(dev.index))
     fl = flops_per_step(spec) * steps_per_iter
     achieved = fl / (stage_ms[1] / 1e3) / 1e12
-    kernel_file = "legged.cu" if spec["dyn"] == "legged" else "rollout.cu"
+    kernel_file = KERNEL_FILE[spec["dyn"]]
     summary = {"chain": "rollout_chain7_arm_B4096.txt", "pointmass": "rollout_pointmass2_B512.txt",
                "legged": "rollout_legged16_B16384.txt"}[spec["dyn"]]
     res["roofline"] = {"bound": "alu", "kernel": ROLLOUT_KERNEL[spec["dyn"]], "achieved": achieved,

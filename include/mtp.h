@@ -241,6 +241,14 @@ mtp_status mtp_plan_step_host(mtp_handle* h, const float* h_x0, int32_t iters, f
  * and repeats the last row (the paper leaves this open). */
 mtp_status mtp_shift(mtp_handle* h, int32_t k, void* stream);
 
+/* Device-side failures since the last call: the rollouts stage their controls
+ * through shared memory with bulk copies and wait for them with a bounded
+ * wait (about two seconds); a wait that gives up marks the handle and scores
+ * its candidates +inf instead of hanging the GPU.  Synchronises the device,
+ * then returns MTP_ERR_TIMEOUT (and clears the mark) if that happened in any
+ * of the handle's rollouts (alone or in a batch), else MTP_OK. */
+mtp_status mtp_device_status(mtp_handle* h);
+
 /* Checkpoint / resume of the planner state: FP64 mean and spread (H, n) and
  * the iteration counter.  Synchronous. */
 mtp_status mtp_get_state(mtp_handle* h, double* h_mu, double* h_sigma, uint32_t* h_iter);
@@ -301,12 +309,17 @@ mtp_status mtp_batch_fill(mtp_batch* b, mtp_handle* const* handles, int32_t coun
 mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, float* d_ustar,
                                void* stream);
 
-/* Picks the rollout block size (candidates per block: 32, 64 or 128) of each
- * (dynamics, dimension) group by timing one rollout launch of each choice.
- * Writes (dynamics, dimension, block) triples to blocks_out (3 * groups
- * entries, may be NULL) and the number of groups to n_groups.  Synchronous;
- * overwrites the handles' cost buffers. */
-mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_groups, void* stream);
+/* Picks the rollout tile of each (dynamics, dimension) group by timing its
+ * rollout launch (best of three) for every choice: candidates per block (32,
+ * 64 or 128) times the horizon chunk of the staged control loads (0: direct
+ * loads; 4 or 8 steps of every candidate's controls copied at once into
+ * shared memory by bulk copies, when every member's rows allow it: 16-byte
+ * aligned, H * n a multiple of 4, one model per candidate).  The legged group
+ * keeps its fixed tile.  Writes (dynamics, dimension, block, chunk) to
+ * tiles_out (4 * groups entries, may be NULL) and the number of groups to
+ * n_groups.  Synchronous; overwrites the handles' cost buffers.  Results do
+ * not depend on the tile. */
+mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_groups, void* stream);
 
 /* mtp_shift(h, k) of every instance of the batch in one launch. */
 mtp_status mtp_batch_shift(mtp_batch* b, int32_t k, void* stream);
@@ -320,9 +333,10 @@ mtp_status mtp_batch_launches(const mtp_batch* b, int32_t iters, int32_t* launch
 /* Device time of each group's rollout launch (Alg. 2 rollout fused with the
  * cost, Eq. 2) run alone on `stream` with its current tile, averaged over
  * `reps` launches timed with CUDA events: ms_out[g] (may be NULL).
- * info_out (6 per group, may be NULL): dynamics, dimension (point-mass axes
- * or links), candidates per block, instances, candidates (sum of B) and
- * rollout steps (sum of B * H).  *n_groups is the group count; max_groups
+ * info_out (7 per group, may be NULL): dynamics, dimension (point-mass axes
+ * or links), candidates per block, instances, candidates (sum of B), rollout
+ * steps (sum of B * H) and the horizon chunk of staged control loads (0:
+ * direct loads).  *n_groups is the group count; max_groups
  * must be at least that when an output array is given.  Synchronous;
  * overwrites the handles' cost buffers. */
 mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, int32_t* info_out,

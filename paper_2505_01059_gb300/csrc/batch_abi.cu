@@ -26,12 +26,16 @@ struct BatchGroup {
   int rows_first = 0;         // offset of this group's row_start segment
   int total_rows = 0;
   int block = 128;
+  int chunk = 0;              // horizon chunk of staged control loads (0: direct loads)
+  bool stageable = false;     // every member's rows can be staged (see can_stage)
   // this group's share of the generation, selection and update launches
   int z_blocks = 0, cand_blocks = 0, local_blocks = 0, upd_threads = 0;
   size_t cand_smem = 0, sel_smem = 0;
 };
 
 constexpr int kMaxGroups = 64;
+// Horizon chunk of staged control loads before the autotuner has run.
+constexpr int kDefaultChunk = 4;
 constexpr size_t kBatchGraphSmem = 40 * 1024;  // four graph blocks per SM
 
 // Device tables of a batch, packed into one device block that is refilled in
@@ -105,7 +109,8 @@ struct mtp_batch {
   BatchTables t;
   int count = 0;
   std::vector<BatchGroup> groups;
-  std::map<std::pair<int, int>, int> tuned;  // (dyn, n) -> block chosen by the autotuner
+  // (dyn, n) -> rollout tile chosen by the autotuner: (candidates per block, horizon chunk)
+  std::map<std::pair<int, int>, std::pair<int, int>> tuned;
   std::vector<int> x0_off, us_off;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t fork_ev = nullptr;
@@ -197,7 +202,8 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
       g.first = pos;
       g.model_first = n_dyn[dyn];
       auto it = b->tuned.find({dyn, n});
-      g.block = it != b->tuned.end() ? it->second : 128;
+      g.block = it != b->tuned.end() ? it->second.first : 128;
+      g.chunk = it != b->tuned.end() ? it->second.second : kDefaultChunk;
       b->groups.push_back(g);
     }
     ++b->groups.back().count;
@@ -274,6 +280,10 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
       row[j + 1] = row[j] + ((h->dm.B + 31) / 32) * 32;
     }
     g.total_rows = row[g.count];
+    g.stageable = g.dyn != MTP_DYN_LEGGED;
+    for (int j = 0; j < g.count; ++j)
+      g.stageable = g.stageable && can_stage(hv.d_ra[g.first + j], group_key_n(handles[order[g.first + j]]));
+    if (!g.stageable) g.chunk = 0;
     rs += g.count + 1;
   }
   // packing of x0 and u*, in the caller's order
@@ -306,15 +316,18 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
   return cudaSuccess;
 }
 
-cudaError_t launch_group(const mtp_batch* b, const BatchGroup& g, int block, cudaStream_t s) {
+cudaError_t launch_group(const mtp_batch* b, const BatchGroup& g, int block, int chunk, cudaStream_t s) {
   const BatchTables& t = b->t;
   const RolloutArgs* ra = t.d_ra + g.first;
   const int* rs = t.d_row_start + g.rows_first;
+  if (!g.stageable) chunk = 0;
   if (g.dyn == MTP_DYN_POINTMASS)
-    return launch_rollout_pointmass_batch(ra, t.d_pm + g.model_first, rs, g.count, g.total_rows, g.n, block, s);
+    return launch_rollout_pointmass_batch(ra, t.d_pm + g.model_first, rs, g.count, g.total_rows, g.n,
+                                          block, chunk, s);
   if (g.dyn == MTP_DYN_LEGGED)  // fixed 64-thread blocks (shared-memory staging)
     return launch_rollout_legged_batch(ra, t.d_lm + g.model_first, rs, g.count, g.total_rows, g.n, s);
-  return launch_rollout_chain_batch(ra, t.d_cm + g.model_first, rs, g.count, g.total_rows, g.n, block, s);
+  return launch_rollout_chain_batch(ra, t.d_cm + g.model_first, rs, g.count, g.total_rows, g.n, block,
+                                    chunk, s);
 }
 
 // One batched Alg. 2 iteration.  Each (dynamics, dimension) group runs its
@@ -335,7 +348,7 @@ cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
     if ((e = launch_candidates_batch(t.d_cand + f, t.d_cand_start + f, g.count, g.cand_blocks, g.cand_smem, gs)))
       return e;
     if ((e = launch_local_batch(t.d_cand + f, t.d_local_start + f, g.count, g.local_blocks, gs))) return e;
-    if ((e = launch_group(b, g, g.block, gs))) return e;
+    if ((e = launch_group(b, g, g.block, g.chunk, gs))) return e;
     if ((e = launch_select_batch(t.d_sel + f, g.count, g.sel_smem, gs))) return e;
     if ((e = launch_update_batch(t.d_upd + f, t.d_warp_start + f, g.count, g.upd_threads, gs))) return e;
     if ((e = cudaEventRecord(b->group_done[gi], gs))) return e;
@@ -409,6 +422,8 @@ mtp_status mtp_batch_reserve(int32_t capacity, mtp_batch** out) {
   cudaGetDevice(&b->device);
   cudaError_t e = init_candidate_attributes();
   if (e == cudaSuccess) e = init_select_attributes();
+  if (e == cudaSuccess) e = init_rollout_pm_batch_attributes();
+  if (e == cudaSuccess) e = init_rollout_chain_batch_attributes();
   if (e == cudaSuccess) e = alloc_batch(b, capacity);
   if (e != cudaSuccess) {
     mtp_status st = batch_fail(nullptr, e == cudaErrorMemoryAllocation ? MTP_ERR_OUT_OF_MEMORY : MTP_ERR_CUDA,
@@ -490,39 +505,48 @@ mtp_status mtp_batch_shift(mtp_batch* b, int32_t k, void* stream) {
   return MTP_OK;
 }
 
-mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_groups, void* stream) {
+mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_groups, void* stream) {
   if (!b) return MTP_ERR_INVALID_ARG;
   if (b->count < 1) return batch_fail(b, MTP_ERR_INVALID_ARG, "autotune: batch never filled");
   DeviceGuard guard(b->device);
   (void)stream;
   cudaEventSynchronize(b->t.copied);  // the tables may have been filled on another stream
-  const int cand[3] = {32, 64, 128};  // the rollout kernels are bounded at 128 threads
+  // rollout tiles: candidates per block (the kernels are bounded at 128
+  // threads) x horizon chunk of the staged control loads (0: direct loads)
+  const int blocks[3] = {32, 64, 128};
+  const int chunks[3] = {0, 4, 8};  // chains stage 4 steps at a time (8 is not tried)
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
   cudaError_t e = cudaSuccess;
   for (auto& g : b->groups) {
-    if (g.dyn == MTP_DYN_LEGGED) continue;  // fixed block size
+    if (g.dyn == MTP_DYN_LEGGED) continue;  // fixed tile
     float best = 1e30f;
-    int best_block = g.block;
-    for (int block : cand) {
-      float ms_min = 1e30f;
-      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-        cudaEventRecord(t0, b->cap_stream);
-        e = launch_group(b, g, block, b->cap_stream);
-        cudaEventRecord(t1, b->cap_stream);
-        cudaEventSynchronize(t1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, t0, t1);
-        ms_min = std::min(ms_min, ms);
-      }
-      if (ms_min < best) {
-        best = ms_min;
-        best_block = block;
+    int best_block = g.block, best_chunk = g.chunk;
+    for (int chunk : chunks) {
+      if (chunk && !g.stageable) continue;
+      if (chunk == 8 && g.dyn == MTP_DYN_CHAIN) continue;
+      for (int block : blocks) {
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+          cudaEventRecord(t0, b->cap_stream);
+          e = launch_group(b, g, block, chunk, b->cap_stream);
+          cudaEventRecord(t1, b->cap_stream);
+          cudaEventSynchronize(t1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, t0, t1);
+          ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best) {
+          best = ms_min;
+          best_block = block;
+          best_chunk = chunk;
+        }
       }
     }
     g.block = best_block;
-    b->tuned[{g.dyn, g.n}] = best_block;
+    g.chunk = best_chunk;
+    b->tuned[{g.dyn, g.n}] = {best_block, best_chunk};
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
@@ -530,11 +554,12 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* blocks_out, int32_t* n_grou
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);  // tiles changed: recapture
   b->graphs.clear();
   if (n_groups) *n_groups = (int32_t)b->groups.size();
-  if (blocks_out)
+  if (tiles_out)
     for (size_t i = 0; i < b->groups.size(); ++i) {
-      blocks_out[3 * i + 0] = b->groups[i].dyn;
-      blocks_out[3 * i + 1] = b->groups[i].n;
-      blocks_out[3 * i + 2] = b->groups[i].block;
+      tiles_out[4 * i + 0] = b->groups[i].dyn;
+      tiles_out[4 * i + 1] = b->groups[i].n;
+      tiles_out[4 * i + 2] = b->groups[i].block;
+      tiles_out[4 * i + 3] = b->groups[i].chunk;
     }
   return MTP_OK;
 }
@@ -569,7 +594,7 @@ mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, i
     double sum = 0.0;
     for (int rep = 0; rep < reps && e == cudaSuccess; ++rep) {
       if ((e = cudaEventRecord(t0, s))) break;
-      if ((e = launch_group(b, g, g.block, s))) break;
+      if ((e = launch_group(b, g, g.block, g.chunk, s))) break;
       if ((e = cudaEventRecord(t1, s))) break;
       if ((e = cudaEventSynchronize(t1))) break;
       float ms = 0.f;
@@ -584,13 +609,14 @@ mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, i
         rows += h->dm.B;
         steps += (long long)h->dm.B * h->dm.H;
       }
-      int32_t* o = info_out + 6 * gi;
+      int32_t* o = info_out + 7 * gi;
       o[0] = g.dyn;
       o[1] = g.n;
       o[2] = g.block;
       o[3] = g.count;
       o[4] = (int32_t)rows;
       o[5] = (int32_t)std::min<long long>(steps, 0x7fffffff);
+      o[6] = g.stageable ? g.chunk : 0;
     }
   }
   cudaEventDestroy(t0);

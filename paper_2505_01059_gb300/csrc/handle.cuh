@@ -56,6 +56,8 @@ struct mtp_handle {
   float* ustar = nullptr;
   float* x0 = nullptr;
   float* Z = nullptr;  // (M, N, n) graph of the current iteration (batched planning)
+  uint32_t* status = nullptr;  // device status word: bits a rollout sets when a bounded wait gave up
+  int rollout_chunk = 4;       // horizon chunk of the staged control loads of a lone rollout
   // replay
   cudaStream_t cap_stream = nullptr;
   std::map<int, cudaGraphExec_t> graphs;   // key: (iterations, cur, first prepared)

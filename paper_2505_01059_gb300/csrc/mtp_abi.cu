@@ -307,6 +307,7 @@ RolloutArgs rollout_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_i
   a.rows = rows;
   a.cost = cost;
   a.kahan = (h->pr.flags & MTP_FLAG_NO_KAHAN) ? 0 : 1;
+  a.status = h->status;
   return a;
 }
 
@@ -377,9 +378,9 @@ cudaError_t launch_generate(const mtp_handle* h, CandArgs& c, cudaStream_t s) {
 
 cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
   const mtp_problem& p = h->pr;
-  if (p.dyn == MTP_DYN_POINTMASS) return launch_rollout_pointmass(a, pointmass_model(p), s);
+  if (p.dyn == MTP_DYN_POINTMASS) return launch_rollout_pointmass(a, pointmass_model(p), h->rollout_chunk, s);
   if (p.dyn == MTP_DYN_LEGGED) return launch_rollout_legged(a, legged_model(p), p.n_links, s);
-  return launch_rollout_chain(a, chain_model(p), p.n_links, s);
+  return launch_rollout_chain(a, chain_model(p), p.n_links, h->rollout_chunk, s);
 }
 
 // Stage event: inside a stream capture it must be an external event record
@@ -590,7 +591,8 @@ void free_handle(mtp_handle* h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   void* ptrs[] = {h->basis, h->bfirst, h->seg, h->delta, h->mu, h->sigma, h->mu_f, h->sigma_f,
                   h->iter_dev,
-                  h->Ubuf[0], h->Ubuf[1], h->cost, h->elite, h->weight, h->ustar, h->x0, h->Z};
+                  h->Ubuf[0], h->Ubuf[1], h->cost, h->elite, h->weight, h->ustar, h->x0, h->Z,
+                  h->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -625,6 +627,8 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   cudaError_t e;
   if ((e = init_candidate_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
   if ((e = init_select_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
+  if ((e = init_rollout_pm_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
+  if ((e = init_rollout_chain_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
   if ((e = pipeline_plan(p, dm, h->paths_per_block, &h->pipeline, &h->prep_local, &h->prep_grid,
                          &h->prep_smem, &h->prep_spb)) !=
       cudaSuccess)
@@ -636,7 +640,8 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
       (e = dalloc(&h->iter_dev, 1)) || (e = dalloc(&h->Ubuf[0], rowsz * dm.B)) ||
       (e = dalloc(&h->cost, dm.B)) || (e = dalloc(&h->elite, dm.E)) ||
       (e = dalloc(&h->weight, dm.E)) || (e = dalloc(&h->ustar, dm.n)) ||
-      (e = dalloc(&h->x0, dm.d)) || (e = dalloc(&h->Z, (size_t)dm.M * dm.N * dm.n)))
+      (e = dalloc(&h->x0, dm.d)) || (e = dalloc(&h->Z, (size_t)dm.M * dm.N * dm.n)) ||
+      (e = dalloc(&h->status, 1)))
     return err(cuda_fail(h, e, "cudaMalloc"));
   std::vector<double> mu(rowsz, p.mu_init), sg(rowsz, p.sigma_init);
   std::vector<float> muf(rowsz, (float)p.mu_init), sgf(rowsz, (float)p.sigma_init);
@@ -646,7 +651,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
       (e = cudaMemcpy(h->mu_f, muf.data(), rowsz * 4, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(h->sigma_f, sgf.data(), rowsz * 4, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(h->iter_dev, &zero, 4, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemset(h->ustar, 0, dm.n * 4)))
+      (e = cudaMemset(h->ustar, 0, dm.n * 4)) || (e = cudaMemset(h->status, 0, 4)))
     return err(cuda_fail(h, e, "cudaMemcpy"));
   h->U = h->Ubuf[0];
   if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -667,7 +672,8 @@ mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes)
            + r(rowsz * p.B * 4) + r((uint64_t)p.B * 4)                        // U, cost
            + r((uint64_t)p.E * 4) + r((uint64_t)p.E * 8)                      // elites, weights
            + r((uint64_t)p.ctrl_dim * 4) + r((uint64_t)p.state_dim * 4)
-           + r((uint64_t)p.M * p.N * p.ctrl_dim * 4);                         // graph Z
+           + r((uint64_t)p.M * p.N * p.ctrl_dim * 4)                          // graph Z
+           + r(4);                                                            // status word
   const Dims dm = dims_of(p);
   bool on = false, local = false;
   int grid = 0;
@@ -1051,6 +1057,18 @@ mtp_status mtp_shift(mtp_handle* h, int32_t k, void* stream) {
                                (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "shift");
   return MTP_OK;
+}
+
+mtp_status mtp_device_status(mtp_handle* h) {
+  if (!h) return MTP_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  uint32_t word = 0;
+  MTP_CUDA(h, cudaDeviceSynchronize());
+  MTP_CUDA(h, cudaMemcpy(&word, h->status, 4, cudaMemcpyDeviceToHost));
+  if (word == 0) return MTP_OK;
+  MTP_CUDA(h, cudaMemset(h->status, 0, 4));
+  return fail(h, MTP_ERR_TIMEOUT,
+              "a rollout's bounded wait for its staged controls gave up (those candidates cost +inf)");
 }
 
 mtp_status mtp_get_state(mtp_handle* h, double* h_mu, double* h_sigma, uint32_t* h_iter) {

@@ -153,7 +153,16 @@ struct RolloutArgs {
   float* cost;       // (rows)
   float* X;          // (H+1, d) states of the single requested row, or null
   int32_t kahan;
+  uint32_t* status;  // device status word of the handle (bits set by a rollout), or null
 };
+
+// Whether a rollout launch may stage its controls through shared memory with
+// bulk copies (see StagedRows): 16-byte aligned rows of a multiple of 4
+// floats, one model per candidate, no state output.
+inline bool can_stage(const RolloutArgs& a, int k) {
+  return a.X == nullptr && a.dr_mode != MTP_DR_SHARED &&
+         ((uintptr_t)a.U % 16u) == 0 && ((long long)a.H * k) % 4 == 0;
+}
 
 struct PointMassModel {
   float target[16];
@@ -217,9 +226,15 @@ cudaError_t launch_candidates(const CandArgs& a, int local_blocks, cudaStream_t 
 cudaError_t launch_sample_tensor(const Dims& dm, Key key, uint32_t iter, const float* umin,
                                  const float* umax, float* Z, int32_t* I, float* C,
                                  cudaStream_t s);
-cudaError_t launch_rollout_pointmass(const RolloutArgs& a, const PointMassModel& m,
+// Rollouts: `chunk` is the horizon chunk of staged control loads (4 or 8
+// steps; 0, or a launch that cannot stage, loads directly).
+cudaError_t init_rollout_pm_attributes();
+cudaError_t init_rollout_chain_attributes();
+cudaError_t init_rollout_pm_batch_attributes();
+cudaError_t init_rollout_chain_batch_attributes();
+cudaError_t launch_rollout_pointmass(const RolloutArgs& a, const PointMassModel& m, int chunk,
                                      cudaStream_t s);
-cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int links,
+cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int links, int chunk,
                                  cudaStream_t s);
 cudaError_t launch_rollout_legged(const RolloutArgs& a, const LeggedModel& m, int links,
                                   cudaStream_t s);
@@ -250,10 +265,10 @@ cudaError_t launch_candidates_batch(const CandArgs* d_args, const int* d_block_s
                                     int total_blocks, size_t smem, cudaStream_t s);
 cudaError_t launch_rollout_pointmass_batch(const RolloutArgs* d_ra, const PointMassModel* d_pm,
                                            const int* d_row_start, int count, int total_rows,
-                                           int k, int block, cudaStream_t s);
+                                           int k, int block, int chunk, cudaStream_t s);
 cudaError_t launch_rollout_chain_batch(const RolloutArgs* d_ra, const ChainModel* d_cm,
                                        const int* d_row_start, int count, int total_rows,
-                                       int links, int block, cudaStream_t s);
+                                       int links, int block, int chunk, cudaStream_t s);
 cudaError_t launch_select_batch(const SelectArgs* d_args, int count, size_t smem, cudaStream_t s);
 cudaError_t launch_update_batch(const UpdateArgs* d_args, const int* d_thread_start, int count,
                                 int total_threads, cudaStream_t s);

@@ -1,10 +1,16 @@
-// rollout.cu -- Alg. 2 batch rollout fused with the cost reduction (Eq. 2).
+// rollout_kernels.cuh -- Alg. 2 batch rollout fused with the cost reduction
+// (Eq. 2) for the k-D point mass and the planar serial chain: the device
+// bodies and kernels, instantiated by rollout_pm.cu and rollout_chain.cu.
 //
 // One thread per candidate keeps the whole state in registers for all H
 // steps and accumulates c(x_t, u_t) with compensated FP32 sums; only the
 // final cost leaves the SM.  The loop bodies are fully unrolled over the
 // compile-time dimension (point-mass axes, chain links), so the per-step
-// linear algebra lives in registers.
+// linear algebra lives in registers.  The controls reach a thread either by
+// direct loads a few steps ahead (T = 0) or staged through shared memory a
+// horizon chunk of T steps at a time by bulk copies (T = 4, 8; see
+// StagedRows): the chunk length is the rollout tile's horizon chunk, picked
+// per launch shape by the batch autotuner.
 //
 // Planar chain: the dynamics are evaluated in absolute link angles phi_j
 // (phi_j = q_1 + ... + q_j).  For uniform thin rods the Lagrangian gives the
@@ -13,13 +19,14 @@
 // g l_j beta_j cos(phi_j) and generalised forces tau_j - tau_{j+1}; the
 // SPD system is solved by an unrolled Cholesky.  Semi-implicit Euler in
 // (phi, w) equals semi-implicit Euler in the relative joint coordinates.
+#pragma once
+
 #include "rollout_common.cuh"
 
 namespace mtp {
 namespace {
 
 constexpr int kThreads = 128;
-
 
 // Threads per block: fill as many SMs as the batch allows (one thread per
 // candidate; small batches get one warp per block).
@@ -28,6 +35,24 @@ inline int rollout_block(int rows) {
   int bd = 128;
   while (bd > 32 && (rows + bd - 1) / bd < sms) bd >>= 1;
   return bd;
+}
+
+// Dynamic shared memory of a rollout block of `block` threads staging K
+// controls per step T steps at a time (0 for direct loads).
+template <int K, int T>
+constexpr size_t staged_smem(int block) {
+  if constexpr (T == 0) return 0;
+  else return (size_t)(block / 32) * StageShape<K, T>::kWarpBytes;
+}
+
+// This warp's staging area in the block's dynamic shared memory.
+__device__ __forceinline__ unsigned char* warp_stage_area(size_t warp_bytes) {
+  extern __shared__ __align__(16) unsigned char rollout_dyn_smem[];
+  return rollout_dyn_smem + (threadIdx.x >> 5) * warp_bytes;
+}
+
+__device__ __forceinline__ void report_stage_timeout(const RolloutArgs& a) {
+  if (a.status) atomicOr(a.status, kStatusStageTimeout);
 }
 
 // ---------------------------------------------------------------------------
@@ -71,16 +96,20 @@ __device__ __forceinline__ float pm_state_cost(const PointMassModel& pm, const f
   return fmaf(pm.w_target, dist2, pm.w_obs * pen);
 }
 
-template <int K, int PF, bool ALL>
+// The K controls of step t drive v += dt g u, p += dt v (g: the per-model
+// control gains of the domain randomisation); the stage cost is taken
+// before the step and the terminal cost on the final state.
+template <int K, int PF, bool ALL, int T>
 __device__ __forceinline__ void rollout_pm_body(const RolloutArgs& a, const PointMassModel& pm,
-                                                int r) {
+                                                int r, bool live, StagedRows<K, T>* st) {
   const int b = a.row0 + r;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
   const float* Ub = a.U + (size_t)r * a.H * K;
   const int models = (a.dr_mode == MTP_DR_SHARED) ? a.R : 1;
   const float dt = a.dt;
   float total = 0.f;
-  for (int mdl = 0; mdl < models; ++mdl) {
+  bool ok = true;
+  for (int mdl = 0; mdl < models && ok; ++mdl) {
     const uint32_t unit = (a.dr_mode == MTP_DR_SHARED) ? (uint32_t)mdl : (uint32_t)b;
     float gain[K], p[K], v[K];
     dr_scales<K>(a, iter, unit, gain);
@@ -98,48 +127,31 @@ __device__ __forceinline__ void rollout_pm_body(const RolloutArgs& a, const Poin
       }
     }
     KahanSum J;
-    // controls are requested PF steps ahead into a rotating register buffer
-    // (the time loop is unrolled by PF so slots are constants)
-    float ubuf[PF][K];
+    ok = for_each_step<K, PF, T>(Ub, a.H, st, [&](int t, const float (&u)[K]) {
+      float uu = 0.f;
 #pragma unroll
-    for (int q = 0; q < PF; ++q)
+      for (int k = 0; k < K; ++k) uu = fmaf(u[k], u[k], uu);
+      J.add(fmaf(pm.w_ctrl, uu, pm_state_cost<K, ALL>(pm, p)), a.kahan);
 #pragma unroll
-      for (int k = 0; k < K; ++k) ubuf[q][k] = __ldg(Ub + min(q, a.H - 1) * K + k);
-    for (int t0 = 0; t0 < a.H; t0 += PF) {
-      Unroll<0, PF>::run([&](auto Q) {
-        constexpr int q = decltype(Q)::value;
-        const int t = t0 + q;
-        if (t < a.H) {
-          float u[K];
-          float uu = 0.f;
-          const int tn = min(t + PF, a.H - 1);
+      for (int k = 0; k < K; ++k) {
+        v[k] = fmaf(gain[k], u[k], v[k]);
+        p[k] = fmaf(dt, v[k], p[k]);
+      }
+      if (a.X) {
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            u[k] = ubuf[q][k];
-            ubuf[q][k] = __ldg(Ub + tn * K + k);
-            uu = fmaf(u[k], u[k], uu);
-          }
-          J.add(fmaf(pm.w_ctrl, uu, pm_state_cost<K, ALL>(pm, p)), a.kahan);
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            v[k] = fmaf(gain[k], u[k], v[k]);
-            p[k] = fmaf(dt, v[k], p[k]);
-          }
-          if (a.X) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-              a.X[(size_t)(t + 1) * 2 * K + k] = p[k];
-              a.X[(size_t)(t + 1) * 2 * K + K + k] = v[k];
-            }
-          }
+        for (int k = 0; k < K; ++k) {
+          a.X[(size_t)(t + 1) * 2 * K + k] = p[k];
+          a.X[(size_t)(t + 1) * 2 * K + K + k] = v[k];
         }
-      });
-    }
+      }
+    });
     J.add(pm.w_term * pm_state_cost<K, ALL>(pm, p), a.kahan);
     total += J.s;
   }
+  if (!live) return;
   float c = total / (float)models;
-  if (!isfinite(c)) c = __int_as_float(0x7f800000);
+  if (!isfinite(c) || !ok) c = __int_as_float(0x7f800000);
+  if (!ok) report_stage_timeout(a);
   a.cost[r] = c;
 }
 
@@ -158,9 +170,9 @@ __device__ __forceinline__ void chain_tip(const float (&len)[NL], const float (&
   }
 }
 
-template <int NL, int PF>
+template <int NL, int PF, int T>
 __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const ChainModel& cm,
-                                                   int r) {
+                                                   int r, bool live, StagedRows<NL, T>* st) {
   const int b = a.row0 + r;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
   const float* Ub = a.U + (size_t)r * a.H * NL;
@@ -170,7 +182,8 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
 #pragma unroll
   for (int j = 0; j < NL; ++j) len[j] = cm.length[j];
   float total = 0.f;
-  for (int mdl = 0; mdl < models; ++mdl) {
+  bool ok = true;
+  for (int mdl = 0; mdl < models && ok; ++mdl) {
     const uint32_t unit = (a.dr_mode == MTP_DR_SHARED) ? (uint32_t)mdl : (uint32_t)b;
     // Lagrangian constants: beta_j = m_j/2 + sum_{i>j} m_i, lb_j = l_j beta_j,
     // D_jj = l_j^2 (m_j/3 + sum_{i>j} m_i), G_j = g l_j beta_j.
@@ -209,22 +222,11 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
       }
     }
     KahanSum J;
-    float ubuf[PF][NL];
-#pragma unroll
-    for (int q = 0; q < PF; ++q)
-#pragma unroll
-      for (int j = 0; j < NL; ++j) ubuf[q][j] = __ldg(Ub + min(q, a.H - 1) * NL + j);
-    for (int t0 = 0; t0 < a.H; t0 += PF) {
-     Unroll<0, PF>::run([&](auto Q) {
-      constexpr int q = decltype(Q)::value;
-      const int t = t0 + q;
-      if (t >= a.H) return;
+    ok = for_each_step<NL, PF, T>(Ub, a.H, st, [&](int t, const float (&u)[NL]) {
       float c[NL], s[NL], tau[NL];
-      const int tn = min(t + PF, a.H - 1);
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
-        tau[j] = ubuf[q][j];
-        ubuf[q][j] = __ldg(Ub + tn * NL + j);  // PF steps ahead
+        tau[j] = u[j];
         sincos_reduced(phi[j], &s[j], &c[j]);
       }
       // stage cost c(x_t, u_t): reach error of the tip and torque penalty
@@ -238,20 +240,20 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
         J.add(fmaf(cm.w_target, fmaf(ex, ex, ey * ey), cm.w_ctrl * tt), a.kahan);
       }
       // mass matrix (lower triangle) and right-hand side
-      using T = Tri<NL>;
-      float A[T::size], rhs[NL], inv[NL];
+      using Tr = Tri<NL>;
+      float A[Tr::size], rhs[NL], inv[NL];
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
         const float q_next = (j + 1 < NL) ? tau[j + 1] : 0.f;
         rhs[j] = fmaf(-G[j], c[j], tau[j] - q_next);
-        A[T::at(j, j)] = Dd[j];
+        A[Tr::at(j, j)] = Dd[j];
       }
       // mass matrix entries below the diagonal: D_jk = l_k lb_j for k < j
       Unroll<1, NL>::run([&](auto J) {
         constexpr int j = decltype(J)::value;
         Unroll<0, j>::run([&](auto K) {
           constexpr int k = decltype(K)::value;
-          A[T::at(j, k)] = (len[k] * lb[j]) * fmaf(c[j], c[k], s[j] * s[k]);  // cos(phi_j - phi_k)
+          A[Tr::at(j, k)] = (len[k] * lb[j]) * fmaf(c[j], c[k], s[j] * s[k]);  // cos(phi_j - phi_k)
         });
       });
       // velocity terms sum_k D_jk sin(phi_j - phi_k) w_k^2 in O(NL): with
@@ -288,20 +290,20 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
       // triangular solves
       Unroll<0, NL>::run([&](auto J) {
         constexpr int j = decltype(J)::value;
-        float d = A[T::at(j, j)];
+        float d = A[Tr::at(j, j)];
         Unroll<0, j>::run([&](auto K) {
           constexpr int k = decltype(K)::value;
-          d = fmaf(-A[T::at(j, k)], A[T::at(j, k)], d);
+          d = fmaf(-A[Tr::at(j, k)], A[Tr::at(j, k)], d);
         });
         inv[j] = rsqrtf(d);
         Unroll<j + 1, NL>::run([&](auto I) {
           constexpr int i = decltype(I)::value;
-          float v = A[T::at(i, j)];
+          float v = A[Tr::at(i, j)];
           Unroll<0, j>::run([&](auto K) {
             constexpr int k = decltype(K)::value;
-            v = fmaf(-A[T::at(i, k)], A[T::at(j, k)], v);
+            v = fmaf(-A[Tr::at(i, k)], A[Tr::at(j, k)], v);
           });
-          A[T::at(i, j)] = v * inv[j];
+          A[Tr::at(i, j)] = v * inv[j];
         });
       });
       Unroll<0, NL>::run([&](auto I) {
@@ -309,7 +311,7 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
         float v = rhs[i];
         Unroll<0, i>::run([&](auto K) {
           constexpr int k = decltype(K)::value;
-          v = fmaf(-A[T::at(i, k)], rhs[k], v);
+          v = fmaf(-A[Tr::at(i, k)], rhs[k], v);
         });
         rhs[i] = v * inv[i];
       });
@@ -318,7 +320,7 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
         float v = rhs[i];
         Unroll<i + 1, NL>::run([&](auto K) {
           constexpr int k = decltype(K)::value;
-          v = fmaf(-A[T::at(k, i)], rhs[k], v);
+          v = fmaf(-A[Tr::at(k, i)], rhs[k], v);
         });
         rhs[i] = v * inv[i];
       });
@@ -336,8 +338,7 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
           xo[NL + j] = w[j] - (j ? w[j - 1] : 0.f);
         }
       }
-     });
-    }
+    });
     {
       float c[NL], s[NL], x, y;
 #pragma unroll
@@ -348,24 +349,38 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
     }
     total += J.s;
   }
+  if (!live) return;
   float cst = total / (float)models;
-  if (!isfinite(cst)) cst = __int_as_float(0x7f800000);
+  if (!isfinite(cst) || !ok) cst = __int_as_float(0x7f800000);
+  if (!ok) report_stage_timeout(a);
   a.cost[r] = cst;
 }
 
-template <int K>
+// Standalone launches: one thread per candidate row.  Direct loads (T = 0)
+// let threads past the last row leave at once; staged loads keep every lane
+// of a warp in the warp's copy protocol.
+template <int K, int T>
 __global__ void __launch_bounds__(kThreads) k_rollout_pm(const RolloutArgs a,
                                                          const PointMassModel pm) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.rows) return;
-  rollout_pm_body<K, kPrefetchAlone, true>(a, pm, r);
+  if constexpr (T == 0) {
+    if (r >= a.rows) return;
+    rollout_pm_body<K, kPrefetchAlone, true, 0>(a, pm, r, true, nullptr);
+  } else {
+    if (__all_sync(0xffffffffu, r >= a.rows)) return;
+    const bool live = r < a.rows;
+    StagedRows<K, T> st;
+    st.init(warp_stage_area(StageShape<K, T>::kWarpBytes), live ? a.U + (size_t)r * a.H * K : nullptr,
+            a.H);
+    rollout_pm_body<K, kPrefetchAlone, true, T>(a, pm, r, live, &st);
+  }
 }
 
 // Rows are padded to whole warps, so a warp belongs to one instance: each
 // warp copies its instance's model (goal, obstacles) to shared memory once.
 // Read from global memory, the obstacle data cost about 6K + 9 loads per
 // step through L1; the standalone kernel reads it as constant operands.
-template <int K>
+template <int K, int T>
 __global__ void __launch_bounds__(kThreads) k_rollout_pm_batch(const RolloutArgs* __restrict__ ra,
                                                                const PointMassModel* __restrict__ pm,
                                                                const int* __restrict__ row_start,
@@ -384,19 +399,36 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm_batch(const RolloutArgs
   }
   const RolloutArgs a = ra[i];
   const int r = g - __ldg(row_start + i);
-  if (r >= a.rows) return;
-  rollout_pm_body<K, kPrefetchBatch, false>(a, m, r);
+  const bool live = r < a.rows;
+  if constexpr (T == 0) {
+    if (!live) return;
+    rollout_pm_body<K, kPrefetchBatch, false, 0>(a, m, r, true, nullptr);
+  } else {
+    StagedRows<K, T> st;
+    st.init(warp_stage_area(StageShape<K, T>::kWarpBytes), live ? a.U + (size_t)r * a.H * K : nullptr,
+            a.H);
+    rollout_pm_body<K, kPrefetchBatch, false, T>(a, m, r, live, &st);
+  }
 }
 
-template <int NL>
+template <int NL, int T>
 __global__ void __launch_bounds__(kThreads) k_rollout_chain(const RolloutArgs a,
                                                             const ChainModel cm) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.rows) return;
-  rollout_chain_body<NL, kPrefetchAlone>(a, cm, r);
+  if constexpr (T == 0) {
+    if (r >= a.rows) return;
+    rollout_chain_body<NL, kPrefetchAlone, 0>(a, cm, r, true, nullptr);
+  } else {
+    if (__all_sync(0xffffffffu, r >= a.rows)) return;
+    const bool live = r < a.rows;
+    StagedRows<NL, T> st;
+    st.init(warp_stage_area(StageShape<NL, T>::kWarpBytes),
+            live ? a.U + (size_t)r * a.H * NL : nullptr, a.H);
+    rollout_chain_body<NL, kPrefetchAlone, T>(a, cm, r, live, &st);
+  }
 }
 
-template <int NL>
+template <int NL, int T>
 __global__ void __launch_bounds__(kThreads) k_rollout_chain_batch(const RolloutArgs* __restrict__ ra,
                                                                   const ChainModel* __restrict__ cms,
                                                                   const int* __restrict__ row_start,
@@ -407,99 +439,17 @@ __global__ void __launch_bounds__(kThreads) k_rollout_chain_batch(const RolloutA
   const RolloutArgs a = ra[i];
   const ChainModel cm = cms[i];
   const int r = g - __ldg(row_start + i);
-  if (r >= a.rows) return;
-  rollout_chain_body<NL, kPrefetchBatch>(a, cm, r);
-}
-
-template <int K>
-cudaError_t pm_dispatch(const RolloutArgs& a, const PointMassModel& m, int k, cudaStream_t s) {
-  if constexpr (K <= 16) {
-    if (k == K) {
-      const int bd = rollout_block(a.rows);
-      k_rollout_pm<K><<<(a.rows + bd - 1) / bd, bd, 0, s>>>(a, m);
-      return cudaGetLastError();
-    }
-    return pm_dispatch<K + 1>(a, m, k, s);
+  const bool live = r < a.rows;
+  if constexpr (T == 0) {
+    if (!live) return;
+    rollout_chain_body<NL, kPrefetchBatch, 0>(a, cm, r, true, nullptr);
   } else {
-    return cudaErrorInvalidValue;
-  }
-}
-
-template <int NL>
-cudaError_t chain_dispatch(const RolloutArgs& a, const ChainModel& m, int links, cudaStream_t s) {
-  if constexpr (NL <= 12) {
-    if (links == NL) {
-      const int bd = rollout_block(a.rows);
-      k_rollout_chain<NL><<<(a.rows + bd - 1) / bd, bd, 0, s>>>(a, m);
-      return cudaGetLastError();
-    }
-    return chain_dispatch<NL + 1>(a, m, links, s);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-}
-
-template <int K>
-cudaError_t pm_batch_dispatch(const RolloutArgs* ra, const PointMassModel* pm, const int* row_start,
-                              int count, int total_rows, int k, int block, cudaStream_t s) {
-  if constexpr (K <= 16) {
-    if (k == K) {
-      k_rollout_pm_batch<K><<<(total_rows + block - 1) / block, block, 0, s>>>(ra, pm, row_start, count);
-      return cudaGetLastError();
-    }
-    return pm_batch_dispatch<K + 1>(ra, pm, row_start, count, total_rows, k, block, s);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-}
-
-template <int NL>
-cudaError_t chain_batch_dispatch(const RolloutArgs* ra, const ChainModel* cm, const int* row_start,
-                                 int count, int total_rows, int links, int block, cudaStream_t s) {
-  if constexpr (NL <= 12) {
-    if (links == NL) {
-      k_rollout_chain_batch<NL><<<(total_rows + block - 1) / block, block, 0, s>>>(ra, cm, row_start,
-                                                                                 count);
-      return cudaGetLastError();
-    }
-    return chain_batch_dispatch<NL + 1>(ra, cm, row_start, count, total_rows, links, block, s);
-  } else {
-    return cudaErrorInvalidValue;
+    StagedRows<NL, T> st;
+    st.init(warp_stage_area(StageShape<NL, T>::kWarpBytes),
+            live ? a.U + (size_t)r * a.H * NL : nullptr, a.H);
+    rollout_chain_body<NL, kPrefetchBatch, T>(a, cm, r, live, &st);
   }
 }
 
 }  // namespace
-
-cudaError_t launch_rollout_pointmass_batch(const RolloutArgs* d_ra, const PointMassModel* d_pm,
-                                           const int* d_row_start, int count, int total_rows,
-                                           int k, int block, cudaStream_t s) {
-  if (total_rows <= 0) return cudaSuccess;
-  return pm_batch_dispatch<1>(d_ra, d_pm, d_row_start, count, total_rows, k, block, s);
-}
-
-cudaError_t launch_rollout_chain_batch(const RolloutArgs* d_ra, const ChainModel* d_cm,
-                                       const int* d_row_start, int count, int total_rows,
-                                       int links, int block, cudaStream_t s) {
-  if (total_rows <= 0) return cudaSuccess;
-  return chain_batch_dispatch<1>(d_ra, d_cm, d_row_start, count, total_rows, links, block, s);
-}
-
-cudaError_t launch_rollout_pointmass(const RolloutArgs& a, const PointMassModel& m,
-                                     cudaStream_t s) {
-  if (a.rows <= 0) return cudaSuccess;
-  return pm_dispatch<1>(a, m, a.n, s);
-}
-
-cudaError_t launch_rollout_chain(const RolloutArgs& a, const ChainModel& m, int links,
-                                 cudaStream_t s) {
-  if (a.rows <= 0) return cudaSuccess;
-  return chain_dispatch<1>(a, m, links, s);
-}
-
-int rollout_blocks(int rows) {
-  if (rows <= 0) return 0;
-  const int bd = rollout_block(rows);
-  return (rows + bd - 1) / bd;
-}
-
 }  // namespace mtp

@@ -43,7 +43,7 @@ EXPORTS = [
     "mtp_set_profiling", "mtp_stage_times", "mtp_stage_times5", "mtp_elite_update_noalloc",
     "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_layout", "mtp_batch_plan_step",
     "mtp_batch_autotune", "mtp_batch_reserve", "mtp_batch_fill", "mtp_batch_shift",
-    "mtp_batch_launches", "mtp_batch_rollout_times",
+    "mtp_batch_launches", "mtp_batch_rollout_times", "mtp_device_status",
     "mtp_problem_device_bytes", "mtp_server_create", "mtp_server_destroy", "mtp_server_register",
     "mtp_submit", "mtp_poll", "mtp_server_get_stats", "mtp_server_last_error",
     "mtp_submit_many", "mtp_poll_many",
@@ -137,6 +137,7 @@ def load_library(path: str = LIB_PATH):
         "mtp_plan_step_host": (i32, [vp, vp, i32, vp, vp]),
         "mtp_shift": (i32, [vp, i32, vp]),
         "mtp_get_state": (i32, [vp, vp, vp, vp]),
+        "mtp_device_status": (i32, [vp]),
         "mtp_set_state": (i32, [vp, vp, vp, u32]),
         "mtp_set_profiling": (i32, [vp, i32]),
         "mtp_stage_times": (i32, [vp, vp, vp]),
@@ -422,6 +423,12 @@ def mtp_shift(h: Handle, k: int, stream=None):
     _check(load_library().mtp_shift(h.ptr, k, _stream(stream)), h.ptr)
 
 
+def mtp_device_status(h: Handle):
+    """Raises MtpError (MTP_ERR_TIMEOUT) if a bounded device wait of the
+    handle's rollouts gave up since the last check; synchronises."""
+    _check(load_library().mtp_device_status(h.ptr), h.ptr)
+
+
 def mtp_get_state(h: Handle):
     s = h.sizes
     mu = np.empty((s["H"], s["n"]), np.float64)
@@ -570,13 +577,13 @@ def mtp_batch_plan_step(b: Batch, x0, iters: int, ustar, stream=None):
 
 
 def mtp_batch_autotune(b: Batch, stream=None):
-    """Returns [(dyn, dim, block), ...] per rollout group."""
+    """Returns [(dyn, dim, block, chunk), ...] per rollout group."""
     groups = len(b.handles)
-    out = (C.c_int32 * (3 * groups))()
+    out = (C.c_int32 * (4 * groups))()
     ng = C.c_int32()
     _check(load_library().mtp_batch_autotune(b.ptr, C.addressof(out), C.addressof(ng),
                                              _stream(stream)))
-    return [(out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i in range(ng.value)]
+    return [tuple(out[4 * i + k] for k in range(4)) for i in range(ng.value)]
 
 
 def mtp_batch_launches(b: Batch, iters: int = 1) -> int:
@@ -591,13 +598,13 @@ def mtp_batch_rollout_times(b: Batch, reps: int = 3, stream=None):
     dim, block, instances, candidates, steps and ms (average device time)."""
     groups = max(1, len(b.handles))
     ms = (C.c_double * groups)()
-    info = (C.c_int32 * (6 * groups))()
+    info = (C.c_int32 * (7 * groups))()
     ng = C.c_int32()
     _check(load_library().mtp_batch_rollout_times(b.ptr, int(reps), C.addressof(ms),
                                                   C.addressof(info), groups, C.addressof(ng),
                                                   _stream(stream)))
-    keys = ("dyn", "dim", "block", "instances", "candidates", "steps")
-    return [dict(zip(keys, (int(info[6 * g + k]) for k in range(6))), ms=float(ms[g]))
+    keys = ("dyn", "dim", "block", "instances", "candidates", "steps", "chunk")
+    return [dict(zip(keys, (int(info[7 * g + k]) for k in range(7))), ms=float(ms[g]))
             for g in range(ng.value)]
 
 

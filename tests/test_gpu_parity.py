@@ -317,6 +317,35 @@ def test_chain_states(mtp, links):
     mtp.mtp_destroy(h)
 
 
+@pytest.mark.parametrize("spec", [W.pointmass(k=3, B=300, H=40), W.pointmass(k=12, B=100, H=32),
+                                  W.chain(links=5, B=200, H=64), W.chain(links=7, B=70, H=36)])
+def test_staged_and_direct_control_loads_agree(mtp, spec):
+    """Rollouts stage each warp's controls through shared memory with bulk
+    copies when the rows are 16-byte aligned; the same rows at a 4-byte
+    offset are read directly instead.  Both give the oracle's costs and the
+    same bits."""
+    h = mtp.mtp_create(spec)
+    s = h.sizes
+    U32 = _rand_U(spec, s["B"], s["n"])
+    n_el = U32.size
+    buf = torch.zeros(n_el + 4, device=DEV)
+    aligned, shifted = buf[:n_el], buf[1:1 + n_el]
+    assert aligned.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 4
+    x0 = _t(np.array(spec["x0"], np.float32))
+    costs = []
+    for view in (aligned, shifted):
+        view.copy_(_t(U32).reshape(-1))
+        c = torch.empty(s["B"], device=DEV)
+        mtp.mtp_rollout_cost(h, 1, x0, view.view(s["B"], s["H"], s["n"]), c)
+        torch.cuda.synchronize()
+        costs.append(_np(c))
+    assert np.array_equal(costs[0], costs[1])
+    ref = orc.rollout_costs(spec, 1, np.array(spec["x0"], np.float64), U32.astype(np.float64))
+    assert _cost_close(costs[0], ref) <= COST_RTOL
+    mtp.mtp_device_status(h)  # no bounded wait gave up
+    mtp.mtp_destroy(h)
+
+
 # ----------------------------------------------------------------------------
 # Top-E and the update
 # ----------------------------------------------------------------------------

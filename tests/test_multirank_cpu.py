@@ -1,6 +1,6 @@
-"""The N>1 path on CPU: two gloo ranks each plan their own instance (replicas,
-no collective on the data path); the timing reduction takes the slowest
-rank and the job rate counts the units of all ranks."""
+"""The N>1 path on CPU: two gloo ranks each plan their own instances
+(replicas, no collective on the data path); the timing reduction takes the
+slowest rank and the job rate counts the units of all ranks."""
 import os
 import socket
 
@@ -25,14 +25,17 @@ def _rank_main(rank, world, port, out_dir):
     import bench
     import oracle
     from paper_2505_01059_gb300 import workloads as W
-    spec = bench.rank_spec(W.pointmass(B=64, E=8, H=16), rank)
-    mu, sigma = W.initial_distribution(spec)
-    out = oracle.plan_iteration(spec, 0, np.array(spec["x0"]), mu, sigma)
+    specs = bench.rank_specs([W.pointmass(B=64, E=8, H=16), W.chain(links=3, B=32, E=4, H=8)],
+                             rank)
+    costs = []
+    for spec in specs:
+        mu, sigma = W.initial_distribution(spec)
+        costs.append(oracle.plan_iteration(spec, 0, np.array(spec["x0"]), mu, sigma)["cost"])
     my_time = 1.0 + rank  # a stand-in per-rank time: rank 1 is the slowest
     t_max = bench.max_over_ranks(my_time, dist, torch.device("cpu"))
-    rate = bench.job_rate(world, spec["B"] * spec["H"], t_max)
-    np.savez(os.path.join(out_dir, f"rank{rank}.npz"), seed=spec["seed"], cost=out["cost"],
-             t_max=t_max, rate=rate)
+    rate = bench.job_rate(world, sum(s["B"] * s["H"] for s in specs), t_max)
+    np.savez(os.path.join(out_dir, f"rank{rank}.npz"), seed=specs[0]["seed"],
+             cost=np.concatenate(costs), t_max=t_max, rate=rate)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -45,4 +48,4 @@ def test_two_gloo_ranks_plan_independent_replicas(tmp_path):
     assert int(r0["seed"]) != int(r1["seed"])              # each rank its own instance
     assert not np.array_equal(r0["cost"], r1["cost"])      # independent work
     assert float(r0["t_max"]) == float(r1["t_max"]) == 2.0  # slowest rank's time on both
-    assert float(r0["rate"]) == pytest.approx(2 * 64 * 16 / 2.0)
+    assert float(r0["rate"]) == pytest.approx(2 * (64 * 16 + 32 * 8) / 2.0)

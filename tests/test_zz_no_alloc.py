@@ -7,8 +7,8 @@ the C ABI it is called twice in a row with different costs, and each time
 its elite indices, u*, new mean and new spread are compared with what
 mtp_elite_update produces from the same inputs on a handle: both run the
 same selection and update kernels, so the results must be the same bits.
-The device's free memory and PyTorch's allocated bytes are read around the
-calls and must not change.  The file is collected last, so a run that stops
+The device's free memory and PyTorch's count of allocations are read around
+the calls and must not change.  The file is collected last, so a run that stops
 at its first failure has run every other test before this one.
 """
 import numpy as np
@@ -34,9 +34,13 @@ def mtp():
 
 
 def _memory():
-    """(free device bytes as the driver reports them, PyTorch's allocated bytes)."""
+    """(free device bytes as the driver reports them, allocations PyTorch's
+    caching allocator has made so far).  The second is a running count of
+    allocation events, so a tensor the test itself frees in between does not
+    move it."""
     torch.cuda.synchronize()
-    return torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    return (torch.cuda.mem_get_info()[0],
+            torch.cuda.memory_stats().get("allocation.all.allocated", 0))
 
 
 @pytest.mark.parametrize("rule,alpha,E,B", [("softmax", 0.0, 64, 4096), ("softmax", 0.25, 512, 4096),
@@ -82,7 +86,7 @@ def test_noalloc_matches_handle_update_twice(mtp, rule, alpha, E, B):
     # the second call allocates nothing at all; the first may only have
     # loaded code (the driver's free count moves in whole pages, if at all)
     assert mem[1][0] == mem[1][1], f"device memory changed over the second call: {mem[1]}"
-    assert mem[0][0][1] == mem[0][1][1], "PyTorch allocated memory during the first call"
+    assert mem[0][0][1] == mem[0][1][1], "PyTorch allocated during the first call"
     mtp.mtp_destroy(h)
 
 
