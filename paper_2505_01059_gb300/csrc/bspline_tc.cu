@@ -1,0 +1,347 @@
+// bspline_tc.cu -- Def. 2 B-spline interpolation of the graph paths as a
+// dense contraction on the 5th-generation tensor cores (tcgen05), for the
+// BF16-operand mode (MTP_FLAG_BF16_BASIS).
+//
+// The graph rows of an iteration are U[b, t, i] = sum_m B[t, m] C[b, m, i]
+// (Def. 2 with the basis B_p sampled at the H evaluation times and the
+// waypoints C of path b, Alg. 1).  Seen as one GEMM, D[t, (b, i)] =
+// sum_m A[t, m] B[m, (b, i)] with A the (H x M) basis table and B the
+// gathered waypoints, K = M.  Each CTA (one warpgroup) takes a tile of up to
+// kPaths paths: it draws their layer indices (Alg. 1), gathers their
+// waypoints from the iteration's graph Z, rounds them to bfloat16 into the
+// B operand (K-major, 16 columns per path, the columns past n zero), and one
+// thread issues tcgen05.mma.cta_group::1.kind::f16 (BF16 x BF16 -> FP32,
+// M = 128 steps per instruction, N = 128, K = 16 per instruction) for each
+// 128-step slice of the horizon, accumulating in tensor memory.  The
+// products of two bfloat16 values are exact in FP32; the sums are FP32.
+// The epilogue reads each path's columns back with tcgen05.ld, clamps them
+// to the control box and writes them through a per-warp shared-memory
+// transpose as contiguous, coalesced rows of U.
+//
+// Shared-memory operands use the canonical K-major layout without swizzle:
+// 8-row x 16-byte core matrices, the two (or more) core matrices of a row
+// group along K 128 bytes apart (leading byte offset) and consecutive row
+// groups 16 K bytes apart (stride byte offset).  Each CTA allocates 256
+// tensor-memory columns (two 128-column accumulators, one per horizon
+// slice) and asks for enough shared memory that at most two CTAs share an
+// SM, so their allocations always fit the SM's 512 columns.
+#include <algorithm>
+
+#include <cuda_bf16.h>
+
+#include "mtp_device.cuh"
+
+namespace mtp {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kPaths = 8;            // paths per tile, 16 accumulator columns each
+constexpr int kNTile = kPaths * 16;  // MMA N
+constexpr int kMaxK = 64;            // layers (M) padded to a multiple of 16
+constexpr int kMaxSlices = 2;        // 128-step horizon slices (H <= 256)
+constexpr uint32_t kTmemCols = 256;
+constexpr size_t kMinSmem = 80 * 1024;  // at most two CTAs per SM (their TMEM fits)
+
+struct TcSmem {
+  __nv_bfloat16 A[kMaxSlices][128 * kMaxK];  // basis, K-major canonical layout
+  __nv_bfloat16 B[kNTile * kMaxK];           // waypoints, K-major canonical layout
+  float stage[kTcThreads / 32][32 * 33];     // per-warp transpose of one path's rows
+  float lo[MTP_MAX_CTRL], hi[MTP_MAX_CTRL];
+  uint64_t mma_bar;
+  uint32_t tmem_base;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of element (row, k) in a K-major, unswizzled canonical layout
+// with K columns: core matrix (row / 8, k / 8), row (row % 8) of 16 bytes.
+__device__ __forceinline__ int kmajor_offset(int row, int k, int K) {
+  return (row >> 3) * (16 * K) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, leading and stride
+// byte offsets (all in 16-byte units), the fixed version field (bits 46-48 =
+// 0b001), no base offset, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1),
+// BF16 A and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17,
+// M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded_tc(uint64_t* bar, uint32_t parity) {
+  const unsigned addr = smem_u32(bar);
+  uint64_t t_start = 0;
+  for (int spin = 0;; ++spin) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    uint64_t now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (spin == 0) t_start = now;
+    else if (now - t_start > 2000000000ull) return false;
+  }
+}
+
+// The basis of one instance as the A operand of each horizon slice:
+// A[s][r][k] = basis[(128 s + r) * M + k], zero past H and past M.
+__device__ void load_basis(TcSmem& S, const CandArgs& a, int K) {
+  const int H = a.dm.H, M = a.dm.M;
+  unsigned char* base = reinterpret_cast<unsigned char*>(&S.A[0][0]);
+  const int slices = (H + 127) / 128;
+  for (int e = threadIdx.x; e < slices * 128 * K; e += blockDim.x) {
+    const int s = e / (128 * K), rem = e - s * 128 * K;
+    const int r = rem / K, k = rem - r * K;
+    const int t = 128 * s + r;
+    const float v = (t < H && k < M) ? a.basis[(size_t)t * M + k] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(base + (size_t)s * sizeof(S.A[0]) + kmajor_offset(r, k, K)) =
+        __float2bfloat16_rn(v);
+  }
+}
+
+// Tile `tile` of one instance's graph rows.  Returns false when the bounded
+// wait for the MMA gave up.
+__device__ bool tc_tile(TcSmem& S, const CandArgs& a, int tile, int K, uint32_t iter,
+                        uint32_t& phase) {
+  const Dims dm = a.dm;
+  const int H = dm.H, n = dm.n, M = dm.M, N = dm.N;
+  const int b0 = tile * kPaths;
+  const int nb = min(kPaths, a.graph_rows - b0);
+  unsigned char* Bb = reinterpret_cast<unsigned char*>(S.B);
+  // Alg. 1 for the tile's paths and the gather of their waypoints, rounded
+  // to bfloat16, into the B operand: column 16 p + i, row m.
+  for (int e = threadIdx.x; e < nb * M; e += blockDim.x) {
+    const int p = e / M, m = e - p * M;
+    const float* z;
+    if (a.C_in) {
+      z = a.C_in + ((size_t)(b0 + p) * M + m) * n;
+    } else {
+      const uint4 r = philox(make_uint4((uint32_t)(b0 + p), (uint32_t)(m >> 2), iter, kTagPath), a.key);
+      const int j = index_of(pick(r, (uint32_t)(m & 3)), (uint32_t)N);
+      z = a.Z_global + ((size_t)m * N + j) * n;
+    }
+    for (int i = 0; i < n; ++i)
+      *reinterpret_cast<__nv_bfloat16*>(Bb + kmajor_offset(16 * p + i, m, K)) = __float2bfloat16_rn(z[i]);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  const int slices = (H + 127) / 128;
+  if (threadIdx.x == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t idesc = idesc_bf16(128, kNTile);
+    const uint32_t sbo = 16u * (uint32_t)K;
+    for (int s = 0; s < slices; ++s) {
+      const uint32_t d_tmem = S.tmem_base + (uint32_t)(s * kNTile);
+      for (int ks = 0; ks < K / 16; ++ks) {
+        const uint64_t ad = smem_desc(smem_u32(&S.A[s][0]) + 256u * ks, 128u, sbo);
+        const uint64_t bd = smem_desc(smem_u32(&S.B[0]) + 256u * ks, 128u, sbo);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&S.mma_bar))
+                 : "memory");
+  }
+  const bool ok = mbar_wait_bounded_tc(&S.mma_bar, phase);
+  phase ^= 1u;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!__syncthreads_and(ok)) return false;
+  // epilogue: warp w reads accumulator lanes 32 w .. 32 w + 31 (steps
+  // t0 .. t0 + 31 of each slice) path by path
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S_row = n | 1;  // odd row stride: conflict-free transposition
+  float* st = S.stage[w];
+  for (int s = 0; s < slices; ++s) {
+    const int t0 = 128 * s + 32 * w;
+    const int rows = min(32, H - t0);
+    for (int p = 0; p < nb; ++p) {
+      const uint32_t taddr = S.tmem_base + ((uint32_t)(32 * w) << 16) + (uint32_t)(s * kNTile + 16 * p);
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+            "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (rows > 0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (i < n) st[lane * S_row + i] = clamp_box(__uint_as_float(v[i]), S.lo[i], S.hi[i]);
+        __syncwarp();
+        float* out = a.U_graph + ((size_t)(b0 + p) * H + t0) * n;
+        const int count = rows * n;
+        int t = lane / n, i = lane - (lane / n) * n;
+        const int dt = 32 / n, di = 32 - (32 / n) * n;
+        for (int e = lane; e < count; e += 32) {
+          out[e] = st[t * S_row + i];
+          t += dt;
+          i += di;
+          if (i >= n) {
+            i -= n;
+            ++t;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  return true;
+}
+
+// Per-CTA set-up for one instance: box, basis operand, a zeroed B operand.
+__device__ void tc_instance_setup(TcSmem& S, const CandArgs& a, int K) {
+  for (int i = threadIdx.x; i < a.dm.n; i += blockDim.x) {
+    S.lo[i] = a.umin[i];
+    S.hi[i] = a.umax[i];
+  }
+  uint32_t* Bw = reinterpret_cast<uint32_t*>(S.B);
+  for (int e = threadIdx.x; e < (int)(sizeof(S.B) / 4); e += blockDim.x) Bw[e] = 0u;
+  load_basis(S, a, K);
+  __syncthreads();
+}
+
+__device__ void tc_begin(TcSmem& S) {
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&S.tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mma_bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Releases the tensor memory.  After a failed wait, first waits (bounded)
+// for the MMA still in flight.
+__device__ void tc_end(TcSmem& S, bool failed, uint32_t phase, uint32_t* status) {
+  if (failed) {
+    mbar_wait_bounded_tc(&S.mma_bar, phase ^ 1u);
+    if (threadIdx.x == 0 && status) atomicOr(status, kStatusTcTimeout);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+__device__ __forceinline__ TcSmem& tc_smem() {
+  extern __shared__ __align__(1024) unsigned char tc_dyn_smem[];
+  return *reinterpret_cast<TcSmem*>(tc_dyn_smem);
+}
+
+// One instance: CTAs loop over its path tiles.
+__global__ void __launch_bounds__(kTcThreads) k_bspline_tc(const CandArgs a, uint32_t* status) {
+  TcSmem& S = tc_smem();
+  const int K = ((a.dm.M + 15) / 16) * 16;
+  const int tiles = (a.graph_rows + kPaths - 1) / kPaths;
+  const uint32_t iter = (a.d_iter ? *a.d_iter : a.iter) + a.iter_offset;
+  tc_begin(S);
+  tc_instance_setup(S, a, K);
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x)
+    failed = !tc_tile(S, a, tile, K, iter, phase);
+  tc_end(S, failed, phase, status);
+}
+
+// Many instances: tile_start (count + 1 entries) numbers each instance's
+// first tile; CTAs loop over the global tile list, set up again whenever
+// the instance changes.
+__global__ void __launch_bounds__(kTcThreads) k_bspline_tc_batch(const CandArgs* __restrict__ args,
+                                                                 const int* __restrict__ tile_start,
+                                                                 int count, uint32_t* status) {
+  TcSmem& S = tc_smem();
+  __shared__ CandArgs sa;
+  tc_begin(S);
+  const int total = tile_start[count];
+  int cur = -1, K = 16;
+  uint32_t iter = 0, phase = 0;
+  bool failed = false;
+  for (int g = blockIdx.x; g < total && !failed; g += gridDim.x) {
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (tile_start[mid] <= g) lo = mid;
+      else hi = mid;
+    }
+    if (lo != cur) {
+      __syncthreads();
+      const int* src = reinterpret_cast<const int*>(args + lo);
+      int* dst = reinterpret_cast<int*>(&sa);
+      for (int q = threadIdx.x; q < (int)(sizeof(CandArgs) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+      __syncthreads();
+      cur = lo;
+      K = ((sa.dm.M + 15) / 16) * 16;
+      iter = (sa.d_iter ? *sa.d_iter : sa.iter) + sa.iter_offset;
+      tc_instance_setup(S, sa, K);
+    }
+    failed = !tc_tile(S, sa, g - tile_start[lo], K, iter, phase);
+  }
+  tc_end(S, failed, phase, status);
+}
+
+size_t tc_smem_bytes() { return sizeof(TcSmem) > kMinSmem ? sizeof(TcSmem) : kMinSmem; }
+
+}  // namespace
+
+bool bspline_tc_eligible(const CandArgs& a) {
+  return a.bf16 && a.interp == MTP_INTERP_BSPLINE && a.dm.H <= 128 * kMaxSlices &&
+         a.dm.M <= kMaxK && a.dm.n <= 16 && a.graph_rows > 0;
+}
+
+int bspline_tc_tiles(int graph_rows) { return (graph_rows + kPaths - 1) / kPaths; }
+
+cudaError_t init_bspline_tc_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_bspline_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_bspline_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes());
+}
+
+cudaError_t launch_bspline_tc(const CandArgs& a, uint32_t* status, cudaStream_t s) {
+  const int tiles = bspline_tc_tiles(a.graph_rows);
+  if (tiles <= 0) return cudaSuccess;
+  const int grid = std::min(tiles, 2 * device_sms());
+  k_bspline_tc<<<grid, kTcThreads, tc_smem_bytes(), s>>>(a, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bspline_tc_batch(const CandArgs* d_args, const int* d_tile_start, int count,
+                                    int total_tiles, uint32_t* status, cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const int grid = std::min(total_tiles, 2 * device_sms());
+  k_bspline_tc_batch<<<grid, kTcThreads, tc_smem_bytes(), s>>>(d_args, d_tile_start, count, status);
+  return cudaGetLastError();
+}
+
+}  // namespace mtp

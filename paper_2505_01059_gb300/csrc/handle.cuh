@@ -58,6 +58,7 @@ struct mtp_handle {
   float* Z = nullptr;  // (M, N, n) graph of the current iteration (batched planning)
   uint32_t* status = nullptr;  // device status word: bits a rollout sets when a bounded wait gave up
   int rollout_chunk = 4;       // horizon chunk of the staged control loads of a lone rollout
+  bool tc_graph = false;       // graph rows contracted on the tensor cores (BF16 B-spline)
   // replay
   cudaStream_t cap_stream = nullptr;
   std::map<int, cudaGraphExec_t> graphs;   // key: (iterations, cur, first prepared)

@@ -367,13 +367,20 @@ namespace {
 // Candidate generation of one handle (graph rows, local rows, mean row as
 // `c` asks), with the graph written first when it is not regenerated per block.
 cudaError_t launch_generate(const mtp_handle* h, CandArgs& c, cudaStream_t s) {
-  if (c.graph_blocks > 0 && h->global_Z && !c.C_in) {
+  const bool tc = c.graph_blocks > 0 && h->tc_graph && bspline_tc_eligible(c);
+  if (c.graph_blocks > 0 && (h->global_Z || tc) && !c.C_in) {
     c.Z_global = h->Z;
     cudaError_t e = launch_graph_Z(c, h->Z, s);
     if (e != cudaSuccess) return e;
   }
   const int local_blocks = c.U_local ? local_blocks_for(h, (long long)c.local_rows + 1) : 0;
-  return launch_candidates(c, local_blocks, s);
+  if (!tc) return launch_candidates(c, local_blocks, s);
+  // graph rows on the tensor cores; local rows and the mean row as usual
+  CandArgs local = c;
+  local.graph_blocks = 0;
+  cudaError_t e = launch_candidates(local, local_blocks, s);
+  if (e != cudaSuccess) return e;
+  return launch_bspline_tc(c, h->status, s);
 }
 
 cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
@@ -556,7 +563,10 @@ cudaError_t pipeline_plan(const mtp_problem& p, const Dims& dm, int paths_per_bl
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = init_prepare_attributes(smem)) != cudaSuccess) return e;
-  if ((p.flags & MTP_FLAG_NO_PIPELINE) || p.dyn == MTP_DYN_LEGGED) return cudaSuccess;
+  // the BF16 basis contraction runs on the tensor cores in its own launch,
+  // which the persistent preparation does not make: not pipelined
+  if ((p.flags & MTP_FLAG_NO_PIPELINE) || (p.flags & MTP_FLAG_BF16_BASIS) || p.dyn == MTP_DYN_LEGGED)
+    return cudaSuccess;
   const int free_sms = sms - rollout_blocks(dm.B);
   if (free_sms < kMinPrepareSMs) return cudaSuccess;
   const bool draws = free_sms >= kFullPrepareSMs && dm.L > 0;
@@ -619,6 +629,11 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   h->key.k1 = (uint32_t)(p.seed >> 32);
   h->global_Z = global_graph(dm);
   h->paths_per_block = paths_per_block_for(dm, p.interp, h->global_Z);
+  {
+    CandArgs probe = cand_args(h, 0, nullptr);
+    probe.graph_rows = dm.P;
+    h->tc_graph = bspline_tc_eligible(probe);
+  }
   auto err = [&](mtp_status s) {
     g_create_error = h->err;
     free_handle(h);
@@ -629,6 +644,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   if ((e = init_select_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
   if ((e = init_rollout_pm_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
   if ((e = init_rollout_chain_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
+  if ((e = init_bspline_tc_attributes()) != cudaSuccess) return err(cuda_fail(h, e, "attributes"));
   if ((e = pipeline_plan(p, dm, h->paths_per_block, &h->pipeline, &h->prep_local, &h->prep_grid,
                          &h->prep_smem, &h->prep_spb)) !=
       cudaSuccess)
@@ -703,7 +719,8 @@ mtp_status mtp_get_sizes(const mtp_handle* h, mtp_sizes* out) {
   const Dims& d = h->dm;
   // candidates (+ graph when written once), rollout, select, update; when
   // pipelined: finish, prepare (graph in its shared memory), rollout, select, update
-  const int kpi = h->pipeline ? 5 : (h->global_Z && d.P > 0 ? 5 : 4);
+  // (tensor-core graph rows: graph, local rows, contraction, rollout, select, update)
+  const int kpi = h->pipeline ? 5 : (h->tc_graph ? 6 : (h->global_Z && d.P > 0 ? 5 : 4));
   *out = mtp_sizes{d.B, d.P, d.L, d.E, d.H, d.n, d.d, d.M, d.N, kpi,
                    h->pipeline ? (h->prep_local ? 2 : 1) : 0};
   return MTP_OK;
@@ -734,7 +751,9 @@ mtp_status mtp_interpolate(mtp_handle* h, const float* d_C, int32_t P, float* d_
   c.U_graph = d_U;
   c.graph_rows = P;
   c.graph_blocks = (P + h->paths_per_block - 1) / h->paths_per_block;
-  cudaError_t e = launch_candidates(c, 0, (cudaStream_t)stream);
+  cudaError_t e = (h->tc_graph && bspline_tc_eligible(c))
+                      ? launch_bspline_tc(c, h->status, (cudaStream_t)stream)
+                      : launch_candidates(c, 0, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "interpolate");
   return MTP_OK;
 }

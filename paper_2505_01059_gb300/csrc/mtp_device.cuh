@@ -156,6 +156,13 @@ struct RolloutArgs {
   uint32_t* status;  // device status word of the handle (bits set by a rollout), or null
 };
 
+// Bits of a handle's device status word, set when a bounded wait gave up:
+// a rollout's wait for its staged controls (those candidates cost +inf), or
+// the tensor-core contraction's wait for its MMA (those graph rows are not
+// written).
+constexpr uint32_t kStatusStageTimeout = 1u;
+constexpr uint32_t kStatusTcTimeout = 2u;
+
 // Whether a rollout launch may stage its controls through shared memory with
 // bulk copies (see StagedRows): 16-byte aligned rows of a multiple of 4
 // floats, one model per candidate, no state output.
@@ -241,6 +248,17 @@ cudaError_t launch_rollout_legged(const RolloutArgs& a, const LeggedModel& m, in
 cudaError_t launch_rollout_legged_batch(const RolloutArgs* d_ra, const LeggedModel* d_lm,
                                         const int* d_row_start, int count, int total_rows,
                                         int links, cudaStream_t s);
+// Def. 2 graph rows on the tensor cores (BF16 operands, FP32 sums): whether a
+// generation's graph part goes there (BF16 B-spline, H <= 256, M <= 64,
+// n <= 16), its tile count, and the launches (standalone and over many
+// instances, tile_start numbering each instance's first tile).  The graph Z
+// must be in global memory (Z_global) unless C_in is given.
+bool bspline_tc_eligible(const CandArgs& a);
+int bspline_tc_tiles(int graph_rows);
+cudaError_t init_bspline_tc_attributes();
+cudaError_t launch_bspline_tc(const CandArgs& a, uint32_t* status, cudaStream_t s);
+cudaError_t launch_bspline_tc_batch(const CandArgs* d_args, const int* d_tile_start, int count,
+                                    int total_tiles, uint32_t* status, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 size_t select_smem_bytes(int B, int E);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);

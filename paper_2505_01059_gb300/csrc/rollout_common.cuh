@@ -265,9 +265,6 @@ __device__ __forceinline__ bool for_each_step(const float* Ub, int H, StagedRows
   }
 }
 
-// Status bit a rollout sets when a bounded wait gave up (its cost is +inf).
-constexpr uint32_t kStatusStageTimeout = 1u;
-
 template <int NL>
 struct Tri {
   static constexpr int size = NL * (NL + 1) / 2;
