@@ -74,9 +74,11 @@ typedef enum { MTP_DR_NONE = 0, MTP_DR_PER_SAMPLE = 1, MTP_DR_SHARED = 2 } mtp_d
 #define MTP_FLAG_BF16_BASIS 0x4u  /* B-spline contraction with BF16 operands: basis
                                      values and knots rounded to the nearest bfloat16
                                      (ties to even), exact products, FP32 sums.  B-spline
-                                     only (MTP_ERR_UNSUPPORTED otherwise).  Runs on the
-                                     FP32 pipe: the contraction stores 4 bytes per p+1
-                                     products, so tensor cores would not shorten it */
+                                     only (MTP_ERR_UNSUPPORTED otherwise).  The graph rows
+                                     are then a dense (H x M) by (M x paths*n) product on
+                                     the tensor cores (tcgen05, BF16 x BF16 -> FP32) when
+                                     H <= 256 and n <= 16, else a (p+1)-term sum on the
+                                     FP32 pipe; such problems are not pipelined */
 #define MTP_FLAG_NO_PIPELINE 0x8u /* mtp_plan_step makes each iteration's candidates in
                                      full on the critical path instead of preparing parts
                                      of the next iteration's during the rollout (results

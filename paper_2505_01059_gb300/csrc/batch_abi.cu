@@ -30,6 +30,10 @@ struct BatchGroup {
   bool stageable = false;     // every member's rows can be staged (see can_stage)
   // this group's share of the generation, selection and update launches
   int z_blocks = 0, cand_blocks = 0, local_blocks = 0, upd_threads = 0;
+  // members whose graph rows are contracted on the tensor cores (BF16 basis):
+  // entries [tc_first, tc_first + tc_count) of the tensor-core argument list,
+  // their tile numbering at tc_start_first of d_tc_start
+  int tc_first = 0, tc_count = 0, tc_start_first = 0, tc_tiles = 0;
   size_t cand_smem = 0, sel_smem = 0;
 };
 
@@ -50,6 +54,8 @@ struct BatchTables {
   CandArgs* d_cand = nullptr;
   int* d_cand_start = nullptr;
   int* d_local_start = nullptr;
+  CandArgs* d_tc = nullptr;     // graph parts contracted on the tensor cores, in group order
+  int* d_tc_start = nullptr;    // one segment of (members + 1) tile offsets per group
   float** d_Z = nullptr;
   int* d_z_start = nullptr;
   RolloutArgs* d_ra = nullptr;  // in group order
@@ -83,6 +89,8 @@ size_t layout_tables(BatchTables* t, unsigned char* base, int count, int n_pm, i
   take(&d->d_cand, count);
   take(&d->d_cand_start, count + 1);
   take(&d->d_local_start, count + 1);
+  take(&d->d_tc, count);
+  take(&d->d_tc_start, count + groups);
   take(&d->d_Z, count);
   take(&d->d_z_start, count + 1);
   take(&d->d_ra, count);
@@ -218,6 +226,8 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
   // candidate generation, selection and update tables in group order, so
   // that each group's stream launches them over a contiguous range
   hv.d_cand_start[0] = hv.d_z_start[0] = hv.d_local_start[0] = hv.d_warp_start[0] = 0;
+  std::vector<CandArgs> tc_args(count);
+  std::vector<char> is_tc(count, 0);
   for (int pos = 0; pos < count; ++pos) {
     mtp_handle* h = handles[order[pos]];
     // a batch makes every iteration's candidates in full, in the first buffer
@@ -240,6 +250,12 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
     c.graph_blocks = 1;  // counts the graph part in candidates_smem_bytes
     while (c.paths_per_block > 1 && candidates_smem_bytes(c) > kBatchGraphSmem) c.paths_per_block /= 2;
     c.graph_blocks = (dm.P + c.paths_per_block - 1) / c.paths_per_block;
+    if (h->tc_graph && bspline_tc_eligible(c)) {
+      tc_args[pos] = c;     // its graph rows go to the tensor cores
+      is_tc[pos] = 1;
+      c.graph_blocks = 0;
+      c.paths_per_block = 1;
+    }
     hv.d_Z[pos] = h->Z;
     hv.d_z_start[pos + 1] = hv.d_z_start[pos] + (dm.M * dm.N * ((dm.n + 3) / 4) + 255) / 256;
     const long long items = ((long long)dm.L + 1) * (((long long)Hn + 3) / 4);
@@ -251,6 +267,25 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
     hv.d_upd[pos] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
                                h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
     hv.d_warp_start[pos + 1] = hv.d_warp_start[pos] + update_threads(dm.H, dm.n);
+  }
+  // tensor-core members, group by group
+  {
+    int tc_pos = 0, seg = 0;
+    for (auto& g : b->groups) {
+      g.tc_first = tc_pos;
+      g.tc_start_first = seg;
+      int tiles = 0;
+      hv.d_tc_start[seg] = 0;
+      for (int pos = g.first; pos < g.first + g.count; ++pos) {
+        if (!is_tc[pos]) continue;
+        hv.d_tc[tc_pos++] = tc_args[pos];
+        tiles += bspline_tc_tiles(tc_args[pos].graph_rows);
+        hv.d_tc_start[seg + (tc_pos - g.tc_first)] = tiles;
+      }
+      g.tc_count = tc_pos - g.tc_first;
+      g.tc_tiles = tiles;
+      seg += g.tc_count + 1;
+    }
   }
   for (auto& g : b->groups) {
     const int a0 = g.first, a1 = g.first + g.count;
@@ -347,6 +382,10 @@ cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
     if ((e = launch_graph_Z_batch(t.d_cand + f, t.d_Z + f, t.d_z_start + f, g.count, g.z_blocks, gs))) return e;
     if ((e = launch_candidates_batch(t.d_cand + f, t.d_cand_start + f, g.count, g.cand_blocks, g.cand_smem, gs)))
       return e;
+    if (g.tc_count > 0 &&
+        (e = launch_bspline_tc_batch(t.d_tc + g.tc_first, t.d_tc_start + g.tc_start_first, g.tc_count,
+                                     g.tc_tiles, gs)))
+      return e;
     if ((e = launch_local_batch(t.d_cand + f, t.d_local_start + f, g.count, g.local_blocks, gs))) return e;
     if ((e = launch_group(b, g, g.block, g.chunk, gs))) return e;
     if ((e = launch_select_batch(t.d_sel + f, g.count, g.sel_smem, gs))) return e;
@@ -423,6 +462,7 @@ mtp_status mtp_batch_reserve(int32_t capacity, mtp_batch** out) {
   cudaError_t e = init_candidate_attributes();
   if (e == cudaSuccess) e = init_select_attributes();
   if (e == cudaSuccess) e = init_rollout_pm_batch_attributes();
+  if (e == cudaSuccess) e = init_bspline_tc_attributes();
   if (e == cudaSuccess) e = init_rollout_chain_batch_attributes();
   if (e == cudaSuccess) e = alloc_batch(b, capacity);
   if (e != cudaSuccess) {
@@ -568,7 +608,7 @@ mtp_status mtp_batch_launches(const mtp_batch* b, int32_t iters, int32_t* launch
   if (!b || !launches || iters < 1 || b->count < 1) return MTP_ERR_INVALID_ARG;
   long long per_iter = 0;
   for (const auto& g : b->groups) {
-    per_iter += (g.z_blocks > 0) + (g.cand_blocks > 0) + (g.local_blocks > 0);
+    per_iter += (g.z_blocks > 0) + (g.cand_blocks > 0) + (g.local_blocks > 0) + (g.tc_count > 0);
     per_iter += (g.total_rows > 0) + (g.count > 0) + (g.upd_threads > 0);
   }
   *launches = (int32_t)(2 + per_iter * iters);  // scatter of x0 and gather of u* once per call

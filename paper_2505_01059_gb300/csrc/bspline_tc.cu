@@ -259,7 +259,7 @@ __device__ __forceinline__ TcSmem& tc_smem() {
 }
 
 // One instance: CTAs loop over its path tiles.
-__global__ void __launch_bounds__(kTcThreads) k_bspline_tc(const CandArgs a, uint32_t* status) {
+__global__ void __launch_bounds__(kTcThreads) k_bspline_tc(const CandArgs a) {
   TcSmem& S = tc_smem();
   const int K = ((a.dm.M + 15) / 16) * 16;
   const int tiles = (a.graph_rows + kPaths - 1) / kPaths;
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kTcThreads) k_bspline_tc(const CandArgs a, uin
   bool failed = false;
   for (int tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x)
     failed = !tc_tile(S, a, tile, K, iter, phase);
-  tc_end(S, failed, phase, status);
+  tc_end(S, failed, phase, a.status);
 }
 
 // Many instances: tile_start (count + 1 entries) numbers each instance's
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kTcThreads) k_bspline_tc(const CandArgs a, uin
 // the instance changes.
 __global__ void __launch_bounds__(kTcThreads) k_bspline_tc_batch(const CandArgs* __restrict__ args,
                                                                  const int* __restrict__ tile_start,
-                                                                 int count, uint32_t* status) {
+                                                                 int count) {
   TcSmem& S = tc_smem();
   __shared__ CandArgs sa;
   tc_begin(S);
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kTcThreads) k_bspline_tc_batch(const CandArgs*
     }
     failed = !tc_tile(S, sa, g - tile_start[lo], K, iter, phase);
   }
-  tc_end(S, failed, phase, status);
+  tc_end(S, failed, phase, cur >= 0 ? sa.status : nullptr);
 }
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) > kMinSmem ? sizeof(TcSmem) : kMinSmem; }
@@ -328,19 +328,19 @@ cudaError_t init_bspline_tc_attributes() {
                               (int)tc_smem_bytes());
 }
 
-cudaError_t launch_bspline_tc(const CandArgs& a, uint32_t* status, cudaStream_t s) {
+cudaError_t launch_bspline_tc(const CandArgs& a, cudaStream_t s) {
   const int tiles = bspline_tc_tiles(a.graph_rows);
   if (tiles <= 0) return cudaSuccess;
   const int grid = std::min(tiles, 2 * device_sms());
-  k_bspline_tc<<<grid, kTcThreads, tc_smem_bytes(), s>>>(a, status);
+  k_bspline_tc<<<grid, kTcThreads, tc_smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bspline_tc_batch(const CandArgs* d_args, const int* d_tile_start, int count,
-                                    int total_tiles, uint32_t* status, cudaStream_t s) {
+                                    int total_tiles, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   const int grid = std::min(total_tiles, 2 * device_sms());
-  k_bspline_tc_batch<<<grid, kTcThreads, tc_smem_bytes(), s>>>(d_args, d_tile_start, count, status);
+  k_bspline_tc_batch<<<grid, kTcThreads, tc_smem_bytes(), s>>>(d_args, d_tile_start, count);
   return cudaGetLastError();
 }
 

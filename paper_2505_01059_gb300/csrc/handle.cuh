@@ -57,7 +57,7 @@ struct mtp_handle {
   float* x0 = nullptr;
   float* Z = nullptr;  // (M, N, n) graph of the current iteration (batched planning)
   uint32_t* status = nullptr;  // device status word: bits a rollout sets when a bounded wait gave up
-  int rollout_chunk = 4;       // horizon chunk of the staged control loads of a lone rollout
+  int rollout_chunk = 0;       // horizon chunk of the staged control loads of a lone rollout (0: direct)
   bool tc_graph = false;       // graph rows contracted on the tensor cores (BF16 B-spline)
   // replay
   cudaStream_t cap_stream = nullptr;

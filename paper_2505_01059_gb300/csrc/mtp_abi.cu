@@ -254,6 +254,7 @@ CandArgs cand_args(const mtp_handle* h, uint32_t iter, const uint32_t* d_iter) {
   a.paths_per_block = h->paths_per_block;
   a.mu = h->mu_f;
   a.sigma = h->sigma_f;
+  a.status = h->status;
   for (int i = 0; i < h->dm.n; ++i) {
     a.umin[i] = h->pr.u_min[i];
     a.umax[i] = h->pr.u_max[i];
@@ -380,7 +381,7 @@ cudaError_t launch_generate(const mtp_handle* h, CandArgs& c, cudaStream_t s) {
   local.graph_blocks = 0;
   cudaError_t e = launch_candidates(local, local_blocks, s);
   if (e != cudaSuccess) return e;
-  return launch_bspline_tc(c, h->status, s);
+  return launch_bspline_tc(c, s);
 }
 
 cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
@@ -752,7 +753,7 @@ mtp_status mtp_interpolate(mtp_handle* h, const float* d_C, int32_t P, float* d_
   c.graph_rows = P;
   c.graph_blocks = (P + h->paths_per_block - 1) / h->paths_per_block;
   cudaError_t e = (h->tc_graph && bspline_tc_eligible(c))
-                      ? launch_bspline_tc(c, h->status, (cudaStream_t)stream)
+                      ? launch_bspline_tc(c, (cudaStream_t)stream)
                       : launch_candidates(c, 0, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "interpolate");
   return MTP_OK;

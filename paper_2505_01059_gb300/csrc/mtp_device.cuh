@@ -137,6 +137,7 @@ struct CandArgs {
   const float* mu;         // (H, n) FP32 copy of the FP64 mean
   const float* sigma;      // (H, n) FP32 copy of the FP64 spread
   float umin[MTP_MAX_CTRL], umax[MTP_MAX_CTRL];
+  uint32_t* status;        // the handle's device status word (bounded waits that gave up)
 };
 
 struct RolloutArgs {
@@ -256,9 +257,9 @@ cudaError_t launch_rollout_legged_batch(const RolloutArgs* d_ra, const LeggedMod
 bool bspline_tc_eligible(const CandArgs& a);
 int bspline_tc_tiles(int graph_rows);
 cudaError_t init_bspline_tc_attributes();
-cudaError_t launch_bspline_tc(const CandArgs& a, uint32_t* status, cudaStream_t s);
+cudaError_t launch_bspline_tc(const CandArgs& a, cudaStream_t s);
 cudaError_t launch_bspline_tc_batch(const CandArgs* d_args, const int* d_tile_start, int count,
-                                    int total_tiles, uint32_t* status, cudaStream_t s);
+                                    int total_tiles, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 size_t select_smem_bytes(int B, int E);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
