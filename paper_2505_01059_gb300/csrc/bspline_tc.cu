@@ -45,7 +45,9 @@ constexpr size_t kMinSmem = 80 * 1024;  // at most two CTAs per SM (their TMEM f
 struct TcSmem {
   __nv_bfloat16 A[kMaxSlices][128 * kMaxK];  // basis, K-major canonical layout
   __nv_bfloat16 B[kNTile * kMaxK];           // waypoints, K-major canonical layout
-  float stage[kTcThreads / 32][32 * 33];     // per-warp transpose of one path's rows
+  // per warp, two buffers of one path's 32 rows x n controls in the order
+  // they take in U (a contiguous block there), written out by bulk copies
+  float stage[kTcThreads / 32][2][32 * 16];
   float lo[MTP_MAX_CTRL], hi[MTP_MAX_CTRL];
   uint64_t mma_bar;
   uint32_t tmem_base;
@@ -166,10 +168,19 @@ __device__ bool tc_tile(TcSmem& S, const CandArgs& a, int tile, int K, uint32_t 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!__syncthreads_and(ok)) return false;
   // epilogue: warp w reads accumulator lanes 32 w .. 32 w + 31 (steps
-  // t0 .. t0 + 31 of each slice) path by path
+  // t0 .. t0 + 31 of each slice) path by path, clamps them to the box (kept
+  // in registers) and writes the path's rows t0 .. t0 + 31, a contiguous
+  // block of U, from shared memory: one bulk copy when its start and length
+  // are whole 16-byte units, else coalesced stores
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int S_row = n | 1;  // odd row stride: conflict-free transposition
-  float* st = S.stage[w];
+  float lo[16], hi[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    lo[i] = i < n ? S.lo[i] : 0.f;
+    hi[i] = i < n ? S.hi[i] : 0.f;
+  }
+  const bool bulk_ok = ((reinterpret_cast<uintptr_t>(a.U_graph) & 15) == 0) && ((H * n) & 3) == 0;
+  int buf = 0;
   for (int s = 0; s < slices; ++s) {
     const int t0 = 128 * s + 32 * w;
     const int rows = min(32, H - t0);
@@ -183,28 +194,37 @@ __device__ bool tc_tile(TcSmem& S, const CandArgs& a, int tile, int K, uint32_t 
             "=r"(v[14]), "=r"(v[15])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (rows > 0) {
+      if (rows <= 0) continue;
+      float* st = S.stage[w][buf];
+      // the bulk copy that last read this buffer (two paths ago) must be done
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+      __syncwarp();
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (i < n) st[lane * S_row + i] = clamp_box(__uint_as_float(v[i]), S.lo[i], S.hi[i]);
+      for (int i = 0; i < 16; ++i)
+        if (i < n) st[lane * n + i] = clamp_box(__uint_as_float(v[i]), lo[i], hi[i]);
+      float* out = a.U_graph + ((size_t)(b0 + p) * H + t0) * n;
+      const int count = rows * n;
+      if (bulk_ok && (count & 3) == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        float* out = a.U_graph + ((size_t)(b0 + p) * H + t0) * n;
-        const int count = rows * n;
-        int t = lane / n, i = lane - (lane / n) * n;
-        const int dt = 32 / n, di = 32 - (32 / n) * n;
-        for (int e = lane; e < count; e += 32) {
-          out[e] = st[t * S_row + i];
-          t += dt;
-          i += di;
-          if (i >= n) {
-            i -= n;
-            ++t;
-          }
+        if (lane == 0) {
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(out),
+                       "r"(smem_u32(st)), "r"((uint32_t)(count * 4))
+                       : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
+        buf ^= 1;
+      } else {
+        __syncwarp();
+        for (int e = lane; e < count; e += 32) out[e] = st[e];
         __syncwarp();
       }
     }
   }
+  // the warp's bulk copies have read their sources before the next tile
+  // refills the buffers
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   return true;
@@ -242,6 +262,8 @@ __device__ void tc_begin(TcSmem& S) {
 // Releases the tensor memory.  After a failed wait, first waits (bounded)
 // for the MMA still in flight.
 __device__ void tc_end(TcSmem& S, bool failed, uint32_t phase, uint32_t* status) {
+  // every bulk copy of rows has landed before the CTA leaves
+  if ((threadIdx.x & 31) == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   if (failed) {
     mbar_wait_bounded_tc(&S.mma_bar, phase ^ 1u);
     if (threadIdx.x == 0 && status) atomicOr(status, kStatusTcTimeout);
