@@ -279,7 +279,7 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
       for (int pos = g.first; pos < g.first + g.count; ++pos) {
         if (!is_tc[pos]) continue;
         hv.d_tc[tc_pos++] = tc_args[pos];
-        tiles += bspline_tc_tiles(tc_args[pos].graph_rows);
+        tiles += bspline_tc_tiles(tc_args[pos]);
         hv.d_tc_start[seg + (tc_pos - g.tc_first)] = tiles;
       }
       g.tc_count = tc_pos - g.tc_first;

@@ -6,14 +6,14 @@
 // (Def. 2 with the basis B_p sampled at the H evaluation times and the
 // waypoints C of path b, Alg. 1).  Seen as one GEMM, D[t, (b, i)] =
 // sum_m A[t, m] B[m, (b, i)] with A the (H x M) basis table and B the
-// gathered waypoints, K = M.  Each CTA (one warpgroup) takes a tile of up to
-// kPaths paths: it draws their layer indices (Alg. 1), gathers their
-// waypoints from the iteration's graph Z, rounds them to bfloat16 into the
-// B operand (K-major, 16 columns per path, the columns past n zero), and one
-// thread issues tcgen05.mma.cta_group::1.kind::f16 (BF16 x BF16 -> FP32,
-// M = 128 steps per instruction, N = 128, K = 16 per instruction) for each
-// 128-step slice of the horizon, accumulating in tensor memory.  The
-// products of two bfloat16 values are exact in FP32; the sums are FP32.
+// gathered waypoints, K = M.  A tile is one 128-step slice of the horizon
+// for up to kPaths paths; each CTA (one warpgroup) loops over tiles: it
+// draws the paths' layer indices (Alg. 1), gathers their waypoints from the
+// iteration's graph Z, rounds them to bfloat16 into the B operand (K-major,
+// 16 columns per path, the columns past n zero), and one thread issues
+// tcgen05.mma.cta_group::1.kind::f16 (BF16 x BF16 -> FP32, M = 128 steps,
+// N = 128, K = 16 per instruction) into tensor memory.  The products of two
+// bfloat16 values are exact in FP32; the sums are FP32.
 // The epilogue reads each path's columns back with tcgen05.ld, clamps them
 // to the control box and writes them through a per-warp shared-memory
 // transpose as contiguous, coalesced rows of U.
@@ -21,10 +21,10 @@
 // Shared-memory operands use the canonical K-major layout without swizzle:
 // 8-row x 16-byte core matrices, the two (or more) core matrices of a row
 // group along K 128 bytes apart (leading byte offset) and consecutive row
-// groups 16 K bytes apart (stride byte offset).  Each CTA allocates 256
-// tensor-memory columns (two 128-column accumulators, one per horizon
-// slice) and asks for enough shared memory that at most two CTAs share an
-// SM, so their allocations always fit the SM's 512 columns.
+// groups 16 K bytes apart (stride byte offset).  Each CTA allocates 128
+// tensor-memory columns (its accumulator) and asks for enough shared memory
+// that at most four CTAs share an SM, so their allocations always fit the
+// SM's 512 columns.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -39,11 +39,11 @@ constexpr int kPaths = 8;            // paths per tile, 16 accumulator columns e
 constexpr int kNTile = kPaths * 16;  // MMA N
 constexpr int kMaxK = 64;            // layers (M) padded to a multiple of 16
 constexpr int kMaxSlices = 2;        // 128-step horizon slices (H <= 256)
-constexpr uint32_t kTmemCols = 256;
-constexpr size_t kMinSmem = 80 * 1024;  // at most two CTAs per SM (their TMEM fits)
+constexpr uint32_t kTmemCols = 128;
+constexpr size_t kMinSmem = 50 * 1024;  // at most four CTAs per SM (their TMEM fits)
 
 struct TcSmem {
-  __nv_bfloat16 A[kMaxSlices][128 * kMaxK];  // basis, K-major canonical layout
+  __nv_bfloat16 A[128 * kMaxK];              // basis of one slice, K-major canonical layout
   __nv_bfloat16 B[kNTile * kMaxK];           // waypoints, K-major canonical layout
   // per warp, two buffers of one path's 32 rows x n controls in the order
   // they take in U (a contiguous block there), written out by bulk copies
@@ -99,29 +99,27 @@ __device__ __forceinline__ bool mbar_wait_bounded_tc(uint64_t* bar, uint32_t par
   }
 }
 
-// The basis of one instance as the A operand of each horizon slice:
-// A[s][r][k] = basis[(128 s + r) * M + k], zero past H and past M.
-__device__ void load_basis(TcSmem& S, const CandArgs& a, int K) {
+// The basis of one horizon slice s as the A operand:
+// A[r][k] = basis[(128 s + r) * M + k], zero past H and past M.
+__device__ void load_basis(TcSmem& S, const CandArgs& a, int K, int s) {
   const int H = a.dm.H, M = a.dm.M;
-  unsigned char* base = reinterpret_cast<unsigned char*>(&S.A[0][0]);
-  const int slices = (H + 127) / 128;
-  for (int e = threadIdx.x; e < slices * 128 * K; e += blockDim.x) {
-    const int s = e / (128 * K), rem = e - s * 128 * K;
-    const int r = rem / K, k = rem - r * K;
+  unsigned char* base = reinterpret_cast<unsigned char*>(&S.A[0]);
+  for (int e = threadIdx.x; e < 128 * K; e += blockDim.x) {
+    const int r = e / K, k = e - r * K;
     const int t = 128 * s + r;
     const float v = (t < H && k < M) ? a.basis[(size_t)t * M + k] : 0.f;
-    *reinterpret_cast<__nv_bfloat16*>(base + (size_t)s * sizeof(S.A[0]) + kmajor_offset(r, k, K)) =
-        __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(base + kmajor_offset(r, k, K)) = __float2bfloat16_rn(v);
   }
 }
 
-// Tile `tile` of one instance's graph rows.  Returns false when the bounded
-// wait for the MMA gave up.
-__device__ bool tc_tile(TcSmem& S, const CandArgs& a, int tile, int K, uint32_t iter,
+// Path group g of one instance's graph rows, horizon slice s (the A operand
+// holds that slice's basis).  Returns false when the bounded wait for the
+// MMA gave up.
+__device__ bool tc_tile(TcSmem& S, const CandArgs& a, int g, int s, int K, uint32_t iter,
                         uint32_t& phase) {
   const Dims dm = a.dm;
   const int H = dm.H, n = dm.n, M = dm.M, N = dm.N;
-  const int b0 = tile * kPaths;
+  const int b0 = g * kPaths;
   const int nb = min(kPaths, a.graph_rows - b0);
   unsigned char* Bb = reinterpret_cast<unsigned char*>(S.B);
   // Alg. 1 for the tile's paths and the gather of their waypoints, rounded
@@ -141,23 +139,20 @@ __device__ bool tc_tile(TcSmem& S, const CandArgs& a, int tile, int K, uint32_t 
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-  const int slices = (H + 127) / 128;
   if (threadIdx.x == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t idesc = idesc_bf16(128, kNTile);
     const uint32_t sbo = 16u * (uint32_t)K;
-    for (int s = 0; s < slices; ++s) {
-      const uint32_t d_tmem = S.tmem_base + (uint32_t)(s * kNTile);
-      for (int ks = 0; ks < K / 16; ++ks) {
-        const uint64_t ad = smem_desc(smem_u32(&S.A[s][0]) + 256u * ks, 128u, sbo);
-        const uint64_t bd = smem_desc(smem_u32(&S.B[0]) + 256u * ks, 128u, sbo);
-        const uint32_t acc = ks > 0 ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-            : "memory");
-      }
+    const uint32_t d_tmem = S.tmem_base;
+    for (int ks = 0; ks < K / 16; ++ks) {
+      const uint64_t ad = smem_desc(smem_u32(&S.A[0]) + 256u * ks, 128u, sbo);
+      const uint64_t bd = smem_desc(smem_u32(&S.B[0]) + 256u * ks, 128u, sbo);
+      const uint32_t acc = ks > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+          : "memory");
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(&S.mma_bar))
@@ -181,11 +176,11 @@ __device__ bool tc_tile(TcSmem& S, const CandArgs& a, int tile, int K, uint32_t 
   }
   const bool bulk_ok = ((reinterpret_cast<uintptr_t>(a.U_graph) & 15) == 0) && ((H * n) & 3) == 0;
   int buf = 0;
-  for (int s = 0; s < slices; ++s) {
+  {
     const int t0 = 128 * s + 32 * w;
     const int rows = min(32, H - t0);
     for (int p = 0; p < nb; ++p) {
-      const uint32_t taddr = S.tmem_base + ((uint32_t)(32 * w) << 16) + (uint32_t)(s * kNTile + 16 * p);
+      const uint32_t taddr = S.tmem_base + ((uint32_t)(32 * w) << 16) + (uint32_t)(16 * p);
       uint32_t v[16];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -230,15 +225,14 @@ __device__ bool tc_tile(TcSmem& S, const CandArgs& a, int tile, int K, uint32_t 
   return true;
 }
 
-// Per-CTA set-up for one instance: box, basis operand, a zeroed B operand.
-__device__ void tc_instance_setup(TcSmem& S, const CandArgs& a, int K) {
+// Per-CTA set-up for one instance: box and a zeroed B operand.
+__device__ void tc_instance_setup(TcSmem& S, const CandArgs& a) {
   for (int i = threadIdx.x; i < a.dm.n; i += blockDim.x) {
     S.lo[i] = a.umin[i];
     S.hi[i] = a.umax[i];
   }
   uint32_t* Bw = reinterpret_cast<uint32_t*>(S.B);
   for (int e = threadIdx.x; e < (int)(sizeof(S.B) / 4); e += blockDim.x) Bw[e] = 0u;
-  load_basis(S, a, K);
   __syncthreads();
 }
 
@@ -280,18 +274,28 @@ __device__ __forceinline__ TcSmem& tc_smem() {
   return *reinterpret_cast<TcSmem*>(tc_dyn_smem);
 }
 
-// One instance: CTAs loop over its path tiles.
+// One instance: CTAs loop over its tiles, slice-major (tile = s * groups + g),
+// so that a CTA changes slice, and reloads the basis, rarely.
 __global__ void __launch_bounds__(kTcThreads) k_bspline_tc(const CandArgs a) {
   TcSmem& S = tc_smem();
   const int K = ((a.dm.M + 15) / 16) * 16;
-  const int tiles = (a.graph_rows + kPaths - 1) / kPaths;
+  const int groups = (a.graph_rows + kPaths - 1) / kPaths;
+  const int tiles = groups * ((a.dm.H + 127) / 128);
   const uint32_t iter = (a.d_iter ? *a.d_iter : a.iter) + a.iter_offset;
   tc_begin(S);
-  tc_instance_setup(S, a, K);
+  tc_instance_setup(S, a);
   uint32_t phase = 0;
   bool failed = false;
-  for (int tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x)
-    failed = !tc_tile(S, a, tile, K, iter, phase);
+  int cur_s = -1;
+  for (int tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+    const int s = tile / groups, g = tile - s * groups;
+    if (s != cur_s) {
+      load_basis(S, a, K, s);
+      __syncthreads();
+      cur_s = s;
+    }
+    failed = !tc_tile(S, a, g, s, K, iter, phase);
+  }
   tc_end(S, failed, phase, a.status);
 }
 
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(kTcThreads) k_bspline_tc_batch(const CandArgs*
   __shared__ CandArgs sa;
   tc_begin(S);
   const int total = tile_start[count];
-  int cur = -1, K = 16;
+  int cur = -1, cur_s = -1, K = 16;
   uint32_t iter = 0, phase = 0;
   bool failed = false;
   for (int g = blockIdx.x; g < total && !failed; g += gridDim.x) {
@@ -322,11 +326,21 @@ __global__ void __launch_bounds__(kTcThreads) k_bspline_tc_batch(const CandArgs*
       for (int q = threadIdx.x; q < (int)(sizeof(CandArgs) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
       __syncthreads();
       cur = lo;
+      cur_s = -1;
       K = ((sa.dm.M + 15) / 16) * 16;
       iter = (sa.d_iter ? *sa.d_iter : sa.iter) + sa.iter_offset;
-      tc_instance_setup(S, sa, K);
+      tc_instance_setup(S, sa);
     }
-    failed = !tc_tile(S, sa, g - tile_start[lo], K, iter, phase);
+    // the instance's tiles slice-major, as in the single-instance kernel
+    const int groups = (sa.graph_rows + kPaths - 1) / kPaths;
+    const int tile = g - tile_start[lo];
+    const int s = tile / groups, pg = tile - s * groups;
+    if (s != cur_s) {
+      load_basis(S, sa, K, s);
+      __syncthreads();
+      cur_s = s;
+    }
+    failed = !tc_tile(S, sa, pg, s, K, iter, phase);
   }
   tc_end(S, failed, phase, cur >= 0 ? sa.status : nullptr);
 }
@@ -340,7 +354,9 @@ bool bspline_tc_eligible(const CandArgs& a) {
          a.dm.M <= kMaxK && a.dm.n <= 16 && a.graph_rows > 0;
 }
 
-int bspline_tc_tiles(int graph_rows) { return (graph_rows + kPaths - 1) / kPaths; }
+int bspline_tc_tiles(const CandArgs& a) {
+  return ((a.graph_rows + kPaths - 1) / kPaths) * ((a.dm.H + 127) / 128);
+}
 
 cudaError_t init_bspline_tc_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_bspline_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -351,9 +367,9 @@ cudaError_t init_bspline_tc_attributes() {
 }
 
 cudaError_t launch_bspline_tc(const CandArgs& a, cudaStream_t s) {
-  const int tiles = bspline_tc_tiles(a.graph_rows);
+  const int tiles = bspline_tc_tiles(a);
   if (tiles <= 0) return cudaSuccess;
-  const int grid = std::min(tiles, 2 * device_sms());
+  const int grid = std::min(tiles, 4 * device_sms());
   k_bspline_tc<<<grid, kTcThreads, tc_smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
@@ -361,7 +377,7 @@ cudaError_t launch_bspline_tc(const CandArgs& a, cudaStream_t s) {
 cudaError_t launch_bspline_tc_batch(const CandArgs* d_args, const int* d_tile_start, int count,
                                     int total_tiles, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
-  const int grid = std::min(total_tiles, 2 * device_sms());
+  const int grid = std::min(total_tiles, 4 * device_sms());
   k_bspline_tc_batch<<<grid, kTcThreads, tc_smem_bytes(), s>>>(d_args, d_tile_start, count);
   return cudaGetLastError();
 }

@@ -255,7 +255,7 @@ cudaError_t launch_rollout_legged_batch(const RolloutArgs* d_ra, const LeggedMod
 // instances, tile_start numbering each instance's first tile).  The graph Z
 // must be in global memory (Z_global) unless C_in is given.
 bool bspline_tc_eligible(const CandArgs& a);
-int bspline_tc_tiles(int graph_rows);
+int bspline_tc_tiles(const CandArgs& a);
 cudaError_t init_bspline_tc_attributes();
 cudaError_t launch_bspline_tc(const CandArgs& a, cudaStream_t s);
 cudaError_t launch_bspline_tc_batch(const CandArgs* d_args, const int* d_tile_start, int count,
