@@ -16,7 +16,7 @@ instance 7-link arm and 16-link legged workloads.  Each rank plans its own
 independent batch (weak scaling, no collective on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload batch|serve|arm7|legged16|pointmass2]
+                  [--workload batch|serve|arm7|legged16|pointmass2|sweep]
 
 Prints one JSON line (rank 0).  The reference arm times the FP64 CPU oracle
 on the host's cores on a bounded sample of the same workload.
@@ -1080,6 +1080,52 @@ def run_single_only(args, name):
         pg.destroy_process_group()
 
 
+def run_sweep(args):
+    """The M, N ablation of the paper's Navigation study (Appendix, sweep of
+    M and N with full tensor sampling, beta = 1, B = 256, 4 seeds) on the
+    synthetic 2-D point mass with circular obstacles: for every (M, N) and
+    interpolation, the best candidate cost after 10 planner iterations and
+    the cost entropy of the last selection (Sec. 4.1), mean over 4 seeds."""
+    import numpy as np
+    import torch
+    from paper_2505_01059_gb300 import workloads as W
+    world, rank, local = dist_init()
+    dev, pg, mtp = setup_gpu(local, world)
+    Ms, Ns, seeds, iters = [2, 3, 4, 6, 8, 12, 16], [4, 8, 16, 32, 64], [11, 12, 13, 14], 10
+    grid = {}
+    t0 = time.perf_counter()
+    for interp in ("bspline", "akima", "linear"):
+        for M in Ms:
+            for N in Ns:
+                best, ent = [], []
+                for seed in seeds:
+                    spec = W.pointmass(seed=seed, M=M, N=N, B=256, beta=1.0, interp=interp,
+                                       degree=min(3, M - 1), E=16,
+                                       flags=mtp.FLAG_COST_ENTROPY)
+                    h = mtp.mtp_create(spec)
+                    x0 = torch.tensor(spec["x0"], dtype=torch.float32, device=dev)
+                    u = torch.empty(spec["n"], device=dev)
+                    mtp.mtp_plan_step(h, x0, iters, u)
+                    buf = mtp.mtp_get_buffers(h)
+                    cost = torch.as_tensor(buf["cost"], device=dev)
+                    best.append(float(cost.min().item()))
+                    ent.append(mtp.mtp_cost_entropy(h))
+                    mtp.mtp_destroy(h)
+                grid[f"{interp} M={M} N={N}"] = {"best_cost": float(np.mean(best)),
+                                                 "best_cost_std": float(np.std(best)),
+                                                 "entropy": float(np.mean(ent))}
+    line = {"metric": "best candidate cost after 10 iterations (mean over 4 seeds)",
+            "unit": "cost", "higher_is_better": False, "n_gpus": 1,
+            "config": {"workload": "2-D point mass, 5 circular obstacles, beta 1 (tensor samples "
+                                   "only), B 256, E 16, H 64, lambda 0.1", "M": Ms, "N": Ns,
+                       "seeds": seeds, "iterations": iters},
+            "grid": grid, "wall_s": time.perf_counter() - t0}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1087,7 +1133,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "serve", "arm7", "pointmass2", "legged16"])
+                    choices=["batch", "serve", "arm7", "pointmass2", "legged16", "sweep"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--robots", type=int, default=1024)
     ap.add_argument("--max-batch", type=int, default=256)
@@ -1110,6 +1156,8 @@ def main():
         run_headline(args)
     elif args.workload == "serve":
         run_serve_only(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_single_only(args, args.workload)
 

@@ -79,6 +79,8 @@ typedef enum { MTP_DR_NONE = 0, MTP_DR_PER_SAMPLE = 1, MTP_DR_SHARED = 2 } mtp_d
                                      the tensor cores (tcgen05, BF16 x BF16 -> FP32) when
                                      H <= 256 and n <= 16, else a (p+1)-term sum on the
                                      FP32 pipe; such problems are not pipelined */
+#define MTP_FLAG_COST_ENTROPY 0x10u /* every selection also computes the cost entropy of
+                                       Sec. 4.1 over all B candidates (mtp_cost_entropy) */
 #define MTP_FLAG_NO_PIPELINE 0x8u /* mtp_plan_step makes each iteration's candidates in
                                      full on the critical path instead of preparing parts
                                      of the next iteration's during the rollout (results
@@ -242,6 +244,15 @@ mtp_status mtp_plan_step_host(mtp_handle* h, const float* h_x0, int32_t iters, f
 /* Warm start between control steps: shifts mean and spread k steps earlier
  * and repeats the last row (the paper leaves this open). */
 mtp_status mtp_shift(mtp_handle* h, int32_t k, void* stream);
+
+/* Sec. 4.1 rollout-cost entropy of the latest selection, a diagnostic of how
+ * spread the candidates' costs are: H = -sum_b p_b log p_b over all B
+ * candidates with p_b proportional to exp(-J_b / lambda) (the paper prints
+ * exp(J_b); the sign is read so that low costs weigh most, as in the update).
+ * Computed by the selection kernel (FP32 weights, FP64 sums) only for
+ * problems created with MTP_FLAG_COST_ENTROPY, else MTP_ERR_INVALID_ARG.
+ * Synchronises the device. */
+mtp_status mtp_cost_entropy(mtp_handle* h, double* h_entropy);
 
 /* Device-side failures since the last call: the rollouts stage their controls
  * through shared memory with bulk copies and wait for them with a bounded

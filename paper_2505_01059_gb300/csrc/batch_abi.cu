@@ -263,7 +263,7 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
     hv.d_cand_start[pos + 1] = hv.d_cand_start[pos] + c.graph_blocks;  // local rows run apart
     hv.d_local_start[pos + 1] = hv.d_local_start[pos] + (int)std::max<long long>(1, (items + 1023) / 1024);
     hv.d_sel[pos] = SelectArgs{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
-                               h->elite, h->weight, h->ustar, nullptr, nullptr};
+                               h->elite, h->weight, h->ustar, nullptr, nullptr, h->entropy};
     hv.d_upd[pos] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
                                h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
     hv.d_warp_start[pos + 1] = hv.d_warp_start[pos] + update_threads(dm.H, dm.n);

@@ -116,6 +116,45 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
     kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
   }
 
+  // Sec. 4.1 cost entropy, read as the entropy of p_b = exp(-J_b / lambda) / Z
+  // over all B candidates: with d_b = J_b - J_min and w_b = exp(-d_b / lambda),
+  // H = -sum_b p_b log p_b = log Z + sum_b w_b d_b / (lambda Z).  The weights
+  // in FP32, their sums in FP64.
+  if (a.entropy) {
+    const float cmin = key_cost(kmin);
+    const float inv_l = (float)a.inv_lambda;
+    double z = 0.0, sd = 0.0;
+    if (cmin < INFINITY) {
+      for (int b = tid; b < B; b += blockDim.x) {
+        const float d = key_cost(keys[b]) - cmin;
+        const float w = expf(-d * inv_l);
+        if (w > 0.f) {
+          z += (double)w;
+          sd += (double)w * (double)d;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      z += __shfl_xor_sync(0xffffffffu, z, o);
+      sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    }
+    __shared__ double s_z[32], s_sd[32];
+    if (lane == 0) {
+      s_z[wid] = z;
+      s_sd[wid] = sd;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double Z = 0.0, SD = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+        Z += s_z[q];
+        SD += s_sd[q];
+      }
+      *a.entropy = Z > 0.0 ? log(Z) + SD * a.inv_lambda / Z : (double)NAN;
+    }
+  }
+
   // radix select of the E-th smallest key (rank 1-based), 8-bit digits from
   // the highest bit where the keys differ down (the bits above it are
   // common to all keys, and a digit over them would put every key in one

@@ -59,6 +59,7 @@ struct mtp_handle {
   uint32_t* status = nullptr;  // device status word: bits a rollout sets when a bounded wait gave up
   int rollout_chunk = 0;       // horizon chunk of the staged control loads of a lone rollout (0: direct)
   bool tc_graph = false;       // graph rows contracted on the tensor cores (BF16 B-spline)
+  double* entropy = nullptr;   // last iteration's cost entropy (MTP_FLAG_COST_ENTROPY)
   // replay
   cudaStream_t cap_stream = nullptr;
   std::map<int, cudaGraphExec_t> graphs;   // key: (iterations, cur, first prepared)

@@ -463,7 +463,7 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, int work, Gen gen, 
   if ((e = launch_rollout(h, r, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[2], s, captured);
   SelectArgs sa{h->cost, U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
-                h->elite, h->weight, h->ustar, nullptr, ustar_out};
+                h->elite, h->weight, h->ustar, nullptr, ustar_out, h->entropy};
   if ((e = launch_select(sa, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[3], s, captured);
   if (h->pipeline && (e = cudaStreamWaitEvent(s, h->ev_join, 0)) != cudaSuccess) return e;
@@ -603,7 +603,7 @@ void free_handle(mtp_handle* h) {
   void* ptrs[] = {h->basis, h->bfirst, h->seg, h->delta, h->mu, h->sigma, h->mu_f, h->sigma_f,
                   h->iter_dev,
                   h->Ubuf[0], h->Ubuf[1], h->cost, h->elite, h->weight, h->ustar, h->x0, h->Z,
-                  h->status};
+                  h->status, h->entropy};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -658,7 +658,8 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
       (e = dalloc(&h->cost, dm.B)) || (e = dalloc(&h->elite, dm.E)) ||
       (e = dalloc(&h->weight, dm.E)) || (e = dalloc(&h->ustar, dm.n)) ||
       (e = dalloc(&h->x0, dm.d)) || (e = dalloc(&h->Z, (size_t)dm.M * dm.N * dm.n)) ||
-      (e = dalloc(&h->status, 1)))
+      (e = dalloc(&h->status, 1)) ||
+      ((p.flags & MTP_FLAG_COST_ENTROPY) && (e = dalloc(&h->entropy, 1))))
     return err(cuda_fail(h, e, "cudaMalloc"));
   std::vector<double> mu(rowsz, p.mu_init), sg(rowsz, p.sigma_init);
   std::vector<float> muf(rowsz, (float)p.mu_init), sgf(rowsz, (float)p.sigma_init);
@@ -690,7 +691,8 @@ mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes)
            + r((uint64_t)p.E * 4) + r((uint64_t)p.E * 8)                      // elites, weights
            + r((uint64_t)p.ctrl_dim * 4) + r((uint64_t)p.state_dim * 4)
            + r((uint64_t)p.M * p.N * p.ctrl_dim * 4)                          // graph Z
-           + r(4);                                                            // status word
+           + r(4)                                                             // status word
+           + ((p.flags & MTP_FLAG_COST_ENTROPY) ? r(8) : 0);                  // entropy
   const Dims dm = dims_of(p);
   bool on = false, local = false;
   int grid = 0;
@@ -821,7 +823,7 @@ mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U
   const Dims& dm = h->dm;
   cudaStream_t s = (cudaStream_t)stream;
   SelectArgs sa{d_cost, d_U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
-                h->elite, h->weight, h->ustar, d_elite, d_ustar};
+                h->elite, h->weight, h->ustar, d_elite, d_ustar, h->entropy};
   cudaError_t e = launch_select(sa, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "select");
   UpdateArgs ua{d_U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
@@ -1076,6 +1078,16 @@ mtp_status mtp_shift(mtp_handle* h, int32_t k, void* stream) {
   cudaError_t e = launch_shift(h->mu, h->sigma, h->mu_f, h->sigma_f, h->dm.H, h->dm.n, k,
                                (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "shift");
+  return MTP_OK;
+}
+
+mtp_status mtp_cost_entropy(mtp_handle* h, double* h_entropy) {
+  if (!h || !h_entropy) return fail(h, MTP_ERR_INVALID_ARG, "cost_entropy: bad argument");
+  if (!h->entropy)
+    return fail(h, MTP_ERR_INVALID_ARG, "cost_entropy: create the problem with MTP_FLAG_COST_ENTROPY");
+  DeviceGuard g(h->device);
+  MTP_CUDA(h, cudaDeviceSynchronize());
+  MTP_CUDA(h, cudaMemcpy(h_entropy, h->entropy, 8, cudaMemcpyDeviceToHost));
   return MTP_OK;
 }
 

@@ -206,6 +206,7 @@ struct SelectArgs {
   float* ustar;       // (n) internal
   int32_t* elite_out; // optional copy
   float* ustar_out;   // optional copy
+  double* entropy;    // optional: the cost entropy of all B costs (Sec. 4.1 diagnostic)
 };
 
 struct UpdateArgs {

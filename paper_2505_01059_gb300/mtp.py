@@ -31,6 +31,7 @@ UPDATE = {"softmax": 0, "plain_cem": 1}
 DR = {"none": 0, "per_sample": 1, "shared": 2}
 FLAG_NO_KAHAN = 0x1
 FLAG_NO_GRAPH = 0x2
+FLAG_COST_ENTROPY = 0x10
 FLAG_BF16_BASIS = 0x4
 FLAG_NO_PIPELINE = 0x8
 
@@ -43,7 +44,7 @@ EXPORTS = [
     "mtp_set_profiling", "mtp_stage_times", "mtp_stage_times5", "mtp_elite_update_noalloc",
     "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_layout", "mtp_batch_plan_step",
     "mtp_batch_autotune", "mtp_batch_reserve", "mtp_batch_fill", "mtp_batch_shift",
-    "mtp_batch_launches", "mtp_batch_rollout_times", "mtp_device_status",
+    "mtp_batch_launches", "mtp_batch_rollout_times", "mtp_device_status", "mtp_cost_entropy",
     "mtp_problem_device_bytes", "mtp_server_create", "mtp_server_destroy", "mtp_server_register",
     "mtp_submit", "mtp_poll", "mtp_server_get_stats", "mtp_server_last_error",
     "mtp_submit_many", "mtp_poll_many",
@@ -138,6 +139,7 @@ def load_library(path: str = LIB_PATH):
         "mtp_shift": (i32, [vp, i32, vp]),
         "mtp_get_state": (i32, [vp, vp, vp, vp]),
         "mtp_device_status": (i32, [vp]),
+        "mtp_cost_entropy": (i32, [vp, vp]),
         "mtp_set_state": (i32, [vp, vp, vp, u32]),
         "mtp_set_profiling": (i32, [vp, i32]),
         "mtp_stage_times": (i32, [vp, vp, vp]),
@@ -421,6 +423,14 @@ def mtp_plan_step_host(h: Handle, x0: np.ndarray, iters: int, ustar: np.ndarray,
 
 def mtp_shift(h: Handle, k: int, stream=None):
     _check(load_library().mtp_shift(h.ptr, k, _stream(stream)), h.ptr)
+
+
+def mtp_cost_entropy(h: Handle) -> float:
+    """Sec. 4.1 cost entropy of the latest selection (problems created with
+    FLAG_COST_ENTROPY)."""
+    v = C.c_double()
+    _check(load_library().mtp_cost_entropy(h.ptr, C.addressof(v)), h.ptr)
+    return float(v.value)
 
 
 def mtp_device_status(h: Handle):

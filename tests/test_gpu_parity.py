@@ -346,6 +346,35 @@ def test_staged_and_direct_control_loads_agree(mtp, spec):
     mtp.mtp_destroy(h)
 
 
+@pytest.mark.parametrize("spec", [W.pointmass(), W.chain(B=2048), W.legged(links=4, B=512, H=32, M=6,
+                                                                       N=16, E=16)])
+def test_cost_entropy_matches_oracle(mtp, spec):
+    """Sec. 4.1 cost entropy computed by the selection kernel against the
+    oracle's on the GPU's own costs, alone and in a batch; refused on a
+    problem created without the flag."""
+    h = mtp.mtp_create(dict(spec, flags=spec.get("flags", 0) | mtp.FLAG_COST_ENTROPY))
+    x0 = _t(np.array(spec["x0"], np.float32))
+    u = torch.empty(h.sizes["n"], device=DEV)
+    for _ in range(2):
+        mtp.mtp_plan_step(h, x0, 1, u)
+        got = mtp.mtp_cost_entropy(h)
+        cg = _np(torch.as_tensor(mtp.mtp_get_buffers(h)["cost"], device=DEV))
+        want = orc.cost_entropy(cg, spec["lambda"])
+        assert got == pytest.approx(want, rel=1e-6, abs=1e-9)
+    b = mtp.mtp_batch_create([h])
+    us = torch.empty(b.ustar_offset[-1], device=DEV)
+    mtp.mtp_batch_plan_step(b, x0, 1, us)
+    got = mtp.mtp_cost_entropy(h)
+    cg = _np(torch.as_tensor(mtp.mtp_get_buffers(h)["cost"], device=DEV))
+    assert got == pytest.approx(orc.cost_entropy(cg, spec["lambda"]), rel=1e-6, abs=1e-9)
+    mtp.mtp_batch_destroy(b)
+    mtp.mtp_destroy(h)
+    h = mtp.mtp_create(spec)
+    with pytest.raises(mtp.MtpError):
+        mtp.mtp_cost_entropy(h)
+    mtp.mtp_destroy(h)
+
+
 # ----------------------------------------------------------------------------
 # Top-E and the update
 # ----------------------------------------------------------------------------

@@ -166,3 +166,17 @@ def test_planner_improves_pointmass(orc):
 def test_cost_entropy(orc):
     assert orc.cost_entropy(np.zeros(64), 0.1) == pytest.approx(np.log(64))
     assert orc.cost_entropy(np.array([0.0, 1e6, 1e6]), 0.1) == pytest.approx(0.0, abs=1e-12)
+
+
+def test_cost_entropy_two_levels(orc):
+    """k candidates at cost 0 and m at cost d: with q = exp(-d / lambda) each
+    cheap candidate has p = 1 / (k + m q) and each dear one p q, so
+    H = log(k + m q) + m q (d / lambda) / (k + m q); the cheap ones weigh
+    more (the exp(-J / lambda) reading)."""
+    k, m, d, lam = 5, 3, 0.7, 0.25
+    q = np.exp(-d / lam)
+    Z = k + m * q
+    want = np.log(Z) + m * q * (d / lam) / Z
+    cost = np.array([0.0] * k + [d] * m)
+    assert orc.cost_entropy(cost, lam) == pytest.approx(want, rel=1e-13)
+    assert orc.cost_entropy(cost + 17.0, lam) == pytest.approx(want, rel=1e-12)  # shift invariant
