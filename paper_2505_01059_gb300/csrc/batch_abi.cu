@@ -446,6 +446,9 @@ extern "C" {
 static mtp_status check_batch_handles(mtp_handle* const* handles, int32_t count, int dev) {
   for (int i = 0; i < count; ++i) {
     if (!handles[i]) return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch: null handle");
+    if (handles[i]->sel_chunks > 0)
+      return batch_fail(nullptr, MTP_ERR_UNSUPPORTED,
+                        "batch: B too large for the one-block selection a batch gives each instance");
     if (handles[i]->device != dev)
       return batch_fail(nullptr, MTP_ERR_INVALID_ARG, "batch: handles must live on the batch's device");
     for (int j = 0; j < i; ++j)

@@ -13,6 +13,9 @@ namespace mtp {
 namespace {
 
 constexpr int kSelThreads = 1024;
+constexpr size_t kSelSmemMax = 200 * 1024;  // dynamic shared memory of one selection block
+constexpr int kOneBlockMax = 32768;         // above this, two stages (measured below)
+constexpr int kChunkKeys = 16384;           // first-stage chunk length
 
 __device__ __forceinline__ uint32_t order_key(float f) {
   if (isnan(f)) f = __int_as_float(0x7f800000);
@@ -62,8 +65,22 @@ __device__ __forceinline__ void warp_sort64(unsigned long long& v0, unsigned lon
   }
 }
 
+// Selection modes: kSelAll takes the B costs to the elites, weights and u*;
+// kSelChunk (block c of many) takes costs [c chunk, (c+1) chunk) to their own
+// top min(E, chunk) (key, index) pairs, sorted, written to pairs[c E ..]
+// (the rest of its E slots padded with all-ones); kSelMerge takes those pairs
+// (B = chunks * E of them) to the elites, weights and u*.  Chunks cover the
+// indices in order and each chunk's pairs are sorted by (key, index), so
+// among equal keys the merge's position order is the index order: the two
+// stages give exactly the one-block result.
+enum SelMode { kSelAll = 0, kSelChunk = 1, kSelMerge = 2 };
+
+template <int MODE>
 __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* sm_raw) {
-  const int B = a.B, E = a.E;
+  const int base = MODE == kSelChunk ? (int)blockIdx.x * a.chunk : 0;
+  const int B = MODE == kSelChunk ? min(a.chunk, a.B - base) : a.B;
+  const int E = MODE == kSelChunk ? min(a.E, B) : a.E;
+  const float* costs = a.cost + base;
   const int Bp = (B + 1) & ~1;
   uint32_t* keys = reinterpret_cast<uint32_t*>(sm_raw);
   unsigned long long* sel = reinterpret_cast<unsigned long long*>(keys + Bp);
@@ -79,17 +96,28 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   // L2 round trip after the other (measured on the legged workload, 16
   // costs per thread: 4.4 us for this phase)
   for (int b0 = tid; b0 < B; b0 += kSelBatch * blockDim.x) {
-    float cv[kSelBatch];
+    uint32_t kv[kSelBatch];
+    if constexpr (MODE == kSelMerge) {
 #pragma unroll
-    for (int j = 0; j < kSelBatch; ++j) {
-      const int b = b0 + j * blockDim.x;
-      cv[j] = b < B ? a.cost[b] : 0.f;
+      for (int j = 0; j < kSelBatch; ++j) {
+        const int b = b0 + j * blockDim.x;
+        kv[j] = b < B ? (uint32_t)(a.pairs[b] >> 32) : 0u;
+      }
+    } else {
+      float cv[kSelBatch];
+#pragma unroll
+      for (int j = 0; j < kSelBatch; ++j) {
+        const int b = b0 + j * blockDim.x;
+        cv[j] = b < B ? costs[b] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < kSelBatch; ++j) kv[j] = order_key(cv[j]);
     }
 #pragma unroll
     for (int j = 0; j < kSelBatch; ++j) {
       const int b = b0 + j * blockDim.x;
       if (b < B) {
-        const uint32_t k = order_key(cv[j]);
+        const uint32_t k = kv[j];
         keys[b] = k;
         kmin = min(kmin, k);
         kmax = max(kmax, k);
@@ -120,7 +148,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   // over all B candidates: with d_b = J_b - J_min and w_b = exp(-d_b / lambda),
   // H = -sum_b p_b log p_b = log Z + sum_b w_b d_b / (lambda Z).  The weights
   // in FP32, their sums in FP64.
-  if (a.entropy) {
+  if (MODE == kSelAll && a.entropy) {
     const float cmin = key_cost(kmin);
     const float inv_l = (float)a.inv_lambda;
     double z = 0.0, sd = 0.0;
@@ -325,9 +353,22 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   }
   __syncthreads();
 
+  if constexpr (MODE == kSelChunk) {
+    unsigned long long* out = a.pairs + (size_t)blockIdx.x * a.E;
+    for (int k = tid; k < a.E; k += blockDim.x)
+      out[k] = k < E ? ((sel[k] & 0xffffffff00000000ull) | (unsigned long long)(uint32_t)(base + (int)(sel[k] & 0xffffffffu)))
+                     : ~0ull;
+    return;
+  }
+  // the candidate index of sorted entry k (a position among the pairs when merging)
+  auto index_of_sel = [&](unsigned long long e) -> int {
+    const int j = (int)(e & 0xffffffffu);
+    if constexpr (MODE == kSelMerge) return (int)(a.pairs[j] & 0xffffffffu);
+    else return j;
+  };
   // u* = U[elite[0], 0, :], requested before the softmax so the load
   // overlaps it
-  const int best_row = (int)(sel[0] & 0xffffffffu);
+  const int best_row = index_of_sel(sel[0]);
   if (E <= 64) {
     // One warp, elites lane and lane + 32, their costs decoded from the
     // sorted order keys (no global reload), no block barrier.  The two
@@ -344,7 +385,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
       const int k = lane + 32 * h;
       if (k < E) {
         const unsigned long long e = sel[k];
-        const int idx = (int)(e & 0xffffffffu);
+        const int idx = index_of_sel(e);
         a.elite[k] = idx;
         if (a.elite_out) a.elite_out[k] = idx;
         const double c = (double)key_cost((uint32_t)(e >> 32));
@@ -379,7 +420,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
   const int k0 = tid;
   double w_first = 0.0;
   for (int k = k0; k < E; k += blockDim.x) {
-    const int idx = (int)(sel[k] & 0xffffffffu);
+    const int idx = index_of_sel(sel[k]);
     a.elite[k] = idx;
     if (a.elite_out) a.elite_out[k] = idx;
     double c = (double)a.cost[idx];
@@ -410,14 +451,26 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, unsigned char* 
 
 __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  select_body(a, sm_raw);
+  select_body<kSelAll>(a, sm_raw);
+}
+
+// First stage of the selection over many CTAs: block c, chunk c of the costs.
+__global__ void __launch_bounds__(kSelThreads) k_select_chunks(const SelectArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  select_body<kSelChunk>(a, sm_raw);
+}
+
+// Second stage: one CTA over the chunks' pairs (a.B = chunks * E).
+__global__ void __launch_bounds__(kSelThreads) k_select_merge(const SelectArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  select_body<kSelMerge>(a, sm_raw);
 }
 
 // One block per planning problem.
 __global__ void __launch_bounds__(kSelThreads) k_select_batch(const SelectArgs* __restrict__ args) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const SelectArgs a = args[blockIdx.x];
-  select_body(a, sm_raw);
+  select_body<kSelAll>(a, sm_raw);
 }
 
 // The FP64 sums over elites follow one canonical order for every launch
@@ -655,9 +708,11 @@ size_t select_smem_bytes(int B, int E) {
 }
 
 cudaError_t init_select_attributes() {
-  cudaError_t e =
-      cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) ||
+      (e = cudaFuncSetAttribute(k_select_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) ||
+      (e = cudaFuncSetAttribute(k_select_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)))
+    return e;
   return cudaFuncSetAttribute(k_select_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               200 * 1024);
 }
@@ -698,6 +753,39 @@ int select_threads(int B, int E) {
 
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s) {
   k_select<<<1, select_threads(a.B, a.E), select_smem_bytes(a.B, a.E), s>>>(a);
+  return cudaGetLastError();
+}
+
+// Two-stage selection plan for B candidates and E elites: the chunk length
+// and chunk count, or chunks = 0 when one block selects them (its keys fit
+// its shared memory and B is at most kOneBlockMax).  Chunks are as long as
+// one block's shared memory allows, and their E-pair outputs must fit the
+// merging block; infeasible sizes return chunks = -1.
+void select_plan(int B, int E, int* chunk, int* chunks) {
+  *chunk = B;
+  *chunks = 0;
+  if (select_smem_bytes(B, E) <= kSelSmemMax && B <= kOneBlockMax) return;
+  int c = kChunkKeys;
+  while (c > E && select_smem_bytes(c, E) > kSelSmemMax) c >>= 1;
+  if (c < E) c = E;
+  const long long n = ((long long)B + c - 1) / c;
+  if (select_smem_bytes(c, E) > kSelSmemMax || select_smem_bytes((int)std::min<long long>(n * E, 1 << 30), E) > kSelSmemMax) {
+    *chunks = -1;
+    return;
+  }
+  *chunk = c;
+  *chunks = (int)n;
+}
+
+cudaError_t launch_select_two_stage(const SelectArgs& a, int chunk, int chunks, cudaStream_t s) {
+  SelectArgs c1 = a;
+  c1.chunk = chunk;
+  k_select_chunks<<<chunks, select_threads(chunk, a.E), select_smem_bytes(chunk, a.E), s>>>(c1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  SelectArgs c2 = a;
+  c2.B = chunks * a.E;
+  k_select_merge<<<1, select_threads(c2.B, a.E), select_smem_bytes(c2.B, a.E), s>>>(c2);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,10 @@ struct mtp_handle {
   int rollout_chunk = 0;       // horizon chunk of the staged control loads of a lone rollout (0: direct)
   bool tc_graph = false;       // graph rows contracted on the tensor cores (BF16 B-spline)
   double* entropy = nullptr;   // last iteration's cost entropy (MTP_FLAG_COST_ENTROPY)
+  // two-stage elite selection (B beyond one block): chunk length, chunk
+  // count (0: one block) and the chunks' (key, index) pairs
+  int sel_chunk = 0, sel_chunks = 0;
+  unsigned long long* sel_pairs = nullptr;
   // replay
   cudaStream_t cap_stream = nullptr;
   std::map<int, cudaGraphExec_t> graphs;   // key: (iterations, cur, first prepared)

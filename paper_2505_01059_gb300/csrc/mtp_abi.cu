@@ -123,7 +123,11 @@ mtp_status validate(const mtp_problem& p) {
   if (p.dr_mode == MTP_DR_SHARED && (p.R < 1 || p.R > 64)) return bad("R must be in 1..64");
   if (p.dr_mode != MTP_DR_NONE && !(p.dr_lo > 0.f && p.dr_lo <= p.dr_hi)) return bad("need 0 < dr_lo <= dr_hi");
   if ((size_t)p.M * p.N * p.ctrl_dim * 4 > 160 * 1024) return bad("graph M*N*n too large for one block's shared memory");
-  if (select_smem_bytes(p.B, p.E) > kMaxSmem) return bad("B and E too large for the single-block elite selection");
+  {
+    int chunk = 0, chunks = 0;
+    select_plan(p.B, p.E, &chunk, &chunks);
+    if (chunks < 0) return bad("B and E too large for the two-stage elite selection");
+  }
   if ((p.flags & MTP_FLAG_BF16_BASIS) && p.interp != MTP_INTERP_BSPLINE)
     return fail(nullptr, MTP_ERR_UNSUPPORTED, "the BF16 basis applies to B-spline interpolation only");
   return MTP_OK;
@@ -384,6 +388,13 @@ cudaError_t launch_generate(const mtp_handle* h, CandArgs& c, cudaStream_t s) {
   return launch_bspline_tc(c, s);
 }
 
+// Alg. 2 elite selection of a handle: one block, or two stages when its B
+// is beyond one block (many blocks select their chunks, one merges).
+cudaError_t launch_selection(const mtp_handle* h, const SelectArgs& a, cudaStream_t s) {
+  if (h->sel_chunks > 0) return launch_select_two_stage(a, h->sel_chunk, h->sel_chunks, s);
+  return launch_select(a, s);
+}
+
 cudaError_t launch_rollout(const mtp_handle* h, const RolloutArgs& a, cudaStream_t s) {
   const mtp_problem& p = h->pr;
   if (p.dyn == MTP_DYN_POINTMASS) return launch_rollout_pointmass(a, pointmass_model(p), h->rollout_chunk, s);
@@ -463,8 +474,8 @@ cudaError_t enqueue_iteration(mtp_handle* h, cudaStream_t s, int work, Gen gen, 
   if ((e = launch_rollout(h, r, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[2], s, captured);
   SelectArgs sa{h->cost, U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
-                h->elite, h->weight, h->ustar, nullptr, ustar_out, h->entropy};
-  if ((e = launch_select(sa, s)) != cudaSuccess) return e;
+                h->elite, h->weight, h->ustar, nullptr, ustar_out, h->entropy, h->sel_pairs, 0};
+  if ((e = launch_selection(h, sa, s)) != cudaSuccess) return e;
   if (ev) stage_event(ev[3], s, captured);
   if (h->pipeline && (e = cudaStreamWaitEvent(s, h->ev_join, 0)) != cudaSuccess) return e;
   UpdateArgs ua{U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
@@ -603,7 +614,7 @@ void free_handle(mtp_handle* h) {
   void* ptrs[] = {h->basis, h->bfirst, h->seg, h->delta, h->mu, h->sigma, h->mu_f, h->sigma_f,
                   h->iter_dev,
                   h->Ubuf[0], h->Ubuf[1], h->cost, h->elite, h->weight, h->ustar, h->x0, h->Z,
-                  h->status, h->entropy};
+                  h->status, h->entropy, h->sel_pairs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -635,6 +646,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
     probe.graph_rows = dm.P;
     h->tc_graph = bspline_tc_eligible(probe);
   }
+  select_plan(dm.B, dm.E, &h->sel_chunk, &h->sel_chunks);
   auto err = [&](mtp_status s) {
     g_create_error = h->err;
     free_handle(h);
@@ -659,7 +671,8 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
       (e = dalloc(&h->weight, dm.E)) || (e = dalloc(&h->ustar, dm.n)) ||
       (e = dalloc(&h->x0, dm.d)) || (e = dalloc(&h->Z, (size_t)dm.M * dm.N * dm.n)) ||
       (e = dalloc(&h->status, 1)) ||
-      ((p.flags & MTP_FLAG_COST_ENTROPY) && (e = dalloc(&h->entropy, 1))))
+      ((p.flags & MTP_FLAG_COST_ENTROPY) && (e = dalloc(&h->entropy, 1))) ||
+      (h->sel_chunks > 0 && (e = dalloc(&h->sel_pairs, (size_t)h->sel_chunks * dm.E))))
     return err(cuda_fail(h, e, "cudaMalloc"));
   std::vector<double> mu(rowsz, p.mu_init), sg(rowsz, p.sigma_init);
   std::vector<float> muf(rowsz, (float)p.mu_init), sgf(rowsz, (float)p.sigma_init);
@@ -693,6 +706,11 @@ mtp_status mtp_problem_device_bytes(const mtp_problem* problem, uint64_t* bytes)
            + r((uint64_t)p.M * p.N * p.ctrl_dim * 4)                          // graph Z
            + r(4)                                                             // status word
            + ((p.flags & MTP_FLAG_COST_ENTROPY) ? r(8) : 0);                  // entropy
+  {
+    int chunk = 0, chunks = 0;
+    select_plan(p.B, p.E, &chunk, &chunks);
+    if (chunks > 0) *bytes += r((uint64_t)chunks * p.E * 8);          // selection pairs
+  }
   const Dims dm = dims_of(p);
   bool on = false, local = false;
   int grid = 0;
@@ -723,7 +741,8 @@ mtp_status mtp_get_sizes(const mtp_handle* h, mtp_sizes* out) {
   // candidates (+ graph when written once), rollout, select, update; when
   // pipelined: finish, prepare (graph in its shared memory), rollout, select, update
   // (tensor-core graph rows: graph, local rows, contraction, rollout, select, update)
-  const int kpi = h->pipeline ? 5 : (h->tc_graph ? 6 : (h->global_Z && d.P > 0 ? 5 : 4));
+  const int kpi = (h->pipeline ? 5 : (h->tc_graph ? 6 : (h->global_Z && d.P > 0 ? 5 : 4))) +
+                  (h->sel_chunks > 0 ? 1 : 0);  // the two-stage selection's second launch
   *out = mtp_sizes{d.B, d.P, d.L, d.E, d.H, d.n, d.d, d.M, d.N, kpi,
                    h->pipeline ? (h->prep_local ? 2 : 1) : 0};
   return MTP_OK;
@@ -823,8 +842,8 @@ mtp_status mtp_elite_update(mtp_handle* h, const float* d_cost, const float* d_U
   const Dims& dm = h->dm;
   cudaStream_t s = (cudaStream_t)stream;
   SelectArgs sa{d_cost, d_U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
-                h->elite, h->weight, h->ustar, d_elite, d_ustar, h->entropy};
-  cudaError_t e = launch_select(sa, s);
+                h->elite, h->weight, h->ustar, d_elite, d_ustar, h->entropy, h->sel_pairs, 0};
+  cudaError_t e = launch_selection(h, sa, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "select");
   UpdateArgs ua{d_U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
                 h->pr.update_rule, h->mu, h->sigma, h->mu_f, h->sigma_f, nullptr};

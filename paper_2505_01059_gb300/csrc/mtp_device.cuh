@@ -207,6 +207,10 @@ struct SelectArgs {
   int32_t* elite_out; // optional copy
   float* ustar_out;   // optional copy
   double* entropy;    // optional: the cost entropy of all B costs (Sec. 4.1 diagnostic)
+  // two-stage selection (B beyond one block): scratch of chunks * E
+  // (key, index) pairs and the first stage's chunk length
+  unsigned long long* pairs;
+  int32_t chunk;
 };
 
 struct UpdateArgs {
@@ -262,6 +266,10 @@ cudaError_t launch_bspline_tc(const CandArgs& a, cudaStream_t s);
 cudaError_t launch_bspline_tc_batch(const CandArgs* d_args, const int* d_tile_start, int count,
                                     int total_tiles, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
+// Two-stage selection for B beyond one block: chunks > 0 stages of `chunk`
+// costs each (select_plan; chunks = 0: one block suffices, -1: too large).
+void select_plan(int B, int E, int* chunk, int* chunks);
+cudaError_t launch_select_two_stage(const SelectArgs& a, int chunk, int chunks, cudaStream_t s);
 size_t select_smem_bytes(int B, int E);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 // batched forms: one launch over many planning problems

@@ -385,6 +385,9 @@ def test_cost_entropy_matches_oracle(mtp, spec):
     (16384, 16384, "ties"), (777, 300, "special"),
     # the radix passes stop at a bin of <= 64 keys, which one warp sorts
     (4096, 100, "rand"), (2000, 64, "special"), (64, 64, "rand"), (65, 64, "ties"), (8192, 7, "rand"),
+    # beyond one block: chunks selected by many blocks, then merged by one
+    (65536, 64, "rand"), (65536, 64, "ties"), (1 << 20, 64, "special"), (1 << 20, 300, "ties"),
+    (100000, 2000, "rand"), (32769, 1, "special"),
 ])
 def test_top_e(mtp, B, E, kind):
     spec = W.pointmass(k=1, H=2, B=B, E=E, beta=0.0)
@@ -459,6 +462,7 @@ def _boundary_ok(cost, E):
     (W.chain(links=12, B=256, H=16, M=3, N=1, E=8, beta=0.1), 2, 1),  # longest chain, one node per layer
     (W.chain(links=1, B=64, H=8, M=2, interp="linear", E=4), 4, 1),   # one link, straight lines
     (W.legged(links=2, B=128, H=16, M=4, N=8, E=4), 2, 1),          # shortest legged robot
+    (W.pointmass(B=40000, H=16, E=100), 2, 0),                       # two-stage selection
 ])
 def test_plan_step_teacher_forced(mtp, spec, iters, min_checked):
     h = mtp.mtp_create(spec)
