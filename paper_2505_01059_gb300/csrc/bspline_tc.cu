@@ -300,8 +300,9 @@ __global__ void __launch_bounds__(kTcThreads) k_bspline_tc(const CandArgs a) {
 }
 
 // Many instances: tile_start (count + 1 entries) numbers each instance's
-// first tile; CTAs loop over the global tile list, set up again whenever
-// the instance changes.
+// first tile; each CTA takes a contiguous range of the global tile list (so
+// it changes instance, and reloads its set-up, rarely) and sets up again
+// whenever the instance or the slice changes.
 __global__ void __launch_bounds__(kTcThreads) k_bspline_tc_batch(const CandArgs* __restrict__ args,
                                                                  const int* __restrict__ tile_start,
                                                                  int count) {
@@ -312,7 +313,9 @@ __global__ void __launch_bounds__(kTcThreads) k_bspline_tc_batch(const CandArgs*
   int cur = -1, cur_s = -1, K = 16;
   uint32_t iter = 0, phase = 0;
   bool failed = false;
-  for (int g = blockIdx.x; g < total && !failed; g += gridDim.x) {
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int g_end = min(total, ((int)blockIdx.x + 1) * per);
+  for (int g = (int)blockIdx.x * per; g < g_end && !failed; ++g) {
     int lo = 0, hi = count;
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
