@@ -828,8 +828,10 @@ def run_serving(args, mtp, dev) -> dict:
     # out of the latency windows; the first pass warms every robot
     gc.collect()
     gc.disable()
-    served_open_loop(mtp, srv, ids, sim, steps_of, 50.0, 1.0, 0.0, rng)
+    # the clock sampler (nvidia-smi) starts before the warm-up pass: its
+    # start-up holds the driver for a while
     with ClockSampler(dev.index) as clocks:
+        served_open_loop(mtp, srv, ids, sim, steps_of, 50.0, 1.0, 0.0, rng)
         for rate in args.serve_rates:
             done, steps, lat, refused = served_open_loop(mtp, srv, ids, sim, steps_of, rate,
                                                          args.serve_seconds, args.serve_warmup, rng)

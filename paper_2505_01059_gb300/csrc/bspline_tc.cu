@@ -41,6 +41,7 @@ constexpr int kMaxK = 64;            // layers (M) padded to a multiple of 16
 constexpr int kMaxSlices = 2;        // 128-step horizon slices (H <= 256)
 constexpr uint32_t kTmemCols = 128;
 constexpr size_t kMinSmem = 50 * 1024;  // at most four CTAs per SM (their TMEM fits)
+constexpr int kBatchTilesPerCta = 8;
 
 struct TcSmem {
   __nv_bfloat16 A[128 * kMaxK];              // basis of one slice, K-major canonical layout
@@ -380,7 +381,10 @@ cudaError_t launch_bspline_tc(const CandArgs& a, cudaStream_t s) {
 cudaError_t launch_bspline_tc_batch(const CandArgs* d_args, const int* d_tile_start, int count,
                                     int total_tiles, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
-  const int grid = std::min(total_tiles, 4 * device_sms());
+  // at least kBatchTilesPerCta tiles per CTA: in a batch the launches of
+  // other groups run beside this one, and each CTA's set-up (tensor memory,
+  // operands) is paid once for its whole range
+  const int grid = std::min((total_tiles + kBatchTilesPerCta - 1) / kBatchTilesPerCta, 4 * device_sms());
   k_bspline_tc_batch<<<grid, kTcThreads, tc_smem_bytes(), s>>>(d_args, d_tile_start, count);
   return cudaGetLastError();
 }
