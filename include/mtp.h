@@ -262,6 +262,16 @@ mtp_status mtp_cost_entropy(mtp_handle* h, double* h_entropy);
  * of the handle's rollouts (alone or in a batch), else MTP_OK. */
 mtp_status mtp_device_status(mtp_handle* h);
 
+/* Self-test of the bounded device waits: one warp waits on an mbarrier whose
+ * expected bytes never arrive, with a time limit of limit_s seconds (0 <
+ * limit_s <= 10) of the GPU's global timer.  The wait can only end by giving
+ * up, so a working library returns MTP_ERR_TIMEOUT after about limit_s, with
+ * the device still usable; *waited_s (may be NULL) gets the host-measured
+ * time.  MTP_OK would mean the wait saw bytes that were never sent;
+ * MTP_ERR_CUDA a launch or copy failure.  Synchronises the device; allocates
+ * 4 bytes of device memory for the result. */
+mtp_status mtp_selftest_bounded_wait(double limit_s, double* waited_s);
+
 /* Checkpoint / resume of the planner state: FP64 mean and spread (H, n) and
  * the iteration counter.  Synchronous. */
 mtp_status mtp_get_state(mtp_handle* h, double* h_mu, double* h_sigma, uint32_t* h_iter);

@@ -104,8 +104,10 @@ struct StageShape {
 };
 
 // Bounded mbarrier wait: try_wait on the phase with the given parity for at
-// most about two seconds of the global timer, then give up (returns false).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// most limit_ns of the global timer (about two seconds by default), then
+// give up (returns false).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = 2000000000ull) {
   const unsigned addr = (unsigned)__cvta_generic_to_shared(bar);
   uint64_t t_start = 0;
   for (int spin = 0;; ++spin) {
@@ -121,7 +123,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     uint64_t now;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
     if (spin == 0) t_start = now;
-    else if (now - t_start > 2000000000ull) return false;
+    else if (now - t_start > limit_ns) return false;
   }
 }
 

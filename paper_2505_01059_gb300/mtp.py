@@ -45,6 +45,7 @@ EXPORTS = [
     "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_layout", "mtp_batch_plan_step",
     "mtp_batch_autotune", "mtp_batch_reserve", "mtp_batch_fill", "mtp_batch_shift",
     "mtp_batch_launches", "mtp_batch_rollout_times", "mtp_device_status", "mtp_cost_entropy",
+    "mtp_selftest_bounded_wait",
     "mtp_problem_device_bytes", "mtp_server_create", "mtp_server_destroy", "mtp_server_register",
     "mtp_submit", "mtp_poll", "mtp_server_get_stats", "mtp_server_last_error",
     "mtp_submit_many", "mtp_poll_many",
@@ -139,6 +140,7 @@ def load_library(path: str = LIB_PATH):
         "mtp_shift": (i32, [vp, i32, vp]),
         "mtp_get_state": (i32, [vp, vp, vp, vp]),
         "mtp_device_status": (i32, [vp]),
+        "mtp_selftest_bounded_wait": (i32, [C.c_double, vp]),
         "mtp_cost_entropy": (i32, [vp, vp]),
         "mtp_set_state": (i32, [vp, vp, vp, u32]),
         "mtp_set_profiling": (i32, [vp, i32]),
@@ -431,6 +433,14 @@ def mtp_cost_entropy(h: Handle) -> float:
     v = C.c_double()
     _check(load_library().mtp_cost_entropy(h.ptr, C.addressof(v)), h.ptr)
     return float(v.value)
+
+
+def mtp_selftest_bounded_wait(limit_s: float):
+    """Runs the bounded-wait self-test; returns (status, host-measured seconds).
+    A working library gives MTP_ERR_TIMEOUT (5) after about limit_s."""
+    waited = C.c_double()
+    st = load_library().mtp_selftest_bounded_wait(float(limit_s), C.addressof(waited))
+    return int(st), float(waited.value)
 
 
 def mtp_device_status(h: Handle):

@@ -735,3 +735,20 @@ def test_legged_plan_step_teacher_forced(mtp, spec, iters):
         np.testing.assert_allclose(sg_g, sg_r, rtol=1e-9, atol=1e-12)
         assert np.array_equal(_np(u), us_r)
     mtp.mtp_destroy(h)
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable(mtp):
+    """The device waits of the rollouts and of the tensor-core contraction are
+    bounded by the global timer: an mbarrier whose bytes never arrive makes
+    the wait give up after its limit and report it, and the next planner
+    step runs normally."""
+    st, waited = mtp.mtp_selftest_bounded_wait(0.05)
+    assert st == 5  # MTP_ERR_TIMEOUT
+    assert 0.04 <= waited < 2.0
+    spec = W.pointmass(B=256, H=16, E=8)
+    h = mtp.mtp_create(spec)
+    u = torch.empty(h.sizes["n"], device=DEV)
+    mtp.mtp_plan_step(h, _t(np.array(spec["x0"], np.float32)), 2, u)
+    mtp.mtp_device_status(h)
+    assert np.all(np.isfinite(_np(u)))
+    mtp.mtp_destroy(h)
