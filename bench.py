@@ -452,6 +452,7 @@ def batch_rollout_roofline(mtp, b, specs, sms: int) -> tuple[dict, list]:
         achieved = fl / (g["ms"] / 1e3) / 1e12
         out.append({"kernel": f"{ROLLOUT_KERNEL[dyn]}_batch<{g['dim']}>", "dyn": dyn,
                     "dim": g["dim"], "block": g["block"], "chunk": g["chunk"],
+                    "samples_per_thread": g["samples"],
                     "instances": g["instances"],
                     "rollout_steps": g["steps"], "flops_per_launch": fl,
                     "duration_us": g["ms"] * 1e3, "achieved_tflops": achieved,

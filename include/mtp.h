@@ -337,11 +337,12 @@ mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, f
  * 64 or 128) times the horizon chunk of the staged control loads (0: direct
  * loads; 4 or 8 steps of every candidate's controls copied at once into
  * shared memory by bulk copies, when every member's rows allow it: 16-byte
- * aligned, H * n a multiple of 4, one model per candidate).  The legged group
- * keeps its fixed tile.  Writes (dynamics, dimension, block, chunk) to
- * tiles_out (4 * groups entries, may be NULL) and the number of groups to
- * n_groups.  Synchronous; overwrites the handles' cost buffers.  Results do
- * not depend on the tile. */
+ * aligned, H * n a multiple of 4, one model per candidate), and for point
+ * masses also two candidates per thread (64 per warp, direct loads).  The
+ * legged group keeps its fixed tile.  Writes (dynamics, dimension, block,
+ * chunk, candidates per thread) to tiles_out (5 * groups entries, may be
+ * NULL) and the number of groups to n_groups.  Synchronous; overwrites the
+ * handles' cost buffers.  Results do not depend on the tile. */
 mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_groups, void* stream);
 
 /* mtp_shift(h, k) of every instance of the batch in one launch. */
@@ -356,10 +357,10 @@ mtp_status mtp_batch_launches(const mtp_batch* b, int32_t iters, int32_t* launch
 /* Device time of each group's rollout launch (Alg. 2 rollout fused with the
  * cost, Eq. 2) run alone on `stream` with its current tile, averaged over
  * `reps` launches timed with CUDA events: ms_out[g] (may be NULL).
- * info_out (7 per group, may be NULL): dynamics, dimension (point-mass axes
+ * info_out (8 per group, may be NULL): dynamics, dimension (point-mass axes
  * or links), candidates per block, instances, candidates (sum of B), rollout
- * steps (sum of B * H) and the horizon chunk of staged control loads (0:
- * direct loads).  *n_groups is the group count; max_groups
+ * steps (sum of B * H), the horizon chunk of staged control loads (0: direct
+ * loads) and candidates per thread.  *n_groups is the group count; max_groups
  * must be at least that when an output array is given.  Synchronous;
  * overwrites the handles' cost buffers. */
 mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, int32_t* info_out,

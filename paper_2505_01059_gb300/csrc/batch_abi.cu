@@ -3,6 +3,7 @@
 // iteration, rollouts grouped by (dynamics, control dimension) on their own
 // streams, and the rollout-tile autotuner.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -27,7 +28,9 @@ struct BatchGroup {
   int total_rows = 0;
   int block = 128;
   int chunk = 0;              // horizon chunk of staged control loads (0: direct loads)
+  int samples = 1;            // candidates per thread (point masses: 1 or 2, direct loads)
   bool stageable = false;     // every member's rows can be staged (see can_stage)
+  bool pairable = false;      // point masses with one model per candidate: 2 per thread allowed
   // this group's share of the generation, selection and update launches
   int z_blocks = 0, cand_blocks = 0, local_blocks = 0, upd_threads = 0;
   // members whose graph rows are contracted on the tensor cores (BF16 basis):
@@ -117,8 +120,9 @@ struct mtp_batch {
   BatchTables t;
   int count = 0;
   std::vector<BatchGroup> groups;
-  // (dyn, n) -> rollout tile chosen by the autotuner: (candidates per block, horizon chunk)
-  std::map<std::pair<int, int>, std::pair<int, int>> tuned;
+  // (dyn, n) -> rollout tile chosen by the autotuner: (candidates per block, horizon chunk,
+  // candidates per thread)
+  std::map<std::pair<int, int>, std::array<int, 3>> tuned;
   std::vector<int> x0_off, us_off;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t fork_ev = nullptr;
@@ -210,8 +214,9 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
       g.first = pos;
       g.model_first = n_dyn[dyn];
       auto it = b->tuned.find({dyn, n});
-      g.block = it != b->tuned.end() ? it->second.first : 128;
-      g.chunk = it != b->tuned.end() ? it->second.second : kDefaultChunk;
+      g.block = it != b->tuned.end() ? it->second[0] : 128;
+      g.chunk = it != b->tuned.end() ? it->second[1] : kDefaultChunk;
+      g.samples = it != b->tuned.end() ? it->second[2] : 1;
       b->groups.push_back(g);
     }
     ++b->groups.back().count;
@@ -312,13 +317,21 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
       if (g.dyn == MTP_DYN_POINTMASS) hv.d_pm[m] = pointmass_model(h->pr);
       else if (g.dyn == MTP_DYN_LEGGED) hv.d_lm[m] = legged_model(h->pr);
       else hv.d_cm[m] = chain_model(h->pr);
-      row[j + 1] = row[j] + ((h->dm.B + 31) / 32) * 32;
+      // whole warps per instance; point masses whole pairs of warps (two
+      // candidates per thread take rows 32 apart)
+      const int pad = g.dyn == MTP_DYN_POINTMASS ? 64 : 32;
+      row[j + 1] = row[j] + ((h->dm.B + pad - 1) / pad) * pad;
     }
     g.total_rows = row[g.count];
     g.stageable = g.dyn != MTP_DYN_LEGGED;
     for (int j = 0; j < g.count; ++j)
       g.stageable = g.stageable && can_stage(hv.d_ra[g.first + j], group_key_n(handles[order[g.first + j]]));
     if (!g.stageable) g.chunk = 0;
+    g.pairable = g.dyn == MTP_DYN_POINTMASS;
+    for (int j = 0; j < g.count; ++j)
+      g.pairable = g.pairable && hv.d_ra[g.first + j].dr_mode != MTP_DR_SHARED;
+    if (!g.pairable) g.samples = 1;
+    if (g.samples == 2) g.chunk = 0;
     rs += g.count + 1;
   }
   // packing of x0 and u*, in the caller's order
@@ -351,14 +364,17 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
   return cudaSuccess;
 }
 
-cudaError_t launch_group(const mtp_batch* b, const BatchGroup& g, int block, int chunk, cudaStream_t s) {
+cudaError_t launch_group(const mtp_batch* b, const BatchGroup& g, int block, int chunk, int samples,
+                         cudaStream_t s) {
   const BatchTables& t = b->t;
   const RolloutArgs* ra = t.d_ra + g.first;
   const int* rs = t.d_row_start + g.rows_first;
   if (!g.stageable) chunk = 0;
+  if (!g.pairable) samples = 1;
+  if (samples == 2) chunk = 0;
   if (g.dyn == MTP_DYN_POINTMASS)
     return launch_rollout_pointmass_batch(ra, t.d_pm + g.model_first, rs, g.count, g.total_rows, g.n,
-                                          block, chunk, s);
+                                          block, chunk, samples, s);
   if (g.dyn == MTP_DYN_LEGGED)  // fixed 64-thread blocks (shared-memory staging)
     return launch_rollout_legged_batch(ra, t.d_lm + g.model_first, rs, g.count, g.total_rows, g.n, s);
   return launch_rollout_chain_batch(ra, t.d_cm + g.model_first, rs, g.count, g.total_rows, g.n, block,
@@ -387,7 +403,7 @@ cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
                                      g.tc_tiles, gs)))
       return e;
     if ((e = launch_local_batch(t.d_cand + f, t.d_local_start + f, g.count, g.local_blocks, gs))) return e;
-    if ((e = launch_group(b, g, g.block, g.chunk, gs))) return e;
+    if ((e = launch_group(b, g, g.block, g.chunk, g.samples, gs))) return e;
     if ((e = launch_select_batch(t.d_sel + f, g.count, g.sel_smem, gs))) return e;
     if ((e = launch_update_batch(t.d_upd + f, t.d_warp_start + f, g.count, g.upd_threads, gs))) return e;
     if ((e = cudaEventRecord(b->group_done[gi], gs))) return e;
@@ -562,34 +578,41 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
   cudaError_t e = cudaSuccess;
+  // tiles: (candidates per block, horizon chunk, candidates per thread)
+  struct Tile {
+    int block, chunk, samples;
+  };
+  std::vector<Tile> tiles;
+  for (int chunk : chunks)
+    for (int block : blocks) tiles.push_back({block, chunk, 1});
+  for (int block : blocks) tiles.push_back({block, 0, 2});
   for (auto& g : b->groups) {
     if (g.dyn == MTP_DYN_LEGGED) continue;  // fixed tile
     float best = 1e30f;
-    int best_block = g.block, best_chunk = g.chunk;
-    for (int chunk : chunks) {
-      if (chunk && !g.stageable) continue;
-      if (chunk == 8 && g.dyn == MTP_DYN_CHAIN) continue;
-      for (int block : blocks) {
-        float ms_min = 1e30f;
-        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-          cudaEventRecord(t0, b->cap_stream);
-          e = launch_group(b, g, block, chunk, b->cap_stream);
-          cudaEventRecord(t1, b->cap_stream);
-          cudaEventSynchronize(t1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, t0, t1);
-          ms_min = std::min(ms_min, ms);
-        }
-        if (ms_min < best) {
-          best = ms_min;
-          best_block = block;
-          best_chunk = chunk;
-        }
+    Tile best_tile{g.block, g.chunk, g.samples};
+    for (const Tile& tl : tiles) {
+      if (tl.chunk && !g.stageable) continue;
+      if (tl.chunk == 8 && g.dyn == MTP_DYN_CHAIN) continue;
+      if (tl.samples == 2 && !g.pairable) continue;
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(t0, b->cap_stream);
+        e = launch_group(b, g, tl.block, tl.chunk, tl.samples, b->cap_stream);
+        cudaEventRecord(t1, b->cap_stream);
+        cudaEventSynchronize(t1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        ms_min = std::min(ms_min, ms);
+      }
+      if (ms_min < best) {
+        best = ms_min;
+        best_tile = tl;
       }
     }
-    g.block = best_block;
-    g.chunk = best_chunk;
-    b->tuned[{g.dyn, g.n}] = {best_block, best_chunk};
+    g.block = best_tile.block;
+    g.chunk = best_tile.chunk;
+    g.samples = best_tile.samples;
+    b->tuned[{g.dyn, g.n}] = {g.block, g.chunk, g.samples};
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
@@ -599,10 +622,11 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
   if (n_groups) *n_groups = (int32_t)b->groups.size();
   if (tiles_out)
     for (size_t i = 0; i < b->groups.size(); ++i) {
-      tiles_out[4 * i + 0] = b->groups[i].dyn;
-      tiles_out[4 * i + 1] = b->groups[i].n;
-      tiles_out[4 * i + 2] = b->groups[i].block;
-      tiles_out[4 * i + 3] = b->groups[i].chunk;
+      tiles_out[5 * i + 0] = b->groups[i].dyn;
+      tiles_out[5 * i + 1] = b->groups[i].n;
+      tiles_out[5 * i + 2] = b->groups[i].block;
+      tiles_out[5 * i + 3] = b->groups[i].chunk;
+      tiles_out[5 * i + 4] = b->groups[i].samples;
     }
   return MTP_OK;
 }
@@ -637,7 +661,7 @@ mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, i
     double sum = 0.0;
     for (int rep = 0; rep < reps && e == cudaSuccess; ++rep) {
       if ((e = cudaEventRecord(t0, s))) break;
-      if ((e = launch_group(b, g, g.block, g.chunk, s))) break;
+      if ((e = launch_group(b, g, g.block, g.chunk, g.samples, s))) break;
       if ((e = cudaEventRecord(t1, s))) break;
       if ((e = cudaEventSynchronize(t1))) break;
       float ms = 0.f;
@@ -652,7 +676,7 @@ mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, i
         rows += h->dm.B;
         steps += (long long)h->dm.B * h->dm.H;
       }
-      int32_t* o = info_out + 7 * gi;
+      int32_t* o = info_out + 8 * gi;
       o[0] = g.dyn;
       o[1] = g.n;
       o[2] = g.block;
@@ -660,6 +684,7 @@ mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, i
       o[4] = (int32_t)rows;
       o[5] = (int32_t)std::min<long long>(steps, 0x7fffffff);
       o[6] = g.stageable ? g.chunk : 0;
+      o[7] = g.pairable ? g.samples : 1;
     }
   }
   cudaEventDestroy(t0);

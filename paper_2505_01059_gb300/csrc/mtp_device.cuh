@@ -293,7 +293,8 @@ cudaError_t launch_candidates_batch(const CandArgs* d_args, const int* d_block_s
                                     int total_blocks, size_t smem, cudaStream_t s);
 cudaError_t launch_rollout_pointmass_batch(const RolloutArgs* d_ra, const PointMassModel* d_pm,
                                            const int* d_row_start, int count, int total_rows,
-                                           int k, int block, int chunk, cudaStream_t s);
+                                           int k, int block, int chunk, int samples,
+                                           cudaStream_t s);
 cudaError_t launch_rollout_chain_batch(const RolloutArgs* d_ra, const ChainModel* d_cm,
                                        const int* d_row_start, int count, int total_rows,
                                        int links, int block, int chunk, cudaStream_t s);

@@ -158,6 +158,70 @@ __device__ __forceinline__ void rollout_pm_body(const RolloutArgs& a, const Poin
 // ---------------------------------------------------------------------------
 // Planar serial chain under joint torques.
 // ---------------------------------------------------------------------------
+// Two candidates per thread (rows r[0] and r[1] of one instance, 32 rows
+// apart), direct loads one step ahead, one model: the two chains of
+// dependent instructions interleave, which the point-mass step needs (its
+// warps otherwise stall on fixed-latency dependencies most of the time).
+// Same arithmetic per candidate as rollout_pm_body, so the same bits.  A
+// candidate without a row (live false) reads the instance's first row and
+// writes nothing.  One model per candidate (no shared-model averaging).
+template <int K>
+__device__ __forceinline__ void rollout_pm_pair(const RolloutArgs& a, const PointMassModel& pm,
+                                                const int (&r)[2], const bool (&live)[2]) {
+  constexpr int S = 2;
+  const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
+  const float dt = a.dt;
+  const int H = a.H;
+  const float* Ub[S];
+  float gain[S][K], p[S][K], v[S][K];
+  KahanSum J[S];
+#pragma unroll
+  for (int c = 0; c < S; ++c) {
+    Ub[c] = a.U + (size_t)(live[c] ? r[c] : 0) * H * K;
+    dr_scales<K>(a, iter, (uint32_t)(a.row0 + r[c]), gain[c]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      gain[c][k] *= dt;
+      p[c][k] = a.x0[k];
+      v[c][k] = a.x0[K + k];
+    }
+  }
+  float ub[S][K];
+#pragma unroll
+  for (int c = 0; c < S; ++c)
+#pragma unroll
+    for (int k = 0; k < K; ++k) ub[c][k] = __ldg(Ub[c] + k);
+  for (int t = 0; t < H; ++t) {
+    const int tn = min(t + 1, H - 1);
+#pragma unroll
+    for (int c = 0; c < S; ++c) {
+      float u[K];
+      float uu = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        u[k] = ub[c][k];
+        ub[c][k] = __ldg(Ub[c] + tn * K + k);
+        uu = fmaf(u[k], u[k], uu);
+      }
+      J[c].add(fmaf(pm.w_ctrl, uu, pm_state_cost<K, false>(pm, p[c])), a.kahan);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        v[c][k] = fmaf(gain[c][k], u[k], v[c][k]);
+        p[c][k] = fmaf(dt, v[c][k], p[c][k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < S; ++c) {
+    J[c].add(pm.w_term * pm_state_cost<K, false>(pm, p[c]), a.kahan);
+    if (live[c]) {
+      float cst = J[c].s;
+      if (!isfinite(cst)) cst = __int_as_float(0x7f800000);
+      a.cost[r[c]] = cst;
+    }
+  }
+}
+
 template <int NL>
 __device__ __forceinline__ void chain_tip(const float (&len)[NL], const float (&c)[NL],
                                           const float (&s)[NL], float& x, float& y) {
@@ -409,6 +473,34 @@ __global__ void __launch_bounds__(kThreads) k_rollout_pm_batch(const RolloutArgs
             a.H);
     rollout_pm_body<K, kPrefetchBatch, false, T>(a, m, r, live, &st);
   }
+}
+
+// Batched point masses, two candidates per thread: instances' rows are
+// padded to 64, and thread g of the launch takes padded rows 64 (g / 32) +
+// (g % 32) and that + 32, which share an instance.
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_rollout_pm_batch2(const RolloutArgs* __restrict__ ra,
+                                                                const PointMassModel* __restrict__ pm,
+                                                                const int* __restrict__ row_start,
+                                                                int count) {
+  __shared__ PointMassModel models[kThreads / 32];
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = (g >> 5) * 64 + (g & 31);
+  if (r0 >= __ldg(row_start + count)) return;  // whole warps: the total is padded to 64
+  const int i = batch_instance(row_start, count, r0);
+  PointMassModel& m = models[threadIdx.x >> 5];
+  {
+    const int* src = reinterpret_cast<const int*>(pm + i);
+    int* dst = reinterpret_cast<int*>(&m);
+    for (int w = threadIdx.x & 31; w < (int)(sizeof(PointMassModel) / sizeof(int)); w += 32)
+      dst[w] = __ldg(src + w);
+    __syncwarp();
+  }
+  const RolloutArgs a = ra[i];
+  const int r[2] = {r0 - __ldg(row_start + i), r0 - __ldg(row_start + i) + 32};
+  const bool live[2] = {r[0] < a.rows, r[1] < a.rows};
+  if (!live[0] && !live[1]) return;
+  rollout_pm_pair<K>(a, m, r, live);
 }
 
 template <int NL, int T>

@@ -18,15 +18,20 @@ cudaError_t pm_batch_launch(const RolloutArgs* ra, const PointMassModel* pm, con
 
 template <int K>
 cudaError_t pm_batch_dispatch(const RolloutArgs* ra, const PointMassModel* pm, const int* row_start,
-                              int count, int total_rows, int k, int block, int chunk,
+                              int count, int total_rows, int k, int block, int chunk, int samples,
                               cudaStream_t s) {
   if constexpr (K <= kMaxPmAxes) {
     if (k == K) {
+      if (samples == 2) {
+        const int threads = total_rows / 2;  // rows are padded to 64 per instance
+        k_rollout_pm_batch2<K><<<(threads + block - 1) / block, block, 0, s>>>(ra, pm, row_start, count);
+        return cudaGetLastError();
+      }
       if (chunk == 8) return pm_batch_launch<K, 8>(ra, pm, row_start, count, total_rows, block, s);
       if (chunk == 4) return pm_batch_launch<K, 4>(ra, pm, row_start, count, total_rows, block, s);
       return pm_batch_launch<K, 0>(ra, pm, row_start, count, total_rows, block, s);
     }
-    return pm_batch_dispatch<K + 1>(ra, pm, row_start, count, total_rows, k, block, chunk, s);
+    return pm_batch_dispatch<K + 1>(ra, pm, row_start, count, total_rows, k, block, chunk, samples, s);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -53,9 +58,9 @@ cudaError_t init_rollout_pm_batch_attributes() { return pm_batch_attributes<1>()
 
 cudaError_t launch_rollout_pointmass_batch(const RolloutArgs* d_ra, const PointMassModel* d_pm,
                                            const int* d_row_start, int count, int total_rows,
-                                           int k, int block, int chunk, cudaStream_t s) {
+                                           int k, int block, int chunk, int samples, cudaStream_t s) {
   if (total_rows <= 0) return cudaSuccess;
-  return pm_batch_dispatch<1>(d_ra, d_pm, d_row_start, count, total_rows, k, block, chunk, s);
+  return pm_batch_dispatch<1>(d_ra, d_pm, d_row_start, count, total_rows, k, block, chunk, samples, s);
 }
 
 }  // namespace mtp

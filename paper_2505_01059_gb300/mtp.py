@@ -597,13 +597,13 @@ def mtp_batch_plan_step(b: Batch, x0, iters: int, ustar, stream=None):
 
 
 def mtp_batch_autotune(b: Batch, stream=None):
-    """Returns [(dyn, dim, block, chunk), ...] per rollout group."""
+    """Returns [(dyn, dim, block, chunk, samples_per_thread), ...] per rollout group."""
     groups = len(b.handles)
-    out = (C.c_int32 * (4 * groups))()
+    out = (C.c_int32 * (5 * groups))()
     ng = C.c_int32()
     _check(load_library().mtp_batch_autotune(b.ptr, C.addressof(out), C.addressof(ng),
                                              _stream(stream)))
-    return [tuple(out[4 * i + k] for k in range(4)) for i in range(ng.value)]
+    return [tuple(out[5 * i + k] for k in range(5)) for i in range(ng.value)]
 
 
 def mtp_batch_launches(b: Batch, iters: int = 1) -> int:
@@ -618,13 +618,13 @@ def mtp_batch_rollout_times(b: Batch, reps: int = 3, stream=None):
     dim, block, instances, candidates, steps and ms (average device time)."""
     groups = max(1, len(b.handles))
     ms = (C.c_double * groups)()
-    info = (C.c_int32 * (7 * groups))()
+    info = (C.c_int32 * (8 * groups))()
     ng = C.c_int32()
     _check(load_library().mtp_batch_rollout_times(b.ptr, int(reps), C.addressof(ms),
                                                   C.addressof(info), groups, C.addressof(ng),
                                                   _stream(stream)))
-    keys = ("dyn", "dim", "block", "instances", "candidates", "steps", "chunk")
-    return [dict(zip(keys, (int(info[7 * g + k]) for k in range(7))), ms=float(ms[g]))
+    keys = ("dyn", "dim", "block", "instances", "candidates", "steps", "chunk", "samples")
+    return [dict(zip(keys, (int(info[8 * g + k]) for k in range(8))), ms=float(ms[g]))
             for g in range(ng.value)]
 
 

@@ -54,7 +54,8 @@ def test_batch_matches_each_instance_alone(mtp, tune):
     b = mtp.mtp_batch_create(handles)
     if tune:
         tiles = mtp.mtp_batch_autotune(b)
-        assert all(blk in (32, 64, 128) and chunk in (0, 4, 8) for _, _, blk, chunk in tiles)
+        assert all(blk in (32, 64, 128) and chunk in (0, 4, 8) and spt in (1, 2)
+                   for _, _, blk, chunk, spt in tiles)
     x0 = torch.tensor(np.concatenate(x0s), device=DEV)
     us = torch.empty(b.ustar_offset[-1], device=DEV)
     mtp.mtp_batch_plan_step(b, x0, 1, us)
