@@ -4,19 +4,23 @@
 //
 // The graph rows of an iteration are U[b, t, i] = sum_m B[t, m] C[b, m, i]
 // (Def. 2 with the basis B_p sampled at the H evaluation times and the
-// waypoints C of path b, Alg. 1).  Seen as one GEMM, D[t, (b, i)] =
-// sum_m A[t, m] B[m, (b, i)] with A the (H x M) basis table and B the
-// gathered waypoints, K = M.  A tile is one 128-step slice of the horizon
-// for up to kPaths paths; each CTA (one warpgroup) loops over tiles: it
-// draws the paths' layer indices (Alg. 1), gathers their waypoints from the
-// iteration's graph Z, rounds them to bfloat16 into the B operand (K-major,
-// 16 columns per path, the columns past n zero), and one thread issues
-// tcgen05.mma.cta_group::1.kind::f16 (BF16 x BF16 -> FP32, M = 128 steps,
-// N = 128, K = 16 per instruction) into tensor memory.  The products of two
-// bfloat16 values are exact in FP32; the sums are FP32.
-// The epilogue reads each path's columns back with tcgen05.ld, clamps them
-// to the control box and writes them through a per-warp shared-memory
-// transpose as contiguous, coalesced rows of U.
+// waypoints C of path b, Alg. 1).  Seen as one GEMM,
+// D[(b, i), t] = sum_m W[(b, i), m] B[t, m] with W the gathered waypoints
+// (one row per path and control dimension) and B the (H x M) basis table,
+// K = M.  A tile is up to 128 (path, dimension) rows by one 128-step slice
+// of the horizon: warp w's 32 accumulator lanes hold floor(32 / n) whole
+// paths (rows 32 w + n p + i), so a path never straddles two warps and the
+// rows are dense for any n.  Each CTA (one warpgroup) loops over tiles: it
+// draws the paths' layer indices (Alg. 1, four layers per generator call),
+// copies their waypoints, already rounded to bfloat16, from the instance's
+// graph (staged in shared memory once per instance) into the A operand, and
+// one thread issues tcgen05.mma.cta_group::1.kind::f16 (BF16 x BF16 -> FP32,
+// M = 128 rows, N = 128 steps, K = 16 per instruction) into tensor memory.
+// The products of two bfloat16 values are exact in FP32; the sums are FP32.
+// The epilogue reads 16 steps of its row at a time with tcgen05.ld, clamps
+// them to the control box and writes them through a per-warp shared-memory
+// transpose: for each of the warp's paths, 16 steps x n controls are one
+// contiguous block of U, stored with 16-byte vector stores.
 //
 // Shared-memory operands use the canonical K-major layout without swizzle:
 // 8-row x 16-byte core matrices, the two (or more) core matrices of a row
@@ -35,20 +39,19 @@ namespace mtp {
 namespace {
 
 constexpr int kTcThreads = 128;
-constexpr int kPaths = 8;            // paths per tile, 16 accumulator columns each
-constexpr int kNTile = kPaths * 16;  // MMA N
 constexpr int kMaxK = 64;            // layers (M) padded to a multiple of 16
 constexpr int kMaxSlices = 2;        // 128-step horizon slices (H <= 256)
+constexpr int kZsMax = 12288;        // graph elements (M N n) staged in shared memory
 constexpr uint32_t kTmemCols = 128;
 constexpr size_t kMinSmem = 50 * 1024;  // at most four CTAs per SM (their TMEM fits)
 constexpr int kBatchTilesPerCta = 8;
 
 struct TcSmem {
-  __nv_bfloat16 A[128 * kMaxK];              // basis of one slice, K-major canonical layout
-  __nv_bfloat16 B[kNTile * kMaxK];           // waypoints, K-major canonical layout
-  // per warp, two buffers of one path's 32 rows x n controls in the order
-  // they take in U (a contiguous block there), written out by bulk copies
-  float stage[kTcThreads / 32][2][32 * 16];
+  __nv_bfloat16 W[128 * kMaxK];   // A operand: waypoints, row 32 w + n p + i, K-major
+  __nv_bfloat16 Bs[128 * kMaxK];  // B operand: basis of one slice, row t, K-major
+  __nv_bfloat16 Zs[kZsMax];       // the instance's graph in bfloat16, when it fits
+  // per warp: 16 steps of its paths' rows, path by path in the order of U
+  float stage[kTcThreads / 32][32 * 16];
   float lo[MTP_MAX_CTRL], hi[MTP_MAX_CTRL];
   uint64_t mma_bar;
   uint32_t tmem_base;
@@ -80,6 +83,15 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// Paths per warp and per tile for n control dimensions (n <= 16).
+__host__ __device__ constexpr int tc_paths_per_warp(int n) { return 32 / n; }
+__host__ __device__ constexpr int tc_paths_per_tile(int n) {
+  return (kTcThreads / 32) * tc_paths_per_warp(n);
+}
+
+// Waits for the MMA's commit, bounded by 2 s of global time; backs off
+// between polls so that the waiting warps leave the issue slots to the
+// co-resident CTAs' epilogues.
 __device__ __forceinline__ bool mbar_wait_bounded_tc(uint64_t* bar, uint32_t parity) {
   const unsigned addr = smem_u32(bar);
   uint64_t t_start = 0;
@@ -97,14 +109,15 @@ __device__ __forceinline__ bool mbar_wait_bounded_tc(uint64_t* bar, uint32_t par
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
     if (spin == 0) t_start = now;
     else if (now - t_start > 2000000000ull) return false;
+    if (spin >= 4) __nanosleep(64);
   }
 }
 
-// The basis of one horizon slice s as the A operand:
-// A[r][k] = basis[(128 s + r) * M + k], zero past H and past M.
+// The basis of one horizon slice s as the B operand:
+// Bs[r][k] = basis[(128 s + r) * M + k], zero past H and past M.
 __device__ void load_basis(TcSmem& S, const CandArgs& a, int K, int s) {
   const int H = a.dm.H, M = a.dm.M;
-  unsigned char* base = reinterpret_cast<unsigned char*>(&S.A[0]);
+  unsigned char* base = reinterpret_cast<unsigned char*>(&S.Bs[0]);
   for (int e = threadIdx.x; e < 128 * K; e += blockDim.x) {
     const int r = e / K, k = e - r * K;
     const int t = 128 * s + r;
@@ -113,41 +126,65 @@ __device__ void load_basis(TcSmem& S, const CandArgs& a, int K, int s) {
   }
 }
 
-// Path group g of one instance's graph rows, horizon slice s (the A operand
+__device__ __forceinline__ bool graph_staged(const CandArgs& a) {
+  return a.C_in == nullptr && a.dm.M * a.dm.N * a.dm.n <= kZsMax;
+}
+
+// Path group g of one instance's graph rows, horizon slice s (the B operand
 // holds that slice's basis).  Returns false when the bounded wait for the
 // MMA gave up.
-__device__ bool tc_tile(TcSmem& S, const CandArgs& a, int g, int s, int K, uint32_t iter,
+__device__ __forceinline__ bool tc_tile(TcSmem& S, const CandArgs& a, int g, int s, int K, uint32_t iter,
                         uint32_t& phase) {
   const Dims dm = a.dm;
   const int H = dm.H, n = dm.n, M = dm.M, N = dm.N;
-  const int b0 = g * kPaths;
-  const int nb = min(kPaths, a.graph_rows - b0);
-  unsigned char* Bb = reinterpret_cast<unsigned char*>(S.B);
-  // Alg. 1 for the tile's paths and the gather of their waypoints, rounded
-  // to bfloat16, into the B operand: column 16 p + i, row m.
-  for (int e = threadIdx.x; e < nb * M; e += blockDim.x) {
-    const int p = e / M, m = e - p * M;
-    const float* z;
-    if (a.C_in) {
-      z = a.C_in + ((size_t)(b0 + p) * M + m) * n;
-    } else {
-      const uint4 r = philox(make_uint4((uint32_t)(b0 + p), (uint32_t)(m >> 2), iter, kTagPath), a.key);
-      const int j = index_of(pick(r, (uint32_t)(m & 3)), (uint32_t)N);
-      z = a.Z_global + ((size_t)m * N + j) * n;
+  const int ppw = tc_paths_per_warp(n);
+  const int b0 = g * tc_paths_per_tile(n);
+  const int nb = min(tc_paths_per_tile(n), a.graph_rows - b0);
+  unsigned char* Wb = reinterpret_cast<unsigned char*>(S.W);
+  const bool staged = graph_staged(a);
+  // Alg. 1 for the tile's paths (one generator call per four layers) and
+  // the copy of their waypoints, in bfloat16, into the A operand: row
+  // 32 (q / ppw) + n (q % ppw) + i for the tile's path q, column m.
+  const int quads = (M + 3) >> 2;
+  for (int e = threadIdx.x; e < nb * quads; e += blockDim.x) {
+    const int q = e / quads, mq = e - q * quads;
+    const int row0 = 32 * (q / ppw) + n * (q % ppw);
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (a.C_in == nullptr)
+      r = philox(make_uint4((uint32_t)(b0 + q), (uint32_t)mq, iter, kTagPath), a.key);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int m = 4 * mq + w;
+      if (m < M) {
+        if (a.C_in) {
+          const float* z = a.C_in + ((size_t)(b0 + q) * M + m) * n;
+          for (int i = 0; i < n; ++i)
+            *reinterpret_cast<__nv_bfloat16*>(Wb + kmajor_offset(row0 + i, m, K)) = __float2bfloat16_rn(z[i]);
+        } else {
+          const int j = index_of(pick(r, (uint32_t)w), (uint32_t)N);
+          if (staged) {
+            const __nv_bfloat16* z = S.Zs + (m * N + j) * n;
+            for (int i = 0; i < n; ++i)
+              *reinterpret_cast<__nv_bfloat16*>(Wb + kmajor_offset(row0 + i, m, K)) = z[i];
+          } else {
+            const float* z = a.Z_global + ((size_t)m * N + j) * n;
+            for (int i = 0; i < n; ++i)
+              *reinterpret_cast<__nv_bfloat16*>(Wb + kmajor_offset(row0 + i, m, K)) = __float2bfloat16_rn(z[i]);
+          }
+        }
+      }
     }
-    for (int i = 0; i < n; ++i)
-      *reinterpret_cast<__nv_bfloat16*>(Bb + kmajor_offset(16 * p + i, m, K)) = __float2bfloat16_rn(z[i]);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if (threadIdx.x == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t idesc = idesc_bf16(128, kNTile);
+    const uint32_t idesc = idesc_bf16(128, 128);
     const uint32_t sbo = 16u * (uint32_t)K;
     const uint32_t d_tmem = S.tmem_base;
     for (int ks = 0; ks < K / 16; ++ks) {
-      const uint64_t ad = smem_desc(smem_u32(&S.A[0]) + 256u * ks, 128u, sbo);
-      const uint64_t bd = smem_desc(smem_u32(&S.B[0]) + 256u * ks, 128u, sbo);
+      const uint64_t ad = smem_desc(smem_u32(&S.W[0]) + 256u * ks, 128u, sbo);
+      const uint64_t bd = smem_desc(smem_u32(&S.Bs[0]) + 256u * ks, 128u, sbo);
       const uint32_t acc = ks > 0 ? 1u : 0u;
       asm volatile(
           "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -163,77 +200,72 @@ __device__ bool tc_tile(TcSmem& S, const CandArgs& a, int g, int s, int K, uint3
   phase ^= 1u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!__syncthreads_and(ok)) return false;
-  // epilogue: warp w reads accumulator lanes 32 w .. 32 w + 31 (steps
-  // t0 .. t0 + 31 of each slice) path by path, clamps them to the box (kept
-  // in registers) and writes the path's rows t0 .. t0 + 31, a contiguous
-  // block of U, from shared memory: one bulk copy when its start and length
-  // are whole 16-byte units, else coalesced stores
+  // epilogue: warp w reads accumulator lanes 32 w .. 32 w + 31, 16 steps
+  // (columns) at a time; lane l holds row (path l / n, dimension l % n) of
+  // the warp's paths.  Clamped values go to the warp's staging area in the
+  // order of U (path-major, then step, then dimension), from which each
+  // path's 16 n contiguous floats of U are written.
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float lo[16], hi[16];
+  const int p = lane / n, i = lane - p * n;
+  const int wb0 = b0 + w * ppw;                          // the warp's first path
+  const int wpaths = max(0, min(ppw, a.graph_rows - wb0));  // its paths in this tile
+  const float lo = i < n ? S.lo[i] : 0.f, hi = i < n ? S.hi[i] : 0.f;
+  const bool vec = ((reinterpret_cast<uintptr_t>(a.U_graph) & 15) == 0) && ((H * n) & 3) == 0;
+  const int t_end = min(128 * (s + 1), H);
+  float* st = S.stage[w];
+  for (int t0 = 128 * s; t0 < t_end; t0 += 16) {
+    const uint32_t taddr = S.tmem_base + ((uint32_t)(32 * w) << 16) + (uint32_t)(t0 - 128 * s);
+    uint32_t v[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (wpaths == 0) continue;
+    const int steps = min(16, H - t0);  // steps of this chunk inside the horizon
+    __syncwarp();                        // the previous chunk's reads of st are done
+    if (p < wpaths) {
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    lo[i] = i < n ? S.lo[i] : 0.f;
-    hi[i] = i < n ? S.hi[i] : 0.f;
-  }
-  const bool bulk_ok = ((reinterpret_cast<uintptr_t>(a.U_graph) & 15) == 0) && ((H * n) & 3) == 0;
-  int buf = 0;
-  {
-    const int t0 = 128 * s + 32 * w;
-    const int rows = min(32, H - t0);
-    for (int p = 0; p < nb; ++p) {
-      const uint32_t taddr = S.tmem_base + ((uint32_t)(32 * w) << 16) + (uint32_t)(16 * p);
-      uint32_t v[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-            "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (rows <= 0) continue;
-      float* st = S.stage[w][buf];
-      // the bulk copy that last read this buffer (two paths ago) must be done
-      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-      __syncwarp();
-#pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (i < n) st[lane * n + i] = clamp_box(__uint_as_float(v[i]), lo[i], hi[i]);
-      float* out = a.U_graph + ((size_t)(b0 + p) * H + t0) * n;
-      const int count = rows * n;
-      if (bulk_ok && (count & 3) == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) {
-          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(out),
-                       "r"(smem_u32(st)), "r"((uint32_t)(count * 4))
-                       : "memory");
-          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        }
-        buf ^= 1;
-      } else {
-        __syncwarp();
-        for (int e = lane; e < count; e += 32) out[e] = st[e];
-        __syncwarp();
+      for (int tt = 0; tt < 16; ++tt)
+        if (tt < steps) st[(p * 16 + tt) * n + i] = clamp_box(__uint_as_float(v[tt]), lo, hi);
+    }
+    __syncwarp();
+    const int piece = steps * n;  // floats of one path in this chunk
+    if (vec && (piece & 3) == 0) {
+      const int q4 = piece >> 2;
+      for (int e = lane; e < wpaths * q4; e += 32) {
+        const int pp = e / q4, o = e - pp * q4;
+        const float4 val = reinterpret_cast<const float4*>(st + pp * 16 * n)[o];
+        reinterpret_cast<float4*>(a.U_graph + ((size_t)(wb0 + pp) * H + t0) * n)[o] = val;
+      }
+    } else {
+      for (int e = lane; e < wpaths * piece; e += 32) {
+        const int pp = e / piece, o = e - pp * piece;
+        a.U_graph[((size_t)(wb0 + pp) * H + t0) * n + o] = st[pp * 16 * n + o];
       }
     }
   }
-  // the warp's bulk copies have read their sources before the next tile
-  // refills the buffers
-  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
   __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   return true;
 }
 
-// Per-CTA set-up for one instance: box and a zeroed B operand.
+// Per-CTA set-up for one instance: box, a zeroed A operand (its columns
+// past M stay zero) and the instance's graph in bfloat16 (when it fits).
 __device__ void tc_instance_setup(TcSmem& S, const CandArgs& a) {
   for (int i = threadIdx.x; i < a.dm.n; i += blockDim.x) {
     S.lo[i] = a.umin[i];
     S.hi[i] = a.umax[i];
   }
-  uint32_t* Bw = reinterpret_cast<uint32_t*>(S.B);
-  for (int e = threadIdx.x; e < (int)(sizeof(S.B) / 4); e += blockDim.x) Bw[e] = 0u;
+  uint32_t* Ww = reinterpret_cast<uint32_t*>(S.W);
+  for (int e = threadIdx.x; e < (int)(sizeof(S.W) / 4); e += blockDim.x) Ww[e] = 0u;
+  if (graph_staged(a)) {
+    const int total = a.dm.M * a.dm.N * a.dm.n;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) S.Zs[e] = __float2bfloat16_rn(a.Z_global[e]);
+  }
   __syncthreads();
 }
 
@@ -280,7 +312,7 @@ __device__ __forceinline__ TcSmem& tc_smem() {
 __global__ void __launch_bounds__(kTcThreads) k_bspline_tc(const CandArgs a) {
   TcSmem& S = tc_smem();
   const int K = ((a.dm.M + 15) / 16) * 16;
-  const int groups = (a.graph_rows + kPaths - 1) / kPaths;
+  const int groups = (a.graph_rows + tc_paths_per_tile(a.dm.n) - 1) / tc_paths_per_tile(a.dm.n);
   const int tiles = groups * ((a.dm.H + 127) / 128);
   const uint32_t iter = (a.d_iter ? *a.d_iter : a.iter) + a.iter_offset;
   tc_begin(S);
@@ -336,7 +368,7 @@ __global__ void __launch_bounds__(kTcThreads) k_bspline_tc_batch(const CandArgs*
       tc_instance_setup(S, sa);
     }
     // the instance's tiles slice-major, as in the single-instance kernel
-    const int groups = (sa.graph_rows + kPaths - 1) / kPaths;
+    const int groups = (sa.graph_rows + tc_paths_per_tile(sa.dm.n) - 1) / tc_paths_per_tile(sa.dm.n);
     const int tile = g - tile_start[lo];
     const int s = tile / groups, pg = tile - s * groups;
     if (s != cur_s) {
@@ -350,6 +382,7 @@ __global__ void __launch_bounds__(kTcThreads) k_bspline_tc_batch(const CandArgs*
 }
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) > kMinSmem ? sizeof(TcSmem) : kMinSmem; }
+static_assert(sizeof(TcSmem) >= kMinSmem, "at most four CTAs per SM keep their TMEM allocations within 512 columns");
 
 }  // namespace
 
@@ -359,21 +392,32 @@ bool bspline_tc_eligible(const CandArgs& a) {
 }
 
 int bspline_tc_tiles(const CandArgs& a) {
-  return ((a.graph_rows + kPaths - 1) / kPaths) * ((a.dm.H + 127) / 128);
+  const int per = tc_paths_per_tile(a.dm.n);
+  return ((a.graph_rows + per - 1) / per) * ((a.dm.H + 127) / 128);
 }
+
+// CTAs of the contraction kernels resident on one SM (set with their
+// attributes; shared memory bounds it)
+static int g_tc_blocks_per_sm = 1;
 
 cudaError_t init_bspline_tc_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_bspline_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tc_smem_bytes());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_bspline_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes());
+  e = cudaFuncSetAttribute(k_bspline_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes());
+  if (e != cudaSuccess) return e;
+  int blocks = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bspline_tc_batch, kTcThreads, tc_smem_bytes());
+  if (e != cudaSuccess) return e;
+  g_tc_blocks_per_sm = std::max(1, std::min(blocks, 4));
+  return cudaSuccess;
 }
 
 cudaError_t launch_bspline_tc(const CandArgs& a, cudaStream_t s) {
   const int tiles = bspline_tc_tiles(a);
   if (tiles <= 0) return cudaSuccess;
-  const int grid = std::min(tiles, 4 * device_sms());
+  const int grid = std::min(tiles, g_tc_blocks_per_sm * device_sms());
   k_bspline_tc<<<grid, kTcThreads, tc_smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
@@ -384,7 +428,8 @@ cudaError_t launch_bspline_tc_batch(const CandArgs* d_args, const int* d_tile_st
   // at least kBatchTilesPerCta tiles per CTA: in a batch the launches of
   // other groups run beside this one, and each CTA's set-up (tensor memory,
   // operands) is paid once for its whole range
-  const int grid = std::min((total_tiles + kBatchTilesPerCta - 1) / kBatchTilesPerCta, 4 * device_sms());
+  const int grid = std::min((total_tiles + kBatchTilesPerCta - 1) / kBatchTilesPerCta,
+                            g_tc_blocks_per_sm * device_sms());
   k_bspline_tc_batch<<<grid, kTcThreads, tc_smem_bytes(), s>>>(d_args, d_tile_start, count);
   return cudaGetLastError();
 }

@@ -156,6 +156,36 @@ def test_interpolate_bf16_basis(mtp, p, M, H, n, P):
     mtp.mtp_destroy(h)
 
 
+@pytest.mark.parametrize("n,H,M,N,B,p", [
+    (1, 40, 4, 8, 1000, 3),      # 32 paths per warp; ragged last 16-step chunk
+    (5, 200, 13, 16, 700, 2),    # two horizon slices, the second ragged; K = 16
+    (7, 33, 20, 8, 300, 3),      # H n not a multiple of 4 (scalar stores); K = 32
+    (16, 256, 64, 32, 257, 3),   # two paths per warp; K = 64; graph too large to stage
+    (11, 64, 8, 64, 513, 1),     # paths of 11 rows, 2 per warp
+])
+def test_generate_bf16_graph_rows(mtp, n, H, M, N, B, p):
+    """Every candidate row of one BF16-basis iteration (graph rows on the
+    tensor cores, from the iteration's graph and Alg. 1 path draws) against
+    the oracle: graph rows to its BF16-operand mode up to FP32 summation,
+    local and mean rows as in FP32."""
+    spec = W.pointmass(k=n, M=M, N=N, H=H, B=B, E=1, beta=0.6, degree=p,
+                       u_min=[-2.0] * n, u_max=[3.0] * n, flags=0x4)
+    h = mtp.mtp_create(spec)
+    it = 3
+    U = torch.empty(B, H, n, device=DEV)
+    mtp.mtp_generate_candidates(h, it, U)
+    Ug = _np(U)
+    P = orc.num_graph_samples(spec["beta"], B)
+    L = B - P - 1
+    UG = np.clip(orc.interpolate(spec, orc.gather_C(spec, orc.graph_Z(spec, it),
+                                                    orc.path_indices(spec, it))), -2.0, 3.0)
+    assert np.abs(Ug[L:L + P] - UG).max() <= 2e-6 * np.abs(UG).max()
+    mu, sg = W.initial_distribution(spec)
+    ref = orc.stack_clamp(spec, orc.local_samples(spec, it, mu, sg), UG, mu)
+    assert np.abs(Ug - ref).max() <= 2e-5 * 5.0
+    mtp.mtp_destroy(h)
+
+
 def test_bf16_basis_plan_step_and_rejections(mtp):
     spec = W.pointmass(flags=0x4)
     h = mtp.mtp_create(spec)
