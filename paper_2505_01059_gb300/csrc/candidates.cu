@@ -78,12 +78,20 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
   const int n = dm.n;
   const int Hn = dm.H * n;
   const int G = (Hn + 3) >> 2;
-  const int rows = a.local_rows + ((MODE != kLocalNoise && a.U_mean) ? 1 : 0);  // + the mean row
+  // the arguments read once into registers: the loops' stores would
+  // otherwise make the compiler reload them (they may alias the arguments)
+  const int local_rows = a.local_rows;
+  float* __restrict__ const U_local = a.U_local;
+  float* __restrict__ const U_mean = a.U_mean;
+  const float* __restrict__ const mu = a.mu;
+  const float* __restrict__ const sigma = a.sigma;
+  const Key key = a.key;
+  const int rows = local_rows + ((MODE != kLocalNoise && U_mean) ? 1 : 0);  // + the mean row
   // whole 16-byte groups: one vector load of mu and sigma and one vector
   // store per generator call (rows of a 16-byte aligned tensor stay aligned)
   const bool vec = (Hn & 3) == 0 &&
-                   ((reinterpret_cast<uintptr_t>(a.U_local) | reinterpret_cast<uintptr_t>(a.mu) |
-                     reinterpret_cast<uintptr_t>(a.sigma)) & 15) == 0;
+                   ((reinterpret_cast<uintptr_t>(U_local) | reinterpret_cast<uintptr_t>(mu) |
+                     reinterpret_cast<uintptr_t>(sigma)) & 15) == 0;
   // threads [0, RS * QS): q-groups t % QS, t % QS + QS, ...; rows t / QS,
   // t / QS + RS, ... (QS = G when there are at least G threads)
   const int T = nlb * blockDim.x;
@@ -99,12 +107,12 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
       const int i = el % n;
       lo[w] = box_lo[i];
       hi[w] = box_hi[i];
-      mv[w] = el < Hn ? a.mu[el] : 0.f;
-      sv[w] = el < Hn ? a.sigma[el] : 0.f;
+      mv[w] = el < Hn ? mu[el] : 0.f;
+      sv[w] = el < Hn ? sigma[el] : 0.f;
     }
     for (int row = t / QS; row < rows; row += RS) {
-      if (row < a.local_rows) {
-        float* dst = a.U_local + (size_t)row * Hn;
+      if (row < local_rows) {
+        float* dst = U_local + (size_t)row * Hn;
         float eps[4];
         if constexpr (MODE == kLocalFinish) {
           if (vec) {
@@ -118,7 +126,7 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
             for (int w = 0; w < 4; ++w) eps[w] = (4 * q + w < Hn) ? dst[4 * q + w] : 0.f;
           }
         } else {
-          const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), a.key);
+          const uint4 r = philox(make_uint4((uint32_t)row, (uint32_t)q, iter, kTagLocal), key);
           box_muller(r.x, r.y, eps[0], eps[1]);
           box_muller(r.z, r.w, eps[2], eps[3]);
         }
@@ -137,7 +145,7 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           const int el = 4 * q + w;
-          if (el < Hn) a.U_mean[el] = clamp_box(mv[w], lo[w], hi[w]);
+          if (el < Hn) U_mean[el] = clamp_box(mv[w], lo[w], hi[w]);
         }
       }
     }
@@ -171,7 +179,7 @@ struct Int {
 // position advances by a fixed stride, so it is carried along instead of
 // divided out.
 template <class F>
-__device__ __forceinline__ void store_rows(const CandArgs& a, float* out, int total, const float* box_lo,
+__device__ __forceinline__ void store_rows(const CandArgs& a, float* __restrict__ out, int total, const float* box_lo,
                                            const float* box_hi, F f) {
   const int H = a.dm.H, n = a.dm.n, Hn = H * n;
   int e = threadIdx.x;
@@ -241,51 +249,56 @@ __device__ __forceinline__ void graph_paths_body(const CandArgs& a, const float*
   }
 
   if (a.interp == MTP_INTERP_AKIMA) {
-    // Eqs. 6-7 in three parallel passes over (path, dimension, knot):
-    // piece slopes m, knot slopes s, then piece coefficients (a, b, c, d).
+    // Eqs. 6-7, one thread per (path, dimension) row walking its knots in
+    // order: piece slopes m, knot slopes s, then piece coefficients
+    // (a, b, c, d).  The row's slopes are its own thread's, so the passes
+    // need no barrier between them (and no division of a flat index).
     const float inv_h = a.inv_h;
     const int K1 = M - 1;
     float* mslope = coef + (size_t)SPB * n * K1 * 4;  // (nb, n, M-1)
     float* kslope = mslope + (size_t)SPB * n * K1;    // (nb, n, M)
-    for (int e = threadIdx.x; e < nb * n * K1; e += blockDim.x) {
-      const int si = e / K1, k = e - si * K1;
-      const int sp = si / n, i = si - sp * n;
+    int sp = threadIdx.x / n;
+    const int i = threadIdx.x - sp * n;
+    const int rows_per_pass = blockDim.x / n;  // whole paths per pass of the block
+    for (; sp < nb && threadIdx.x < rows_per_pass * n; sp += rows_per_pass) {
+      const int si = sp * n + i;
       const float* z = C + sp * M * n + i;
-      mslope[e] = (z[(k + 1) * n] - z[k * n]) * inv_h;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * n * M; e += blockDim.x) {
-      const int si = e / M, k = e - si * M;
-      const float* m = mslope + si * K1;
-      kslope[e] = akima_knot_slope(k, M, [&](int j) { return m[j]; });
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * n * K1; e += blockDim.x) {
-      const int si = e / K1, k = e - si * K1;
-      const int sp = si / n, i = si - sp * n;
-      const float mk = mslope[e];
-      const float s_left = kslope[si * M + k], s_right = kslope[si * M + k + 1];
-      float* cf = coef + (size_t)e * 4;
-      cf[0] = C[(sp * M + k) * n + i];
-      cf[1] = s_left;
-      cf[2] = (3.f * mk - 2.f * s_left - s_right) * inv_h;
-      cf[3] = (s_left + s_right - 2.f * mk) * (inv_h * inv_h);
+      float* m = mslope + si * K1;
+      float* ks = kslope + si * M;
+      for (int k = 0; k < K1; ++k) m[k] = (z[(k + 1) * n] - z[k * n]) * inv_h;
+      for (int k = 0; k < M; ++k) ks[k] = akima_knot_slope(k, M, [&](int j) { return m[j]; });
+      for (int k = 0; k < K1; ++k) {
+        const float mk = m[k];
+        const float s_left = ks[k], s_right = ks[k + 1];
+        float* cf = coef + ((size_t)si * K1 + k) * 4;
+        cf[0] = z[k * n];
+        cf[1] = s_left;
+        cf[2] = (3.f * mk - 2.f * s_left - s_right) * inv_h;
+        cf[3] = (s_left + s_right - 2.f * mk) * (inv_h * inv_h);
+      }
     }
     __syncthreads();
   }
 
   // Interpolate and store rows b0 .. b0+nb-1 (coalesced over (t, i)),
   // with the interpolation kind (and the B-spline degree) fixed at compile
-  // time so the per-element sum is unrolled.
-  float* out = a.U_graph + (size_t)b0 * Hn;
+  // time so the per-element sum is unrolled.  The tables' addresses are
+  // read into registers first: the stores would otherwise make the compiler
+  // reload them from the arguments for every element.
+  float* __restrict__ const out = a.U_graph + (size_t)b0 * Hn;
+  const int32_t* __restrict__ const bfirst = a.bfirst;
+  const float* __restrict__ const basis = a.basis;
+  const int32_t* __restrict__ const seg = a.seg;
+  const float* __restrict__ const delta = a.delta;
+  const float inv_h_t = a.inv_h;
   const int total = nb * Hn;
   if (a.interp == MTP_INTERP_BSPLINE) {
     // Def. 2: sum over the (p+1)-wide non-zero window of basis row t.
     auto bspline = [&](auto D) {
       store_rows(a, out, total, box_lo, box_hi, [&](int sp, int t, int i) {
         constexpr int deg = decltype(D)::value;
-        const int f = a.bfirst[t];
-        const float* brow = a.basis + (size_t)t * M;
+        const int f = bfirst[t];
+        const float* brow = basis + (size_t)t * M;
         const float* zc = C + sp * M * n + i;
         float u = 0.f;
 #pragma unroll
@@ -308,15 +321,15 @@ __device__ __forceinline__ void graph_paths_body(const CandArgs& a, const float*
     }
   } else if (a.interp == MTP_INTERP_AKIMA) {
     store_rows(a, out, total, box_lo, box_hi, [&](int sp, int t, int i) {
-      const int k = a.seg[t];
-      const float dl = a.delta[t];
+      const int k = seg[t];
+      const float dl = delta[t];
       const float* cf = coef + ((size_t)(sp * n + i) * (M - 1) + k) * 4;
       return fmaf(fmaf(fmaf(cf[3], dl, cf[2]), dl, cf[1]), dl, cf[0]);
     });
   } else {
     store_rows(a, out, total, box_lo, box_hi, [&](int sp, int t, int i) {
-      const int k = a.seg[t];
-      const float w = fminf(a.delta[t] * a.inv_h, 1.f);
+      const int k = seg[t];
+      const float w = fminf(delta[t] * inv_h_t, 1.f);
       const float z0 = C[(sp * M + k) * n + i], z1 = C[(sp * M + k + 1) * n + i];
       return fmaf(w, z1 - z0, z0);
     });

@@ -172,12 +172,15 @@ inline bool can_stage(const RolloutArgs& a, int k) {
          ((uintptr_t)a.U % 16u) == 0 && ((long long)a.H * k) % 4 == 0;
 }
 
-struct PointMassModel {
+// The obstacle centres first and the struct 16-byte aligned: each centre
+// row starts on a 16-byte boundary, so a rollout reads it (from shared
+// memory in the batched kernel) with 16-byte vector loads.
+struct alignas(16) PointMassModel {
+  float obs_c[MTP_MAX_OBSTACLES][16];
   float target[16];
+  float obs_r[MTP_MAX_OBSTACLES];
   float w_target, w_obs, w_ctrl, w_term;
   int32_t n_obs;
-  float obs_c[MTP_MAX_OBSTACLES][16];
-  float obs_r[MTP_MAX_OBSTACLES];
 };
 
 struct ChainModel {
