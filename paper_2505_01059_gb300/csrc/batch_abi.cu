@@ -38,12 +38,14 @@ struct BatchGroup {
   // their tile numbering at tc_start_first of d_tc_start
   int tc_first = 0, tc_count = 0, tc_start_first = 0, tc_tiles = 0;
   size_t cand_smem = 0, sel_smem = 0;
+  double est = 0.0;  // expected rollout time (ms): sets the groups' launch order
 };
 
 constexpr int kMaxGroups = 64;
 // Horizon chunk of staged control loads before the autotuner has run.
 constexpr int kDefaultChunk = 4;
 constexpr size_t kBatchGraphSmem = 40 * 1024;  // four graph blocks per SM
+constexpr int kLocalRowsPerThreadBatch = 16;
 
 // Device tables of a batch, packed into one device block that is refilled in
 // place from a pinned host mirror with one copy.  The layout depends on the
@@ -123,6 +125,10 @@ struct mtp_batch {
   // (dyn, n) -> rollout tile chosen by the autotuner: (candidates per block, horizon chunk,
   // candidates per thread)
   std::map<std::pair<int, int>, std::array<int, 3>> tuned;
+  // (dyn, n) -> the autotuner's rollout time of the group (ms) per rollout step
+  std::map<std::pair<int, int>, double> tuned_ms_per_step;
+  // groups in launch order: longest expected rollout first
+  std::vector<int> launch_order;
   std::vector<int> x0_off, us_off;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t fork_ev = nullptr;
@@ -134,6 +140,34 @@ struct mtp_batch {
 };
 
 namespace {
+
+// Groups are launched longest first.  The GPU takes a launch's blocks in
+// the order the launches arrive, and the groups' rollouts are long,
+// latency-bound launches: enqueued last, the longest groups would start
+// only when the earlier ones had drained and end the iteration alone
+// (measured on the batch of 256: the 9-link chains started 2.4 ms into a
+// 3.3 ms iteration).  A group's expected time is its rollout steps times the
+// autotuner's time per step for its (dynamics, dimension), or before
+// tuning a per-step cost model: the chains' step grows with the square of
+// the link count (the mass matrix and its factorisation), the point mass
+// step with its axes.
+template <class StepsFn>
+void set_launch_order(mtp_batch* b, StepsFn steps_of) {
+  for (auto& g : b->groups) {
+    const double steps = (double)steps_of(g);
+    auto it = b->tuned_ms_per_step.find({g.dyn, g.n});
+    if (it != b->tuned_ms_per_step.end()) {
+      g.est = steps * it->second;
+    } else {
+      const double w = g.dyn == MTP_DYN_POINTMASS ? 40.0 * g.n : 12.0 * g.n * g.n;  // instructions per step
+      g.est = steps * w * 1e-9;
+    }
+  }
+  b->launch_order.resize(b->groups.size());
+  for (size_t i = 0; i < b->groups.size(); ++i) b->launch_order[i] = (int)i;
+  std::stable_sort(b->launch_order.begin(), b->launch_order.end(),
+                   [&](int x, int y) { return b->groups[x].est > b->groups[y].est; });
+}
 
 mtp_status batch_fail(mtp_batch* b, mtp_status st, const std::string& msg) {
   if (b) b->err = msg;
@@ -266,7 +300,11 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
     const long long items = ((long long)dm.L + 1) * (((long long)Hn + 3) / 4);
     hv.d_cand[pos] = c;
     hv.d_cand_start[pos + 1] = hv.d_cand_start[pos] + c.graph_blocks;  // local rows run apart
-    hv.d_local_start[pos + 1] = hv.d_local_start[pos] + (int)std::max<long long>(1, (items + 1023) / 1024);
+    // 16 groups of four elements per thread: each thread's set-up (instance
+    // search, box, its group's mean and spread) is paid once for 16 rows
+    hv.d_local_start[pos + 1] =
+        hv.d_local_start[pos] + (int)std::max<long long>(1, (items + 256 * kLocalRowsPerThreadBatch - 1) /
+                                                                (256 * kLocalRowsPerThreadBatch));
     hv.d_sel[pos] = SelectArgs{h->cost, h->U, dm.B, dm.E, dm.H, dm.n, 1.0 / h->pr.lambda, h->pr.update_rule,
                                h->elite, h->weight, h->ustar, nullptr, nullptr, h->entropy};
     hv.d_upd[pos] = UpdateArgs{h->U, h->elite, h->weight, dm.E, dm.H, dm.n, h->pr.alpha, h->pr.sigma_min,
@@ -334,6 +372,14 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
     if (g.samples == 2) g.chunk = 0;
     rs += g.count + 1;
   }
+  set_launch_order(b, [&](const BatchGroup& g) {
+    long long steps = 0;
+    for (int j = 0; j < g.count; ++j) {
+      const mtp_handle* h = handles[order[g.first + j]];
+      steps += (long long)h->dm.B * h->dm.H;
+    }
+    return steps;
+  });
   // packing of x0 and u*, in the caller's order
   b->x0_off.assign(count + 1, 0);
   b->us_off.assign(count + 1, 0);
@@ -390,7 +436,7 @@ cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
   cudaError_t e;
   const BatchTables& t = b->t;
   if ((e = cudaEventRecord(b->fork_ev, s))) return e;
-  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+  for (const int gi : b->launch_order) {
     const BatchGroup& g = b->groups[gi];
     cudaStream_t gs = b->group_stream[gi];
     const int f = g.first;
@@ -586,11 +632,17 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
   for (int chunk : chunks)
     for (int block : blocks) tiles.push_back({block, chunk, 1});
   for (int block : blocks) tiles.push_back({block, 0, 2});
+  auto group_steps = [&](const BatchGroup& g) {
+    long long steps = 0;
+    for (int j = 0; j < g.count; ++j) steps += (long long)b->hs_sorted[g.first + j]->dm.B * b->hs_sorted[g.first + j]->dm.H;
+    return steps;
+  };
   for (auto& g : b->groups) {
-    if (g.dyn == MTP_DYN_LEGGED) continue;  // fixed tile
     float best = 1e30f;
     Tile best_tile{g.block, g.chunk, g.samples};
     for (const Tile& tl : tiles) {
+      // the legged rollout has one fixed tile: timed once, for the launch order
+      if (g.dyn == MTP_DYN_LEGGED && (tl.block != blocks[0] || tl.chunk || tl.samples != 1)) continue;
       if (tl.chunk && !g.stageable) continue;
       if (tl.chunk == 8 && g.dyn == MTP_DYN_CHAIN) continue;
       if (tl.samples == 2 && !g.pairable) continue;
@@ -609,11 +661,15 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
         best_tile = tl;
       }
     }
+    if (e == cudaSuccess && best < 1e30f)
+      b->tuned_ms_per_step[{g.dyn, g.n}] = (double)best / (double)std::max(1LL, (long long)group_steps(g));
+    if (g.dyn == MTP_DYN_LEGGED) continue;
     g.block = best_tile.block;
     g.chunk = best_tile.chunk;
     g.samples = best_tile.samples;
     b->tuned[{g.dyn, g.n}] = {g.block, g.chunk, g.samples};
   }
+  set_launch_order(b, group_steps);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));

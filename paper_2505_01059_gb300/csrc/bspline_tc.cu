@@ -227,23 +227,32 @@ __device__ __forceinline__ bool tc_tile(TcSmem& S, const CandArgs& a, int g, int
     const int steps = min(16, H - t0);  // steps of this chunk inside the horizon
     __syncwarp();                        // the previous chunk's reads of st are done
     if (p < wpaths) {
+      float* sp = st + p * 16 * n + i;
 #pragma unroll
-      for (int tt = 0; tt < 16; ++tt)
-        if (tt < steps) st[(p * 16 + tt) * n + i] = clamp_box(__uint_as_float(v[tt]), lo, hi);
+      for (int tt = 0; tt < 16; ++tt) {
+        if (tt < steps) *sp = clamp_box(__uint_as_float(v[tt]), lo, hi);
+        sp += n;
+      }
     }
     __syncwarp();
     const int piece = steps * n;  // floats of one path in this chunk
+    // flat over the warp's pieces; the piece index e / len is taken as
+    // (e + 1/2) * (1 / len) rounded down, exact here (e < 2^12, len <= 256:
+    // the product's rounding error stays far below the 1/(2 len) margin)
+    const size_t Hn = (size_t)H * n;
     if (vec && (piece & 3) == 0) {
       const int q4 = piece >> 2;
+      const float inv = 1.f / (float)q4;
       for (int e = lane; e < wpaths * q4; e += 32) {
-        const int pp = e / q4, o = e - pp * q4;
-        const float4 val = reinterpret_cast<const float4*>(st + pp * 16 * n)[o];
-        reinterpret_cast<float4*>(a.U_graph + ((size_t)(wb0 + pp) * H + t0) * n)[o] = val;
+        const int pp = __float2int_rz(((float)e + 0.5f) * inv), o = e - pp * q4;
+        reinterpret_cast<float4*>(a.U_graph + (wb0 + pp) * Hn + (size_t)t0 * n)[o] =
+            reinterpret_cast<const float4*>(st + pp * 16 * n)[o];
       }
     } else {
+      const float inv = 1.f / (float)piece;
       for (int e = lane; e < wpaths * piece; e += 32) {
-        const int pp = e / piece, o = e - pp * piece;
-        a.U_graph[((size_t)(wb0 + pp) * H + t0) * n + o] = st[pp * 16 * n + o];
+        const int pp = __float2int_rz(((float)e + 0.5f) * inv), o = e - pp * piece;
+        a.U_graph[(wb0 + pp) * Hn + (size_t)t0 * n + o] = st[pp * 16 * n + o];
       }
     }
   }

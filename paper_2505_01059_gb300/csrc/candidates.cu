@@ -101,12 +101,13 @@ __device__ __forceinline__ void local_rows_body(const CandArgs& a, int lb, int n
   if (t >= RS * QS) return;
   for (int q = t % QS; q < G; q += QS) {
     float mv[4], sv[4], lo[4], hi[4];
+    int i = (4 * q) % n;  // dimension of the group's first element; the next ones step from it
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const int el = 4 * q + w;
-      const int i = el % n;
       lo[w] = box_lo[i];
       hi[w] = box_hi[i];
+      i = i + 1 == n ? 0 : i + 1;
       mv[w] = el < Hn ? mu[el] : 0.f;
       sv[w] = el < Hn ? sigma[el] : 0.f;
     }
