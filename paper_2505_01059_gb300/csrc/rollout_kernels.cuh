@@ -27,6 +27,12 @@ namespace mtp {
 namespace {
 
 constexpr int kThreads = 128;
+// Chains of at least this many links solve their mass matrix by the O(NL)
+// semiseparable Cholesky, shorter ones by the dense factor.
+#ifndef MTP_SEMISEP_LINKS
+#define MTP_SEMISEP_LINKS 7
+#endif
+constexpr int kSemisepLinks = MTP_SEMISEP_LINKS;
 
 // Threads per block: fill as many SMs as the batch allows (one thread per
 // candidate; small batches get one warp per block).
@@ -303,23 +309,13 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
         for (int j = 0; j < NL; ++j) tt = fmaf(tau[j], tau[j], tt);
         J.add(fmaf(cm.w_target, fmaf(ex, ex, ey * ey), cm.w_ctrl * tt), a.kahan);
       }
-      // mass matrix (lower triangle) and right-hand side
-      using Tr = Tri<NL>;
-      float A[Tr::size], rhs[NL], inv[NL];
+      // right-hand side: generalised forces and gravity
+      float rhs[NL];
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
         const float q_next = (j + 1 < NL) ? tau[j + 1] : 0.f;
         rhs[j] = fmaf(-G[j], c[j], tau[j] - q_next);
-        A[Tr::at(j, j)] = Dd[j];
       }
-      // mass matrix entries below the diagonal: D_jk = l_k lb_j for k < j
-      Unroll<1, NL>::run([&](auto J) {
-        constexpr int j = decltype(J)::value;
-        Unroll<0, j>::run([&](auto K) {
-          constexpr int k = decltype(K)::value;
-          A[Tr::at(j, k)] = (len[k] * lb[j]) * fmaf(c[j], c[k], s[j] * s[k]);  // cos(phi_j - phi_k)
-        });
-      });
       // velocity terms sum_k D_jk sin(phi_j - phi_k) w_k^2 in O(NL): with
       // a_k = c_k w_k^2, b_k = s_k w_k^2 the sum is
       // s_j (lb_j Pa_j + l_j Sa_j) - c_j (lb_j Pb_j + l_j Sb_j), where P sums
@@ -350,44 +346,99 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
           Pb = fmaf(len[j], wb[j], Pb);
         }
       }
-      // Cholesky A = L L^T in place (inv holds 1 / L_jj), then the two
-      // triangular solves
-      Unroll<0, NL>::run([&](auto J) {
-        constexpr int j = decltype(J)::value;
-        float d = A[Tr::at(j, j)];
-        Unroll<0, j>::run([&](auto K) {
-          constexpr int k = decltype(K)::value;
-          d = fmaf(-A[Tr::at(j, k)], A[Tr::at(j, k)], d);
-        });
-        inv[j] = rsqrtf(d);
-        Unroll<j + 1, NL>::run([&](auto I) {
-          constexpr int i = decltype(I)::value;
-          float v = A[Tr::at(i, j)];
+      if constexpr (NL >= kSemisepLinks) {
+        // Below the diagonal A_jk = u_j . v_k with u_j = lb_j (cos phi_j,
+        // sin phi_j) and v_k = l_k (cos phi_k, sin phi_k): a rank-2
+        // semiseparable matrix plus its diagonal Dd.  Its Cholesky factor
+        // has the same form, L_jk = u_j . w_k, built link by link with the
+        // running 2 x 2 matrix M = sum_{i<k} w_i w_i^T:
+        //   d_k^2 = Dd_k - u_k^T M u_k,  w_k = (v_k - M u_k) / d_k,  M += w_k w_k^T;
+        // then L y = rhs and L^T phi'' = y with running 2-vectors: O(NL)
+        // work and registers, against O(NL^3) work and O(NL^2) registers
+        // for the dense factor.
+        float u1[NL], u2[NL], w1[NL], w2[NL], dinv[NL];
+        float m11 = 0.f, m12 = 0.f, m22 = 0.f;
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+          u1[k] = lb[k] * c[k];
+          u2[k] = lb[k] * s[k];
+          const float mu1 = fmaf(m11, u1[k], m12 * u2[k]);
+          const float mu2 = fmaf(m12, u1[k], m22 * u2[k]);
+          const float inv = rsqrtf(Dd[k] - fmaf(u1[k], mu1, u2[k] * mu2));
+          dinv[k] = inv;
+          w1[k] = fmaf(len[k], c[k], -mu1) * inv;
+          w2[k] = fmaf(len[k], s[k], -mu2) * inv;
+          m11 = fmaf(w1[k], w1[k], m11);
+          m12 = fmaf(w1[k], w2[k], m12);
+          m22 = fmaf(w2[k], w2[k], m22);
+        }
+        float z1 = 0.f, z2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          rhs[j] = (rhs[j] - fmaf(u1[j], z1, u2[j] * z2)) * dinv[j];
+          z1 = fmaf(w1[j], rhs[j], z1);
+          z2 = fmaf(w2[j], rhs[j], z2);
+        }
+        float r1 = 0.f, r2 = 0.f;
+#pragma unroll
+        for (int k = NL - 1; k >= 0; --k) {
+          rhs[k] = (rhs[k] - fmaf(w1[k], r1, w2[k] * r2)) * dinv[k];
+          r1 = fmaf(u1[k], rhs[k], r1);
+          r2 = fmaf(u2[k], rhs[k], r2);
+        }
+      } else {
+        // the dense mass matrix (lower triangle), A_jk = D_jk cos(phi_j - phi_k)
+        // with D_jk = l_k lb_j below the diagonal
+        using Tr = Tri<NL>;
+        float A[Tr::size], inv[NL];
+#pragma unroll
+        for (int j = 0; j < NL; ++j) A[Tr::at(j, j)] = Dd[j];
+        Unroll<1, NL>::run([&](auto J) {
+          constexpr int j = decltype(J)::value;
           Unroll<0, j>::run([&](auto K) {
             constexpr int k = decltype(K)::value;
-            v = fmaf(-A[Tr::at(i, k)], A[Tr::at(j, k)], v);
+            A[Tr::at(j, k)] = (len[k] * lb[j]) * fmaf(c[j], c[k], s[j] * s[k]);  // cos(phi_j - phi_k)
           });
-          A[Tr::at(i, j)] = v * inv[j];
         });
-      });
-      Unroll<0, NL>::run([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        float v = rhs[i];
-        Unroll<0, i>::run([&](auto K) {
-          constexpr int k = decltype(K)::value;
-          v = fmaf(-A[Tr::at(i, k)], rhs[k], v);
+        // Cholesky A = L L^T in place (inv holds 1 / L_jj), then the two
+        // triangular solves
+        Unroll<0, NL>::run([&](auto J) {
+          constexpr int j = decltype(J)::value;
+          float d = A[Tr::at(j, j)];
+          Unroll<0, j>::run([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            d = fmaf(-A[Tr::at(j, k)], A[Tr::at(j, k)], d);
+          });
+          inv[j] = rsqrtf(d);
+          Unroll<j + 1, NL>::run([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            float v = A[Tr::at(i, j)];
+            Unroll<0, j>::run([&](auto K) {
+              constexpr int k = decltype(K)::value;
+              v = fmaf(-A[Tr::at(i, k)], A[Tr::at(j, k)], v);
+            });
+            A[Tr::at(i, j)] = v * inv[j];
+          });
         });
-        rhs[i] = v * inv[i];
-      });
-      Unroll<0, NL>::run([&](auto I) {
-        constexpr int i = NL - 1 - decltype(I)::value;
-        float v = rhs[i];
-        Unroll<i + 1, NL>::run([&](auto K) {
-          constexpr int k = decltype(K)::value;
-          v = fmaf(-A[Tr::at(k, i)], rhs[k], v);
+        Unroll<0, NL>::run([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          float v = rhs[i];
+          Unroll<0, i>::run([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            v = fmaf(-A[Tr::at(i, k)], rhs[k], v);
+          });
+          rhs[i] = v * inv[i];
         });
-        rhs[i] = v * inv[i];
-      });
+        Unroll<0, NL>::run([&](auto I) {
+          constexpr int i = NL - 1 - decltype(I)::value;
+          float v = rhs[i];
+          Unroll<i + 1, NL>::run([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            v = fmaf(-A[Tr::at(k, i)], rhs[k], v);
+          });
+          rhs[i] = v * inv[i];
+        });
+      }
       // semi-implicit Euler in absolute coordinates
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
