@@ -74,6 +74,11 @@ BATCH_LABEL = ("batched: 256 uneven instances (point masses k 2..12 and 3..9-lin
                "through the plain path")
 
 
+# chains of at least this many links use the semiseparable mass-matrix solve
+# (kSemisepLinks of the rollout kernels)
+SEMISEP_LINKS = 7
+
+
 def flops_per_step(spec: dict) -> int:
     """FP32 flops (an FMA counts 2) of one rollout step of one candidate as the
     rollout kernel computes it; transcendental MUFU ops (sincos, sqrt, rsqrt)
@@ -83,11 +88,16 @@ def flops_per_step(spec: dict) -> int:
         pairs = L * (L - 1) // 2
         cost = 6 * L + 12            # tip position, reach error, torque penalty, compensated add
         rhs = 3 * L                  # tau_j - tau_{j+1} - g l_j beta_j cos(phi_j)
-        mass_matrix = 5 * pairs      # D_jk cos(phi_j - phi_k) below the diagonal
         velocity = 21 * L - 4        # O(L) prefix / suffix form of the velocity terms
-        chol = L * (L - 1) + sum((L - 1 - j) * (2 * j + 1) for j in range(L))
-        solves = 2 * L * L
         integrate = 4 * L
+        if L >= SEMISEP_LINKS:
+            # rank-2 semiseparable Cholesky (2 x 2 recursion per link) and the
+            # forward / backward solves with running 2-vectors
+            mass_matrix, chol, solves = 0, 24 * L, 18 * L
+        else:
+            mass_matrix = 5 * pairs  # D_jk cos(phi_j - phi_k) below the diagonal
+            chol = L * (L - 1) + sum((L - 1 - j) * (2 * j + 1) for j in range(L))
+            solves = 2 * L * L
         return cost + rhs + mass_matrix + velocity + chol + solves + integrate
     if spec["dyn"] == "legged":
         L = spec["n_links"]
@@ -163,7 +173,9 @@ def profiled_traffic(kernel_file: str, summary: str, key: str = "dram_bytes_per_
             os.path.join(ROOT, "paper_2505_01059_gb300/csrc", kernel_file)):
         return None
     text = open(prof).read()
-    m_hash = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    # a summary covering several kernel files names each one's digest
+    m_hash = (re.search(r"source_sha256 " + re.escape(kernel_file) + r":\s*([0-9a-f]{64})", text) or
+              re.search(r"source_sha256:\s*([0-9a-f]{64})", text))
     m_bytes = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", text)
     if not m_hash or not m_bytes or m_hash.group(1) != source_digest(kernel_file):
         return None
