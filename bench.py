@@ -76,7 +76,7 @@ BATCH_LABEL = ("batched: 256 uneven instances (point masses k 2..12 and 3..9-lin
 
 # chains of at least this many links use the semiseparable mass-matrix solve
 # (kSemisepLinks of the rollout kernels)
-SEMISEP_LINKS = 7
+SEMISEP_LINKS = 8
 
 
 def flops_per_step(spec: dict) -> int:
@@ -607,13 +607,22 @@ class HostSim:
     cos(phi_j - phi_k), velocity terms D_jk sin(phi_j - phi_k) w_k^2,
     gravity and torque differences), solved for all robots of one link
     count at once.  Completions are buffered and advanced in batches; a
-    robot's state is brought up to date before it submits again."""
+    robot's state is brought up to date before it submits again.  A robot
+    whose motion leaves the range its model is integrated well in (a joint
+    faster than ARM_MAX_RATE rad/s, a point mass beyond PM_MAX_POS, or any
+    non-finite value) starts a new episode from its initial state; `resets`
+    counts those."""
+
+    ARM_MAX_RATE = 50.0
+    PM_MAX_POS = 100.0
 
     def __init__(self, specs, x0s):
         import numpy as np
         self.np = np
         self.specs = specs
         self.x = [np.asarray(x, np.float64).copy() for x in x0s]
+        self.x_init = [x.copy() for x in self.x]
+        self.resets = 0
         self.pending = {}
         self.groups = {}
         for r, s in enumerate(specs):
@@ -677,8 +686,17 @@ class HostSim:
                 q = np.diff(phi, axis=1, prepend=0.0)
                 qd = np.diff(w, axis=1, prepend=0.0)
                 X = np.concatenate([q, qd], axis=1)
+            if kind == "pm":
+                bad = np.abs(X[:, :dim]).max(axis=1) > self.PM_MAX_POS
+            else:
+                bad = np.abs(X[:, dim:]).max(axis=1) > self.ARM_MAX_RATE
+            bad |= ~np.isfinite(X).all(axis=1)
             for i, r in enumerate(rs):
-                self.x[r] = X[i]
+                if bad[i]:
+                    self.x[r] = self.x_init[r].copy()
+                    self.resets += 1
+                else:
+                    self.x[r] = X[i]
         self.pending.clear()
 
 
@@ -852,6 +870,7 @@ def run_serving(args, mtp, dev) -> dict:
                                       {"rate_hz_per_robot": rate, "refused": refused}))
     stats = mtp.mtp_server_get_stats(srv)
     srv.close()
+    out["served_episode_resets"] = sim.resets
     out["served"] = served
     out["served_clocks"] = clocks.summary()
     out["server_cycles"] = stats["cycles"]
@@ -861,8 +880,13 @@ def run_serving(args, mtp, dev) -> dict:
     handles = [mtp.mtp_create(dict(s)) for s in specs]
     sim = HostSim(specs, x0s)
     u = np.empty(32, np.float32)
-    for r, h in enumerate(handles):            # capture each handle's graphs
-        mtp.mtp_plan_step_host(h, sim.state(r).astype(np.float32), 1, u)
+    # capture every graph a handle replays: the first step makes its
+    # candidates in full, and a pipelined handle then alternates between its
+    # two candidate buffers, each with a graph of its own
+    for r, h in enumerate(handles):
+        for _ in range(3):
+            mtp.mtp_plan_step_host(h, sim.state(r).astype(np.float32), 1, u)
+            mtp.mtp_shift(h, 1)
     torch.cuda.synchronize()
     probe = rng.integers(0, R, size=256)
     t0 = time.perf_counter()
@@ -883,6 +907,7 @@ def run_serving(args, mtp, dev) -> dict:
     for h in handles:
         mtp.mtp_destroy(h)
     out["plain"] = plain
+    out["plain_episode_resets"] = sim.resets
     out["plain_service_ms"] = service * 1e3
     out["plain_capacity_requests_per_s"] = capacity
 

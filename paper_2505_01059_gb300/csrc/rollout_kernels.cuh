@@ -28,9 +28,12 @@ namespace {
 
 constexpr int kThreads = 128;
 // Chains of at least this many links solve their mass matrix by the O(NL)
-// semiseparable Cholesky, shorter ones by the dense factor.
+// semiseparable Cholesky, shorter ones by the dense factor.  At 7 links the
+// dense factor is the faster of the two: as fast in a batch, and 99 -> 79 us
+// for a lone 4096-candidate arm, whose one warp per SM sub-partition runs
+// the step's serial chain (the recursion's is longer).
 #ifndef MTP_SEMISEP_LINKS
-#define MTP_SEMISEP_LINKS 7
+#define MTP_SEMISEP_LINKS 8
 #endif
 constexpr int kSemisepLinks = MTP_SEMISEP_LINKS;
 
@@ -316,6 +319,23 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
         const float q_next = (j + 1 < NL) ? tau[j + 1] : 0.f;
         rhs[j] = fmaf(-G[j], c[j], tau[j] - q_next);
       }
+      // the dense mass matrix (lower triangle) of the shorter chains, built
+      // before the velocity terms so that its independent products overlap
+      // their prefix sums: A_jk = D_jk cos(phi_j - phi_k) with D_jk = l_k lb_j
+      // below the diagonal
+      using Tr = Tri<NL>;
+      float A[Tr::size];
+      if constexpr (NL < kSemisepLinks) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) A[Tr::at(j, j)] = Dd[j];
+        Unroll<1, NL>::run([&](auto J) {
+          constexpr int j = decltype(J)::value;
+          Unroll<0, j>::run([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            A[Tr::at(j, k)] = (len[k] * lb[j]) * fmaf(c[j], c[k], s[j] * s[k]);  // cos(phi_j - phi_k)
+          });
+        });
+      }
       // velocity terms sum_k D_jk sin(phi_j - phi_k) w_k^2 in O(NL): with
       // a_k = c_k w_k^2, b_k = s_k w_k^2 the sum is
       // s_j (lb_j Pa_j + l_j Sa_j) - c_j (lb_j Pb_j + l_j Sb_j), where P sums
@@ -387,19 +407,7 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
           r2 = fmaf(u2[k], rhs[k], r2);
         }
       } else {
-        // the dense mass matrix (lower triangle), A_jk = D_jk cos(phi_j - phi_k)
-        // with D_jk = l_k lb_j below the diagonal
-        using Tr = Tri<NL>;
-        float A[Tr::size], inv[NL];
-#pragma unroll
-        for (int j = 0; j < NL; ++j) A[Tr::at(j, j)] = Dd[j];
-        Unroll<1, NL>::run([&](auto J) {
-          constexpr int j = decltype(J)::value;
-          Unroll<0, j>::run([&](auto K) {
-            constexpr int k = decltype(K)::value;
-            A[Tr::at(j, k)] = (len[k] * lb[j]) * fmaf(c[j], c[k], s[j] * s[k]);  // cos(phi_j - phi_k)
-          });
-        });
+        float inv[NL];
         // Cholesky A = L L^T in place (inv holds 1 / L_jj), then the two
         // triangular solves
         Unroll<0, NL>::run([&](auto J) {
