@@ -51,14 +51,17 @@ ROLLOUT_KERNEL = {"pointmass": "k_rollout_pm", "chain": "k_rollout_chain",
 DYN_NAMES = {0: "pointmass", 1: "chain", 2: "legged"}
 
 
-def workload(name: str) -> dict:
+def workload(name: str, B: int | None = None) -> dict:
+    """A single-instance workload; B overrides its candidate count (a
+    smaller case of the same kernel, for profiler captures)."""
     from paper_2505_01059_gb300 import workloads as W
+    over = {"B": B} if B else {}
     if name == "arm7":
-        return W.chain()
+        return W.chain(**over)
     if name == "pointmass2":
-        return W.pointmass()
+        return W.pointmass(**over)
     if name == "legged16":
-        return W.legged()
+        return W.legged(**over)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -985,7 +988,7 @@ def run_single(args, mtp, dev, spec, name, steps, pg=None, world=1, rank=0, flus
     achieved = fl / (stage_ms[1] / 1e3) / 1e12
     kernel_file = KERNEL_FILE[spec["dyn"]]
     summary = {"chain": "rollout_chain7_arm_B4096.txt", "pointmass": "rollout_pointmass2_B512.txt",
-               "legged": "rollout_legged16_B16384.txt"}[spec["dyn"]]
+               "legged": "rollout_legged16_B4096.txt"}[spec["dyn"]]
     res["roofline"] = {"bound": "alu", "kernel": ROLLOUT_KERNEL[spec["dyn"]], "achieved": achieved,
                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                        "traffic": profiled_traffic(kernel_file, summary),
@@ -1100,7 +1103,8 @@ def run_serve_only(args):
 def run_single_only(args, name):
     world, rank, local = dist_init()
     dev, pg, mtp = setup_gpu(local, world)
-    res = run_single(args, mtp, dev, workload(name), name, args.steps, pg, world, rank)
+    res = run_single(args, mtp, dev, workload(name, args.candidates), name, args.steps, pg, world,
+                     rank)
     if rank == 0:
         line = base_line(args, world, res["value"], res["ms_per_step"],
                          {"workload": res["workload"], "parallelism": f"replicas{world}",
@@ -1109,7 +1113,7 @@ def run_single_only(args, name):
         line.update({k: v for k, v in res.items() if k not in ("value", "ms_per_step", "workload")})
         if world == 1 and not args.no_cpu_baseline:
             cpu = host_cpu()
-            c = cpu_oracle_single(workload(name), args.cpu_seconds, cpu["cores"])
+            c = cpu_oracle_single(workload(name, args.candidates), args.cpu_seconds, cpu["cores"])
             line["cpu_baseline"] = {"value": c["value"], "unit": UNIT, "cores": cpu["cores"],
                                     "kind": "oracle", "cpu_model": cpu["model"],
                                     "sample": f"one Alg. 2 iteration on {c['rows']} candidates in "
@@ -1175,6 +1179,8 @@ def main():
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "serve", "arm7", "pointmass2", "legged16", "sweep"])
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--candidates", type=int, default=None,
+                    help="arm7 / pointmass2 / legged16: candidates B instead of the workload's own")
     ap.add_argument("--robots", type=int, default=1024)
     ap.add_argument("--max-batch", type=int, default=256)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[25.0, 50.0, 100.0, 125.0],
