@@ -49,6 +49,7 @@ FP32_LANES_PER_SM = 128
 ROLLOUT_KERNEL = {"pointmass": "k_rollout_pm", "chain": "k_rollout_chain",
                   "legged": "k_rollout_legged"}
 DYN_NAMES = {0: "pointmass", 1: "chain", 2: "legged"}
+ROLLOUT_MODES = {"groups": 0, "persistent-staged": 1, "persistent-direct": 2}
 
 
 def workload(name: str, B: int | None = None) -> dict:
@@ -495,6 +496,10 @@ def run_batch_arms(args, mtp, dev, pg, world, rank) -> dict:
     handles = [mtp.mtp_create(s) for s in specs]
     b = mtp.mtp_batch_create(handles)
     tiles = mtp.mtp_batch_autotune(b)
+    tuned_mode, mode_ms = mtp.mtp_batch_rollout_mode(b)
+    if args.rollout_mode != "auto":
+        mtp.mtp_batch_set_rollout_mode(b, ROLLOUT_MODES[args.rollout_mode])
+    mode = mtp.mtp_batch_rollout_mode(b)[0]
     x0 = torch.tensor(np.concatenate([np.array(s["x0"], np.float32) for s in specs]), device=dev)
     us = torch.empty(b.ustar_offset[-1], device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -526,6 +531,10 @@ def run_batch_arms(args, mtp, dev, pg, world, rank) -> dict:
                        "what": "device time of one batched iteration: every instance's re-plan "
                                "completes at its end"},
         "gpu_launches": mtp.mtp_batch_launches(b, 1) * args.steps,
+        "rollout_mode": {"timed": mtp.BATCH_ROLLOUT_NAMES[mode],
+                         "autotuner_pick": mtp.BATCH_ROLLOUT_NAMES[tuned_mode],
+                         "autotuner_iteration_ms": {mtp.BATCH_ROLLOUT_NAMES[k]: v
+                                                    for k, v in enumerate(mode_ms)}},
     }
     if rank != 0 or args.quick:
         mtp.mtp_batch_destroy(b)
@@ -1055,6 +1064,7 @@ def run_headline(args):
             "rollout_groups": res.get("rollout_groups"),
             "whole_step_fp32": res.get("whole_step_fp32"),
             "tiles": res["tiles"],
+            "rollout_mode": res["rollout_mode"],
             "arm7": extras.get("arm7"),
             "legged16": extras.get("legged16"),
             "e2e": res.get("e2e"),
@@ -1194,6 +1204,8 @@ def main():
     ap.add_argument("--reference-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched timed region only")
+    ap.add_argument("--rollout-mode", default="auto", choices=["auto"] + list(ROLLOUT_MODES),
+                    help="batched rollouts: the autotuner's pick, or one mode forced")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -341,17 +341,50 @@ mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, f
  * masses also two candidates per thread (64 per warp, direct loads).  The
  * legged group keeps its fixed tile.  Writes (dynamics, dimension, block,
  * chunk, candidates per thread) to tiles_out (5 * groups entries, may be
- * NULL) and the number of groups to n_groups.  Synchronous; overwrites the
- * handles' cost buffers.  Results do not depend on the tile. */
+ * NULL) and the number of groups to n_groups.  Then it picks the rollout
+ * mode (mtp_batch_set_rollout_mode) by timing whole iterations in each mode
+ * (best of three after one untimed run), with every instance's planner state
+ * (mean, spread, iteration counter) saved before and restored after, so the
+ * instances' next iteration is the one they would have run.  Synchronous;
+ * overwrites the handles' candidate, cost, elite and u* buffers, and
+ * allocates (and frees) device memory for the saved states.  Results do not
+ * depend on the tile or the mode. */
 mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_groups, void* stream);
+
+/* How a batch runs its rollouts.
+ * MTP_BATCH_ROLLOUT_GROUPS: each (dynamics, dimension) group's rollout is its
+ *   own launch, in that group's chain of launches on its stream (groups
+ *   overlap one another).
+ * MTP_BATCH_ROLLOUT_PERSISTENT_STAGED / _DIRECT: the rollouts of every point
+ *   mass (up to 16 axes) and every chain (up to 9 links) of the batch run in
+ *   one persistent launch, after all instances' candidates are made: each
+ *   warp takes warp tiles of 32 candidates of one instance from a device
+ *   counter, longest expected rollout first (H times the group's time per
+ *   step), with their controls staged through shared memory 4 steps at a
+ *   time where the instance's rows allow it (_STAGED) or loaded directly
+ *   (_DIRECT).  Legged robots and longer chains keep their own launches
+ *   beside it.  The launch is counted as one kernel by mtp_batch_launches.
+ * Results are the same bits in every mode.  The mode takes effect at the
+ * next mtp_batch_plan_step (captured graphs are dropped).  Errors:
+ * MTP_ERR_INVALID_ARG for an unknown mode. */
+#define MTP_BATCH_ROLLOUT_GROUPS 0
+#define MTP_BATCH_ROLLOUT_PERSISTENT_STAGED 1
+#define MTP_BATCH_ROLLOUT_PERSISTENT_DIRECT 2
+mtp_status mtp_batch_set_rollout_mode(mtp_batch* b, int32_t mode);
+
+/* The batch's current rollout mode, and (ms3, 3 entries, may be NULL) the
+ * autotuner's iteration time of each mode in milliseconds (0 where it has
+ * not timed that mode; modes that cover no instance are not timed). */
+mtp_status mtp_batch_rollout_mode(const mtp_batch* b, int32_t* mode, double* ms3);
 
 /* mtp_shift(h, k) of every instance of the batch in one launch. */
 mtp_status mtp_batch_shift(mtp_batch* b, int32_t k, void* stream);
 
 /* Kernel launches one mtp_batch_plan_step(b, ..., iters, ...) issues: per
  * iteration, each (dynamics, dimension) group's graph, graph-path, local-row,
- * rollout, selection and update launches that have work, plus the scatter of
- * the start states and the gather of u* once per call. */
+ * rollout, selection and update launches that have work (in a persistent
+ * rollout mode the covered groups' rollouts count as one launch), plus the
+ * scatter of the start states and the gather of u* once per call. */
 mtp_status mtp_batch_launches(const mtp_batch* b, int32_t iters, int32_t* launches);
 
 /* Device time of each group's rollout launch (Alg. 2 rollout fused with the

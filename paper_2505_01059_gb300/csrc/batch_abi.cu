@@ -75,6 +75,13 @@ struct BatchTables {
   float** d_ustar_src = nullptr;
   int* d_x0_off = nullptr;
   int* d_us_off = nullptr;
+  // the persistent rollout launch: one entry per instance it covers,
+  // longest expected rollout first (PersistArgs)
+  int* d_p_order = nullptr;
+  int* d_p_wstart = nullptr;
+  int* d_p_code = nullptr;
+  int* d_p_model = nullptr;
+  unsigned* d_p_head = nullptr;
 };
 
 // Packs the tables of `count` instances (n_pm point masses, n_cm chains,
@@ -110,6 +117,11 @@ size_t layout_tables(BatchTables* t, unsigned char* base, int count, int n_pm, i
   take(&d->d_ustar_src, count);
   take(&d->d_x0_off, count + 1);
   take(&d->d_us_off, count + 1);
+  take(&d->d_p_order, count);
+  take(&d->d_p_wstart, count + 1);
+  take(&d->d_p_code, count);
+  take(&d->d_p_model, count);
+  take(&d->d_p_head, 1);
   return off;
 }
 
@@ -136,6 +148,17 @@ struct mtp_batch {
   cudaEvent_t group_done[kMaxGroups] = {};
   std::map<int, cudaGraphExec_t> graphs;  // key: graph_key(iterations, cur, first prepared)
   int runs_since_fill = 0;
+  // How the rollouts run (MTP_BATCH_ROLLOUT_*): one launch per group on its
+  // stream, or the point-mass and chain groups (up to kPersistMaxAxes axes,
+  // kPersistMaxLinks links) in one persistent launch, their tiles staged or
+  // loaded directly.
+  int rollout_mode = MTP_BATCH_ROLLOUT_GROUPS;
+  std::vector<char> covered;    // per group: its rollouts are in the persistent launch
+  int p_count = 0, p_total_warps = 0;
+  size_t p_warp_bytes = 0;      // staged tiles' shared memory per warp (0: none stageable)
+  int p_blocks[2] = {0, 0};     // resident CTAs per SM: staged mode, direct mode
+  cudaEvent_t persist_ev = nullptr;
+  double mode_ms[3] = {0, 0, 0};  // the autotuner's iteration time per mode (0: not timed)
   std::string err;
 };
 
@@ -191,6 +214,7 @@ void free_batch(mtp_batch* b) {
   }
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->persist_ev) cudaEventDestroy(b->persist_ev);
   delete b;
 }
 
@@ -205,7 +229,8 @@ cudaError_t alloc_batch(mtp_batch* b, int cap) {
       (e = cudaEventCreateWithFlags(&t.copied, cudaEventDisableTiming)) ||
       (e = cudaEventRecord(t.copied, 0)) ||
       (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) ||
-      (e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)))
+      (e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)) ||
+      (e = cudaEventCreateWithFlags(&b->persist_ev, cudaEventDisableTiming)))
     return e;
   return cudaSuccess;
 }
@@ -380,6 +405,54 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
     }
     return steps;
   });
+  // the persistent launch's entries: every instance of a covered group,
+  // longest warp tile first (H steps at the group's time per step)
+  {
+    b->covered.assign(b->groups.size(), 0);
+    struct Entry {
+      double est;
+      int pos, code, model, warps;
+    };
+    std::vector<Entry> ent;
+    int max_pm = 0, max_links = 0;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+      const BatchGroup& g = b->groups[gi];
+      const bool cov = (g.dyn == MTP_DYN_POINTMASS && g.n <= kPersistMaxAxes) ||
+                       (g.dyn == MTP_DYN_CHAIN && g.n <= kPersistMaxLinks);
+      if (!cov || g.total_rows <= 0) continue;
+      b->covered[gi] = 1;
+      auto it = b->tuned_ms_per_step.find({g.dyn, g.n});
+      const double per_step = it != b->tuned_ms_per_step.end()
+                                  ? it->second
+                                  : (g.dyn == MTP_DYN_POINTMASS ? 40.0 * g.n : 12.0 * g.n * g.n) * 1e-9;
+      for (int j = 0; j < g.count; ++j) {
+        const int pos = g.first + j;
+        const mtp_handle* h = handles[order[pos]];
+        const bool stage = can_stage(hv.d_ra[pos], g.n);
+        if (stage) (g.dyn == MTP_DYN_POINTMASS ? max_pm : max_links) = std::max(
+                       g.dyn == MTP_DYN_POINTMASS ? max_pm : max_links, g.n);
+        ent.push_back({per_step * h->dm.H, pos, g.dyn | (g.n << 8) | (stage ? 1 << 16 : 0),
+                       g.model_first + j, (h->dm.B + 31) / 32});
+      }
+    }
+    std::stable_sort(ent.begin(), ent.end(), [](const Entry& x, const Entry& y) { return x.est > y.est; });
+    int w = 0;
+    for (size_t k = 0; k < ent.size(); ++k) {
+      hv.d_p_order[k] = ent[k].pos;
+      hv.d_p_code[k] = ent[k].code;
+      hv.d_p_model[k] = ent[k].model;
+      hv.d_p_wstart[k] = w;
+      w += ent[k].warps;
+    }
+    hv.d_p_wstart[ent.size()] = w;
+    *hv.d_p_head = 0u;
+    b->p_count = (int)ent.size();
+    b->p_total_warps = w;
+    b->p_warp_bytes = persist_warp_bytes(max_pm, max_links);
+    b->p_blocks[0] = persist_blocks_per_sm(b->p_warp_bytes);
+    b->p_blocks[1] = persist_blocks_per_sm(0);
+    if (b->p_count > 0 && (b->p_blocks[0] < 1 || b->p_blocks[1] < 1)) return cudaErrorInvalidConfiguration;
+  }
   // packing of x0 and u*, in the caller's order
   b->x0_off.assign(count + 1, 0);
   b->us_off.assign(count + 1, 0);
@@ -432,9 +505,79 @@ cudaError_t launch_group(const mtp_batch* b, const BatchGroup& g, int block, int
 // its instances, its rollouts, one selection block per instance, the update.
 // Groups overlap one another (one group's generation fills the issue slots
 // that the others' latency-bound rollouts leave idle).
+PersistArgs persist_args(const mtp_batch* b, bool staged) {
+  const BatchTables& t = b->t;
+  PersistArgs p{};
+  p.ra = t.d_ra;
+  p.pm = t.d_pm;
+  p.cm = t.d_cm;
+  p.order = t.d_p_order;
+  p.wstart = t.d_p_wstart;
+  p.code = t.d_p_code;
+  p.model = t.d_p_model;
+  p.head = t.d_p_head;
+  p.count = b->p_count;
+  p.total_warps = b->p_total_warps;
+  p.warp_bytes = staged ? b->p_warp_bytes : 0;
+  return p;
+}
+
+cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s);
+
+// One batched iteration with the covered groups' rollouts in one persistent
+// launch: every group generates its candidates on its own stream; the
+// persistent launch starts when the covered groups' candidates are all made
+// (the groups it does not cover keep their own rollout launch); then each
+// covered group selects and updates on its stream.  Staged tiles, or every
+// tile with direct loads (`staged` false).
+cudaError_t enqueue_batch_iteration_persistent(mtp_batch* b, cudaStream_t s, bool staged) {
+  cudaError_t e;
+  const BatchTables& t = b->t;
+  if ((e = cudaEventRecord(b->fork_ev, s))) return e;
+  for (const int gi : b->launch_order) {
+    const BatchGroup& g = b->groups[gi];
+    cudaStream_t gs = b->group_stream[gi];
+    const int f = g.first;
+    if ((e = cudaStreamWaitEvent(gs, b->fork_ev, 0))) return e;
+    if ((e = launch_graph_Z_batch(t.d_cand + f, t.d_Z + f, t.d_z_start + f, g.count, g.z_blocks, gs))) return e;
+    if ((e = launch_candidates_batch(t.d_cand + f, t.d_cand_start + f, g.count, g.cand_blocks, g.cand_smem, gs)))
+      return e;
+    if (g.tc_count > 0 &&
+        (e = launch_bspline_tc_batch(t.d_tc + g.tc_first, t.d_tc_start + g.tc_start_first, g.tc_count,
+                                     g.tc_tiles, gs)))
+      return e;
+    if ((e = launch_local_batch(t.d_cand + f, t.d_local_start + f, g.count, g.local_blocks, gs))) return e;
+    if (!b->covered[gi]) {
+      if ((e = launch_group(b, g, g.block, g.chunk, g.samples, gs))) return e;
+      if ((e = launch_select_batch(t.d_sel + f, g.count, g.sel_smem, gs))) return e;
+      if ((e = launch_update_batch(t.d_upd + f, t.d_warp_start + f, g.count, g.upd_threads, gs))) return e;
+    }
+    if ((e = cudaEventRecord(b->group_done[gi], gs))) return e;
+  }
+  for (size_t gi = 0; gi < b->groups.size(); ++gi)
+    if (b->covered[gi] && (e = cudaStreamWaitEvent(s, b->group_done[gi], 0))) return e;
+  if ((e = launch_rollout_persistent(persist_args(b, staged), b->p_blocks[staged ? 0 : 1], s))) return e;
+  if ((e = cudaEventRecord(b->persist_ev, s))) return e;
+  for (const int gi : b->launch_order) {
+    if (!b->covered[gi]) continue;
+    const BatchGroup& g = b->groups[gi];
+    cudaStream_t gs = b->group_stream[gi];
+    const int f = g.first;
+    if ((e = cudaStreamWaitEvent(gs, b->persist_ev, 0))) return e;
+    if ((e = launch_select_batch(t.d_sel + f, g.count, g.sel_smem, gs))) return e;
+    if ((e = launch_update_batch(t.d_upd + f, t.d_warp_start + f, g.count, g.upd_threads, gs))) return e;
+    if ((e = cudaEventRecord(b->group_done[gi], gs))) return e;
+  }
+  for (size_t gi = 0; gi < b->groups.size(); ++gi)
+    if ((e = cudaStreamWaitEvent(s, b->group_done[gi], 0))) return e;
+  return cudaSuccess;
+}
+
 cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
   cudaError_t e;
   const BatchTables& t = b->t;
+  if (b->rollout_mode != MTP_BATCH_ROLLOUT_GROUPS && b->p_total_warps > 0)
+    return enqueue_batch_iteration_persistent(b, s, b->rollout_mode == MTP_BATCH_ROLLOUT_PERSISTENT_STAGED);
   if ((e = cudaEventRecord(b->fork_ev, s))) return e;
   for (const int gi : b->launch_order) {
     const BatchGroup& g = b->groups[gi];
@@ -504,6 +647,91 @@ cudaError_t run_batch(mtp_batch* b, const float* d_x0, int iters, float* d_ustar
 }  // namespace
 
 extern "C" {
+
+namespace {
+
+// Planner state of every instance of the batch (mean, spread, their FP32
+// copies, the iteration counter), saved to one device buffer so that timing
+// runs of whole iterations can be undone.
+struct SavedStates {
+  unsigned char* d = nullptr;
+  std::vector<size_t> off;
+  cudaError_t save(const mtp_batch* b, cudaStream_t s) {
+    size_t bytes = 0;
+    off.clear();
+    for (const mtp_handle* h : b->hs) {
+      off.push_back(bytes);
+      const size_t hn = (size_t)h->dm.H * h->dm.n;
+      bytes += ((2 * hn * sizeof(double) + 2 * hn * sizeof(float) + sizeof(uint32_t)) + 255) & ~size_t(255);
+    }
+    cudaError_t e = cudaMalloc((void**)&d, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess) return e;
+    return copy(b, s, true);
+  }
+  cudaError_t copy(const mtp_batch* b, cudaStream_t s, bool to_saved) {
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < b->hs.size() && e == cudaSuccess; ++i) {
+      const mtp_handle* h = b->hs[i];
+      const size_t hn = (size_t)h->dm.H * h->dm.n;
+      unsigned char* p = d + off[i];
+      void* live[5] = {h->mu, h->sigma, h->mu_f, h->sigma_f, h->iter_dev};
+      const size_t len[5] = {hn * sizeof(double), hn * sizeof(double), hn * sizeof(float), hn * sizeof(float),
+                             sizeof(uint32_t)};
+      for (int k = 0; k < 5 && e == cudaSuccess; ++k) {
+        e = to_saved ? cudaMemcpyAsync(p, live[k], len[k], cudaMemcpyDeviceToDevice, s)
+                     : cudaMemcpyAsync(live[k], p, len[k], cudaMemcpyDeviceToDevice, s);
+        p += len[k];
+      }
+    }
+    return e;
+  }
+  ~SavedStates() {
+    if (d) cudaFree(d);
+  }
+};
+
+// Times one iteration in each rollout mode (best of three after one untimed
+// run, every run from the saved states) and keeps the fastest; the states
+// are restored afterwards.
+cudaError_t tune_rollout_mode(mtp_batch* b) {
+  cudaStream_t s = b->cap_stream;
+  SavedStates st;
+  cudaError_t e = st.save(b, s);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  int best_mode = MTP_BATCH_ROLLOUT_GROUPS;
+  double best = 1e30;
+  for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+    b->mode_ms[mode] = 0.0;
+    if (mode != MTP_BATCH_ROLLOUT_GROUPS && b->p_total_warps <= 0) continue;
+    b->rollout_mode = mode;
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      if ((e = st.copy(b, s, false))) break;
+      if ((e = cudaEventRecord(t0, s))) break;
+      if ((e = enqueue_batch_iteration(b, s))) break;
+      if ((e = cudaEventRecord(t1, s))) break;
+      if ((e = cudaEventSynchronize(t1))) break;
+      float ms = 0.f;
+      if ((e = cudaEventElapsedTime(&ms, t0, t1))) break;
+      if (rep > 0) ms_min = std::min(ms_min, ms);
+    }
+    b->mode_ms[mode] = ms_min;
+    if (ms_min < best) {
+      best = ms_min;
+      best_mode = mode;
+    }
+  }
+  b->rollout_mode = best_mode;
+  if (e == cudaSuccess) e = st.copy(b, s, false);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  return e;
+}
+
+}  // namespace
 
 static mtp_status check_batch_handles(mtp_handle* const* handles, int32_t count, int dev) {
   for (int i = 0; i < count; ++i) {
@@ -672,6 +900,14 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
   set_launch_order(b, group_steps);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
+  // refill with the tuned tiles and times per step (the persistent launch's
+  // longest-first order uses them), then time the rollout modes
+  if (e == cudaSuccess) {
+    std::vector<mtp_handle*> hs = b->hs;
+    e = fill_batch(b, hs.data(), (int)hs.size(), b->cap_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap_stream);
+  }
+  if (e == cudaSuccess) e = tune_rollout_mode(b);
   if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);  // tiles changed: recapture
   b->graphs.clear();
@@ -689,12 +925,33 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
 
 mtp_status mtp_batch_launches(const mtp_batch* b, int32_t iters, int32_t* launches) {
   if (!b || !launches || iters < 1 || b->count < 1) return MTP_ERR_INVALID_ARG;
-  long long per_iter = 0;
-  for (const auto& g : b->groups) {
+  const bool persistent = b->rollout_mode != MTP_BATCH_ROLLOUT_GROUPS && b->p_total_warps > 0;
+  long long per_iter = persistent ? 1 : 0;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const BatchGroup& g = b->groups[gi];
     per_iter += (g.z_blocks > 0) + (g.cand_blocks > 0) + (g.local_blocks > 0) + (g.tc_count > 0);
-    per_iter += (g.total_rows > 0) + (g.count > 0) + (g.upd_threads > 0);
+    per_iter += (g.total_rows > 0 && !(persistent && b->covered[gi])) + (g.count > 0) + (g.upd_threads > 0);
   }
   *launches = (int32_t)(2 + per_iter * iters);  // scatter of x0 and gather of u* once per call
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_set_rollout_mode(mtp_batch* b, int32_t mode) {
+  if (!b || mode < MTP_BATCH_ROLLOUT_GROUPS || mode > MTP_BATCH_ROLLOUT_PERSISTENT_DIRECT)
+    return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_set_rollout_mode: unknown mode");
+  if (b->rollout_mode != mode) {
+    b->rollout_mode = mode;
+    drop_graphs(b);
+    b->runs_since_fill = 0;
+  }
+  return MTP_OK;
+}
+
+mtp_status mtp_batch_rollout_mode(const mtp_batch* b, int32_t* mode, double* ms3) {
+  if (!b || !mode) return MTP_ERR_INVALID_ARG;
+  *mode = b->rollout_mode;
+  if (ms3)
+    for (int k = 0; k < 3; ++k) ms3[k] = b->mode_ms[k];
   return MTP_OK;
 }
 

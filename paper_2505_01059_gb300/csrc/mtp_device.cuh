@@ -257,6 +257,34 @@ cudaError_t launch_rollout_legged(const RolloutArgs& a, const LeggedModel& m, in
 cudaError_t launch_rollout_legged_batch(const RolloutArgs* d_ra, const LeggedModel* d_lm,
                                         const int* d_row_start, int count, int total_rows,
                                         int links, cudaStream_t s);
+// The rollouts of many instances in one persistent launch
+// (rollout_persist.cu): warp tiles of 32 candidates, taken in order from a
+// device counter by every warp of the launch.  Entry k of the tables is one
+// instance, longest expected rollout first: its position in the batch's
+// RolloutArgs, its model, its code (dynamics | dimension << 8 | staged << 16)
+// and its first warp tile wstart[k] (count + 1 entries).  Point masses of up
+// to kPersistMaxAxes axes and chains of up to kPersistMaxLinks links.
+constexpr int kPersistMaxAxes = 16;
+constexpr int kPersistMaxLinks = 9;
+struct PersistArgs {
+  const RolloutArgs* ra;
+  const PointMassModel* pm;
+  const ChainModel* cm;
+  const int* order;
+  const int* wstart;
+  const int* code;
+  const int* model;
+  unsigned* head;     // the tile counter, zeroed by the launch
+  int count, total_warps;
+  size_t warp_bytes;  // shared memory per warp: two mbarriers and two staging buffers (0: no staging)
+};
+// Shared memory per warp for staged tiles of at most these widths (0: none).
+size_t persist_warp_bytes(int max_pm_axes_staged, int max_links_staged);
+// Resident 128-thread CTAs per SM of the persistent launch with that much
+// shared memory per warp (0 on error); also sets the launch's shared-memory
+// attribute.
+int persist_blocks_per_sm(size_t warp_bytes);
+cudaError_t launch_rollout_persistent(const PersistArgs& p, int blocks_per_sm, cudaStream_t s);
 // Def. 2 graph rows on the tensor cores (BF16 operands, FP32 sums): whether a
 // generation's graph part goes there (BF16 B-spline, H <= 256, M <= 64,
 // n <= 16), its tile count, and the launches (standalone and over many

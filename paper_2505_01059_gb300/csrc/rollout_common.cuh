@@ -127,6 +127,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// The two mbarriers of a warp's staging, initialised by one lane.
+__device__ __forceinline__ void init_stage_bars(uint64_t* bars) {
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned b0 = (unsigned)__cvta_generic_to_shared(bars);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+}
+
 template <int K, int T>
 struct StagedRows {
   using Shape = StageShape<K, T>;
@@ -156,6 +167,23 @@ struct StagedRows {
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
+  }
+
+  // Binds this warp's next row set to barriers and buffers that the warp
+  // keeps across rows of different widths: `bars` holds two mbarriers
+  // initialised once (init_bars), `buffer` two buffers of at least kBuf
+  // floats, and `seq_` counts the chunks this warp has consumed on those
+  // barriers so far (it sets their phases).  Every lane calls it.
+  __device__ __forceinline__ void attach(uint64_t* bars, float* buffer, const float* my_row, int H_,
+                                         int seq_) {
+    buf = buffer;
+    bar = bars;
+    row = my_row;
+    H = H_;
+    chunks = (H + T - 1) / T;
+    seq = seq_;
+    lane = threadIdx.x & 31;
+    live = __ballot_sync(0xffffffffu, my_row != nullptr);
   }
 
   // Data chunk c (steps c*T ..) as the g-th chunk of this warp's sequence,

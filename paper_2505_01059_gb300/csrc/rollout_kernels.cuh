@@ -109,7 +109,7 @@ __device__ __forceinline__ float pm_state_cost(const PointMassModel& pm, const f
 // control gains of the domain randomisation); the stage cost is taken
 // before the step and the terminal cost on the final state.
 template <int K, int PF, bool ALL, int T>
-__device__ __forceinline__ void rollout_pm_body(const RolloutArgs& a, const PointMassModel& pm,
+__device__ __forceinline__ bool rollout_pm_body(const RolloutArgs& a, const PointMassModel& pm,
                                                 int r, bool live, StagedRows<K, T>* st) {
   const int b = a.row0 + r;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
@@ -157,11 +157,12 @@ __device__ __forceinline__ void rollout_pm_body(const RolloutArgs& a, const Poin
     J.add(pm.w_term * pm_state_cost<K, ALL>(pm, p), a.kahan);
     total += J.s;
   }
-  if (!live) return;
+  if (!live) return ok;
   float c = total / (float)models;
   if (!isfinite(c) || !ok) c = __int_as_float(0x7f800000);
   if (!ok) report_stage_timeout(a);
   a.cost[r] = c;
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -244,7 +245,7 @@ __device__ __forceinline__ void chain_tip(const float (&len)[NL], const float (&
 }
 
 template <int NL, int PF, int T>
-__device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const ChainModel& cm,
+__device__ __forceinline__ bool rollout_chain_body(const RolloutArgs& a, const ChainModel& cm,
                                                    int r, bool live, StagedRows<NL, T>* st) {
   const int b = a.row0 + r;
   const uint32_t iter = a.d_iter ? *a.d_iter : a.iter;
@@ -472,11 +473,12 @@ __device__ __forceinline__ void rollout_chain_body(const RolloutArgs& a, const C
     }
     total += J.s;
   }
-  if (!live) return;
+  if (!live) return ok;
   float cst = total / (float)models;
   if (!isfinite(cst) || !ok) cst = __int_as_float(0x7f800000);
   if (!ok) report_stage_timeout(a);
   a.cost[r] = cst;
+  return ok;
 }
 
 // Standalone launches: one thread per candidate row.  Direct loads (T = 0)

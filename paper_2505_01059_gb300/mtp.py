@@ -44,7 +44,8 @@ EXPORTS = [
     "mtp_set_profiling", "mtp_stage_times", "mtp_stage_times5", "mtp_elite_update_noalloc",
     "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_layout", "mtp_batch_plan_step",
     "mtp_batch_autotune", "mtp_batch_reserve", "mtp_batch_fill", "mtp_batch_shift",
-    "mtp_batch_launches", "mtp_batch_rollout_times", "mtp_device_status", "mtp_cost_entropy",
+    "mtp_batch_launches", "mtp_batch_rollout_times", "mtp_batch_set_rollout_mode",
+    "mtp_batch_rollout_mode", "mtp_device_status", "mtp_cost_entropy",
     "mtp_selftest_bounded_wait",
     "mtp_problem_device_bytes", "mtp_server_create", "mtp_server_destroy", "mtp_server_register",
     "mtp_submit", "mtp_poll", "mtp_server_get_stats", "mtp_server_last_error",
@@ -154,6 +155,8 @@ def load_library(path: str = LIB_PATH):
         "mtp_batch_plan_step": (i32, [vp, vp, i32, vp, vp]),
         "mtp_batch_autotune": (i32, [vp, vp, vp, vp]),
         "mtp_batch_launches": (i32, [vp, i32, vp]),
+        "mtp_batch_set_rollout_mode": (i32, [vp, i32]),
+        "mtp_batch_rollout_mode": (i32, [vp, vp, vp]),
         "mtp_batch_rollout_times": (i32, [vp, i32, vp, vp, i32, vp, vp]),
         "mtp_batch_reserve": (i32, [i32, C.POINTER(vp)]),
         "mtp_batch_fill": (i32, [vp, C.POINTER(vp), i32, vp]),
@@ -604,6 +607,25 @@ def mtp_batch_autotune(b: Batch, stream=None):
     _check(load_library().mtp_batch_autotune(b.ptr, C.addressof(out), C.addressof(ng),
                                              _stream(stream)))
     return [tuple(out[5 * i + k] for k in range(5)) for i in range(ng.value)]
+
+
+# how a batch runs its rollouts (mtp_batch_set_rollout_mode)
+BATCH_ROLLOUT_GROUPS = 0
+BATCH_ROLLOUT_PERSISTENT_STAGED = 1
+BATCH_ROLLOUT_PERSISTENT_DIRECT = 2
+BATCH_ROLLOUT_NAMES = {0: "groups", 1: "persistent, staged", 2: "persistent, direct"}
+
+
+def mtp_batch_set_rollout_mode(b: Batch, mode: int) -> None:
+    _check(load_library().mtp_batch_set_rollout_mode(b.ptr, int(mode)))
+
+
+def mtp_batch_rollout_mode(b: Batch):
+    """(mode, [the autotuner's iteration ms per mode, 0 where not timed])."""
+    mode = C.c_int32()
+    ms = (C.c_double * 3)()
+    _check(load_library().mtp_batch_rollout_mode(b.ptr, C.addressof(mode), C.addressof(ms)))
+    return int(mode.value), [float(v) for v in ms]
 
 
 def mtp_batch_launches(b: Batch, iters: int = 1) -> int:

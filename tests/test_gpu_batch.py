@@ -76,6 +76,88 @@ def test_batch_matches_each_instance_alone(mtp, tune):
         mtp.mtp_destroy(h)
 
 
+def _mode_specs():
+    specs = _specs()
+    specs.append(W.chain(links=11, B=300, H=48))            # longer than the persistent launch covers
+    specs.append(W.legged(links=4, B=256, H=32, M=4, N=8))  # legged: its own launch
+    specs.append(W.pointmass(k=3, H=33, B=100))             # H * n not a multiple of 4: direct loads
+    return specs
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_persistent_rollouts_match_each_instance_alone(mtp, mode):
+    """The point-mass and chain rollouts of the whole batch in one persistent
+    launch (staged or direct tiles), beside the launches of the groups it
+    does not cover: every instance's u*, costs and next state are the bits
+    it gets alone."""
+    specs = _mode_specs()
+    rng = np.random.default_rng(1)
+    x0s = [rng.uniform(-0.2, 0.2, size=s["d"]).astype(np.float32) for s in specs]
+    iters = 3
+    handles = [mtp.mtp_create(s) for s in specs]
+    b = mtp.mtp_batch_create(handles)
+    groups_launches = mtp.mtp_batch_launches(b, 1)
+    mtp.mtp_batch_set_rollout_mode(b, mode)
+    assert mtp.mtp_batch_rollout_mode(b)[0] == mode
+    covered = len({(s["dyn"], s["n"] if s["dyn"] == "pointmass" else s["n_links"]) for s in specs
+                   if (s["dyn"] == "pointmass" and s["n"] <= 16) or
+                   (s["dyn"] == "chain" and s["n_links"] <= 9)})
+    assert mtp.mtp_batch_launches(b, 1) == groups_launches - covered + 1
+    x0 = torch.tensor(np.concatenate(x0s), device=DEV)
+    us = torch.empty(b.ustar_offset[-1], device=DEV)
+    mtp.mtp_batch_plan_step(b, x0, 1, us)          # direct launches
+    mtp.mtp_batch_plan_step(b, x0, iters - 1, us)  # graph replay
+    torch.cuda.synchronize()
+    for h in handles:
+        mtp.mtp_device_status(h)  # raises if a bounded wait gave up
+    ref = _run_alone(mtp, specs, x0s, iters)
+    for i, (h, (mu, sg, it, u, cost)) in enumerate(zip(handles, ref)):
+        mu_b, sg_b, it_b = mtp.mtp_get_state(h)
+        assert it_b == it == iters
+        assert np.array_equal(mu_b, mu), i
+        assert np.array_equal(sg_b, sg), i
+        lo, hi = b.ustar_offset[i], b.ustar_offset[i + 1]
+        assert np.array_equal(us[lo:hi].cpu().numpy(), u), i
+        cost_b = torch.as_tensor(mtp.mtp_get_buffers(h)["cost"], device=DEV).cpu().numpy()
+        assert np.array_equal(cost_b, cost), i
+    with pytest.raises(mtp.MtpError):
+        mtp.mtp_batch_set_rollout_mode(b, 3)
+    mtp.mtp_batch_destroy(b)
+    for h in handles:
+        mtp.mtp_destroy(h)
+
+
+def test_autotune_times_every_rollout_mode_and_restores_states(mtp):
+    """The autotuner times whole iterations in each rollout mode from saved
+    planner states and restores them: the tuned batch's next iterations are
+    still the bits each instance gets alone."""
+    specs = _mode_specs()
+    rng = np.random.default_rng(2)
+    x0s = [rng.uniform(-0.2, 0.2, size=s["d"]).astype(np.float32) for s in specs]
+    handles = [mtp.mtp_create(s) for s in specs]
+    b = mtp.mtp_batch_create(handles)
+    x0 = torch.tensor(np.concatenate(x0s), device=DEV)
+    us = torch.empty(b.ustar_offset[-1], device=DEV)
+    mtp.mtp_batch_plan_step(b, x0, 1, us)
+    mtp.mtp_batch_autotune(b)
+    mode, ms = mtp.mtp_batch_rollout_mode(b)
+    assert mode in (0, 1, 2) and all(v > 0 for v in ms)
+    assert ms[mode] == min(ms)
+    mtp.mtp_batch_plan_step(b, x0, 2, us)
+    torch.cuda.synchronize()
+    ref = _run_alone(mtp, specs, x0s, 3)
+    for i, (h, (mu, sg, it, u, cost)) in enumerate(zip(handles, ref)):
+        mu_b, sg_b, it_b = mtp.mtp_get_state(h)
+        assert it_b == 3
+        assert np.array_equal(mu_b, mu), i
+        assert np.array_equal(sg_b, sg), i
+        lo, hi = b.ustar_offset[i], b.ustar_offset[i + 1]
+        assert np.array_equal(us[lo:hi].cpu().numpy(), u), i
+    mtp.mtp_batch_destroy(b)
+    for h in handles:
+        mtp.mtp_destroy(h)
+
+
 def test_batch_rejects_bad_input(mtp):
     h = mtp.mtp_create(W.pointmass(B=64, E=8))
     with pytest.raises(mtp.MtpError):
