@@ -359,8 +359,9 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
  *   mass (up to 16 axes) and every chain (up to 9 links) of the batch run in
  *   one persistent launch, after all instances' candidates are made: each
  *   warp takes warp tiles of 32 candidates of one instance from a device
- *   counter, longest expected rollout first (H times the group's time per
- *   step), with their controls staged through shared memory 4 steps at a
+ *   counter, group by group (the longest group first, within a group the
+ *   longest expected rollout first: H times the group's time per step),
+ *   with their controls staged through shared memory 4 steps at a
  *   time where the instance's rows allow it (_STAGED) or loaded directly
  *   (_DIRECT).  Legged robots and longer chains keep their own launches
  *   beside it.  The launch is counted as one kernel by mtp_batch_launches.

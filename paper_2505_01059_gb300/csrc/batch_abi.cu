@@ -75,8 +75,8 @@ struct BatchTables {
   float** d_ustar_src = nullptr;
   int* d_x0_off = nullptr;
   int* d_us_off = nullptr;
-  // the persistent rollout launch: one entry per instance it covers,
-  // longest expected rollout first (PersistArgs)
+  // the persistent rollout launch: one entry per instance it covers, group
+  // by group, longest expected rollout first within a group (PersistArgs)
   int* d_p_order = nullptr;
   int* d_p_wstart = nullptr;
   int* d_p_code = nullptr;
@@ -406,7 +406,7 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
     return steps;
   });
   // the persistent launch's entries: every instance of a covered group,
-  // longest warp tile first (H steps at the group's time per step)
+  // ordered below (H steps at the group's time per step sets a tile's length)
   {
     b->covered.assign(b->groups.size(), 0);
     struct Entry {
@@ -435,7 +435,28 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
                        g.model_first + j, (h->dm.B + 31) / 32});
       }
     }
-    std::stable_sort(ent.begin(), ent.end(), [](const Entry& x, const Entry& y) { return x.est > y.est; });
+    // groups in their launch order (longest group first), and within a group
+    // the longest tiles first: warps that run at the same time then mostly
+    // run the same body, which keeps the instruction cache warm (with every
+    // tile ordered by length alone, warps of one SM ran different bodies and
+    // half of their stall samples were instruction fetches)
+    std::vector<int> group_rank(b->groups.size(), 0);
+    for (size_t r = 0; r < b->launch_order.size(); ++r) group_rank[b->launch_order[r]] = (int)r;
+    std::vector<int> entry_group;
+    for (const Entry& en : ent) {
+      int gi = 0;
+      while (!(en.pos >= b->groups[gi].first && en.pos < b->groups[gi].first + b->groups[gi].count)) ++gi;
+      entry_group.push_back(group_rank[gi]);
+    }
+    std::vector<int> idx(ent.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = (int)k;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+      if (entry_group[x] != entry_group[y]) return entry_group[x] < entry_group[y];
+      return ent[x].est > ent[y].est;
+    });
+    std::vector<Entry> sorted;
+    for (int k : idx) sorted.push_back(ent[k]);
+    ent.swap(sorted);
     int w = 0;
     for (size_t k = 0; k < ent.size(); ++k) {
       hv.d_p_order[k] = ent[k].pos;

@@ -260,7 +260,8 @@ cudaError_t launch_rollout_legged_batch(const RolloutArgs* d_ra, const LeggedMod
 // The rollouts of many instances in one persistent launch
 // (rollout_persist.cu): warp tiles of 32 candidates, taken in order from a
 // device counter by every warp of the launch.  Entry k of the tables is one
-// instance, longest expected rollout first: its position in the batch's
+// instance, group by group and within a group longest expected rollout
+// first: its position in the batch's
 // RolloutArgs, its model, its code (dynamics | dimension << 8 | staged << 16)
 // and its first warp tile wstart[k] (count + 1 entries).  Point masses of up
 // to kPersistMaxAxes axes and chains of up to kPersistMaxLinks links.

@@ -2,15 +2,16 @@
 // launch (Alg. 2 rollout fused with the Eq. 2 cost, rollout_kernels.cuh).
 //
 // Work items are warp tiles: 32 consecutive candidates of one instance.  The
-// instances are listed longest expected rollout first (H times the time per
-// step of their dynamics and dimension) and numbered by a prefix of their
-// warp tiles, so item w belongs to the instance whose range holds w.  Each
+// instances are listed group by group, the longest group first and within a
+// group the longest expected rollout first (H times the time per step of the
+// group's dynamics and dimension), and numbered by a prefix of their warp
+// tiles, so item w belongs to the instance whose range holds w.  Each
 // warp of the launch repeatedly takes the next item from a device counter
 // (one atomic add per item), looks its instance up by binary search, and
 // runs that tile's rollout: a point mass of K axes or a planar chain of L
 // links, with direct control loads or staged 4 steps at a time.  A warp
-// therefore moves between instances of different sizes and dynamics, and
-// the longest tiles start first, so the launch drains evenly.  The bodies
+// therefore moves between instances of different sizes and dynamics, while
+// the warps running at one time mostly run the same body.  The bodies
 // are the per-candidate rollouts of the other kernels (the same templates),
 // so every cost is the same bits as in a per-group or standalone launch.
 //
@@ -24,13 +25,18 @@
 // slower on the batch of 256.  The launch is bounded at three 128-thread
 // CTAs per SM, i.e. at most 170 registers per thread (168 used, no spills).
 //
-// Measured on GB300 against the per-group launches (whole iteration of the
-// 256-instance batch, the autotuner's timing): 3.35-3.49 ms with staged
-// tiles and 3.46-3.48 ms with direct loads, against 3.05-3.15 ms with each
-// group's rollout launched in its own stream's chain.  The persistent launch
-// waits for every covered instance's candidates, so it loses the overlap of
-// one group's generation with another's rollout, and its register bound is
-// the largest body's for every tile.
+// Measured on GB300 on the 256-instance batch (whole iterations, the
+// autotuner's timing): 2.85-2.89 ms with staged tiles and 3.40-3.44 ms with
+// direct loads, against 2.92-3.10 ms with each group's rollout launched in
+// its own stream's chain.  The order of the tiles matters: sorted by length
+// alone across all groups, the warps of an SM ran different bodies at once,
+// half of their stall samples were instruction fetches, and the staged
+// launch took 3.36-3.47 ms; tiles are therefore taken group by group
+// (longest group first, longest tiles first within it).  The launch waits
+// for every covered instance's candidates, so it gives up the overlap of
+// one group's generation with another's rollout; on this batch the
+// iteration is then 1.12 ms of generation, 1.54 ms of this launch and
+// 0.18 ms of selection and update.
 #include <map>
 #include <mutex>
 
