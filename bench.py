@@ -150,11 +150,15 @@ BATCH_KERNEL_FILE = {"pointmass": "rollout_pm_batch.cu", "chain": "rollout_chain
 
 def _code_text(path: str) -> str:
     """A C / CUDA source with its comments removed and its whitespace
-    collapsed: what the compiler sees, less the prose."""
+    collapsed: what the compiler sees, less the prose.  Of the public header
+    only the types, constants and macros count: its function prototypes are
+    the host interface, which no kernel is compiled from."""
     with open(path) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
     text = re.sub(r"//[^\n]*", " ", text)
+    if path.endswith(os.path.join("include", "mtp.h")):
+        text = re.sub(r"\b(?:mtp_status|const\s+char\s*\*)\s*\w+\s*\([^;{]*\)\s*;", " ", text)
     return " ".join(text.split())
 
 
@@ -544,7 +548,24 @@ def run_batch_arms(args, mtp, dev, pg, world, rank) -> dict:
 
     # group rollouts, each alone, for the roofline
     res["roofline"], res["rollout_groups"] = batch_rollout_roofline(mtp, b, specs, device_sms(dev.index))
-    peak, _ = fp32_peak(peaks().get("sm_max_mhz", 2070.0), device_sms(dev.index))
+    peak, note = fp32_peak(peaks().get("sm_max_mhz", 2070.0), device_sms(dev.index))
+    if mode != 0:
+        # the iteration's rollouts are the persistent launch: it is the dominant kernel
+        p_ms, p_steps = mtp.mtp_batch_persistent_time(b, reps=5)
+        covered = [s for s in specs if (s["dyn"] == "pointmass" and s["n"] <= 16) or
+                   (s["dyn"] == "chain" and s["n_links"] <= 9)]
+        assert sum(s["B"] * s["H"] for s in covered) == p_steps
+        fl = sum(flops_per_step(s) * s["B"] * s["H"] for s in covered)
+        achieved = fl / (p_ms / 1e3) / 1e12
+        res["roofline"] = {
+            "bound": "alu", "kernel": "k_rollout_persistent", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": profiled_traffic("rollout_persist.cu", "rollout_persist_batch64.txt",
+                                        key="dram_bytes_per_launch_batch256"),
+            "flops_per_launch": fl, "duration_us": p_ms * 1e3, "rollout_steps": p_steps,
+            "timing": "CUDA events around the persistent rollout launch run alone on its stream "
+                      "(5 launches averaged), after the timed region",
+            "peak_note": note + " (of measured clock)"}
     flops_iter = sum(flops_per_step(s) * s["B"] * s["H"] for s in specs)
     res["whole_step_fp32"] = {"achieved": flops_iter / (res["ms_per_step"] / 1e3) / 1e12,
                               "peak": peak, "unit": "TFLOP/s",

@@ -378,6 +378,15 @@ mtp_status mtp_batch_set_rollout_mode(mtp_batch* b, int32_t mode);
  * not timed that mode; modes that cover no instance are not timed). */
 mtp_status mtp_batch_rollout_mode(const mtp_batch* b, int32_t* mode, double* ms3);
 
+/* Device time of the persistent rollout launch alone (the covered groups'
+ * rollouts, Alg. 2 rollout fused with the cost, Eq. 2) on `stream`, with
+ * staged tiles when the batch's mode is MTP_BATCH_ROLLOUT_PERSISTENT_STAGED
+ * and direct loads otherwise, averaged over `reps` launches timed with CUDA
+ * events: *ms (0 when the launch covers no instance).  *steps receives the
+ * rollout steps (sum of B * H) it covers.  Synchronous; overwrites the
+ * covered handles' cost buffers (with the same values). */
+mtp_status mtp_batch_persistent_time(mtp_batch* b, int32_t reps, double* ms, int64_t* steps, void* stream);
+
 /* mtp_shift(h, k) of every instance of the batch in one launch. */
 mtp_status mtp_batch_shift(mtp_batch* b, int32_t k, void* stream);
 

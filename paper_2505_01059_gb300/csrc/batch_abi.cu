@@ -976,6 +976,43 @@ mtp_status mtp_batch_rollout_mode(const mtp_batch* b, int32_t* mode, double* ms3
   return MTP_OK;
 }
 
+mtp_status mtp_batch_persistent_time(mtp_batch* b, int32_t reps, double* ms, int64_t* steps, void* stream) {
+  if (!b || reps < 1 || !ms) return batch_fail(b, MTP_ERR_INVALID_ARG, "persistent_time: bad argument");
+  if (b->count < 1) return batch_fail(b, MTP_ERR_INVALID_ARG, "persistent_time: batch never filled");
+  DeviceGuard guard(b->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  *ms = 0.0;
+  long long covered_steps = 0;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    if (!b->covered[gi]) continue;
+    const BatchGroup& g = b->groups[gi];
+    for (int j = 0; j < g.count; ++j)
+      covered_steps += (long long)b->hs_sorted[g.first + j]->dm.B * b->hs_sorted[g.first + j]->dm.H;
+  }
+  if (steps) *steps = covered_steps;
+  if (b->p_total_warps <= 0) return MTP_OK;
+  const bool staged = b->rollout_mode == MTP_BATCH_ROLLOUT_PERSISTENT_STAGED;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->t.copied, 0);
+  double sum = 0.0;
+  for (int rep = 0; rep < reps && e == cudaSuccess; ++rep) {
+    if ((e = cudaEventRecord(t0, s))) break;
+    if ((e = launch_rollout_persistent(persist_args(b, staged), b->p_blocks[staged ? 0 : 1], s))) break;
+    if ((e = cudaEventRecord(t1, s))) break;
+    if ((e = cudaEventSynchronize(t1))) break;
+    float v = 0.f;
+    if ((e = cudaEventElapsedTime(&v, t0, t1))) break;
+    sum += v;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e != cudaSuccess) return batch_fail(b, MTP_ERR_CUDA, std::string("persistent_time: ") + cudaGetErrorString(e));
+  *ms = sum / reps;
+  return MTP_OK;
+}
+
 mtp_status mtp_batch_rollout_times(mtp_batch* b, int32_t reps, double* ms_out, int32_t* info_out,
                                    int32_t max_groups, int32_t* n_groups, void* stream) {
   if (!b || reps < 1 || !n_groups) return MTP_ERR_INVALID_ARG;

@@ -45,7 +45,7 @@ EXPORTS = [
     "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_layout", "mtp_batch_plan_step",
     "mtp_batch_autotune", "mtp_batch_reserve", "mtp_batch_fill", "mtp_batch_shift",
     "mtp_batch_launches", "mtp_batch_rollout_times", "mtp_batch_set_rollout_mode",
-    "mtp_batch_rollout_mode", "mtp_device_status", "mtp_cost_entropy",
+    "mtp_batch_rollout_mode", "mtp_batch_persistent_time", "mtp_device_status", "mtp_cost_entropy",
     "mtp_selftest_bounded_wait",
     "mtp_problem_device_bytes", "mtp_server_create", "mtp_server_destroy", "mtp_server_register",
     "mtp_submit", "mtp_poll", "mtp_server_get_stats", "mtp_server_last_error",
@@ -157,6 +157,7 @@ def load_library(path: str = LIB_PATH):
         "mtp_batch_launches": (i32, [vp, i32, vp]),
         "mtp_batch_set_rollout_mode": (i32, [vp, i32]),
         "mtp_batch_rollout_mode": (i32, [vp, vp, vp]),
+        "mtp_batch_persistent_time": (i32, [vp, i32, vp, vp, vp]),
         "mtp_batch_rollout_times": (i32, [vp, i32, vp, vp, i32, vp, vp]),
         "mtp_batch_reserve": (i32, [i32, C.POINTER(vp)]),
         "mtp_batch_fill": (i32, [vp, C.POINTER(vp), i32, vp]),
@@ -626,6 +627,15 @@ def mtp_batch_rollout_mode(b: Batch):
     ms = (C.c_double * 3)()
     _check(load_library().mtp_batch_rollout_mode(b.ptr, C.addressof(mode), C.addressof(ms)))
     return int(mode.value), [float(v) for v in ms]
+
+
+def mtp_batch_persistent_time(b: Batch, reps: int = 5, stream=None):
+    """(ms, rollout steps) of the persistent rollout launch timed alone."""
+    ms = C.c_double()
+    steps = C.c_int64()
+    _check(load_library().mtp_batch_persistent_time(b.ptr, int(reps), C.addressof(ms),
+                                                    C.addressof(steps), _stream(stream)))
+    return float(ms.value), int(steps.value)
 
 
 def mtp_batch_launches(b: Batch, iters: int = 1) -> int:
