@@ -120,6 +120,12 @@ def test_persistent_rollouts_match_each_instance_alone(mtp, mode):
         assert np.array_equal(us[lo:hi].cpu().numpy(), u), i
         cost_b = torch.as_tensor(mtp.mtp_get_buffers(h)["cost"], device=DEV).cpu().numpy()
         assert np.array_equal(cost_b, cost), i
+    # the persistent launch timed alone covers the point-mass and chain rollouts
+    ms, steps = mtp.mtp_batch_persistent_time(b, reps=2)
+    assert ms > 0
+    assert steps == sum(s["B"] * s["H"] for s in specs
+                        if (s["dyn"] == "pointmass" and s["n"] <= 16) or
+                        (s["dyn"] == "chain" and s["n_links"] <= 9))
     with pytest.raises(mtp.MtpError):
         mtp.mtp_batch_set_rollout_mode(b, 3)
     mtp.mtp_batch_destroy(b)
