@@ -49,7 +49,7 @@ FP32_LANES_PER_SM = 128
 ROLLOUT_KERNEL = {"pointmass": "k_rollout_pm", "chain": "k_rollout_chain",
                   "legged": "k_rollout_legged"}
 DYN_NAMES = {0: "pointmass", 1: "chain", 2: "legged"}
-ROLLOUT_MODES = {"groups": 0, "persistent-staged": 1, "persistent-direct": 2}
+ROLLOUT_MODES = {"groups": 0, "persistent-staged": 1, "persistent-direct": 2, "persistent-split": 3}
 
 
 def workload(name: str, B: int | None = None) -> dict:

@@ -342,8 +342,9 @@ mtp_status mtp_batch_plan_step(mtp_batch* b, const float* d_x0, int32_t iters, f
  * legged group keeps its fixed tile.  Writes (dynamics, dimension, block,
  * chunk, candidates per thread) to tiles_out (5 * groups entries, may be
  * NULL) and the number of groups to n_groups.  Then it picks the rollout
- * mode (mtp_batch_set_rollout_mode) by timing whole iterations in each mode
- * (best of three after one untimed run), with every instance's planner state
+ * mode (mtp_batch_set_rollout_mode) by timing whole iterations in each mode,
+ * each captured as the CUDA graph that mtp_batch_plan_step replays (best of
+ * three replays after one untimed one), with every instance's planner state
  * (mean, spread, iteration counter) saved before and restored after, so the
  * instances' next iteration is the one they would have run.  Synchronous;
  * overwrites the handles' candidate, cost, elite and u* buffers, and
@@ -365,23 +366,31 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
  *   time where the instance's rows allow it (_STAGED) or loaded directly
  *   (_DIRECT).  Legged robots and longer chains keep their own launches
  *   beside it.  The launch is counted as one kernel by mtp_batch_launches.
+ * MTP_BATCH_ROLLOUT_PERSISTENT_SPLIT: the same with staged tiles, in two
+ *   persistent launches split at a group boundary near half of the expected
+ *   rollout work: the first starts as soon as its groups' candidates are made
+ *   (their generation on high-priority streams) and leaves one CTA per SM to
+ *   the second part's generation, which overlaps it; the second starts when
+ *   its own candidates are made.
  * Results are the same bits in every mode.  The mode takes effect at the
  * next mtp_batch_plan_step (captured graphs are dropped).  Errors:
  * MTP_ERR_INVALID_ARG for an unknown mode. */
 #define MTP_BATCH_ROLLOUT_GROUPS 0
 #define MTP_BATCH_ROLLOUT_PERSISTENT_STAGED 1
 #define MTP_BATCH_ROLLOUT_PERSISTENT_DIRECT 2
+#define MTP_BATCH_ROLLOUT_PERSISTENT_SPLIT 3
 mtp_status mtp_batch_set_rollout_mode(mtp_batch* b, int32_t mode);
 
-/* The batch's current rollout mode, and (ms3, 3 entries, may be NULL) the
- * autotuner's iteration time of each mode in milliseconds (0 where it has
- * not timed that mode; modes that cover no instance are not timed). */
-mtp_status mtp_batch_rollout_mode(const mtp_batch* b, int32_t* mode, double* ms3);
+/* The batch's current rollout mode, and (ms4, 4 entries, one per mode, may
+ * be NULL) the autotuner's iteration time of each mode in milliseconds (0
+ * where it has not timed that mode; modes that cover no instance are not
+ * timed). */
+mtp_status mtp_batch_rollout_mode(const mtp_batch* b, int32_t* mode, double* ms4);
 
 /* Device time of the persistent rollout launch alone (the covered groups'
  * rollouts, Alg. 2 rollout fused with the cost, Eq. 2) on `stream`, with
- * staged tiles when the batch's mode is MTP_BATCH_ROLLOUT_PERSISTENT_STAGED
- * and direct loads otherwise, averaged over `reps` launches timed with CUDA
+ * staged tiles unless the batch's mode is MTP_BATCH_ROLLOUT_PERSISTENT_DIRECT
+ * (one launch over all covered instances in every mode), averaged over `reps` launches timed with CUDA
  * events: *ms (0 when the launch covers no instance).  *steps receives the
  * rollout steps (sum of B * H) it covers.  Synchronous; overwrites the
  * covered handles' cost buffers (with the same values). */

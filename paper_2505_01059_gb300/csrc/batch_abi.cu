@@ -121,7 +121,7 @@ size_t layout_tables(BatchTables* t, unsigned char* base, int count, int n_pm, i
   take(&d->d_p_wstart, count + 1);
   take(&d->d_p_code, count);
   take(&d->d_p_model, count);
-  take(&d->d_p_head, 1);
+  take(&d->d_p_head, 2);
   return off;
 }
 
@@ -155,10 +155,17 @@ struct mtp_batch {
   int rollout_mode = MTP_BATCH_ROLLOUT_GROUPS;
   std::vector<char> covered;    // per group: its rollouts are in the persistent launch
   int p_count = 0, p_total_warps = 0;
+  // the two-launch persistent mode: entries [0, p_split) and [p_split,
+  // p_count), split at a group boundary near half of the expected work;
+  // groups of launch rank < p_split_rank are in the first launch
+  int p_split = 0, p_split_warps = 0, p_split_rank = 0;
+  cudaStream_t persist_stream[2] = {nullptr, nullptr};
+  cudaEvent_t persist_ev2 = nullptr;
+  cudaStream_t group_stream_hi[kMaxGroups] = {};  // high priority: the first launch's generation
   size_t p_warp_bytes = 0;      // staged tiles' shared memory per warp (0: none stageable)
   int p_blocks[2] = {0, 0};     // resident CTAs per SM: staged mode, direct mode
   cudaEvent_t persist_ev = nullptr;
-  double mode_ms[3] = {0, 0, 0};  // the autotuner's iteration time per mode (0: not timed)
+  double mode_ms[4] = {0, 0, 0, 0};  // the autotuner's iteration time per mode (0: not timed)
   std::string err;
 };
 
@@ -215,6 +222,11 @@ void free_batch(mtp_batch* b) {
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->persist_ev) cudaEventDestroy(b->persist_ev);
+  if (b->persist_ev2) cudaEventDestroy(b->persist_ev2);
+  for (int k = 0; k < 2; ++k)
+    if (b->persist_stream[k]) cudaStreamDestroy(b->persist_stream[k]);
+  for (int g = 0; g < kMaxGroups; ++g)
+    if (b->group_stream_hi[g]) cudaStreamDestroy(b->group_stream_hi[g]);
   delete b;
 }
 
@@ -230,7 +242,10 @@ cudaError_t alloc_batch(mtp_batch* b, int cap) {
       (e = cudaEventRecord(t.copied, 0)) ||
       (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) ||
       (e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)) ||
-      (e = cudaEventCreateWithFlags(&b->persist_ev, cudaEventDisableTiming)))
+      (e = cudaEventCreateWithFlags(&b->persist_ev, cudaEventDisableTiming)) ||
+      (e = cudaEventCreateWithFlags(&b->persist_ev2, cudaEventDisableTiming)) ||
+      (e = cudaStreamCreateWithFlags(&b->persist_stream[0], cudaStreamNonBlocking)) ||
+      (e = cudaStreamCreateWithFlags(&b->persist_stream[1], cudaStreamNonBlocking)))
     return e;
   return cudaSuccess;
 }
@@ -455,7 +470,11 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
       return ent[x].est > ent[y].est;
     });
     std::vector<Entry> sorted;
-    for (int k : idx) sorted.push_back(ent[k]);
+    std::vector<int> sorted_group;
+    for (int k : idx) {
+      sorted.push_back(ent[k]);
+      sorted_group.push_back(entry_group[k]);
+    }
     ent.swap(sorted);
     int w = 0;
     for (size_t k = 0; k < ent.size(); ++k) {
@@ -466,7 +485,22 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
       w += ent[k].warps;
     }
     hv.d_p_wstart[ent.size()] = w;
-    *hv.d_p_head = 0u;
+    hv.d_p_head[0] = hv.d_p_head[1] = 0u;
+    {
+      double total = 0.0, acc = 0.0;
+      for (const Entry& en : ent) total += en.est * en.warps;
+      b->p_split = (int)ent.size();
+      b->p_split_rank = (int)b->groups.size();
+      for (size_t k = 0; k < ent.size(); ++k) {
+        if (k > 0 && sorted_group[k] != sorted_group[k - 1] && acc >= 0.5 * total) {
+          b->p_split = (int)k;
+          b->p_split_rank = sorted_group[k];
+          break;
+        }
+        acc += ent[k].est * ent[k].warps;
+      }
+      b->p_split_warps = hv.d_p_wstart[b->p_split];
+    }
     b->p_count = (int)ent.size();
     b->p_total_warps = w;
     b->p_warp_bytes = persist_warp_bytes(max_pm, max_links);
@@ -496,8 +530,11 @@ cudaError_t fill_batch(mtp_batch* b, mtp_handle* const* handles, int count, cuda
   b->count = count;
   for (size_t g = 0; g < b->groups.size(); ++g) {
     if (!b->group_stream[g]) {
+      int lo = 0, hi = 0;
       if ((e = cudaStreamCreateWithFlags(&b->group_stream[g], cudaStreamNonBlocking)) ||
-          (e = cudaEventCreateWithFlags(&b->group_done[g], cudaEventDisableTiming)))
+          (e = cudaEventCreateWithFlags(&b->group_done[g], cudaEventDisableTiming)) ||
+          (e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) ||
+          (e = cudaStreamCreateWithPriority(&b->group_stream_hi[g], cudaStreamNonBlocking, hi)))
         return e;
     }
   }
@@ -526,7 +563,9 @@ cudaError_t launch_group(const mtp_batch* b, const BatchGroup& g, int block, int
 // its instances, its rollouts, one selection block per instance, the update.
 // Groups overlap one another (one group's generation fills the issue slots
 // that the others' latency-bound rollouts leave idle).
-PersistArgs persist_args(const mtp_batch* b, bool staged) {
+// part 0: every entry; part 1 / 2: the first / second launch of the
+// two-launch mode
+PersistArgs persist_args(const mtp_batch* b, bool staged, int part = 0) {
   const BatchTables& t = b->t;
   PersistArgs p{};
   p.ra = t.d_ra;
@@ -539,7 +578,22 @@ PersistArgs persist_args(const mtp_batch* b, bool staged) {
   p.head = t.d_p_head;
   p.count = b->p_count;
   p.total_warps = b->p_total_warps;
+  p.w_base = 0;
   p.warp_bytes = staged ? b->p_warp_bytes : 0;
+  if (part == 1) {
+    p.count = b->p_split;
+    p.total_warps = b->p_split_warps;
+  } else if (part == 2) {
+    const int k = b->p_split;
+    p.order += k;
+    p.wstart += k;
+    p.code += k;
+    p.model += k;
+    p.head += 1;
+    p.count = b->p_count - k;
+    p.total_warps = b->p_total_warps - b->p_split_warps;
+    p.w_base = b->p_split_warps;
+  }
   return p;
 }
 
@@ -551,13 +605,17 @@ cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s);
 // (the groups it does not cover keep their own rollout launch); then each
 // covered group selects and updates on its stream.  Staged tiles, or every
 // tile with direct loads (`staged` false).
-cudaError_t enqueue_batch_iteration_persistent(mtp_batch* b, cudaStream_t s, bool staged) {
+cudaError_t enqueue_batch_iteration_persistent(mtp_batch* b, cudaStream_t s, bool staged, bool split) {
   cudaError_t e;
   const BatchTables& t = b->t;
+  split = split && b->p_split > 0 && b->p_split < b->p_count;
+  std::vector<int> rank(b->groups.size(), 0);
+  for (size_t r = 0; r < b->launch_order.size(); ++r) rank[b->launch_order[r]] = (int)r;
+  auto first_part = [&](int gi) { return split && rank[gi] < b->p_split_rank; };
   if ((e = cudaEventRecord(b->fork_ev, s))) return e;
   for (const int gi : b->launch_order) {
     const BatchGroup& g = b->groups[gi];
-    cudaStream_t gs = b->group_stream[gi];
+    cudaStream_t gs = first_part(gi) ? b->group_stream_hi[gi] : b->group_stream[gi];
     const int f = g.first;
     if ((e = cudaStreamWaitEvent(gs, b->fork_ev, 0))) return e;
     if ((e = launch_graph_Z_batch(t.d_cand + f, t.d_Z + f, t.d_z_start + f, g.count, g.z_blocks, gs))) return e;
@@ -575,16 +633,34 @@ cudaError_t enqueue_batch_iteration_persistent(mtp_batch* b, cudaStream_t s, boo
     }
     if ((e = cudaEventRecord(b->group_done[gi], gs))) return e;
   }
-  for (size_t gi = 0; gi < b->groups.size(); ++gi)
-    if (b->covered[gi] && (e = cudaStreamWaitEvent(s, b->group_done[gi], 0))) return e;
-  if ((e = launch_rollout_persistent(persist_args(b, staged), b->p_blocks[staged ? 0 : 1], s))) return e;
-  if ((e = cudaEventRecord(b->persist_ev, s))) return e;
+  if (!split) {
+    for (size_t gi = 0; gi < b->groups.size(); ++gi)
+      if (b->covered[gi] && (e = cudaStreamWaitEvent(s, b->group_done[gi], 0))) return e;
+    if ((e = launch_rollout_persistent(persist_args(b, staged), b->p_blocks[staged ? 0 : 1], s))) return e;
+    if ((e = cudaEventRecord(b->persist_ev, s))) return e;
+  } else {
+    // the first launch starts when the first part's candidates are made and
+    // keeps one CTA per SM free for the second part's generation; the second
+    // starts when its own candidates are made
+    cudaStream_t ps[2] = {b->persist_stream[0], b->persist_stream[1]};
+    cudaEvent_t pev[2] = {b->persist_ev, b->persist_ev2};
+    for (int part = 0; part < 2; ++part) {
+      if ((e = cudaStreamWaitEvent(ps[part], b->fork_ev, 0))) return e;
+      for (size_t gi = 0; gi < b->groups.size(); ++gi)
+        if (b->covered[gi] && first_part((int)gi) == (part == 0) &&
+            (e = cudaStreamWaitEvent(ps[part], b->group_done[gi], 0)))
+          return e;
+      const int blocks = part == 0 ? std::max(1, b->p_blocks[staged ? 0 : 1] - 1) : b->p_blocks[staged ? 0 : 1];
+      if ((e = launch_rollout_persistent(persist_args(b, staged, part + 1), blocks, ps[part]))) return e;
+      if ((e = cudaEventRecord(pev[part], ps[part]))) return e;
+    }
+  }
   for (const int gi : b->launch_order) {
     if (!b->covered[gi]) continue;
     const BatchGroup& g = b->groups[gi];
-    cudaStream_t gs = b->group_stream[gi];
+    cudaStream_t gs = first_part(gi) ? b->group_stream_hi[gi] : b->group_stream[gi];
     const int f = g.first;
-    if ((e = cudaStreamWaitEvent(gs, b->persist_ev, 0))) return e;
+    if ((e = cudaStreamWaitEvent(gs, split && !first_part(gi) ? b->persist_ev2 : b->persist_ev, 0))) return e;
     if ((e = launch_select_batch(t.d_sel + f, g.count, g.sel_smem, gs))) return e;
     if ((e = launch_update_batch(t.d_upd + f, t.d_warp_start + f, g.count, g.upd_threads, gs))) return e;
     if ((e = cudaEventRecord(b->group_done[gi], gs))) return e;
@@ -598,7 +674,8 @@ cudaError_t enqueue_batch_iteration(mtp_batch* b, cudaStream_t s) {
   cudaError_t e;
   const BatchTables& t = b->t;
   if (b->rollout_mode != MTP_BATCH_ROLLOUT_GROUPS && b->p_total_warps > 0)
-    return enqueue_batch_iteration_persistent(b, s, b->rollout_mode == MTP_BATCH_ROLLOUT_PERSISTENT_STAGED);
+    return enqueue_batch_iteration_persistent(b, s, b->rollout_mode != MTP_BATCH_ROLLOUT_PERSISTENT_DIRECT,
+                                              b->rollout_mode == MTP_BATCH_ROLLOUT_PERSISTENT_SPLIT);
   if ((e = cudaEventRecord(b->fork_ev, s))) return e;
   for (const int gi : b->launch_order) {
     const BatchGroup& g = b->groups[gi];
@@ -645,7 +722,9 @@ cudaError_t run_batch(mtp_batch* b, const float* d_x0, int iters, float* d_ustar
         if (e != cudaSuccess) return e;
         if (e2 != cudaSuccess) return e2;
         cudaGraphExec_t exec;
-        e = cudaGraphInstantiate(&exec, graph, 0);
+        // kernel nodes keep the priority of the stream they were captured
+        // from (the two-launch persistent mode's first-part generation)
+        e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return e;
         it = b->graphs.emplace(chunk, exec).first;
@@ -711,9 +790,10 @@ struct SavedStates {
   }
 };
 
-// Times one iteration in each rollout mode (best of three after one untimed
-// run, every run from the saved states) and keeps the fastest; the states
-// are restored afterwards.
+// Times one iteration in each rollout mode as a captured graph, the form
+// mtp_batch_plan_step replays (best of three after one untimed replay, every
+// replay from the saved states), and keeps the fastest; the states are
+// restored afterwards.
 cudaError_t tune_rollout_mode(mtp_batch* b) {
   cudaStream_t s = b->cap_stream;
   SavedStates st;
@@ -723,21 +803,30 @@ cudaError_t tune_rollout_mode(mtp_batch* b) {
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   int best_mode = MTP_BATCH_ROLLOUT_GROUPS;
   double best = 1e30;
-  for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+  for (int mode = 0; mode < 4 && e == cudaSuccess; ++mode) {
     b->mode_ms[mode] = 0.0;
     if (mode != MTP_BATCH_ROLLOUT_GROUPS && b->p_total_warps <= 0) continue;
     b->rollout_mode = mode;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) break;
+    e = enqueue_batch_iteration(b, s);
+    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+    if (graph) cudaGraphDestroy(graph);
     float ms_min = 1e30f;
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
       if ((e = st.copy(b, s, false))) break;
       if ((e = cudaEventRecord(t0, s))) break;
-      if ((e = enqueue_batch_iteration(b, s))) break;
+      if ((e = cudaGraphLaunch(exec, s))) break;
       if ((e = cudaEventRecord(t1, s))) break;
       if ((e = cudaEventSynchronize(t1))) break;
       float ms = 0.f;
       if ((e = cudaEventElapsedTime(&ms, t0, t1))) break;
       if (rep > 0) ms_min = std::min(ms_min, ms);
     }
+    if (exec) cudaGraphExecDestroy(exec);
     b->mode_ms[mode] = ms_min;
     if (ms_min < best) {
       best = ms_min;
@@ -947,7 +1036,9 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
 mtp_status mtp_batch_launches(const mtp_batch* b, int32_t iters, int32_t* launches) {
   if (!b || !launches || iters < 1 || b->count < 1) return MTP_ERR_INVALID_ARG;
   const bool persistent = b->rollout_mode != MTP_BATCH_ROLLOUT_GROUPS && b->p_total_warps > 0;
-  long long per_iter = persistent ? 1 : 0;
+  const bool split = b->rollout_mode == MTP_BATCH_ROLLOUT_PERSISTENT_SPLIT && b->p_split > 0 &&
+                     b->p_split < b->p_count;
+  long long per_iter = persistent ? (split ? 2 : 1) : 0;
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
     const BatchGroup& g = b->groups[gi];
     per_iter += (g.z_blocks > 0) + (g.cand_blocks > 0) + (g.local_blocks > 0) + (g.tc_count > 0);
@@ -958,7 +1049,7 @@ mtp_status mtp_batch_launches(const mtp_batch* b, int32_t iters, int32_t* launch
 }
 
 mtp_status mtp_batch_set_rollout_mode(mtp_batch* b, int32_t mode) {
-  if (!b || mode < MTP_BATCH_ROLLOUT_GROUPS || mode > MTP_BATCH_ROLLOUT_PERSISTENT_DIRECT)
+  if (!b || mode < MTP_BATCH_ROLLOUT_GROUPS || mode > MTP_BATCH_ROLLOUT_PERSISTENT_SPLIT)
     return batch_fail(b, MTP_ERR_INVALID_ARG, "batch_set_rollout_mode: unknown mode");
   if (b->rollout_mode != mode) {
     b->rollout_mode = mode;
@@ -968,11 +1059,11 @@ mtp_status mtp_batch_set_rollout_mode(mtp_batch* b, int32_t mode) {
   return MTP_OK;
 }
 
-mtp_status mtp_batch_rollout_mode(const mtp_batch* b, int32_t* mode, double* ms3) {
+mtp_status mtp_batch_rollout_mode(const mtp_batch* b, int32_t* mode, double* ms4) {
   if (!b || !mode) return MTP_ERR_INVALID_ARG;
   *mode = b->rollout_mode;
-  if (ms3)
-    for (int k = 0; k < 3; ++k) ms3[k] = b->mode_ms[k];
+  if (ms4)
+    for (int k = 0; k < 4; ++k) ms4[k] = b->mode_ms[k];
   return MTP_OK;
 }
 
@@ -991,7 +1082,7 @@ mtp_status mtp_batch_persistent_time(mtp_batch* b, int32_t reps, double* ms, int
   }
   if (steps) *steps = covered_steps;
   if (b->p_total_warps <= 0) return MTP_OK;
-  const bool staged = b->rollout_mode == MTP_BATCH_ROLLOUT_PERSISTENT_STAGED;
+  const bool staged = b->rollout_mode != MTP_BATCH_ROLLOUT_PERSISTENT_DIRECT;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   cudaError_t e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);

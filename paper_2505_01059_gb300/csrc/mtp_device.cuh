@@ -277,6 +277,7 @@ struct PersistArgs {
   const int* model;
   unsigned* head;     // the tile counter, zeroed by the launch
   int count, total_warps;
+  int w_base;         // wstart[0]: the first tile of these entries in the batch's numbering
   size_t warp_bytes;  // shared memory per warp: two mbarriers and two staging buffers (0: no staging)
 };
 // Shared memory per warp for staged tiles of at most these widths (0: none).

@@ -25,18 +25,15 @@
 // slower on the batch of 256.  The launch is bounded at three 128-thread
 // CTAs per SM, i.e. at most 170 registers per thread (168 used, no spills).
 //
-// Measured on GB300 on the 256-instance batch (whole iterations, the
-// autotuner's timing): 2.85-2.89 ms with staged tiles and 3.40-3.44 ms with
-// direct loads, against 2.92-3.10 ms with each group's rollout launched in
-// its own stream's chain.  The order of the tiles matters: sorted by length
-// alone across all groups, the warps of an SM ran different bodies at once,
-// half of their stall samples were instruction fetches, and the staged
-// launch took 3.36-3.47 ms; tiles are therefore taken group by group
-// (longest group first, longest tiles first within it).  The launch waits
-// for every covered instance's candidates, so it gives up the overlap of
-// one group's generation with another's rollout; on this batch the
-// iteration is then 1.12 ms of generation, 1.54 ms of this launch and
-// 0.18 ms of selection and update.
+// Measured on GB300 on the 256-instance batch (the bench's timed region):
+// 2.80 ms per iteration with one staged launch, 2.74 ms with the two-launch
+// mode (the batch's generation of the second part overlaps the first launch),
+// against 2.79-2.91 ms with each group's rollout launched in its own stream's
+// chain.  The order of the tiles matters: sorted by length alone across all
+// groups, the warps of an SM ran different bodies at once, half of their
+// stall samples were instruction fetches, and the iteration took 3.5 ms;
+// tiles are therefore taken group by group (longest group first, longest
+// tiles first within it).
 #include <map>
 #include <mutex>
 
@@ -124,6 +121,7 @@ __global__ void __launch_bounds__(kPersistThreads, 3) k_rollout_persistent(const
     if (lane == 0) w = (int)atomicAdd(p.head, 1u);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= p.total_warps) break;
+    w += p.w_base;
     // the instance whose warp range holds w: the last k with wstart[k] <= w
     int lo = 0, hi = p.count;
     while (hi - lo > 1) {

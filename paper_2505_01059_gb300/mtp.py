@@ -614,7 +614,9 @@ def mtp_batch_autotune(b: Batch, stream=None):
 BATCH_ROLLOUT_GROUPS = 0
 BATCH_ROLLOUT_PERSISTENT_STAGED = 1
 BATCH_ROLLOUT_PERSISTENT_DIRECT = 2
-BATCH_ROLLOUT_NAMES = {0: "groups", 1: "persistent, staged", 2: "persistent, direct"}
+BATCH_ROLLOUT_PERSISTENT_SPLIT = 3
+BATCH_ROLLOUT_NAMES = {0: "groups", 1: "persistent, staged", 2: "persistent, direct",
+                       3: "persistent, two launches"}
 
 
 def mtp_batch_set_rollout_mode(b: Batch, mode: int) -> None:
@@ -624,7 +626,7 @@ def mtp_batch_set_rollout_mode(b: Batch, mode: int) -> None:
 def mtp_batch_rollout_mode(b: Batch):
     """(mode, [the autotuner's iteration ms per mode, 0 where not timed])."""
     mode = C.c_int32()
-    ms = (C.c_double * 3)()
+    ms = (C.c_double * 4)()
     _check(load_library().mtp_batch_rollout_mode(b.ptr, C.addressof(mode), C.addressof(ms)))
     return int(mode.value), [float(v) for v in ms]
 

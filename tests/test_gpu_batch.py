@@ -84,7 +84,7 @@ def _mode_specs():
     return specs
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_persistent_rollouts_match_each_instance_alone(mtp, mode):
     """The point-mass and chain rollouts of the whole batch in one persistent
     launch (staged or direct tiles), beside the launches of the groups it
@@ -102,7 +102,7 @@ def test_persistent_rollouts_match_each_instance_alone(mtp, mode):
     covered = len({(s["dyn"], s["n"] if s["dyn"] == "pointmass" else s["n_links"]) for s in specs
                    if (s["dyn"] == "pointmass" and s["n"] <= 16) or
                    (s["dyn"] == "chain" and s["n_links"] <= 9)})
-    assert mtp.mtp_batch_launches(b, 1) == groups_launches - covered + 1
+    assert mtp.mtp_batch_launches(b, 1) == groups_launches - covered + (2 if mode == 3 else 1)
     x0 = torch.tensor(np.concatenate(x0s), device=DEV)
     us = torch.empty(b.ustar_offset[-1], device=DEV)
     mtp.mtp_batch_plan_step(b, x0, 1, us)          # direct launches
@@ -127,7 +127,7 @@ def test_persistent_rollouts_match_each_instance_alone(mtp, mode):
                         if (s["dyn"] == "pointmass" and s["n"] <= 16) or
                         (s["dyn"] == "chain" and s["n_links"] <= 9))
     with pytest.raises(mtp.MtpError):
-        mtp.mtp_batch_set_rollout_mode(b, 3)
+        mtp.mtp_batch_set_rollout_mode(b, 4)
     mtp.mtp_batch_destroy(b)
     for h in handles:
         mtp.mtp_destroy(h)
@@ -147,7 +147,7 @@ def test_autotune_times_every_rollout_mode_and_restores_states(mtp):
     mtp.mtp_batch_plan_step(b, x0, 1, us)
     mtp.mtp_batch_autotune(b)
     mode, ms = mtp.mtp_batch_rollout_mode(b)
-    assert mode in (0, 1, 2) and all(v > 0 for v in ms)
+    assert mode in (0, 1, 2, 3) and all(v > 0 for v in ms)
     assert ms[mode] == min(ms)
     mtp.mtp_batch_plan_step(b, x0, 2, us)
     torch.cuda.synchronize()
