@@ -416,9 +416,24 @@ cudaError_t init_bspline_tc_attributes() {
   e = cudaFuncSetAttribute(k_bspline_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem_bytes());
   if (e != cudaSuccess) return e;
-  int blocks = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bspline_tc_batch, kTcThreads, tc_smem_bytes());
-  if (e != cudaSuccess) return e;
+  // the largest shared-memory carveout, so that several CTAs fit an SM
+  for (const void* k : {(const void*)k_bspline_tc, (const void*)k_bspline_tc_batch}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  // CTAs per SM from the SM's shared memory (the occupancy query answered 1
+  // for these kernels, while ncu's launch statistics, with the maximum
+  // carveout, showed room for 3; at 1 CTA per SM the legged workload's 1230
+  // tiles ran 8 to a CTA, one after another)
+  int dev = 0, smem_sm = 0, reserved = 0;
+  if ((e = cudaGetDevice(&dev)) ||
+      (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) ||
+      (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)))
+    return e;
+  cudaFuncAttributes fa{};
+  if ((e = cudaFuncGetAttributes(&fa, k_bspline_tc_batch))) return e;
+  const size_t per_cta = tc_smem_bytes() + fa.sharedSizeBytes + (size_t)reserved;
+  const int blocks = (int)((size_t)smem_sm / per_cta);
   g_tc_blocks_per_sm = std::max(1, std::min(blocks, 4));
   return cudaSuccess;
 }

@@ -373,12 +373,29 @@ namespace {
 // `c` asks), with the graph written first when it is not regenerated per block.
 cudaError_t launch_generate(const mtp_handle* h, CandArgs& c, cudaStream_t s) {
   const bool tc = c.graph_blocks > 0 && h->tc_graph && bspline_tc_eligible(c);
+  const int local_blocks = c.U_local ? local_blocks_for(h, (long long)c.local_rows + 1) : 0;
+  if (tc && h->side && !h->pipeline && local_blocks > 0) {
+    // the graph (its Z, then the tensor-core rows) on the side stream beside
+    // the local rows and the mean row: they write disjoint rows of U.  On the
+    // 16-link legged workload this took generation from 183 to about 120 us
+    // (the serial launches left the tensor-core rows on the critical path)
+    cudaError_t e;
+    if ((e = cudaEventRecord(h->ev_fork, s)) || (e = cudaStreamWaitEvent(h->side, h->ev_fork, 0))) return e;
+    if (!c.C_in) {
+      c.Z_global = h->Z;
+      if ((e = launch_graph_Z(c, h->Z, h->side))) return e;
+    }
+    if ((e = launch_bspline_tc(c, h->side)) || (e = cudaEventRecord(h->ev_join, h->side))) return e;
+    CandArgs local = c;
+    local.graph_blocks = 0;
+    if ((e = launch_candidates(local, local_blocks, s))) return e;
+    return cudaStreamWaitEvent(s, h->ev_join, 0);
+  }
   if (c.graph_blocks > 0 && (h->global_Z || tc) && !c.C_in) {
     c.Z_global = h->Z;
     cudaError_t e = launch_graph_Z(c, h->Z, s);
     if (e != cudaSuccess) return e;
   }
-  const int local_blocks = c.U_local ? local_blocks_for(h, (long long)c.local_rows + 1) : 0;
   if (!tc) return launch_candidates(c, local_blocks, s);
   // graph rows on the tensor cores; local rows and the mean row as usual
   CandArgs local = c;
@@ -563,6 +580,21 @@ constexpr int kFullPrepareSMs = 64;
 // many SMs, with how much shared memory per block.  The point-mass and
 // chain rollouts take one block per 32-128 candidates; the legged rollout
 // fills the GPU and is not pipelined.
+// Whether a problem's graph rows go to the tensor cores: BF16-basis
+// B-splines of a shape the contraction takes (H <= 256, M <= 64, n <= 16).
+// Other BF16-basis problems use the FP32-pipe window sum with the same BF16
+// operands.  (A size threshold, the window sum below 1 M graph outputs, was
+// measured and not kept: on the batch of 256 it changed nothing, 2.75 against
+// 2.74-2.83 ms.)
+bool tc_graph_rule(const mtp_problem& p, const Dims& dm) {
+  CandArgs probe{};
+  probe.dm = dm;
+  probe.bf16 = (p.flags & MTP_FLAG_BF16_BASIS) ? 1 : 0;
+  probe.interp = p.interp;
+  probe.graph_rows = dm.P;
+  return bspline_tc_eligible(probe);
+}
+
 cudaError_t pipeline_plan(const mtp_problem& p, const Dims& dm, int paths_per_block, bool* on,
                           bool* local, int* grid, size_t* smem, int* prep_spb) {
   *on = false;
@@ -575,9 +607,10 @@ cudaError_t pipeline_plan(const mtp_problem& p, const Dims& dm, int paths_per_bl
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = init_prepare_attributes(smem)) != cudaSuccess) return e;
-  // the BF16 basis contraction runs on the tensor cores in its own launch,
-  // which the persistent preparation does not make: not pipelined
-  if ((p.flags & MTP_FLAG_NO_PIPELINE) || (p.flags & MTP_FLAG_BF16_BASIS) || p.dyn == MTP_DYN_LEGGED)
+  // graph rows contracted on the tensor cores sum in the tensor cores' order,
+  // which the persistent preparation (an FP32-pipe sum) does not reproduce:
+  // not pipelined
+  if ((p.flags & MTP_FLAG_NO_PIPELINE) || tc_graph_rule(p, dm) || p.dyn == MTP_DYN_LEGGED)
     return cudaSuccess;
   const int free_sms = sms - rollout_blocks(dm.B);
   if (free_sms < kMinPrepareSMs) return cudaSuccess;
@@ -641,11 +674,7 @@ mtp_status mtp_create(const mtp_problem* problem, mtp_handle** out) {
   h->key.k1 = (uint32_t)(p.seed >> 32);
   h->global_Z = global_graph(dm);
   h->paths_per_block = paths_per_block_for(dm, p.interp, h->global_Z);
-  {
-    CandArgs probe = cand_args(h, 0, nullptr);
-    probe.graph_rows = dm.P;
-    h->tc_graph = bspline_tc_eligible(probe);
-  }
+  h->tc_graph = tc_graph_rule(p, dm);
   select_plan(dm.B, dm.E, &h->sel_chunk, &h->sel_chunks);
   auto err = [&](mtp_status s) {
     g_create_error = h->err;
@@ -886,6 +915,21 @@ static mtp_status read_stage_events(mtp_handle* h, const cudaEvent_t* ev, double
 // batches never needs them).  If they cannot be made the handle plans
 // without the pipeline, which gives the same results.
 static void ensure_pipeline(mtp_handle* h) {
+  if (h->tc_graph && !h->pipeline && !h->side) {
+    // a tensor-core handle's side stream for its graph rows (launch_generate);
+    // without it the rows are made after the local rows, with the same bits
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (h->side) cudaStreamDestroy(h->side);
+      if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+      if (h->ev_join) cudaEventDestroy(h->ev_join);
+      h->side = nullptr;
+      h->ev_fork = h->ev_join = nullptr;
+    }
+    return;
+  }
   if (!h->pipeline || h->side) return;
   const size_t n = (size_t)h->dm.H * h->dm.n * h->dm.B;
   if (dalloc(&h->Ubuf[1], n) != cudaSuccess ||
