@@ -367,7 +367,7 @@ mtp_status mtp_batch_autotune(mtp_batch* b, int32_t* tiles_out, int32_t* n_group
  *   (_DIRECT).  Legged robots and longer chains keep their own launches
  *   beside it.  The launch is counted as one kernel by mtp_batch_launches.
  * MTP_BATCH_ROLLOUT_PERSISTENT_SPLIT: the same with staged tiles, in two
- *   persistent launches split at a group boundary near half of the expected
+ *   persistent launches split at a group boundary near 65 % of the expected
  *   rollout work: the first starts as soon as its groups' candidates are made
  *   (their generation on high-priority streams) and leaves one CTA per SM to
  *   the second part's generation, which overlaps it; the second starts when
