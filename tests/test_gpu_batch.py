@@ -133,6 +133,39 @@ def test_persistent_rollouts_match_each_instance_alone(mtp, mode):
         mtp.mtp_destroy(h)
 
 
+@pytest.mark.parametrize("mode", [1, 3])
+def test_persistent_modes_with_one_or_no_covered_group(mtp, mode):
+    """Degenerate batches for the persistent modes: only legged robots (no
+    instance is covered, the groups' own launches run) and a single covered
+    group beside a legged robot (the two-launch mode has no group boundary to
+    split at and runs one launch).  Bits as alone."""
+    for specs in ([W.legged(links=4, B=256, H=32, M=4, N=8, seed=s) for s in (5, 6)],
+                  [W.chain(links=5, B=700, H=40, seed=s) for s in (7, 8, 9)] +
+                  [W.legged(links=4, B=256, H=32, M=4, N=8)]):
+        rng = np.random.default_rng(len(specs))
+        x0s = [rng.uniform(-0.2, 0.2, size=s["d"]).astype(np.float32) for s in specs]
+        handles = [mtp.mtp_create(s) for s in specs]
+        b = mtp.mtp_batch_create(handles)
+        mtp.mtp_batch_set_rollout_mode(b, mode)
+        x0 = torch.tensor(np.concatenate(x0s), device=DEV)
+        us = torch.empty(b.ustar_offset[-1], device=DEV)
+        mtp.mtp_batch_plan_step(b, x0, 1, us)
+        mtp.mtp_batch_plan_step(b, x0, 1, us)
+        torch.cuda.synchronize()
+        ms, steps = mtp.mtp_batch_persistent_time(b, reps=1)
+        covered = sum(s["B"] * s["H"] for s in specs if s["dyn"] == "chain")
+        assert steps == covered and (ms > 0) == (covered > 0)
+        ref = _run_alone(mtp, specs, x0s, 2)
+        for i, (h, (mu, sg, it, u, cost)) in enumerate(zip(handles, ref)):
+            mu_b, sg_b, it_b = mtp.mtp_get_state(h)
+            assert it_b == 2 and np.array_equal(mu_b, mu) and np.array_equal(sg_b, sg), i
+            lo, hi = b.ustar_offset[i], b.ustar_offset[i + 1]
+            assert np.array_equal(us[lo:hi].cpu().numpy(), u), i
+        mtp.mtp_batch_destroy(b)
+        for h in handles:
+            mtp.mtp_destroy(h)
+
+
 def test_autotune_times_every_rollout_mode_and_restores_states(mtp):
     """The autotuner times whole iterations in each rollout mode from saved
     planner states and restores them: the tuned batch's next iterations are
