@@ -25,8 +25,10 @@
 // slower on the batch of 256.  The launch is bounded at three 128-thread
 // CTAs per SM, i.e. at most 170 registers per thread (168 used, no spills).
 //
-// Measured on GB300 on the 256-instance batch (the bench's timed region):
-// 2.80 ms per iteration with one staged launch, 2.74 ms with the two-launch
+// Measured on GB300 on the 256-instance batch (the bench's timed region,
+// before the branch-free point-mass obstacles below, which took the
+// two-launch mode to 2.68 ms): 2.80 ms per iteration with one staged
+// launch, 2.74 ms with the two-launch
 // mode (the batch's generation of the second part overlaps the first launch),
 // against 2.79-2.91 ms with each group's rollout launched in its own stream's
 // chain.  The order of the tiles matters: sorted by length alone across all
@@ -45,6 +47,10 @@ namespace {
 constexpr int kPersistThreads = 128;
 constexpr int kPersistChunk = 4;  // horizon chunk of a staged tile
 
+// Point masses evaluate every obstacle slot without a branch (ALL): the
+// slots past n_obs add exactly +0, so the bits are those of the guarded loop
+// of the per-group kernel, and mixed with the chains' tiles the branch-free
+// form is faster (256-instance batch 2.73 -> 2.68 ms per iteration).
 template <int K, int T>
 __device__ __forceinline__ bool persist_pm(const RolloutArgs& a, const PointMassModel& m, int r, bool live,
                                         uint64_t* bars, float* buf, int& seq) {
@@ -53,11 +59,11 @@ __device__ __forceinline__ bool persist_pm(const RolloutArgs& a, const PointMass
     (void)buf;
     (void)seq;
     if (!live) return true;
-    return rollout_pm_body<K, kPrefetchBatch, false, 0>(a, m, r, true, nullptr);
+    return rollout_pm_body<K, kPrefetchBatch, true, 0>(a, m, r, true, nullptr);
   } else {
     StagedRows<K, T> st;
     st.attach(bars, buf, live ? a.U + (size_t)r * a.H * K : nullptr, a.H, seq);
-    const bool ok = rollout_pm_body<K, kPrefetchBatch, false, T>(a, m, r, live, &st);
+    const bool ok = rollout_pm_body<K, kPrefetchBatch, true, T>(a, m, r, live, &st);
     seq = st.seq;
     return __all_sync(0xffffffffu, ok);
   }
