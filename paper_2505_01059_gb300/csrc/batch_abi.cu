@@ -46,8 +46,9 @@ constexpr int kMaxGroups = 64;
 // this fraction of the expected rollout work, and runs this many CTAs per SM
 // fewer than the second, leaving them to the second part's generation.
 // Measured on the batch of 256 (ms per iteration): fraction 0.35 / 0.5 /
-// 0.65: 2.84 / 2.74-2.75 / 2.73; the first launch with as many CTAs as the
-// second: 2.81.
+// 0.65 / 0.75 / 0.85: 2.84 / 2.74-2.75 / 2.73 / 2.77 / 2.98 (0.65 measured
+// again with the later point-mass change: 2.69 against 2.77 / 2.98); the
+// first launch with as many CTAs as the second: 2.81.
 #ifndef MTP_PERSIST_SPLIT_FRACTION
 #define MTP_PERSIST_SPLIT_FRACTION 0.65
 #endif
