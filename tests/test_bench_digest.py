@@ -24,3 +24,19 @@ def test_code_text_sees_code_changes(tmp_path):
     b.write_text("int f(int x) { return x + 2; }\n")
     assert bench._code_text(str(a)) != bench._code_text(str(b))
 
+
+
+def test_public_header_prototypes_do_not_count(tmp_path):
+    """A new entry point in include/mtp.h is host interface: the profiles of
+    the kernels stay valid; a change to a type the kernels use retires them."""
+    d = tmp_path / "include"
+    d.mkdir()
+    h = d / "mtp.h"
+    base = "typedef struct { int a; } mtp_x;\nmtp_status mtp_f(mtp_x* p, int n);\n"
+    h.write_text(base)
+    t0 = bench._code_text(str(h))
+    h.write_text(base + "/* new */\nmtp_status mtp_g(const float* d, int32_t k,\n                  void* s);\n"
+                 "const char* mtp_name(const mtp_x* p);\n")
+    assert bench._code_text(str(h)) == t0 == "typedef struct { int a; } mtp_x;"
+    h.write_text(base.replace("int a;", "int a; int b;"))
+    assert bench._code_text(str(h)) != t0
