@@ -1,19 +1,22 @@
 // rollout_persist.cu -- the rollouts of a whole batch in one persistent
-// launch (Alg. 2 rollout fused with the Eq. 2 cost, rollout_kernels.cuh).
+// launch, or two (Alg. 2 rollout fused with the Eq. 2 cost, the bodies of
+// rollout_kernels.cuh).
 //
 // Work items are warp tiles: 32 consecutive candidates of one instance.  The
 // instances are listed group by group, the longest group first and within a
 // group the longest expected rollout first (H times the time per step of the
 // group's dynamics and dimension), and numbered by a prefix of their warp
-// tiles, so item w belongs to the instance whose range holds w.  Each
-// warp of the launch repeatedly takes the next item from a device counter
-// (one atomic add per item), looks its instance up by binary search, and
-// runs that tile's rollout: a point mass of K axes or a planar chain of L
-// links, with direct control loads or staged 4 steps at a time.  A warp
-// therefore moves between instances of different sizes and dynamics, while
-// the warps running at one time mostly run the same body.  The bodies
-// are the per-candidate rollouts of the other kernels (the same templates),
-// so every cost is the same bits as in a per-group or standalone launch.
+// tiles, so item w belongs to the instance whose range holds w.  Each warp of
+// the launch repeatedly takes the next item from a device counter (one
+// atomic add per item), looks its instance up by binary search, and runs
+// that tile's rollout: a point mass of K axes or a planar chain of L links,
+// with direct control loads or staged 4 steps at a time.  A warp therefore
+// moves between instances of different sizes and dynamics, while the warps
+// running at one time mostly run the same body.  The bodies are the
+// per-candidate rollouts of the other kernels (the same templates), so every
+// cost is the same bits as in a per-group or standalone launch.  The
+// two-launch mode of the batch runs the same kernel over two ranges of the
+// entries (w_base numbers the second range's tiles).
 //
 // The warps never wait on one another: an item, once taken, depends only on
 // the candidates generated before the launch.  A staged tile's waits are the
@@ -25,17 +28,13 @@
 // slower on the batch of 256.  The launch is bounded at three 128-thread
 // CTAs per SM, i.e. at most 170 registers per thread (168 used, no spills).
 //
-// Measured on GB300 on the 256-instance batch (the bench's timed region,
-// before the branch-free point-mass obstacles below, which took the
-// two-launch mode to 2.68 ms): 2.80 ms per iteration with one staged
-// launch, 2.74 ms with the two-launch
-// mode (the batch's generation of the second part overlaps the first launch),
-// against 2.79-2.91 ms with each group's rollout launched in its own stream's
-// chain.  The order of the tiles matters: sorted by length alone across all
-// groups, the warps of an SM ran different bodies at once, half of their
-// stall samples were instruction fetches, and the iteration took 3.5 ms;
-// tiles are therefore taken group by group (longest group first, longest
-// tiles first within it).
+// Measured on GB300 on the 256-instance batch (the bench's timed region):
+// 2.68 ms per iteration with two launches, against 2.79-2.91 ms with each
+// group's rollout launched in its own stream's chain.  The order of the
+// tiles matters: sorted by length alone across all groups, the warps of an
+// SM ran different bodies at once, half of their stall samples were
+// instruction fetches, and the iteration took 3.5 ms; tiles are therefore
+// taken group by group (longest group first, longest tiles first within it).
 #include <map>
 #include <mutex>
 
