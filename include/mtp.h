@@ -293,10 +293,11 @@ mtp_status mtp_stage_times(mtp_handle* h, double* ms4, int32_t* iterations);
 mtp_status mtp_stage_times5(mtp_handle* h, double* ms5, int32_t* iterations);
 
 /* Batched planning over many handles (uneven sizes, point masses and chains
- * mixed).  One iteration is one CUDA graph: the candidates of every instance
- * in one launch, the rollouts grouped by (dynamics, control dimension) and
- * run concurrently on their own streams, one selection block per instance,
- * one update launch.  This is the GPU form of the paper's vectorised
+ * mixed).  One iteration is one CUDA graph: the candidates of every
+ * (dynamics, control dimension) group made on the group's own stream, the
+ * rollouts either per group on those streams or in persistent launches over
+ * the whole batch (mtp_batch_set_rollout_mode; the autotuner picks), one
+ * selection block per instance, one update launch per group.  This is the GPU form of the paper's vectorised
  * planning of many model instances (Sec. 3.3, Sec. 4 practical settings);
  * each instance computes exactly what mtp_plan_step computes for it alone.
  * The handles must stay alive while the batch exists; their states advance. */
